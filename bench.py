@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark: Stokes cavity solves per second to 1e-8 relative residual on GB300.
+
+Workload (default, ``--workload cavity32``): the 3D lid-driven cavity on 32^3 elements,
+pressure degree p = 3 (velocity degree 4 in its own direction), nu = 1, lid (1, 0, 0) on x2 = 1,
+solved for each preconditioner of the sweep hyper-power order {2, 3} x steps {0, 1, 2, 3}
+(Schur sequence with inner updates). One step = the 8 solves of the sweep; value = solves/s.
+``--workload cavity128`` runs a 128^3, p = 3 cavity with order 2, steps 2 in the plain FP64 form
+and the mixed-precision form.
+
+Timing: W warm-up steps, then K steps between a barrier + device synchronize on both sides,
+CUDA events on the library's stream, L2 flushed (a 256 MiB write) before every step, the max over
+ranks. Ranks (torchrun) run independent replicas (weak scaling, no collective on the data path).
+``e2e``: the same sweep through stokes_solve_host (pinned host rhs and x, copies in the call).
+``roofline``: the dominant kernel class, from a separate profiled pass (CUDA events around each
+launch). ``cpu_baseline``: the FP64 oracle on the host cores on a bounded sample.
+``--impl reference``: the oracle as the reference arm (rank 0 only).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Stokes solves/s to 1e-8 rel. residual; HBM GB/s & TC util vs peak; mixed vs FP64"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 FMA rate of GB300: 2 DFMA per clock per SM (measured by an FMA-throughput probe at
+# 1.20 TFLOP/s) x 152 SMs x 2 flop x 2.07 GHz maximum SM clock.
+FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 128 * 152 * 2 * 2.07e9 / 1e12
+
+WORKLOADS = {
+    "cavity32": dict(n=32, p=3, sweep=[(q, s) for q in (2, 3) for s in (0, 1, 2, 3)],
+                     precision="fp64",
+                     desc="3D lid-driven cavity, 32^3 elements, p=3 (velocity degree 4 in its own "
+                          "direction), nu=1, FP64 MINRES to 1e-8, hyper-power order {2,3} x steps "
+                          "{0..3} (Schur with inner updates), one RHS per solve"),
+    "cavity8": dict(n=8, p=2, sweep=[(2, 1)], precision="fp64",
+                    desc="3D lid-driven cavity, 8^3 elements, p=2, nu=1, FP64 MINRES to 1e-8, "
+                         "order 2, 1 step"),
+    "cavity128": dict(n=128, p=3, sweep=[(2, 2)], precision="fp64",
+                      desc="3D lid-driven cavity, 128^3 elements, p=3, nu=1, FP64 MINRES to 1e-8, "
+                           "order 2, 2 steps"),
+}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except (OSError, ValueError):
+        return None
+
+
+def oracle_solver(n, p):
+    """Oracle pieces for one cavity problem (matrix-free above 12^3)."""
+    import warnings
+    warnings.filterwarnings("ignore", category=DeprecationWarning)
+    from oracle.matfree import MatrixFreeStokes
+    from oracle.precond import BasePreconditioner
+    from oracle.stokes import StokesSystem
+    S = StokesSystem(n, p, assemble=False)
+    F = MatrixFreeStokes(S)
+    base = BasePreconditioner(S, A_apply=F.apply_A, B_apply=F.apply_B, Bt_apply=F.apply_Bt)
+    return S, F, base
+
+
+def cpu_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max((i.get("num_threads", 1) for i in info), default=os.cpu_count())
+    except Exception:
+        return os.cpu_count()
+
+
+def oracle_sample(n, p, q, s, repeats):
+    """Time `repeats` oracle MINRES solves (the oracle as it stands)."""
+    from oracle.krylov import minres
+    from oracle.precond import HyperPowerPreconditioner
+    S, F, base = oracle_solver(n, p)
+    f = S.rhs_lid(1.0)
+    P = HyperPowerPreconditioner(base, q, s)
+    t0 = time.perf_counter()
+    its = None
+    for _ in range(repeats):
+        its = minres(F.apply_K, P, f, 1e-8).iterations
+    return time.perf_counter() - t0, its
+
+
+def run_reference(args, wl):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    q, s = (2, 1) if (2, 1) in wl["sweep"] else wl["sweep"][0]
+    for _ in range(args.warmup):
+        oracle_sample(wl["n"], wl["p"], q, s, 1)
+    dt, its = oracle_sample(wl["n"], wl["p"], q, s, args.steps)
+    value = args.steps / dt
+    sample = (f"oracle (NumPy/SciPy FP64, matrix-free Kronecker mode products) MINRES solve of "
+              f"the {wl['n']}^3 p={wl['p']} cavity with order {q}, {s} step(s) "
+              f"({its} iterations), one solve per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["desc"], "n_elems": wl["n"], "degree_p": wl["p"],
+                       "reference_sample": f"order {q}, steps {s}"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cavity32", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "tf32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = dict(WORKLOADS[args.workload])
+    if args.precision:
+        wl["precision"] = args.precision
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2311_06926_gb300 import Stokes
+    from paper_2311_06926_gb300.binding import kernel_launches
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev_index = torch.cuda.current_device()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    n, p, sweep = wl["n"], wl["p"], wl["sweep"]
+    prec = wl["precision"]
+    max_steps = max(s for _, s in sweep)
+    max_order = max(q for q, _ in sweep)
+    G = Stokes(n, p, precision=prec, max_order=max_order, max_steps=max_steps)
+    stream = torch.cuda.current_stream()
+    f = G.rhs_cavity(1.0)
+    x = G.empty()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    iters = {}
+
+    def step():
+        flush.fill_(1.0)
+        for q, s in sweep:
+            G.set_preconditioner(q, s)
+            _, it, rr, _ = G.solve(f, 1e-8, out=x)
+            iters[(q, s)] = (it, rr)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    sampler = ClockSampler(dev_index)
+    sampler.start()
+    launches0 = kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    launches = kernel_launches() - launches0
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    solves = len(sweep) * args.steps * ws
+    value = solves / (ms_max / 1e3)
+
+    # per-preconditioner solve times (one solve each, not part of the headline)
+    per = {}
+    for q, s in sweep:
+        G.set_preconditioner(q, s)
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        G.solve(f, 1e-8, out=x)
+        b.record(stream)
+        torch.cuda.synchronize()
+        per[f"q{q}s{s}"] = {"ms": a.elapsed_time(b), "iterations": iters[(q, s)][0],
+                            "true_rel_res": iters[(q, s)][1]}
+
+    # end to end through the host-buffer C-ABI call (pinned host memory)
+    rhs_h = f.cpu().pin_memory()
+    x_h = torch.empty_like(rhs_h).pin_memory()
+
+    def step_e2e():
+        flush.fill_(1.0)
+        for q, s in sweep:
+            G.set_preconditioner(q, s)
+            G.solve_host(rhs_h, x_h, 1e-8)
+
+    step_e2e()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
+    e2e_value = solves / float(e2e_s.item())
+    bytes_per_solve = G.size * 8
+
+    # profiled pass: per-kernel-class event timing over one step
+    G.profile_begin()
+    step()
+    prof = G.profile_end()
+    dom_name = max(prof, key=lambda k: prof[k]["ms"])
+    dom = prof[dom_name]
+    peaks = load_peaks() or {}
+    if dom_name in ("mode_product", "band_pass") and prec == "fp64":
+        achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": dom_name, "launches_per_step": dom["launches"],
+                "avg_launch_us": 1e3 * dom["ms"] / max(dom["launches"], 1),
+                "peak_note": "FP64 FMA peak derived: 2 DFMA/clk/SM (probe: 1.20 TFLOP/s) x 152 "
+                             "SMs x 2.07 GHz"}
+    else:
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "kernel": dom_name,
+                "launches_per_step": dom["launches"],
+                "avg_launch_us": 1e3 * dom["ms"] / max(dom["launches"], 1),
+                "peak_note": "of measured" if "hbm_gbs" in peaks else "of fallback"}
+    step_ms_profiled = sum(v["ms"] for v in prof.values())
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        q, s = (2, 1) if (2, 1) in sweep else sweep[0]
+        dt, its = oracle_sample(n, p, q, s, 1)
+        reps = max(1, min(20, int(15.0 / max(dt, 1e-3))))
+        if reps > 1:
+            dt, its = oracle_sample(n, p, q, s, reps)
+        cpu = {"value": reps / dt, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"{reps} oracle FP64 MINRES solve(s) of the {n}^3 p={p} cavity, order "
+                         f"{q}, {s} step(s), {its} iterations, matrix-free NumPy"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "fp64" else f"{prec}+f64",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"], "n_elems": n, "degree_p": p,
+                       "unknowns": G.size, "precision": prec, "solves_per_step": len(sweep),
+                       "tol": 1e-8, "l2": "flushed by a 256 MiB write before every step",
+                       "parallelism": f"replicas x{ws}"},
+            "per_preconditioner": per,
+            "roofline": roof,
+            "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                                   "share": round(v["ms"] / step_ms_profiled, 4)}
+                               for k, v in prof.items()},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "solves/s",
+                    "h2d_bytes_per_step": bytes_per_solve * len(sweep),
+                    "d2h_bytes_per_step": bytes_per_solve * len(sweep)},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    G.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,170 @@
+/*
+ * stokes_hp.h - C ABI of a GB300 (sm_103a) library for the hyper-power preconditioned Krylov
+ * solve of the 3D Stokes saddle-point system of arXiv 2311.06926 ("Matrix-free polynomial
+ * preconditioning of saddle point systems using the hyper-power method").
+ *
+ * Problem (Sec. 3): Stokes flow on the unit cube, n^3 uniform elements, div-conforming B-spline
+ * (isogeometric Raviart-Thomas) spaces (App. B.2). With this library's degree p (the pressure
+ * degree; the paper's degree is p + 1):
+ *   velocity component c: degree p+1 (C^p) in direction c, degree p (C^(p-1)) in the others;
+ *   pressure: degree p (C^(p-1)) in every direction.
+ * Normal velocity is zero strongly (the first and last spline in direction c is removed);
+ * tangential velocity is imposed weakly by Nitsche's method with alpha = C_pen / h (Sec. 3.2).
+ * The discrete system (Eq. 3.3) is K [u; q] = [f; 0] with
+ *   K = [[A, B], [B^T, 0]],  A_ij = a(v_j, v_i) + sigma(v_j, v_i),  B_ij = int div(v_i) q_j.
+ *
+ * Sizes: a = n + p - 1, b = n + p. Vector layout (every vector argument): the three velocity
+ * components then the pressure, each a 3D coefficient tensor stored with x1 fastest:
+ *   u1 (a, b, b), u2 (b, a, b), u3 (b, b, a), q (b, b, b)   [extents along (x1, x2, x3)]
+ * n_vel = 3 a b^2, n_pres = b^3. All values are float64.
+ *
+ * Memory and streams: unless a name ends in _host, every vector pointer is a DEVICE pointer to
+ * caller-owned memory of the stated length; the library never frees or retains it. The context
+ * owns its own device workspace (allocated by stokes_setup, freed by stokes_destroy). Every call
+ * is ordered on the context's stream (stokes_opts.stream, or a stream the library creates) and
+ * returns after its work is enqueued, except stokes_solve / stokes_solve_host, which return when
+ * the solve has finished.
+ *
+ * Errors: every int-returning call returns STOKES_OK (0) or a negative STOKES_ERR_* code and
+ * never throws; stokes_last_error(ctx) gives a message. A context whose call failed with
+ * STOKES_ERR_CUDA should be destroyed.
+ */
+#ifndef STOKES_HP_H
+#define STOKES_HP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  STOKES_OK = 0,
+  STOKES_ERR_ARG = -1,        /* invalid argument (null pointer, size, order < 2, ...) */
+  STOKES_ERR_CUDA = -2,       /* a CUDA call failed */
+  STOKES_ERR_NONFINITE = -3,  /* NaN or Inf met in the Krylov recurrence */
+  STOKES_ERR_NOT_SPD = -4,    /* preconditioner not positive definite (<z, r> < 0) */
+  STOKES_ERR_MAXIT = -5,      /* iteration cap reached; x holds the last iterate */
+  STOKES_ERR_BREAKDOWN = -6,  /* Krylov breakdown */
+  STOKES_ERR_SETUP = -7       /* setup failed (1D matrix not positive definite, ...) */
+};
+
+enum { STOKES_SCHUR_INNER = 0, STOKES_SCHUR_NONE = 1 };
+enum { STOKES_PREC_FP64 = 0, STOKES_PREC_FP32 = 1, STOKES_PREC_TF32 = 2, STOKES_PREC_BF16 = 3 };
+enum { STOKES_SOLVER_MINRES = 0, STOKES_SOLVER_FGMRES = 1 };
+
+typedef struct stokes_opts {
+  double c_pen;       /* Nitsche penalty constant C_pen (Sec. 3.2); <= 0 selects 14 */
+  int schur;          /* Q-block sequence: STOKES_SCHUR_INNER = Eq. 4.5 (with inner updates,
+                         the sequence of Table 1), STOKES_SCHUR_NONE = Eq. 4.6 */
+  int precision;      /* arithmetic of the preconditioner (base blocks and hyper-power
+                         steps): STOKES_PREC_FP64, or FP32 / TF32 / BF16 with FP32 accumulation;
+                         the outer Krylov residual, K apply and inner products are always FP64 */
+  int solver;         /* STOKES_SOLVER_MINRES (needs an FP64 preconditioner) or
+                         STOKES_SOLVER_FGMRES (flexible GMRES, for reduced precision) */
+  int max_order;      /* largest hyper-power order used with this context (workspace); >= 2 */
+  int max_steps;      /* largest hyper-power step count used with this context; >= 0 */
+  int maxit;          /* Krylov iteration cap */
+  int restart;        /* FGMRES restart length */
+  void* stream;       /* cudaStream_t to run on; NULL: the library creates one */
+} stokes_opts;
+
+typedef struct stokes_ctx* stokes_t;
+
+/* Fill *o with the defaults: c_pen 14, Schur with inner updates, FP64, MINRES, max_order 3,
+ * max_steps 4, maxit 2000, restart 60, stream NULL. */
+void stokes_default_opts(stokes_opts* o);
+
+/* Build the univariate matrices (App. B.3, T-check of Sec. 3.3), the fast-diagonalisation
+ * factors (generalised eigenpairs, App. A.4) and the device workspace for n_elems^3 elements,
+ * degree_p >= 1 (pressure degree), viscosity nu > 0. opts may be NULL (defaults). On success
+ * *out receives a new context. Errors: STOKES_ERR_ARG, STOKES_ERR_SETUP, STOKES_ERR_CUDA. */
+int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stokes_opts* opts);
+
+/* n_vel = 3 a b^2 and n_pres = b^3 (either pointer may be NULL). */
+int stokes_sizes(stokes_t ctx, int64_t* n_vel, int64_t* n_pres);
+
+/* Select the preconditioner used by stokes_solve: the order-`order` hyper-power sequence after
+ * `steps` steps (Eq. 2.1 for order 2; steps = 0 is the base P_0). Requires 2 <= order <=
+ * max_order and 0 <= steps <= max_steps. */
+int stokes_set_preconditioner(stokes_t ctx, int order, int steps);
+
+/* y = A x on the velocity block (x, y: n_vel). A = the 15 Kronecker products of Sec. 3.3 with
+ * the weak-form scaling (2 nu on the printed diagonal blocks, nu on the off-diagonal ones). */
+int stokes_apply_A(stokes_t ctx, const double* x, double* y);
+
+/* y = K x on the full saddle-point system (Eq. 3.3; x, y: n_vel + n_pres). */
+int stokes_apply_K(stokes_t ctx, const double* x, double* y);
+
+/* y = P_0^-1 x, the base block preconditioner (Eq. 4.1): fast diagonalisation of the three
+ * diagonal blocks of A (Sec. 4, App. A.4) and the pressure mass block M-check^3 / (2 nu)
+ * (Sec. 4). Runs in the context's preconditioner precision. x, y: n_vel + n_pres. */
+int stokes_apply_P(stokes_t ctx, const double* x, double* y);
+
+/* y = P_s^-1 x for the order-q hyper-power sequence (Eqs. 2.1, 4.4 for the velocity block,
+ * 4.5 or 4.6 for the pressure block) with q = order, s = steps; steps = 0 equals
+ * stokes_apply_P. One application costs q^s base applications and q^s - 1 applications of the
+ * approximation (Eq. 4.8). */
+int stokes_apply_hyperpower(stokes_t ctx, int order, int steps, const double* x, double* y);
+
+/* f = load of the lid-driven cavity (Sec. 5, Fig. 2): tangential lid velocity (lid_speed, 0, 0)
+ * on the face x2 = 1 through the Nitsche terms, no slip elsewhere, no body force.
+ * f: n_vel + n_pres (pressure part zero). */
+int stokes_rhs_cavity(stokes_t ctx, double lid_speed, double* f);
+
+/* f = load int b . v of the body force b_c(x) = sum_m coef[c*n_modes+m] prod_d
+ * sin(waves[(c*n_modes+m)*3+d] pi x_d) (Sec. 3.1, l(v)). coef and waves are HOST arrays of
+ * 3*n_modes and 9*n_modes entries (wave numbers >= 1). If accumulate != 0 the load is added to f. */
+int stokes_rhs_body(stokes_t ctx, int n_modes, const double* coef, const int* waves,
+                    int accumulate, double* f);
+
+/* Solve K x = rhs with the selected preconditioner and solver to relative tolerance tol
+ * (MINRES: ||r||_{P^-1} / ||rhs||_{P^-1}; FGMRES: ||r||_2 / ||rhs||_2), starting from x = 0,
+ * then shift the pressure to zero mean. iterations and final_rel_res (the true
+ * ||rhs - K x||_2 / ||rhs||_2) may be NULL. rhs, x: device, n_vel + n_pres.
+ * Returns STOKES_OK, or STOKES_ERR_MAXIT / _NONFINITE / _NOT_SPD / _BREAKDOWN with x holding the
+ * last iterate. */
+int stokes_solve(stokes_t ctx, const double* rhs, double tol, double* x, int* iterations,
+                 double* final_rel_res);
+
+/* As stokes_solve with HOST buffers rhs_host and x_host (pinned memory gives full copy speed):
+ * the host-to-device copy, the solve and the device-to-host copy all happen inside the call. */
+int stokes_solve_host(stokes_t ctx, const double* rhs_host, double tol, double* x_host,
+                      int* iterations, double* final_rel_res);
+
+/* Per-iteration convergence ratios of the last solve: copies min(capacity, iterations) values
+ * into the host array ratios and returns the number copied (or a negative error). */
+int stokes_last_ratios(stokes_t ctx, double* ratios, int capacity);
+
+/* ---- instrumentation (no counterpart in the paper) ------------------------------------------
+ * Kernel classes: 0 banded Kronecker passes, 1 dense mode products on CUDA cores, 2 discrete
+ * divergence / transpose, 3 Krylov vector kernels, 4 tensor-core mode products.
+ * stokes_profile_begin brackets every later launch of this thread with CUDA events on the
+ * launching stream; stokes_profile_end synchronizes, writes per-class totals (launches, summed
+ * event intervals in ms, algorithmic flops and bytes: each input read once, each output written
+ * once) into out[0 .. capacity) and returns the number of classes written. The events add a
+ * little time per launch, so profiled runs are not used as throughput numbers. */
+typedef struct stokes_kernel_stat {
+  int kernel_class;
+  int64_t launches;
+  double ms;
+  double flops;
+  double bytes;
+} stokes_kernel_stat;
+int stokes_profile_begin(stokes_t ctx);
+int stokes_profile_end(stokes_t ctx, stokes_kernel_stat* out, int capacity);
+/* Number of kernels this library has launched in this process (all contexts and threads). */
+int64_t stokes_kernel_launches(void);
+
+/* Release the context and its device workspace. NULL is ignored. */
+void stokes_destroy(stokes_t ctx);
+
+/* Message of the last error on ctx ("" if none); ctx may be NULL (setup errors). The string
+ * stays valid until the next call on ctx. */
+const char* stokes_last_error(stokes_t ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STOKES_HP_H */

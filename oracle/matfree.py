@@ -13,12 +13,13 @@ import numpy as np
 
 def mode(D, T, axis):
     """Multiply the tensor T (C-order (x3, x2, x1)) by D along parametric direction ``axis``
-    (1, 2 or 3)."""
+    (1, 2 or 3): Y[.., i, ..] = sum_j D[i, j] T[.., j, ..], one matrix product per mode."""
     if axis == 1:
-        return np.einsum("ij,klj->kli", D, T, optimize=True)
+        return T @ D.T
     if axis == 2:
-        return np.einsum("ij,kjl->kil", D, T, optimize=True)
-    return np.einsum("ij,jkl->ikl", D, T, optimize=True)
+        return np.matmul(D, T)
+    n3 = T.shape[0]
+    return (D @ T.reshape(n3, -1)).reshape((D.shape[0],) + T.shape[1:])
 
 
 def kron3_apply(D3, D2, D1, T):

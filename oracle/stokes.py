@@ -37,7 +37,8 @@ def default_c_pen(p):
 class StokesSystem:
     """Assembled blocks for n^3 elements, pressure degree p, viscosity nu."""
 
-    def __init__(self, n, p, nu=1.0, c_pen=None):
+    def __init__(self, n, p, nu=1.0, c_pen=None, assemble=True):
+        """``assemble=False`` keeps only the 1D data and sizes (for ``oracle.matfree``)."""
         self.n, self.p, self.nu = n, p, float(nu)
         self.c_pen = default_c_pen(p) if c_pen is None else float(c_pen)
         u = self.uv = Univariate(n, p, self.c_pen)
@@ -48,6 +49,11 @@ class StokesSystem:
         self.n_vel = 3 * self.nv_c
         self.n_pres = b ** 3
         self.size = self.n_vel + self.n_pres
+        # coefficient vector of the constant pressure 1 (c (x) c (x) c, c_i = int N_{i,p})
+        c = u.const_M
+        self.z_const = np.kron(c, np.kron(c, c))
+        if not assemble:
+            return
         M, K, C, Mc, Tc, Cc = u.M, u.K, u.C, u.Mc, u.Tc, u.Cc
         nu2 = 2.0 * self.nu
         # diagonal blocks (generalised Kronecker sums, Sec. 3.3) times 2 nu
@@ -67,9 +73,6 @@ class StokesSystem:
         self.B3 = kron3(Cc, Mc, Mc)
         self.B = sp.vstack([self.B1, self.B2, self.B3]).tocsr()
         self.K = sp.bmat([[self.A, self.B], [self.B.T, None]]).tocsr()
-        # coefficient vector of the constant pressure 1 (c (x) c (x) c, c_i = int N_{i,p})
-        c = u.const_M
-        self.z_const = np.kron(c, np.kron(c, c))
 
     # ----- vector helpers -------------------------------------------------------------
     def split(self, x):

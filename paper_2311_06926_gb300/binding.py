@@ -1,0 +1,255 @@
+"""Thin ctypes binding of the C ABI in include/stokes_hp.h.
+
+Argument marshalling only: every step of the solve runs in the CUDA library. PyTorch supplies
+device memory and the stream (the context runs on the torch stream current at construction).
+There is no fallback: if the library is missing or fails to load, an error is raised.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libstokes_hp.so")
+
+STOKES_OK = 0
+ERRORS = {-1: "ARG", -2: "CUDA", -3: "NONFINITE", -4: "NOT_SPD", -5: "MAXIT", -6: "BREAKDOWN",
+          -7: "SETUP"}
+SCHUR = {"inner": 0, "none": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+SOLVER = {"minres": 0, "fgmres": 1}
+
+
+class StokesError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"stokes error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("c_pen", ctypes.c_double), ("schur", ctypes.c_int), ("precision", ctypes.c_int),
+                ("solver", ctypes.c_int), ("max_order", ctypes.c_int), ("max_steps", ctypes.c_int),
+                ("maxit", ctypes.c_int), ("restart", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("kernel_class", ctypes.c_int), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+KERNEL_CLASSES = ["band_pass", "mode_product", "divergence", "vector", "mma_mode_product"]
+
+_lib = None
+
+
+def load_library(path=None):
+    """Load libstokes_hp.so (raises OSError if it is missing: build it with
+    ``python -c "import __graft_entry__ as g; g.build()"``)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError(f"CUDA library not built: {p} is missing")
+    lib = ctypes.CDLL(p)
+    vp, dp, ip, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), \
+        ctypes.POINTER(ctypes.c_int64)
+    sig = {
+        "stokes_default_opts": (None, [ctypes.POINTER(_Opts)]),
+        "stokes_setup": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_double, ctypes.POINTER(_Opts)]),
+        "stokes_sizes": (ctypes.c_int, [vp, i64p, i64p]),
+        "stokes_set_preconditioner": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
+        "stokes_apply_A": (ctypes.c_int, [vp, vp, vp]),
+        "stokes_apply_K": (ctypes.c_int, [vp, vp, vp]),
+        "stokes_apply_P": (ctypes.c_int, [vp, vp, vp]),
+        "stokes_apply_hyperpower": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp]),
+        "stokes_rhs_cavity": (ctypes.c_int, [vp, ctypes.c_double, vp]),
+        "stokes_rhs_body": (ctypes.c_int, [vp, ctypes.c_int, dp, ip, ctypes.c_int, vp]),
+        "stokes_solve": (ctypes.c_int, [vp, vp, ctypes.c_double, vp, ip, dp]),
+        "stokes_solve_host": (ctypes.c_int, [vp, vp, ctypes.c_double, vp, ip, dp]),
+        "stokes_last_ratios": (ctypes.c_int, [vp, dp, ctypes.c_int]),
+        "stokes_profile_begin": (ctypes.c_int, [vp]),
+        "stokes_profile_end": (ctypes.c_int, [vp, ctypes.POINTER(KernelStat), ctypes.c_int]),
+        "stokes_kernel_launches": (ctypes.c_int64, []),
+        "stokes_destroy": (None, [vp]),
+        "stokes_last_error": (ctypes.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def kernel_launches():
+    """Kernels launched by the library in this process so far."""
+    return load_library().stokes_kernel_launches()
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Stokes:
+    """One discretised cavity (n^3 elements, pressure degree p, viscosity nu) on the GPU."""
+
+    def __init__(self, n, p, nu=1.0, c_pen=14.0, schur="inner", precision="fp64",
+                 solver=None, max_order=3, max_steps=4, maxit=2000, restart=60, device=None):
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("Stokes needs a CUDA device")
+        self.device = torch.device(device or "cuda")
+        if solver is None:
+            solver = "minres" if precision == "fp64" else "fgmres"
+        o = _Opts()
+        self.lib.stokes_default_opts(ctypes.byref(o))
+        o.c_pen = c_pen
+        o.schur = SCHUR[schur]
+        o.precision = PRECISION[precision]
+        o.solver = SOLVER[solver]
+        o.max_order, o.max_steps, o.maxit, o.restart = max_order, max_steps, maxit, restart
+        with torch.cuda.device(self.device):
+            # the library runs on its own stream, ordered against the caller's current stream
+            # at every call (inputs ready before, outputs visible after)
+            self.stream = torch.cuda.Stream(device=self.device)
+            o.stream = self.stream.cuda_stream
+            h = ctypes.c_void_p()
+            rc = self.lib.stokes_setup(ctypes.byref(h), n, p, nu, ctypes.byref(o))
+        if rc != STOKES_OK:
+            raise StokesError(rc, self.lib.stokes_last_error(None).decode())
+        self.h = h
+        self.n, self.p, self.nu = n, p, nu
+        nv, npr = ctypes.c_int64(), ctypes.c_int64()
+        self.lib.stokes_sizes(self.h, ctypes.byref(nv), ctypes.byref(npr))
+        self.n_vel, self.n_pres = nv.value, npr.value
+        self.size = self.n_vel + self.n_pres
+        self.a, self.b = n + p - 1, n + p
+
+    # -- helpers -------------------------------------------------------------------------------
+    def _call(self, fn, *args):
+        cur = torch.cuda.current_stream(self.device)
+        self.stream.wait_stream(cur)
+        rc = fn(*args)
+        cur.wait_stream(self.stream)
+        return rc
+
+    def _check(self, rc):
+        if rc != STOKES_OK:
+            raise StokesError(rc, self.lib.stokes_last_error(self.h).decode())
+
+    def _vec(self, x, n):
+        if not (x.is_cuda and x.dtype == torch.float64 and x.is_contiguous() and x.numel() == n):
+            raise ValueError(f"expected a contiguous float64 CUDA tensor of {n} entries")
+        return x
+
+    def empty(self, n=None):
+        return torch.empty(n or self.size, dtype=torch.float64, device=self.device)
+
+    # -- C ABI ----------------------------------------------------------------------------------
+    def set_preconditioner(self, order, steps):
+        self._check(self.lib.stokes_set_preconditioner(self.h, order, steps))
+
+    def apply_A(self, x, out=None):
+        y = out if out is not None else self.empty(self.n_vel)
+        self._check(self._call(self.lib.stokes_apply_A, self.h, _ptr(self._vec(x, self.n_vel)),
+                                            _ptr(self._vec(y, self.n_vel))))
+        return y
+
+    def apply_K(self, x, out=None):
+        y = out if out is not None else self.empty()
+        self._check(self._call(self.lib.stokes_apply_K, self.h, _ptr(self._vec(x, self.size)),
+                                            _ptr(self._vec(y, self.size))))
+        return y
+
+    def apply_P(self, x, out=None):
+        y = out if out is not None else self.empty()
+        self._check(self._call(self.lib.stokes_apply_P, self.h, _ptr(self._vec(x, self.size)),
+                                            _ptr(self._vec(y, self.size))))
+        return y
+
+    def apply_hyperpower(self, order, steps, x, out=None):
+        y = out if out is not None else self.empty()
+        self._check(self._call(self.lib.stokes_apply_hyperpower, self.h, order, steps,
+                                                     _ptr(self._vec(x, self.size)),
+                                                     _ptr(self._vec(y, self.size))))
+        return y
+
+    def rhs_cavity(self, lid_speed=1.0, out=None):
+        f = out if out is not None else self.empty()
+        self._check(self._call(self.lib.stokes_rhs_cavity, self.h, float(lid_speed), _ptr(self._vec(f, self.size))))
+        return f
+
+    def rhs_body(self, coef, waves, accumulate=False, out=None):
+        import numpy as np
+        coef = np.ascontiguousarray(coef, dtype=np.float64)
+        waves = np.ascontiguousarray(waves, dtype=np.int32)
+        m = coef.shape[1]
+        f = out if out is not None else self.empty()
+        self._check(self._call(self.lib.stokes_rhs_body, 
+            self.h, m, coef.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            waves.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(accumulate),
+            _ptr(self._vec(f, self.size))))
+        return f
+
+    def solve(self, rhs, tol=1e-8, out=None, raise_on_error=True):
+        """Returns (x, iterations, true relative residual, status code)."""
+        x = out if out is not None else self.empty()
+        it = ctypes.c_int()
+        rr = ctypes.c_double()
+        rc = self._call(self.lib.stokes_solve, self.h, _ptr(self._vec(rhs, self.size)), float(tol),
+                                   _ptr(self._vec(x, self.size)), ctypes.byref(it),
+                                   ctypes.byref(rr))
+        if raise_on_error:
+            self._check(rc)
+        return x, it.value, rr.value, rc
+
+    def solve_host(self, rhs_host, x_host, tol=1e-8):
+        """Solve with HOST (preferably pinned) float64 tensors; copies happen inside the call."""
+        for t in (rhs_host, x_host):
+            if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != self.size:
+                raise ValueError("expected contiguous float64 host tensors")
+        it = ctypes.c_int()
+        rr = ctypes.c_double()
+        self._check(self._call(self.lib.stokes_solve_host, self.h, ctypes.c_void_p(rhs_host.data_ptr()),
+                                               float(tol), ctypes.c_void_p(x_host.data_ptr()),
+                                               ctypes.byref(it), ctypes.byref(rr)))
+        return it.value, rr.value
+
+    def last_ratios(self, capacity=100000):
+        buf = (ctypes.c_double * capacity)()
+        k = self.lib.stokes_last_ratios(self.h, buf, capacity)
+        if k < 0:
+            raise StokesError(k, "last_ratios")
+        return [buf[i] for i in range(k)]
+
+    def profile_begin(self):
+        self._check(self.lib.stokes_profile_begin(self.h))
+
+    def profile_end(self):
+        """Per kernel class: dict(launches, ms, flops, bytes) of the launches since
+        profile_begin (CUDA events on the launching stream)."""
+        buf = (KernelStat * len(KERNEL_CLASSES))()
+        k = self.lib.stokes_profile_end(self.h, buf, len(KERNEL_CLASSES))
+        if k < 0:
+            raise StokesError(k, "profile_end")
+        return {KERNEL_CLASSES[i]: dict(launches=buf[i].launches, ms=buf[i].ms,
+                                        flops=buf[i].flops, bytes=buf[i].bytes) for i in range(k)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.stokes_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

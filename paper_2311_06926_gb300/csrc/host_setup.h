@@ -1,0 +1,48 @@
+// Host-side construction of the univariate data of the discretisation (App. B.1, B.3; Sec. 3.3)
+// and of the fast-diagonalisation factors (App. A.4). Plain C++, run once per context.
+#pragma once
+#include <vector>
+
+namespace shp {
+
+struct Dense {             // row-major dense matrix
+  int rows = 0, cols = 0;
+  std::vector<double> v;
+  Dense() = default;
+  Dense(int r, int c) : rows(r), cols(c), v((size_t)r * c, 0.0) {}
+  double& operator()(int i, int j) { return v[(size_t)i * cols + j]; }
+  double operator()(int i, int j) const { return v[(size_t)i * cols + j]; }
+};
+
+struct Band {              // banded rows: D(i, start[i] + w) = val[i * width + w]
+  int rows = 0, cols = 0, width = 0;
+  std::vector<int> start;
+  std::vector<double> val;
+};
+
+// Univariate data for n elements and pressure degree p (velocity degree p+1 in its own
+// direction). Interior N functions only (strong no-penetration).
+struct Univariate {
+  int n = 0, p = 0, a = 0, b = 0;
+  double h = 0, c_pen = 0;
+  Dense M, K;              // a x a: int N_i N_j, int N_i' N_j'
+  Dense Mc, Kc, Tc;        // b x b: int M_i M_j, int M_i' M_j', T-check
+  std::vector<double> int_N;         // a: integrals of the interior N functions
+  std::vector<double> M_at_1, dM_at_1;  // b: M_i(1), M_i'(1)
+  std::vector<double> const_M;       // b: coefficients of the constant 1 in the M basis
+};
+
+Univariate build_univariate(int n, int p, double c_pen);
+
+// Symmetric-definite generalised eigenproblem K U = M U diag(lam), U^T M U = I, by Cholesky
+// reduction (App. A.3) and cyclic Jacobi rotations. Eigenvalues ascending. Returns false if M is
+// not positive definite.
+bool generalized_eigh(const Dense& K, const Dense& M, std::vector<double>& lam, Dense& U);
+
+Band to_band(const Dense& D, double drop_tol);
+
+// 1D load of a sine mode against the interior N functions (own direction) or the M functions.
+std::vector<double> sine_load_N(const Univariate& u, int k);
+std::vector<double> sine_load_M(const Univariate& u, int k);
+
+}  // namespace shp

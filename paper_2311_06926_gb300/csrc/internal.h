@@ -1,0 +1,119 @@
+// Internal interfaces shared by the CUDA translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace shp {
+
+// Banded 1D matrix on the device: D(i, start[i] + w) = val[i * width + w].
+template <typename T>
+struct BandD {
+  int rows, cols, width;
+  const int* start;
+  const T* val;
+};
+
+// Extents of a 3D tensor, x1 fastest: index = i1 + n1 * (i2 + n2 * i3).
+struct Dims {
+  int n1, n2, n3;
+  __host__ __device__ int64_t size() const { return (int64_t)n1 * n2 * n3; }
+  __host__ __device__ int get(int axis) const { return axis == 1 ? n1 : (axis == 2 ? n2 : n3); }
+  __host__ __device__ Dims with(int axis, int m) const {
+    Dims d = *this;
+    if (axis == 1) d.n1 = m; else if (axis == 2) d.n2 = m; else d.n3 = m;
+    return d;
+  }
+};
+
+// ---- banded passes (k_band.cu) -----------------------------------------------------------
+// Y = c0 (D0 .axis X0) [+ c1 (D1 .axis X1)] [+ cz Z] [+ Dt_axis g  (difference transpose along
+// axis `gaxis` of the b^3 tensor g, see k_band.cu)]. X0/X1 have extents `in`; Y has extents
+// in.with(axis, D0.rows). Z (may alias Y) and g may be null.
+template <typename T>
+struct PassArgs {
+  const T* X0; const T* X1;
+  BandD<T> D0, D1;
+  T c0, c1;
+  const T* Z; T cz;
+  const T* g; int gaxis; Dims gdims;
+  T* Y;
+  Dims in;
+  int axis;
+  int nterms;
+};
+template <typename T>
+void band_pass(const PassArgs<T>& a, cudaStream_t s);
+
+// delta = sum_c D .c u_c: exact discrete divergence of the velocity coefficients (App. B.2),
+// output b^3. (D beta)_i = beta_i - beta_{i-1} with beta_{-1} = beta_a = 0.
+template <typename T>
+void divergence(const T* u1, const T* u2, const T* u3, int a, int b, T* delta, cudaStream_t s);
+
+// y_c (+)= D^T .c g for the three components (grad of a b^3 field onto velocity coefficients).
+template <typename T>
+void div_transpose(const T* g, int a, int b, T* y1, T* y2, T* y3, int accumulate,
+                   cudaStream_t s);
+
+// ---- dense mode products (k_dense.cu) ----------------------------------------------------
+// Y[l, i, r] = sum_j Op(i, j) X[l, j, r] along `axis` of X (extents `in`), Op(i, j) =
+// trans ? U[j * ld + i] : U[i * ld + j], output extents in.with(axis, m).
+// If lam1 != null the result is divided by scale * (lam1[i1] + lam2[i2] + lam3[i3]) at output
+// index (i1, i2, i3) (fast-diagonalisation scaling, App. A.4).
+template <typename T>
+struct ModeArgs {
+  const T* X; T* Y;
+  const T* U; int ld; int trans; int m;
+  Dims in; int axis;
+  const T* lam1; const T* lam2; const T* lam3; T scale;
+  T post;   // if lam1 == null: the result is multiplied by post
+};
+template <typename T>
+void mode_product(const ModeArgs<T>& a, cudaStream_t s);
+
+// ---- vector kernels (k_vec.cu) -----------------------------------------------------------
+// Deterministic dot product: fixed grid, fixed-order tree reduction. Result written to *out
+// (device). `partials` holds kDotBlocks values.
+constexpr int kDotBlocks = 512;
+template <typename T>
+void dot(const T* x, const T* y, int64_t n, T* partials, T* out, cudaStream_t s);
+// y = a x + b y with a, b from host
+template <typename T>
+void axpby(T a, const T* x, T b, T* y, int64_t n, cudaStream_t s);
+// r = r - u; acc = acc + r  (one hyper-power Horner step, Eq. 2.1 generalised)
+template <typename T>
+void hp_update(T* r, const T* u, T* acc, int64_t n, cudaStream_t s);
+void copy_async(void* dst, const void* src, size_t bytes, cudaStream_t s);
+// y += sign * (*alpha) * x with alpha in device memory
+void axpy_dev(const double* alpha, double sign, const double* x, double* y, int64_t n,
+              cudaStream_t s);
+// y[k] = <V_k, w> for k < nvec (V_k = V + k * ldv); deterministic, partials: nvec * kDotBlocks
+void multi_dot(const double* V, int64_t ldv, int nvec, const double* w, int64_t n,
+               double* partials, double* out, cudaStream_t s);
+// w += sign * sum_k h[k] V_k (h in device memory)
+void multi_axpy(const double* V, int64_t ldv, int nvec, const double* h, double sign, double* w,
+                int64_t n, cudaStream_t s);
+// y = x * (1 / *alpha)
+void scale_inv_dev(const double* alpha, const double* x, double* y, int64_t n, cudaStream_t s);
+void fill_zero(void* dst, size_t bytes, cudaStream_t s);
+
+// MINRES device state and fused kernels (k_vec.cu)
+struct MinresState {
+  double gamma, gamma_old, eta, eta0, c, c_old, s, s_old;
+  double delta, gg;          // dot products written by the dot kernel
+  double a1, a2, a3, xcoef;  // update coefficients of the current iteration
+  double ratio;
+  int iter, status, done, pad;
+};
+void minres_scale_z(double* z, MinresState* st, int64_t n, cudaStream_t s);
+void minres_lanczos(const double* Kz, const double* v, double* vold_inout, MinresState* st,
+                    int64_t n, cudaStream_t s);
+void minres_scalars(MinresState* st, double tol, cudaStream_t s);
+void minres_update(const double* z, double* w_old_inout, const double* w, double* x,
+                   MinresState* st, int64_t n, cudaStream_t s);
+void minres_init(MinresState* st, cudaStream_t s);
+
+// float <-> double conversions for the mixed-precision preconditioner
+void to_float(const double* x, float* y, int64_t n, cudaStream_t s);
+void to_double(const float* x, double* y, int64_t n, cudaStream_t s);
+
+}  // namespace shp

@@ -1,0 +1,354 @@
+// Vector kernels of the Krylov iteration: deterministic dot products, fused axpys, and the
+// preconditioned MINRES recurrences (Lanczos three-term step, Givens QR scalars, update of the
+// direction and the iterate) with all scalars kept in device memory.
+#include <cmath>
+
+#include "internal.h"
+#include "profile.h"
+
+namespace shp {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(int64_t total) {
+  int64_t b = (total + kThreads - 1) / kThreads;
+  if (b > 152 * 32) b = 152 * 32;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+template <typename T>
+__device__ T block_sum(T v, T* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+// Stage 1: block b sums elements b*256+t, b*256+t+G*256, ... in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_dot_partial(const T* __restrict__ x,
+                                                          const T* __restrict__ y, int64_t n,
+                                                          T* __restrict__ partials) {
+  __shared__ T sh[kThreads];
+  T s = 0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads)
+    s += x[i] * y[i];
+  const T tot = block_sum(s, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// Stage 2: one block sums the partials in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_dot_final(const T* __restrict__ partials, int np,
+                                                        T* __restrict__ out) {
+  __shared__ T sh[kThreads];
+  T s = 0;
+  for (int i = threadIdx.x; i < np; i += kThreads) s += partials[i];
+  const T tot = block_sum(s, sh);
+  if (threadIdx.x == 0) *out = tot;
+}
+
+template <typename T>
+__global__ void k_axpby(T a, const T* __restrict__ x, T b, T* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+
+template <typename T>
+__global__ void k_hp_update(T* __restrict__ r, const T* __restrict__ u, T* __restrict__ acc,
+                            int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T ri = r[i] - u[i];
+    r[i] = ri;
+    acc[i] += ri;
+  }
+}
+
+__global__ void k_to_float(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
+__global__ void k_to_double(const float* __restrict__ x, double* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+
+__global__ void k_axpy_dev(const double* __restrict__ alpha, double sign,
+                           const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+  const double a = sign * (*alpha);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+
+__global__ void k_scale_inv_dev(const double* __restrict__ alpha, const double* __restrict__ x,
+                                double* __restrict__ y, int64_t n) {
+  const double a = 1.0 / (*alpha);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+
+// Partial dot products of w with nvec vectors: block b handles the same slice for every vector.
+__global__ void __launch_bounds__(kThreads) k_multi_dot_partial(const double* __restrict__ V,
+                                                                int64_t ldv, int nvec,
+                                                                const double* __restrict__ w,
+                                                                int64_t n,
+                                                                double* __restrict__ partials) {
+  __shared__ double sh[kThreads];
+  for (int k = 0; k < nvec; ++k) {
+    const double* v = V + k * ldv;
+    double s = 0;
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * kThreads)
+      s += v[i] * w[i];
+    const double tot = block_sum(s, sh);
+    if (threadIdx.x == 0) partials[(int64_t)k * gridDim.x + blockIdx.x] = tot;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_multi_dot_final(const double* __restrict__ partials,
+                                                              int np, double* __restrict__ out) {
+  __shared__ double sh[kThreads];
+  const double* p = partials + (int64_t)blockIdx.x * np;
+  double s = 0;
+  for (int i = threadIdx.x; i < np; i += kThreads) s += p[i];
+  const double tot = block_sum(s, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = tot;
+}
+
+__global__ void k_multi_axpy(const double* __restrict__ V, int64_t ldv, int nvec,
+                             const double* __restrict__ h, double sign, double* __restrict__ w,
+                             int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0;
+    for (int k = 0; k < nvec; ++k) s += h[k] * V[k * ldv + i];
+    w[i] += sign * s;
+  }
+}
+
+// ---- MINRES ---------------------------------------------------------------------------------
+// status codes mirror the public error codes
+constexpr int kStatusNonfinite = -3;
+constexpr int kStatusNotSpd = -4;
+
+__global__ void k_minres_init(MinresState* st) {
+  const double gg = st->gg;
+  st->status = 0;
+  st->iter = 0;
+  st->done = 0;
+  st->pad = 0;
+  if (!isfinite(gg)) {
+    st->status = kStatusNonfinite;
+    st->done = 1;
+    return;
+  }
+  if (gg < 0.0) {
+    st->status = kStatusNotSpd;
+    st->done = 1;
+    return;
+  }
+  st->gamma = sqrt(gg);
+  st->gamma_old = 1.0;
+  st->eta = st->gamma;
+  st->eta0 = st->gamma;
+  st->c = st->c_old = 1.0;
+  st->s = st->s_old = 0.0;
+  st->ratio = 1.0;
+  if (st->gamma == 0.0) {       // zero right-hand side: x = 0 is the solution
+    st->ratio = 0.0;
+    st->done = 1;
+  }
+}
+
+__global__ void k_minres_scale_z(double* __restrict__ z, const MinresState* __restrict__ st,
+                                 int64_t n) {
+  if (st->done) return;
+  const double inv = 1.0 / st->gamma;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    z[i] *= inv;
+}
+
+// v_new = Kz - (delta / gamma) v - (gamma / gamma_old) v_old, written over v_old.
+__global__ void k_minres_lanczos(const double* __restrict__ Kz, const double* __restrict__ v,
+                                 double* __restrict__ vold, const MinresState* __restrict__ st,
+                                 int64_t n) {
+  if (st->done) return;
+  const double a = st->delta / st->gamma, b = st->gamma / st->gamma_old;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    vold[i] = Kz[i] - a * v[i] - b * vold[i];
+}
+
+// Givens QR of the Lanczos tridiagonal: apply the two previous rotations to the new column
+// (gamma, delta, gamma_new), form the new rotation, and update the residual estimate |eta|.
+__global__ void k_minres_scalars(MinresState* st, double tol) {
+  st->pad = 0;                   // "update this iteration" flag read by the update kernel
+  if (st->done) return;
+  const double gg = st->gg, delta = st->delta;
+  if (!isfinite(gg) || !isfinite(delta)) {
+    st->status = kStatusNonfinite;
+    st->done = 1;
+    return;
+  }
+  if (gg < 0.0) {
+    st->status = kStatusNotSpd;
+    st->done = 1;
+    return;
+  }
+  const double gamma = st->gamma, gamma_new = sqrt(gg);
+  const double c = st->c, c_old = st->c_old, s = st->s, s_old = st->s_old;
+  const double a0 = c * delta - c_old * s * gamma;
+  const double a1 = sqrt(a0 * a0 + gamma_new * gamma_new);
+  const double a2 = s * delta + c_old * c * gamma;
+  const double a3 = s_old * gamma;
+  const double c_new = a0 / a1, s_new = gamma_new / a1;
+  st->a1 = a1;
+  st->a2 = a2;
+  st->a3 = a3;
+  st->xcoef = c_new * st->eta;
+  st->eta = -s_new * st->eta;
+  st->ratio = fabs(st->eta) / st->eta0;
+  st->c_old = c;
+  st->c = c_new;
+  st->s_old = s;
+  st->s = s_new;
+  st->gamma_old = gamma;
+  st->gamma = gamma_new;
+  st->iter += 1;
+  st->pad = 1;
+  if (st->ratio <= tol) st->done = 1;
+}
+
+// w_new = (z - a3 w_old - a2 w) / a1 over w_old; x += (c_new eta) w_new.
+__global__ void k_minres_update(const double* __restrict__ z, double* __restrict__ wold,
+                                const double* __restrict__ w, double* __restrict__ x,
+                                const MinresState* __restrict__ st, int64_t n) {
+  if (!st->pad) return;
+  const double inv = 1.0 / st->a1, a2 = st->a2, a3 = st->a3, xc = st->xcoef;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double wn = (z[i] - a3 * wold[i] - a2 * w[i]) * inv;
+    wold[i] = wn;
+    x[i] += xc * wn;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void dot(const T* x, const T* y, int64_t n, T* partials, T* out, cudaStream_t s) {
+  launch_begin(kClassVector, s);
+  k_dot_partial<T><<<kDotBlocks, kThreads, 0, s>>>(x, y, n, partials);
+  launch_end(kClassVector, s, 0.0, 0.0);
+  launch_begin(kClassVector, s);
+  k_dot_final<T><<<1, kThreads, 0, s>>>(partials, kDotBlocks, out);
+  launch_end(kClassVector, s, 0.0, 0.0);
+}
+
+template <typename T>
+void axpby(T a, const T* x, T b, T* y, int64_t n, cudaStream_t s) {
+  launch_begin(kClassVector, s);
+  k_axpby<T><<<grid_for(n), kThreads, 0, s>>>(a, x, b, y, n);
+  launch_end(kClassVector, s, 0.0, 0.0);
+}
+
+template <typename T>
+void hp_update(T* r, const T* u, T* acc, int64_t n, cudaStream_t s) {
+  launch_begin(kClassVector, s);
+  k_hp_update<T><<<grid_for(n), kThreads, 0, s>>>(r, u, acc, n);
+  launch_end(kClassVector, s, 0.0, 0.0);
+}
+
+void copy_async(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
+}
+
+void fill_zero(void* dst, size_t bytes, cudaStream_t s) { cudaMemsetAsync(dst, 0, bytes, s); }
+
+void to_float(const double* x, float* y, int64_t n, cudaStream_t s) {
+  launch_begin(kClassVector, s);
+  k_to_float<<<grid_for(n), kThreads, 0, s>>>(x, y, n);
+  launch_end(kClassVector, s, 0.0, 0.0);
+}
+void to_double(const float* x, double* y, int64_t n, cudaStream_t s) {
+  launch_begin(kClassVector, s);
+  k_to_double<<<grid_for(n), kThreads, 0, s>>>(x, y, n);
+  launch_end(kClassVector, s, 0.0, 0.0);
+}
+
+void axpy_dev(const double* alpha, double sign, const double* x, double* y, int64_t n,
+              cudaStream_t s) {
+  launch_begin(kClassVector, s);
+  k_axpy_dev<<<grid_for(n), kThreads, 0, s>>>(alpha, sign, x, y, n);
+  launch_end(kClassVector, s, 0.0, 0.0);
+}
+void scale_inv_dev(const double* alpha, const double* x, double* y, int64_t n, cudaStream_t s) {
+  launch_begin(kClassVector, s);
+  k_scale_inv_dev<<<grid_for(n), kThreads, 0, s>>>(alpha, x, y, n);
+  launch_end(kClassVector, s, 0.0, 0.0);
+}
+void multi_dot(const double* V, int64_t ldv, int nvec, const double* w, int64_t n,
+               double* partials, double* out, cudaStream_t s) {
+  launch_begin(kClassVector, s);
+  k_multi_dot_partial<<<kDotBlocks, kThreads, 0, s>>>(V, ldv, nvec, w, n, partials);
+  launch_end(kClassVector, s, 0.0, 0.0);
+  launch_begin(kClassVector, s);
+  k_multi_dot_final<<<nvec, kThreads, 0, s>>>(partials, kDotBlocks, out);
+  launch_end(kClassVector, s, 0.0, 0.0);
+}
+void multi_axpy(const double* V, int64_t ldv, int nvec, const double* h, double sign, double* w,
+                int64_t n, cudaStream_t s) {
+  launch_begin(kClassVector, s);
+  k_multi_axpy<<<grid_for(n), kThreads, 0, s>>>(V, ldv, nvec, h, sign, w, n);
+  launch_end(kClassVector, s, 0.0, 0.0);
+}
+
+void minres_init(MinresState* st, cudaStream_t s) { launch_begin(kClassVector, s);
+  k_minres_init<<<1, 1, 0, s>>>(st);
+  launch_end(kClassVector, s, 0.0, 0.0); }
+void minres_scale_z(double* z, MinresState* st, int64_t n, cudaStream_t s) {
+  launch_begin(kClassVector, s);
+  k_minres_scale_z<<<grid_for(n), kThreads, 0, s>>>(z, st, n);
+  launch_end(kClassVector, s, 0.0, 0.0);
+}
+void minres_lanczos(const double* Kz, const double* v, double* vold, MinresState* st, int64_t n,
+                    cudaStream_t s) {
+  launch_begin(kClassVector, s);
+  k_minres_lanczos<<<grid_for(n), kThreads, 0, s>>>(Kz, v, vold, st, n);
+  launch_end(kClassVector, s, 0.0, 0.0);
+}
+void minres_scalars(MinresState* st, double tol, cudaStream_t s) {
+  launch_begin(kClassVector, s);
+  k_minres_scalars<<<1, 1, 0, s>>>(st, tol);
+  launch_end(kClassVector, s, 0.0, 0.0);
+}
+void minres_update(const double* z, double* wold, const double* w, double* x, MinresState* st,
+                   int64_t n, cudaStream_t s) {
+  launch_begin(kClassVector, s);
+  k_minres_update<<<grid_for(n), kThreads, 0, s>>>(z, wold, w, x, st, n);
+  launch_end(kClassVector, s, 0.0, 0.0);
+}
+
+template void dot<double>(const double*, const double*, int64_t, double*, double*, cudaStream_t);
+template void dot<float>(const float*, const float*, int64_t, float*, float*, cudaStream_t);
+template void axpby<double>(double, const double*, double, double*, int64_t, cudaStream_t);
+template void axpby<float>(float, const float*, float, float*, int64_t, cudaStream_t);
+template void hp_update<double>(double*, const double*, double*, int64_t, cudaStream_t);
+template void hp_update<float>(float*, const float*, float*, int64_t, cudaStream_t);
+
+}  // namespace shp

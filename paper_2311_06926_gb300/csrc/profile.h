@@ -1,0 +1,31 @@
+// Launch accounting: a process-wide launch counter and an optional per-thread profiler that
+// brackets each launch with CUDA events on the launching stream and records the launch's
+// algorithmic flops and bytes.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace shp {
+
+enum KernelClass {
+  kClassBand = 0,      // banded Kronecker passes
+  kClassMode = 1,      // dense mode products (fast diagonalisation, pressure mass inverse)
+  kClassDiv = 2,       // discrete divergence and its transpose
+  kClassVector = 3,    // Krylov vector kernels, dot products, conversions
+  kClassMma = 4,       // tensor-core mode products
+  kNumClasses = 5
+};
+
+void launch_begin(int cls, cudaStream_t s);
+void launch_end(int cls, cudaStream_t s, double flops, double bytes);
+int64_t launch_count();
+
+struct Profiler;
+Profiler* profiler_create();
+void profiler_destroy(Profiler* p);
+void profiler_activate(Profiler* p);   // nullptr: deactivate (this thread)
+// Per class: launches, milliseconds (sum of event intervals), flops, bytes. Synchronizes.
+void profiler_collect(Profiler* p, int64_t* launches, double* ms, double* flops, double* bytes);
+
+}  // namespace shp

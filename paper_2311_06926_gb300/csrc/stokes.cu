@@ -1,0 +1,973 @@
+// Context, operator sequences, hyper-power recursion, Krylov drivers and the C ABI.
+//
+// Operators (Sec. 3.3). Because interior N-splines vanish at both ends of [0, 1], integration by
+// parts and the derivative identity of App. B.2 give C = -D^T M-check and C-check = D^T M-check,
+// with D the (b x a) coefficient difference (D beta)_i = beta_i - beta_{i-1}. The six printed
+// off-diagonal Kronecker products of A and the three of B then factor through the pressure mass
+// matrix M_q = M-check^3 and the exact discrete divergence D_div:
+//   B = D_div^T M_q,   B^T = M_q D_div,
+//   A = blockdiag(A'_cc) + nu D_div^T M_q D_div,   A'_cc = A_cc - nu D_c^T M_q D_c,
+// where D_c^T M_q D_c = (mass) (x) (mass) (x) K in direction c because K = D^T M-check D. For
+// component 1, A'_11 = nu Mc (x) Mc (x) K + 2 nu (Mc (x) Tc (x) M + Tc (x) Mc (x) M). This is
+// the same matrix as the 15 printed products, evaluated with fewer banded passes.
+//
+// Base preconditioner (Eq. 4.1): fast diagonalisation of the diagonal blocks A_cc (App. A.4) and
+// the pressure block M_q / (2 nu), whose inverse 2 nu (U_T U_T^T)^(x)3 reuses the (T-check,
+// M-check) eigenvectors: U_T^T M-check U_T = I gives M-check^-1 = U_T U_T^T.
+//
+// Hyper-power sequence of order q (Eq. 2.1 for q = 2): X_{k+1} x = X_k sum_{j<q} (I - A~ X_k)^j x,
+// evaluated as r = x, acc = x, then (q - 1) times {r -= A~ X_k r; acc += r}, then X_k acc.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "host_setup.h"
+#include "internal.h"
+#include "profile.h"
+#include "stokes_hp.h"
+
+namespace shp {
+namespace {
+
+struct CudaError {
+  cudaError_t e;
+  const char* what;
+};
+
+inline void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) throw CudaError{e, what};
+}
+
+struct ArgError {
+  std::string msg;
+};
+struct SetupError {
+  std::string msg;
+};
+
+// ---- device memory owned by a context ---------------------------------------------------------
+struct Arena {
+  std::vector<void*> ptrs;
+  template <typename T>
+  T* alloc(size_t count) {
+    void* p = nullptr;
+    if (count == 0) count = 1;
+    ck(cudaMalloc(&p, count * sizeof(T)), "cudaMalloc");
+    ptrs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  ~Arena() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+
+template <typename T>
+BandD<T> upload_band(Arena& ar, const Band& b, cudaStream_t s) {
+  BandD<T> d;
+  d.rows = b.rows;
+  d.cols = b.cols;
+  d.width = b.width;
+  int* st = ar.alloc<int>(b.start.size());
+  T* v = ar.alloc<T>(b.val.size());
+  std::vector<T> tv(b.val.begin(), b.val.end());
+  ck(cudaMemcpyAsync(st, b.start.data(), b.start.size() * sizeof(int), cudaMemcpyHostToDevice, s),
+     "upload band");
+  ck(cudaMemcpyAsync(v, tv.data(), tv.size() * sizeof(T), cudaMemcpyHostToDevice, s),
+     "upload band");
+  ck(cudaStreamSynchronize(s), "upload band");
+  d.start = st;
+  d.val = v;
+  return d;
+}
+
+template <typename T>
+T* upload(Arena& ar, const std::vector<double>& h, cudaStream_t s) {
+  T* d = ar.alloc<T>(h.size());
+  std::vector<T> tv(h.begin(), h.end());
+  ck(cudaMemcpyAsync(d, tv.data(), tv.size() * sizeof(T), cudaMemcpyHostToDevice, s), "upload");
+  ck(cudaStreamSynchronize(s), "upload");
+  return d;
+}
+
+// ---- operators in precision T ------------------------------------------------------------------
+template <typename T>
+struct Ops {
+  int a = 0, b = 0;
+  T nu = 0;
+  int64_t nvc = 0, nvel = 0, npres = 0;
+  BandD<T> M{}, K{}, Mc{}, Tc{};
+  const T *U_N = nullptr, *lam_N = nullptr, *U_T = nullptr, *lam_T = nullptr;
+  T *tK = nullptr, *tM = nullptr, *tS = nullptr, *tR = nullptr;   // component-size temporaries
+  T *f1 = nullptr, *f2 = nullptr;                                 // mode-product ping-pong
+  T *delta = nullptr, *m1 = nullptr, *m2 = nullptr;               // pressure-size temporaries
+  cudaStream_t s = nullptr;
+
+  Dims comp(int c) const {
+    if (c == 0) return Dims{a, b, b};
+    if (c == 1) return Dims{b, a, b};
+    return Dims{b, b, a};
+  }
+
+  void pass(const T* X0, const BandD<T>& D0, T c0, const T* X1, const BandD<T>* D1, T c1, Dims in,
+            int axis, T* Y, const T* Z = nullptr, T cz = 0, const T* g = nullptr,
+            int gaxis = 0) const {
+    PassArgs<T> p{};
+    p.X0 = X0;
+    p.D0 = D0;
+    p.c0 = c0;
+    p.X1 = X1;
+    if (D1) p.D1 = *D1; else p.D1 = D0;
+    p.c1 = c1;
+    p.nterms = X1 ? 2 : 1;
+    p.Z = Z;
+    p.cz = cz;
+    p.g = g;
+    p.gaxis = gaxis;
+    p.gdims = Dims{b, b, b};
+    p.Y = Y;
+    p.in = in;
+    p.axis = axis;
+    band_pass<T>(p, s);
+  }
+
+  // y = A'_cc u (+ D^T g along the own direction of component c if g != null)
+  void adiag(int c, const T* u, T* y, const T* g) const {
+    const Dims d = comp(c);
+    const int own = c + 1;
+    const int o1 = c == 0 ? 2 : 1;
+    const int o2 = c == 2 ? 2 : 3;
+    const T nu2 = 2 * nu;
+    pass(u, K, 1, nullptr, nullptr, 0, d, own, tK);
+    pass(u, M, 1, nullptr, nullptr, 0, d, own, tM);
+    pass(tK, Mc, nu, tM, &Tc, nu2, d, o1, tS);
+    pass(tM, Mc, 1, nullptr, nullptr, 0, d, o1, tR);
+    pass(tS, Mc, 1, tR, &Tc, nu2, d, o2, y, nullptr, 0, g, own);
+  }
+
+  // y = coef * M_q x (+ cz Z)
+  void mq(const T* x, T* y, T coef, const T* Z = nullptr, T cz = 0) const {
+    const Dims d{b, b, b};
+    pass(x, Mc, 1, nullptr, nullptr, 0, d, 1, f1);
+    pass(f1, Mc, 1, nullptr, nullptr, 0, d, 2, f2);
+    pass(f2, Mc, coef, nullptr, nullptr, 0, d, 3, y, Z, cz);
+  }
+
+  void apply_K(const T* x, T* y) const {
+    const T* u1 = x;
+    const T* u2 = x + nvc;
+    const T* u3 = x + 2 * nvc;
+    const T* q = x + nvel;
+    T* yq = y + nvel;
+    divergence<T>(u1, u2, u3, a, b, delta, s);
+    mq(delta, yq, 1);                 // B^T u = M_q D_div u
+    mq(q, m2, 1, yq, nu);             // g = M_q q + nu M_q D_div u
+    for (int c = 0; c < 3; ++c) adiag(c, x + c * nvc, y + c * nvc, m2);
+  }
+
+  void apply_A(const T* x, T* y) const {
+    divergence<T>(x, x + nvc, x + 2 * nvc, a, b, delta, s);
+    mq(delta, m2, nu);
+    for (int c = 0; c < 3; ++c) adiag(c, x + c * nvc, y + c * nvc, m2);
+  }
+
+  void apply_B(const T* q, T* yu) const {   // B q = D_div^T M_q q
+    mq(q, m2, 1);
+    div_transpose<T>(m2, a, b, yu, yu + nvc, yu + 2 * nvc, 0, s);
+  }
+
+  void apply_Bt(const T* u, T* yq) const {  // B^T u = M_q D_div u
+    divergence<T>(u, u + nvc, u + 2 * nvc, a, b, delta, s);
+    mq(delta, yq, 1);
+  }
+
+  void mode(const T* X, T* Y, const T* U, int n, int trans, Dims in, int axis,
+            const T* l1 = nullptr, const T* l2 = nullptr, const T* l3 = nullptr, T scale = 1,
+            T post = 1) const {
+    ModeArgs<T> m{};
+    m.X = X;
+    m.Y = Y;
+    m.U = U;
+    m.ld = n;
+    m.trans = trans;
+    m.m = n;
+    m.in = in;
+    m.axis = axis;
+    m.lam1 = l1;
+    m.lam2 = l2;
+    m.lam3 = l3;
+    m.scale = scale;
+    m.post = post;
+    mode_product<T>(m, s);
+  }
+
+  // fast diagonalisation of A_cc (App. A.4): y = (U3 U2 U1) diag(1/(2 nu sum lam)) (U3 U2 U1)^T x
+  void fd_comp(int c, const T* x, T* y) const {
+    const Dims d = comp(c);
+    const T* U[3];
+    const T* L[3];
+    int n[3];
+    for (int k = 0; k < 3; ++k) {
+      const bool own = k == c;
+      U[k] = own ? U_N : U_T;
+      L[k] = own ? lam_N : lam_T;
+      n[k] = own ? a : b;
+    }
+    mode(x, f1, U[0], n[0], 1, d, 1);
+    mode(f1, f2, U[1], n[1], 1, d, 2);
+    mode(f2, f1, U[2], n[2], 1, d, 3, L[0], L[1], L[2], 2 * nu);
+    mode(f1, f2, U[2], n[2], 0, d, 3);
+    mode(f2, f1, U[1], n[1], 0, d, 2);
+    mode(f1, y, U[0], n[0], 0, d, 1);
+  }
+
+  void fd_V(const T* x, T* y) const {
+    for (int c = 0; c < 3; ++c) fd_comp(c, x + c * nvc, y + c * nvc);
+  }
+
+  // pressure block: y = 2 nu (M-check^-1)^(x)3 x = 2 nu (U_T U_T^T)^(x)3 x
+  void minv_Q(const T* x, T* y) const {
+    const Dims d{b, b, b};
+    mode(x, f1, U_T, b, 1, d, 1);
+    mode(f1, f2, U_T, b, 1, d, 2);
+    mode(f2, f1, U_T, b, 1, d, 3);
+    mode(f1, f2, U_T, b, 0, d, 3);
+    mode(f2, f1, U_T, b, 0, d, 2);
+    mode(f1, y, U_T, b, 0, d, 1, nullptr, nullptr, nullptr, 1, 2 * nu);
+  }
+};
+
+// ---- hyper-power recursion in precision T ------------------------------------------------------
+template <typename T>
+struct HyperPower {
+  const Ops<T>* op = nullptr;
+  int order = 2;
+  int schur = STOKES_SCHUR_INNER;
+  std::vector<T*> vr, vacc, vt, vu;   // velocity buffers per level 1..max_steps
+  std::vector<T*> qr, qacc, qt, qu;   // pressure buffers per level
+  T *bv = nullptr, *hv = nullptr;     // velocity buffers of the Schur approximation
+  int64_t counts[4] = {0, 0, 0, 0};   // fd_V, minv_Q, A, (B + B^T)
+
+  void V(int s, const T* x, T* y) {
+    const int64_t n = op->nvel;
+    if (s == 0) {
+      op->fd_V(x, y);
+      ++counts[0];
+      return;
+    }
+    T *r = vr[s], *acc = vacc[s], *t = vt[s], *u = vu[s];
+    copy_async(r, x, n * sizeof(T), op->s);
+    copy_async(acc, x, n * sizeof(T), op->s);
+    for (int j = 1; j < order; ++j) {
+      V(s - 1, r, t);
+      op->apply_A(t, u);
+      ++counts[2];
+      hp_update<T>(r, u, acc, n, op->s);
+    }
+    V(s - 1, acc, y);
+  }
+
+  int level_of(int m) const {
+    if (schur == STOKES_SCHUR_NONE) return 0;
+    return m == 1 ? 0 : m;
+  }
+
+  void Q(int m, const T* x, T* y) {
+    const int64_t n = op->npres;
+    if (m == 0) {
+      op->minv_Q(x, y);
+      ++counts[1];
+      return;
+    }
+    T *r = qr[m], *acc = qacc[m], *t = qt[m], *u = qu[m];
+    const int l = level_of(m);
+    copy_async(r, x, n * sizeof(T), op->s);
+    copy_async(acc, x, n * sizeof(T), op->s);
+    for (int j = 1; j < order; ++j) {
+      Q(m - 1, r, t);
+      op->apply_B(t, bv);          // A~_Q t = B^T P_{V,l}^-1 B t
+      V(l, bv, hv);
+      op->apply_Bt(hv, u);
+      ++counts[3];
+      hp_update<T>(r, u, acc, n, op->s);
+    }
+    Q(m - 1, acc, y);
+  }
+
+  void apply(int steps, const T* x, T* y) {
+    V(steps, x, y);
+    Q(steps, x + op->nvel, y + op->nvel);
+  }
+};
+
+}  // namespace
+}  // namespace shp
+
+using namespace shp;
+
+struct stokes_ctx {
+  int n = 0, p = 0, a = 0, b = 0;
+  double nu = 0, c_pen = 0;
+  int64_t nvc = 0, nvel = 0, npres = 0, ntot = 0;
+  stokes_opts opts{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Arena arena;
+  Univariate uv;
+  Ops<double> od;
+  Ops<float> of;
+  HyperPower<double> hd;
+  HyperPower<float> hf;
+  float *xf = nullptr, *yf = nullptr;    // reduced-precision preconditioner in/out
+  double *zconst = nullptr, *ones = nullptr, *partials = nullptr, *dsc = nullptr;
+  MinresState* st = nullptr;
+  MinresState* st_host = nullptr;
+  double* pinned = nullptr;              // small pinned host scratch
+  // Krylov vectors
+  double *kv[8] = {nullptr};
+  double *V = nullptr, *Z = nullptr;     // FGMRES bases ((restart + 1) x ntot, restart x ntot)
+  double *io_rhs = nullptr, *io_x = nullptr;
+  int order = 2, steps = 0;
+  std::vector<double> ratios;
+  std::string err;
+  Profiler* prof = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_setup_error;
+
+int fail(stokes_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg; else g_setup_error = msg;
+  return code;
+}
+
+int cuda_fail(stokes_ctx* c, const CudaError& e) {
+  return fail(c, STOKES_ERR_CUDA, std::string(e.what) + ": " + cudaGetErrorString(e.e));
+}
+
+void check_launch(const char* what) {
+  ck(cudaGetLastError(), what);
+}
+
+template <typename T>
+void init_ops(stokes_ctx* c, Ops<T>& o, const Band& M, const Band& K, const Band& Mc,
+              const Band& Tc, const std::vector<double>& UN, const std::vector<double>& lN,
+              const std::vector<double>& UT, const std::vector<double>& lT) {
+  Arena& ar = c->arena;
+  cudaStream_t s = c->stream;
+  o.a = c->a;
+  o.b = c->b;
+  o.nu = (T)c->nu;
+  o.nvc = c->nvc;
+  o.nvel = c->nvel;
+  o.npres = c->npres;
+  o.s = s;
+  o.M = upload_band<T>(ar, M, s);
+  o.K = upload_band<T>(ar, K, s);
+  o.Mc = upload_band<T>(ar, Mc, s);
+  o.Tc = upload_band<T>(ar, Tc, s);
+  o.U_N = upload<T>(ar, UN, s);
+  o.lam_N = upload<T>(ar, lN, s);
+  o.U_T = upload<T>(ar, UT, s);
+  o.lam_T = upload<T>(ar, lT, s);
+  const size_t big = (size_t)c->b * c->b * c->b;   // >= a b^2
+  o.tK = ar.alloc<T>(big);
+  o.tM = ar.alloc<T>(big);
+  o.tS = ar.alloc<T>(big);
+  o.tR = ar.alloc<T>(big);
+  o.f1 = ar.alloc<T>(big);
+  o.f2 = ar.alloc<T>(big);
+  o.delta = ar.alloc<T>(big);
+  o.m1 = ar.alloc<T>(big);
+  o.m2 = ar.alloc<T>(big);
+}
+
+template <typename T>
+void init_hp(stokes_ctx* c, HyperPower<T>& h, const Ops<T>& o) {
+  Arena& ar = c->arena;
+  h.op = &o;
+  h.schur = c->opts.schur;
+  const int L = c->opts.max_steps;
+  h.vr.assign(L + 1, nullptr);
+  h.vacc.assign(L + 1, nullptr);
+  h.vt.assign(L + 1, nullptr);
+  h.vu.assign(L + 1, nullptr);
+  h.qr.assign(L + 1, nullptr);
+  h.qacc.assign(L + 1, nullptr);
+  h.qt.assign(L + 1, nullptr);
+  h.qu.assign(L + 1, nullptr);
+  for (int l = 1; l <= L; ++l) {
+    h.vr[l] = ar.alloc<T>(c->nvel);
+    h.vacc[l] = ar.alloc<T>(c->nvel);
+    h.vt[l] = ar.alloc<T>(c->nvel);
+    h.vu[l] = ar.alloc<T>(c->nvel);
+    h.qr[l] = ar.alloc<T>(c->npres);
+    h.qacc[l] = ar.alloc<T>(c->npres);
+    h.qt[l] = ar.alloc<T>(c->npres);
+    h.qu[l] = ar.alloc<T>(c->npres);
+  }
+  if (L > 0) {
+    h.bv = ar.alloc<T>(c->nvel);
+    h.hv = ar.alloc<T>(c->nvel);
+  }
+}
+
+bool reduced(const stokes_ctx* c) { return c->opts.precision != STOKES_PREC_FP64; }
+
+// y = P_s^-1 x in the context's preconditioner precision (x, y: FP64 device vectors)
+void apply_prec(stokes_ctx* c, int order, int steps, const double* x, double* y) {
+  if (!reduced(c)) {
+    c->hd.order = order;
+    c->hd.apply(steps, x, y);
+  } else {
+    to_float(x, c->xf, c->ntot, c->stream);
+    c->hf.order = order;
+    c->hf.apply(steps, c->xf, c->yf);
+    to_double(c->yf, y, c->ntot, c->stream);
+  }
+}
+
+double read_scalar(stokes_ctx* c, const double* d) {
+  ck(cudaMemcpyAsync(c->pinned, d, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read");
+  ck(cudaStreamSynchronize(c->stream), "sync");
+  return c->pinned[0];
+}
+
+// zero-mean pressure (the constant pressure spans the null space of K, Sec. 3.2)
+void normalize_pressure(stokes_ctx* c, double* x) {
+  double* q = x + c->nvel;
+  dot<double>(q, c->ones, c->npres, c->partials, c->dsc + 0, c->stream);
+  axpy_dev(c->dsc + 0, -1.0, c->zconst, q, c->npres, c->stream);
+}
+
+// true relative residual ||f - K x|| / ||f||
+double true_residual(stokes_ctx* c, const double* f, const double* x, double* tmp) {
+  c->od.apply_K(x, tmp);
+  axpby<double>(1.0, f, -1.0, tmp, c->ntot, c->stream);
+  dot<double>(tmp, tmp, c->ntot, c->partials, c->dsc + 1, c->stream);
+  dot<double>(f, f, c->ntot, c->partials, c->dsc + 2, c->stream);
+  ck(cudaMemcpyAsync(c->pinned, c->dsc + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                     c->stream), "read");
+  ck(cudaStreamSynchronize(c->stream), "sync");
+  const double rr = c->pinned[0], ff = c->pinned[1];
+  return ff > 0 ? std::sqrt(rr / ff) : std::sqrt(rr);
+}
+
+int run_minres(stokes_ctx* c, const double* f, double tol, double* x, int* iters) {
+  const int64_t n = c->ntot;
+  cudaStream_t s = c->stream;
+  double* vold = c->kv[0];
+  double* v = c->kv[1];
+  double* z = c->kv[2];
+  double* zn = c->kv[3];
+  double* Kz = c->kv[4];
+  double* wold = c->kv[5];
+  double* w = c->kv[6];
+  fill_zero(x, n * sizeof(double), s);
+  fill_zero(vold, n * sizeof(double), s);
+  fill_zero(wold, n * sizeof(double), s);
+  fill_zero(w, n * sizeof(double), s);
+  copy_async(v, f, n * sizeof(double), s);
+  apply_prec(c, c->order, c->steps, v, z);
+  dot<double>(z, v, n, c->partials, &c->st->gg, s);
+  minres_init(c->st, s);
+  check_launch("minres init");
+  c->ratios.clear();
+  ck(cudaMemcpyAsync(c->st_host, c->st, sizeof(MinresState), cudaMemcpyDeviceToHost, s), "state");
+  ck(cudaStreamSynchronize(s), "sync");
+  if (c->st_host->status != 0) {
+    *iters = 0;
+    return c->st_host->status;
+  }
+  if (c->st_host->done) {
+    *iters = 0;
+    return STOKES_OK;
+  }
+  for (int it = 0; it < c->opts.maxit; ++it) {
+    minres_scale_z(z, c->st, n, s);
+    c->od.apply_K(z, Kz);
+    dot<double>(Kz, z, n, c->partials, &c->st->delta, s);
+    minres_lanczos(Kz, v, vold, c->st, n, s);
+    apply_prec(c, c->order, c->steps, vold, zn);
+    dot<double>(zn, vold, n, c->partials, &c->st->gg, s);
+    minres_scalars(c->st, tol, s);
+    minres_update(z, wold, w, x, c->st, n, s);
+    check_launch("minres iteration");
+    std::swap(vold, v);
+    std::swap(z, zn);
+    std::swap(wold, w);
+    ck(cudaMemcpyAsync(c->st_host, c->st, sizeof(MinresState), cudaMemcpyDeviceToHost, s),
+       "state");
+    ck(cudaStreamSynchronize(s), "sync");
+    const MinresState& h = *c->st_host;
+    if (h.pad) c->ratios.push_back(h.ratio);
+    if (h.status != 0) {
+      *iters = h.iter;
+      return h.status;
+    }
+    if (h.done) {
+      *iters = h.iter;
+      return STOKES_OK;
+    }
+  }
+  *iters = c->st_host->iter;
+  return STOKES_ERR_MAXIT;
+}
+
+// Right-preconditioned flexible GMRES (Saad 1993) with classical Gram-Schmidt applied twice
+// (one fused multi-dot and one fused multi-axpy per sweep) and Givens rotations on the host.
+int run_fgmres(stokes_ctx* c, const double* f, double tol, double* x, int* iters) {
+  const int64_t n = c->ntot;
+  cudaStream_t s = c->stream;
+  const int m = c->opts.restart;
+  double* w = c->kv[0];
+  double* r = c->kv[1];
+  double* hdev = c->dsc + 8;           // m + 1 Hessenberg column entries
+  double* h2dev = c->dsc + 8 + (m + 2);
+  fill_zero(x, n * sizeof(double), s);
+  c->ratios.clear();
+  dot<double>(f, f, n, c->partials, c->dsc + 3, s);
+  const double fnorm = std::sqrt(read_scalar(c, c->dsc + 3));
+  if (!std::isfinite(fnorm)) return STOKES_ERR_NONFINITE;
+  if (fnorm == 0.0) {
+    *iters = 0;
+    return STOKES_OK;
+  }
+  int it = 0;
+  copy_async(r, f, n * sizeof(double), s);
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  std::vector<double> col(m + 2);
+  while (it < c->opts.maxit) {
+    dot<double>(r, r, n, c->partials, c->dsc + 4, s);
+    const double beta = std::sqrt(read_scalar(c, c->dsc + 4));
+    if (!std::isfinite(beta)) return STOKES_ERR_NONFINITE;
+    if (beta == 0.0) {
+      *iters = it;
+      return STOKES_OK;
+    }
+    c->pinned[0] = beta;
+    ck(cudaMemcpyAsync(c->dsc + 5, c->pinned, sizeof(double), cudaMemcpyHostToDevice, s), "beta");
+    scale_inv_dev(c->dsc + 5, r, c->V, n, s);
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k_used = 0;
+    bool done = false;
+    for (int j = 0; j < m; ++j) {
+      double* Vj = c->V + (int64_t)j * n;
+      double* Zj = c->Z + (int64_t)j * n;
+      apply_prec(c, c->order, c->steps, Vj, Zj);
+      c->od.apply_K(Zj, w);
+      // CGS2: h = V^T w; w -= V h; h2 = V^T w; w -= V h2; h += h2
+      multi_dot(c->V, n, j + 1, w, n, c->partials, hdev, s);
+      multi_axpy(c->V, n, j + 1, hdev, -1.0, w, n, s);
+      multi_dot(c->V, n, j + 1, w, n, c->partials, h2dev, s);
+      multi_axpy(c->V, n, j + 1, h2dev, -1.0, w, n, s);
+      dot<double>(w, w, n, c->partials, c->dsc + 6, s);
+      check_launch("fgmres arnoldi");
+      ck(cudaMemcpyAsync(col.data(), hdev, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, s),
+         "read h");
+      std::vector<double> col2(j + 1);
+      ck(cudaMemcpyAsync(col2.data(), h2dev, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, s),
+         "read h2");
+      ck(cudaMemcpyAsync(c->pinned, c->dsc + 6, sizeof(double), cudaMemcpyDeviceToHost, s),
+         "read norm");
+      ck(cudaStreamSynchronize(s), "sync");
+      const double hn = std::sqrt(c->pinned[0]);
+      if (!std::isfinite(hn)) return STOKES_ERR_NONFINITE;
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = col[i] + col2[i];
+      H[(size_t)(j + 1) * m + j] = hn;
+      if (hn > 0.0) {   // V_{j+1} = w / h_{j+1,j}
+        c->pinned[1] = hn;
+        ck(cudaMemcpyAsync(c->dsc + 7, c->pinned + 1, sizeof(double), cudaMemcpyHostToDevice, s),
+           "hn");
+        scale_inv_dev(c->dsc + 7, w, c->V + (int64_t)(j + 1) * n, n, s);
+      }
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[(size_t)i * m + j] + sn[i] * H[(size_t)(i + 1) * m + j];
+        H[(size_t)(i + 1) * m + j] = -sn[i] * H[(size_t)i * m + j] + cs[i] * H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = t;
+      }
+      const double hjj = H[(size_t)j * m + j], hj1 = H[(size_t)(j + 1) * m + j];
+      const double den = std::hypot(hjj, hj1);
+      if (den == 0.0) return STOKES_ERR_BREAKDOWN;
+      cs[j] = hjj / den;
+      sn[j] = hj1 / den;
+      H[(size_t)j * m + j] = den;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++it;
+      k_used = j + 1;
+      const double ratio = std::fabs(g[j + 1]) / fnorm;
+      c->ratios.push_back(ratio);
+      if (ratio <= tol || it >= c->opts.maxit || hn == 0.0) {
+        done = true;
+        break;
+      }
+    }
+    // y = H^-1 g (upper triangular), x += Z y
+    for (int i = k_used - 1; i >= 0; --i) {
+      double sacc = g[i];
+      for (int k = i + 1; k < k_used; ++k) sacc -= H[(size_t)i * m + k] * y[k];
+      y[i] = sacc / H[(size_t)i * m + i];
+    }
+    ck(cudaMemcpyAsync(hdev, y.data(), k_used * sizeof(double), cudaMemcpyHostToDevice, s), "y");
+    multi_axpy(c->Z, n, k_used, hdev, 1.0, x, n, s);
+    check_launch("fgmres update");
+    ck(cudaStreamSynchronize(s), "sync");
+    if (done) {
+      *iters = it;
+      return c->ratios.back() <= tol ? STOKES_OK : STOKES_ERR_MAXIT;
+    }
+    // restart: r = f - K x
+    c->od.apply_K(x, r);
+    axpby<double>(1.0, f, -1.0, r, n, s);
+  }
+  *iters = it;
+  return STOKES_ERR_MAXIT;
+}
+
+int solve_impl(stokes_ctx* c, const double* rhs, double tol, double* x, int* iterations,
+               double* final_rel_res) {
+  int its = 0;
+  int rc;
+  if (c->opts.solver == STOKES_SOLVER_FGMRES) rc = run_fgmres(c, rhs, tol, x, &its);
+  else rc = run_minres(c, rhs, tol, x, &its);
+  normalize_pressure(c, x);
+  const double rr = true_residual(c, rhs, x, c->kv[7]);
+  if (iterations) *iterations = its;
+  if (final_rel_res) *final_rel_res = rr;
+  if (rc == STOKES_ERR_MAXIT) c->err = "iteration cap reached";
+  else if (rc == STOKES_ERR_NONFINITE) c->err = "non-finite value in the Krylov recurrence";
+  else if (rc == STOKES_ERR_NOT_SPD) c->err = "preconditioner is not positive definite";
+  else if (rc == STOKES_ERR_BREAKDOWN) c->err = "Krylov breakdown";
+  return rc;
+}
+
+}  // namespace
+
+// ============================================================================================
+// C ABI
+// ============================================================================================
+extern "C" {
+
+void stokes_default_opts(stokes_opts* o) {
+  if (!o) return;
+  o->c_pen = 14.0;
+  o->schur = STOKES_SCHUR_INNER;
+  o->precision = STOKES_PREC_FP64;
+  o->solver = STOKES_SOLVER_MINRES;
+  o->max_order = 3;
+  o->max_steps = 4;
+  o->maxit = 2000;
+  o->restart = 60;
+  o->stream = nullptr;
+}
+
+int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stokes_opts* opts) {
+  g_setup_error.clear();
+  if (!out) return fail(nullptr, STOKES_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_elems < 1 || n_elems > 4096) return fail(nullptr, STOKES_ERR_ARG, "n_elems out of range");
+  if (degree_p < 1 || degree_p > 12) return fail(nullptr, STOKES_ERR_ARG, "degree out of range");
+  if (!(nu > 0.0) || !std::isfinite(nu)) return fail(nullptr, STOKES_ERR_ARG, "nu must be > 0");
+  stokes_opts o;
+  stokes_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.c_pen > 0.0)) o.c_pen = 14.0;
+  if (o.max_order < 2 || o.max_steps < 0 || o.max_steps > 8 || o.maxit < 1 || o.restart < 1 ||
+      o.restart > 400 || (o.schur != STOKES_SCHUR_INNER && o.schur != STOKES_SCHUR_NONE) ||
+      o.precision < STOKES_PREC_FP64 || o.precision > STOKES_PREC_BF16 ||
+      (o.solver != STOKES_SOLVER_MINRES && o.solver != STOKES_SOLVER_FGMRES))
+    return fail(nullptr, STOKES_ERR_ARG, "invalid options");
+  if (o.solver == STOKES_SOLVER_MINRES && o.precision != STOKES_PREC_FP64)
+    return fail(nullptr, STOKES_ERR_ARG,
+                "MINRES needs a fixed SPD preconditioner: use FP64 or the FGMRES solver");
+  stokes_ctx* c = new (std::nothrow) stokes_ctx();
+  if (!c) return fail(nullptr, STOKES_ERR_SETUP, "out of host memory");
+  try {
+    c->n = n_elems;
+    c->p = degree_p;
+    c->nu = nu;
+    c->c_pen = o.c_pen;
+    c->opts = o;
+    c->a = n_elems + degree_p - 1;
+    c->b = n_elems + degree_p;
+    c->nvc = (int64_t)c->a * c->b * c->b;
+    c->nvel = 3 * c->nvc;
+    c->npres = (int64_t)c->b * c->b * c->b;
+    c->ntot = c->nvel + c->npres;
+    if (o.stream) {
+      c->stream = (cudaStream_t)o.stream;
+    } else {
+      ck(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream");
+      c->own_stream = true;
+    }
+    c->uv = build_univariate(n_elems, degree_p, o.c_pen);
+    const Univariate& u = c->uv;
+    std::vector<double> lN, lT;
+    Dense UN, UT;
+    if (!generalized_eigh(u.K, u.M, lN, UN))
+      throw SetupError{"mass matrix of the N basis is not positive definite"};
+    if (!generalized_eigh(u.Tc, u.Mc, lT, UT))
+      throw SetupError{"pressure mass matrix is not positive definite"};
+    for (double l : lT)
+      if (!(l > 0.0)) throw SetupError{"T-check is not positive definite (raise C_pen)"};
+    for (double l : lN)
+      if (!(l > 0.0)) throw SetupError{"K is not positive definite"};
+    const Band bM = to_band(u.M, 1e-15), bK = to_band(u.K, 1e-15);
+    const Band bMc = to_band(u.Mc, 1e-15), bTc = to_band(u.Tc, 1e-15);
+    init_ops<double>(c, c->od, bM, bK, bMc, bTc, UN.v, lN, UT.v, lT);
+    init_hp<double>(c, c->hd, c->od);
+    if (reduced(c)) {
+      init_ops<float>(c, c->of, bM, bK, bMc, bTc, UN.v, lN, UT.v, lT);
+      init_hp<float>(c, c->hf, c->of);
+      c->xf = c->arena.alloc<float>(c->ntot);
+      c->yf = c->arena.alloc<float>(c->ntot);
+    }
+    // constant-pressure coefficients z = c (x) c (x) c
+    std::vector<double> z((size_t)c->npres), one((size_t)c->npres, 1.0);
+    const int b = c->b;
+    for (int k = 0; k < b; ++k)
+      for (int j = 0; j < b; ++j)
+        for (int i = 0; i < b; ++i)
+          z[(size_t)i + (size_t)b * (j + (size_t)b * k)] = u.const_M[i] * u.const_M[j] * u.const_M[k];
+    c->zconst = upload<double>(c->arena, z, c->stream);
+    c->ones = upload<double>(c->arena, one, c->stream);
+    c->partials = c->arena.alloc<double>((size_t)kDotBlocks * (o.restart + 2));
+    c->dsc = c->arena.alloc<double>(16 + 2 * (o.restart + 2));
+    c->st = c->arena.alloc<MinresState>(1);
+    ck(cudaMallocHost(&c->st_host, sizeof(MinresState)), "pinned");
+    ck(cudaMallocHost(&c->pinned, 64 * sizeof(double)), "pinned");
+    for (int i = 0; i < 8; ++i) c->kv[i] = c->arena.alloc<double>(c->ntot);
+    if (o.solver == STOKES_SOLVER_FGMRES) {
+      c->V = c->arena.alloc<double>((size_t)(o.restart + 1) * c->ntot);
+      c->Z = c->arena.alloc<double>((size_t)o.restart * c->ntot);
+    }
+    c->io_rhs = c->arena.alloc<double>(c->ntot);
+    c->io_x = c->arena.alloc<double>(c->ntot);
+    ck(cudaStreamSynchronize(c->stream), "setup");
+  } catch (const CudaError& e) {
+    std::string m = std::string(e.what) + ": " + cudaGetErrorString(e.e);
+    stokes_destroy(c);
+    return fail(nullptr, STOKES_ERR_CUDA, m);
+  } catch (const SetupError& e) {
+    std::string m = e.msg;
+    stokes_destroy(c);
+    return fail(nullptr, STOKES_ERR_SETUP, m);
+  } catch (const std::bad_alloc&) {
+    stokes_destroy(c);
+    return fail(nullptr, STOKES_ERR_SETUP, "out of host memory");
+  }
+  *out = c;
+  return STOKES_OK;
+}
+
+int stokes_sizes(stokes_t c, int64_t* n_vel, int64_t* n_pres) {
+  if (!c) return STOKES_ERR_ARG;
+  if (n_vel) *n_vel = c->nvel;
+  if (n_pres) *n_pres = c->npres;
+  return STOKES_OK;
+}
+
+int stokes_set_preconditioner(stokes_t c, int order, int steps) {
+  if (!c) return STOKES_ERR_ARG;
+  if (order < 2 || order > c->opts.max_order || steps < 0 || steps > c->opts.max_steps)
+    return fail(c, STOKES_ERR_ARG, "order/steps outside [2, max_order] x [0, max_steps]");
+  c->order = order;
+  c->steps = steps;
+  return STOKES_OK;
+}
+
+int stokes_apply_A(stokes_t c, const double* x, double* y) {
+  if (!c || !x || !y) return c ? fail(c, STOKES_ERR_ARG, "null vector") : STOKES_ERR_ARG;
+  try {
+    c->od.apply_A(x, y);
+    check_launch("apply_A");
+  } catch (const CudaError& e) {
+    return cuda_fail(c, e);
+  }
+  return STOKES_OK;
+}
+
+int stokes_apply_K(stokes_t c, const double* x, double* y) {
+  if (!c || !x || !y) return c ? fail(c, STOKES_ERR_ARG, "null vector") : STOKES_ERR_ARG;
+  try {
+    c->od.apply_K(x, y);
+    check_launch("apply_K");
+  } catch (const CudaError& e) {
+    return cuda_fail(c, e);
+  }
+  return STOKES_OK;
+}
+
+int stokes_apply_hyperpower(stokes_t c, int order, int steps, const double* x, double* y) {
+  if (!c || !x || !y) return c ? fail(c, STOKES_ERR_ARG, "null vector") : STOKES_ERR_ARG;
+  if (order < 2 || order > c->opts.max_order || steps < 0 || steps > c->opts.max_steps)
+    return fail(c, STOKES_ERR_ARG, "order/steps outside [2, max_order] x [0, max_steps]");
+  try {
+    apply_prec(c, order, steps, x, y);
+    check_launch("apply_hyperpower");
+  } catch (const CudaError& e) {
+    return cuda_fail(c, e);
+  }
+  return STOKES_OK;
+}
+
+int stokes_apply_P(stokes_t c, const double* x, double* y) {
+  return stokes_apply_hyperpower(c, 2, 0, x, y);
+}
+
+int stokes_rhs_cavity(stokes_t c, double lid_speed, double* f) {
+  if (!c || !f) return c ? fail(c, STOKES_ERR_ARG, "null vector") : STOKES_ERR_ARG;
+  if (!std::isfinite(lid_speed)) return fail(c, STOKES_ERR_ARG, "lid speed must be finite");
+  // Nitsche load of g = (U, 0, 0) on x2 = 1 (derived from sigma of Sec. 3.1 with boundary data):
+  // f1[i1, i2, i3] = nu U (2 alpha M_i2(1) - M'_i2(1)) int N_i1 int M_i3, int M = 1.
+  const Univariate& u = c->uv;
+  const double alpha = c->c_pen / u.h;
+  std::vector<double> f1((size_t)c->nvc);
+  for (int i3 = 0; i3 < c->b; ++i3)
+    for (int i2 = 0; i2 < c->b; ++i2) {
+      const double g2 = c->nu * lid_speed * (2.0 * alpha * u.M_at_1[i2] - u.dM_at_1[i2]);
+      for (int i1 = 0; i1 < c->a; ++i1)
+        f1[(size_t)i1 + (size_t)c->a * (i2 + (size_t)c->b * i3)] = g2 * u.int_N[i1];
+    }
+  try {
+    fill_zero(f, c->ntot * sizeof(double), c->stream);
+    ck(cudaMemcpyAsync(f, f1.data(), f1.size() * sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream), "rhs upload");
+    ck(cudaStreamSynchronize(c->stream), "rhs");
+  } catch (const CudaError& e) {
+    return cuda_fail(c, e);
+  }
+  return STOKES_OK;
+}
+
+int stokes_rhs_body(stokes_t c, int n_modes, const double* coef, const int* waves, int accumulate,
+                    double* f) {
+  if (!c || !f || n_modes < 0 || (n_modes > 0 && (!coef || !waves)))
+    return c ? fail(c, STOKES_ERR_ARG, "invalid body-force arguments") : STOKES_ERR_ARG;
+  for (int i = 0; i < 9 * n_modes; ++i)
+    if (waves[i] < 1 || waves[i] > 64) return fail(c, STOKES_ERR_ARG, "wave numbers in [1, 64]");
+  const Univariate& u = c->uv;
+  std::vector<double> host((size_t)c->nvel, 0.0);
+  for (int comp = 0; comp < 3; ++comp) {
+    const int e1 = comp == 0 ? c->a : c->b, e2 = comp == 1 ? c->a : c->b;
+    const int e3 = comp == 2 ? c->a : c->b;
+    double* dst = host.data() + (size_t)comp * c->nvc;
+    for (int m = 0; m < n_modes; ++m) {
+      const double cf = coef[comp * n_modes + m];
+      const int* k = waves + (size_t)(comp * n_modes + m) * 3;
+      std::vector<double> l1 = comp == 0 ? sine_load_N(u, k[0]) : sine_load_M(u, k[0]);
+      std::vector<double> l2 = comp == 1 ? sine_load_N(u, k[1]) : sine_load_M(u, k[1]);
+      std::vector<double> l3 = comp == 2 ? sine_load_N(u, k[2]) : sine_load_M(u, k[2]);
+      for (int i3 = 0; i3 < e3; ++i3)
+        for (int i2 = 0; i2 < e2; ++i2) {
+          const double s23 = cf * l2[i2] * l3[i3];
+          double* row = dst + (size_t)e1 * (i2 + (size_t)e2 * i3);
+          for (int i1 = 0; i1 < e1; ++i1) row[i1] += s23 * l1[i1];
+        }
+    }
+  }
+  try {
+    double* tmp = c->kv[7];
+    ck(cudaMemcpyAsync(tmp, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream), "rhs upload");
+    if (accumulate) {
+      axpby<double>(1.0, tmp, 1.0, f, c->nvel, c->stream);
+    } else {
+      fill_zero(f, c->ntot * sizeof(double), c->stream);
+      copy_async(f, tmp, c->nvel * sizeof(double), c->stream);
+    }
+    check_launch("rhs_body");
+    ck(cudaStreamSynchronize(c->stream), "rhs");
+  } catch (const CudaError& e) {
+    return cuda_fail(c, e);
+  }
+  return STOKES_OK;
+}
+
+int stokes_solve(stokes_t c, const double* rhs, double tol, double* x, int* iterations,
+                 double* final_rel_res) {
+  if (!c || !rhs || !x) return c ? fail(c, STOKES_ERR_ARG, "null vector") : STOKES_ERR_ARG;
+  if (!(tol > 0.0) || !(tol < 1.0)) return fail(c, STOKES_ERR_ARG, "tol must be in (0, 1)");
+  if (rhs == x) return fail(c, STOKES_ERR_ARG, "rhs and x must not alias");
+  try {
+    return solve_impl(c, rhs, tol, x, iterations, final_rel_res);
+  } catch (const CudaError& e) {
+    return cuda_fail(c, e);
+  }
+}
+
+int stokes_solve_host(stokes_t c, const double* rhs_host, double tol, double* x_host,
+                      int* iterations, double* final_rel_res) {
+  if (!c || !rhs_host || !x_host)
+    return c ? fail(c, STOKES_ERR_ARG, "null vector") : STOKES_ERR_ARG;
+  if (!(tol > 0.0) || !(tol < 1.0)) return fail(c, STOKES_ERR_ARG, "tol must be in (0, 1)");
+  try {
+    const size_t bytes = c->ntot * sizeof(double);
+    ck(cudaMemcpyAsync(c->io_rhs, rhs_host, bytes, cudaMemcpyHostToDevice, c->stream), "h2d");
+    const int rc = solve_impl(c, c->io_rhs, tol, c->io_x, iterations, final_rel_res);
+    ck(cudaMemcpyAsync(x_host, c->io_x, bytes, cudaMemcpyDeviceToHost, c->stream), "d2h");
+    ck(cudaStreamSynchronize(c->stream), "d2h");
+    return rc;
+  } catch (const CudaError& e) {
+    return cuda_fail(c, e);
+  }
+}
+
+int stokes_last_ratios(stokes_t c, double* ratios, int capacity) {
+  if (!c || (!ratios && capacity > 0) || capacity < 0) return STOKES_ERR_ARG;
+  const int k = std::min<int>(capacity, (int)c->ratios.size());
+  for (int i = 0; i < k; ++i) ratios[i] = c->ratios[i];
+  return k;
+}
+
+int stokes_profile_begin(stokes_t c) {
+  if (!c) return STOKES_ERR_ARG;
+  if (!c->prof) c->prof = profiler_create();
+  profiler_activate(c->prof);
+  return STOKES_OK;
+}
+
+int stokes_profile_end(stokes_t c, stokes_kernel_stat* out, int capacity) {
+  if (!c || !c->prof || (!out && capacity > 0) || capacity < 0) return STOKES_ERR_ARG;
+  int64_t l[kNumClasses];
+  double ms[kNumClasses], fl[kNumClasses], by[kNumClasses];
+  profiler_collect(c->prof, l, ms, fl, by);
+  profiler_activate(nullptr);
+  const int k = std::min(capacity, (int)kNumClasses);
+  for (int i = 0; i < k; ++i) {
+    out[i].kernel_class = i;
+    out[i].launches = l[i];
+    out[i].ms = ms[i];
+    out[i].flops = fl[i];
+    out[i].bytes = by[i];
+  }
+  return k;
+}
+
+int64_t stokes_kernel_launches(void) { return launch_count(); }
+
+void stokes_destroy(stokes_t c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->prof) profiler_destroy(c->prof);
+  if (c->st_host) cudaFreeHost(c->st_host);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  cudaStream_t s = c->own_stream ? c->stream : nullptr;
+  delete c;   // frees the arena
+  if (s) cudaStreamDestroy(s);
+}
+
+const char* stokes_last_error(stokes_t c) {
+  return c ? c->err.c_str() : g_setup_error.c_str();
+}
+
+}  // extern "C"

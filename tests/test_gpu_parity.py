@@ -1,0 +1,165 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Sizes span one to several 64-wide tiles of the dense mode products with ragged tails
+(b = 2 ... 65) and the cfg1 workload (8^3, p = 2)."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import dev, host, oracle, relerr
+from oracle.krylov import minres
+from oracle.precond import HyperPowerPreconditioner, hyperpower_Q, hyperpower_V
+from paper_2311_06926_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+
+CASES = [(1, 1, 1.0), (2, 1, 0.7), (3, 2, 1.0), (4, 3, 2.5), (8, 2, 1.0), (5, 4, 0.4),
+         (13, 3, 1.0), (62, 3, 1.0)]
+
+
+def _ctx(n, p, nu, **kw):
+    from paper_2311_06926_gb300 import Stokes
+    return Stokes(n, p, nu=nu, **kw)
+
+
+@pytest.mark.parametrize("n,p,nu", CASES)
+def test_operator_applies(n, p, nu):
+    S, base, Kop, F = oracle(n, p, nu)
+    G = _ctx(n, p, nu)
+    x = synthetic.random_vector(S.size, 100 + n)
+    assert relerr(host(G.apply_K(dev(x))), Kop(x)) < 1e-13
+    xu = x[:S.n_vel]
+    assert relerr(host(G.apply_A(dev(xu))), F.apply_A(xu)) < 1e-13
+    G.close()
+
+
+@pytest.mark.parametrize("n,p,nu", CASES)
+def test_base_preconditioner(n, p, nu):
+    S, base, Kop, F = oracle(n, p, nu)
+    G = _ctx(n, p, nu)
+    x = synthetic.random_vector(S.size, 200 + n)
+    ref = np.concatenate([base.pv0_inv(x[:S.n_vel]), base.pq0_inv(x[S.n_vel:])])
+    assert relerr(host(G.apply_P(dev(x))), ref) < 1e-12
+    G.close()
+
+
+@pytest.mark.parametrize("n,p", [(2, 1), (4, 2), (6, 3)])
+@pytest.mark.parametrize("q,s", [(2, 1), (2, 2), (3, 1), (2, 3), (3, 2)])
+@pytest.mark.parametrize("schur", ["inner", "none"])
+def test_hyperpower(n, p, q, s, schur):
+    S, base, Kop, F = oracle(n, p)
+    G = _ctx(n, p, 1.0, schur=schur)
+    x = synthetic.random_vector(S.size, 300 + 10 * q + s)
+    ref = np.concatenate([hyperpower_V(base, x[:S.n_vel], q, s),
+                          hyperpower_Q(base, x[S.n_vel:], q, s, schur)])
+    assert relerr(host(G.apply_hyperpower(q, s, dev(x))), ref) < 1e-11
+    G.close()
+
+
+@pytest.mark.parametrize("n,p,nu", [(1, 1, 1.0), (3, 2, 0.5), (8, 2, 1.0), (9, 3, 2.0)])
+def test_loads(n, p, nu):
+    S, base, Kop, F = oracle(n, p, nu, matrix_free=False)
+    G = _ctx(n, p, nu)
+    assert relerr(host(G.rhs_cavity(1.7)), S.rhs_lid(1.7)) < 1e-13
+    modes = synthetic.forcing_modes(5)
+    assert relerr(host(G.rhs_body(*modes)), S.rhs_body(modes)) < 1e-12
+    f = G.rhs_cavity(0.8)
+    G.rhs_body(*modes, accumulate=True, out=f)
+    assert relerr(host(f), S.rhs_lid(0.8) + S.rhs_body(modes)) < 1e-12
+    G.close()
+
+
+def _compare_solve(n, p, q, s, rhs_kind="cavity", tol=1e-8):
+    S, base, Kop, F = oracle(n, p)
+    f = S.rhs_lid(1.0) if rhs_kind == "cavity" else S.rhs_lid(1.3) + S.rhs_body(
+        synthetic.forcing_modes(7))
+    ref = minres(Kop, HyperPowerPreconditioner(base, q, s), f, tol)
+    xo = S.normalize_pressure(ref.x)
+    G = _ctx(n, p, 1.0)
+    G.set_preconditioner(q, s)
+    x, it, rr, rc = G.solve(dev(f), tol)
+    xg = host(x)
+    ratios = G.last_ratios()
+    G.close()
+    near = abs(ref.ratios[-1] - tol) < 1e-6 * tol or (
+        len(ref.ratios) > 1 and abs(ref.ratios[-2] - tol) < 1e-6 * tol)
+    if not near:
+        assert it == ref.iterations, (it, ref.iterations)
+    assert np.allclose(ratios[:len(ref.ratios)], ref.ratios[:len(ratios)], rtol=1e-6, atol=1e-14)
+    assert np.linalg.norm(xg - xo) <= 1e-10 * np.linalg.norm(xo)
+    assert rr < 1e-6
+    return it
+
+
+@pytest.mark.parametrize("q,s", [(2, 0), (2, 1), (3, 1), (2, 2)])
+def test_solve_cfg1_cavity(q, s):
+    """8^3, p = 2, nu = 1 cavity; MINRES to 1e-8: identical iterations, solution to 1e-10."""
+    _compare_solve(8, 2, q, s)
+
+
+@pytest.mark.parametrize("n,p", [(1, 1), (2, 3), (5, 2)])
+def test_solve_small_and_forced(n, p):
+    _compare_solve(n, p, 2, 1, rhs_kind="forced")
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("q", [2, 3])
+@pytest.mark.parametrize("s", [0, 1, 2, 3])
+def test_solve_cfg2_sweep(q, s):
+    """32^3, p = 3 cavity (cfg2): the full order x steps sweep against the matrix-free oracle."""
+    _compare_solve(32, 3, q, s)
+
+
+def test_error_paths():
+    from paper_2311_06926_gb300 import Stokes, StokesError
+    G = Stokes(3, 2)
+    f = G.rhs_cavity(1.0)
+    bad = f.clone()
+    bad[5] = float("nan")
+    x, it, rr, rc = G.solve(bad, 1e-8, raise_on_error=False)
+    assert rc == -3
+    G2 = Stokes(3, 2, maxit=3)
+    x, it, rr, rc = G2.solve(f, 1e-12, raise_on_error=False)
+    assert rc == -5 and it == 3 and np.isfinite(host(x)).all()
+    z = torch.zeros_like(f)
+    x, it, rr, rc = G.solve(z, 1e-8)
+    assert it == 0 and float(host(x).__abs__().max()) == 0.0
+    with pytest.raises(StokesError):
+        G.set_preconditioner(1, 0)
+    with pytest.raises(StokesError):
+        Stokes(3, 2, c_pen=0.05)         # T-check not positive definite
+    G.close()
+    G2.close()
+
+
+def _direct(S, f):
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    e = np.concatenate([np.zeros(S.n_vel), np.ones(S.n_pres)])
+    Kb = sp.bmat([[S.K, sp.csr_matrix(e[:, None])], [sp.csr_matrix(e[None, :]), None]]).tocsc()
+    return S.normalize_pressure(spla.spsolve(Kb, np.concatenate([f, [0.0]]))[:-1])
+
+
+def _condition_number(S):
+    """kappa(K) on the complement of the constant-pressure null space."""
+    w = np.abs(np.linalg.eigvalsh(S.K.toarray()))
+    w = np.sort(w)[1:]
+    return w[-1] / w[0]
+
+
+@pytest.mark.parametrize("prec", ["fp32"])
+def test_mixed_precision_fgmres_accuracy(prec):
+    """FP32 preconditioner + FP64 flexible GMRES: the true relative residual reaches 1e-8 and
+    the error against the exact (direct) solution obeys ||e|| / ||x|| <= kappa(K) ||r|| / ||f||."""
+    n, p = 6, 2
+    S, base, Kop, F = oracle(n, p)
+    f = S.rhs_lid(1.0)
+    xo = _direct(S, f)
+    kappa = _condition_number(S)
+    G = _ctx(n, p, 1.0, precision=prec)
+    G.set_preconditioner(2, 1)
+    x, it, rr, rc = G.solve(dev(f), 1e-8)
+    G.close()
+    assert rr <= 1e-8 * 1.01
+    err = np.linalg.norm(host(x) - xo) / np.linalg.norm(xo)
+    assert err <= kappa * rr
