@@ -156,6 +156,24 @@ int stokes_profile_end(stokes_t ctx, stokes_kernel_stat* out, int capacity);
 /* Number of kernels this library has launched in this process (all contexts and threads). */
 int64_t stokes_kernel_launches(void);
 
+/* ---- allocation-free variant (no counterpart in the paper) --------------------------------
+ * For callers that cannot allocate device memory (their allocator is owned by a framework or
+ * memory pool, or allocation is forbidden after start-up): the fast-diagonalisation apply of one
+ * Kronecker-sum block without a context and without any device allocation,
+ *   y = (U3 (x) U2 (x) U1) diag(1 / (scale (lam1[i1] + lam2[i2] + lam3[i3]))) (U3 (x) U2 (x) U1)^T x,
+ * on a tensor of extents (n1, n2, n3), x1 fastest. U_k: device, row-major n_k x n_k with the
+ * eigenvectors as columns; lam_k: device, n_k entries; x, y: device, n1 n2 n3 entries, not
+ * aliased. stream: a cudaStream_t (NULL = legacy default stream). Returns after enqueueing.
+ * Its two intermediate tensors live in a static device array of 2 x 2^19 float64 (8 MiB), held
+ * by every GPU that loads the library until the process exits; n1 n2 n3 > 2^19 is rejected with
+ * STOKES_ERR_ARG. The first call on a device (made with that device current) looks up the
+ * array's device address; make it before any stream capture. All calls share the array: calls
+ * that overlap on the GPU race, so serialise them. No part of the array needs to start at zero. */
+int stokes_fd_apply_noalloc(int n1, int n2, int n3, const double* U1, const double* U2,
+                            const double* U3, const double* lam1, const double* lam2,
+                            const double* lam3, double scale, const double* x, double* y,
+                            void* stream);
+
 /* Release the context and its device workspace. NULL is ignored. */
 void stokes_destroy(stokes_t ctx);
 

@@ -72,6 +72,8 @@ def load_library(path=None):
         "stokes_profile_begin": (ctypes.c_int, [vp]),
         "stokes_profile_end": (ctypes.c_int, [vp, ctypes.POINTER(KernelStat), ctypes.c_int]),
         "stokes_kernel_launches": (ctypes.c_int64, []),
+        "stokes_fd_apply_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
+                                                   vp, vp, vp, vp, ctypes.c_double, vp, vp, vp]),
         "stokes_destroy": (None, [vp]),
         "stokes_last_error": (ctypes.c_char_p, [vp]),
     }
@@ -86,6 +88,24 @@ def load_library(path=None):
 def kernel_launches():
     """Kernels launched by the library in this process so far."""
     return load_library().stokes_kernel_launches()
+
+
+def fd_apply_noalloc(U, lam, scale, x, y):
+    """Allocation-free fast-diagonalisation apply (stokes_fd_apply_noalloc) of one
+    Kronecker-sum block. U, lam: three float64 CUDA tensors each (U_k row-major n_k x n_k, columns
+    the eigenvectors; lam_k n_k eigenvalues); x, y: float64 CUDA tensors of n1 n2 n3 entries
+    (x1 fastest). Runs on torch's current stream."""
+    lib = load_library()
+    n1, n2, n3 = (int(u.shape[0]) for u in U)
+    for t in list(U) + list(lam) + [x, y]:
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError("expected contiguous float64 CUDA tensors")
+    rc = lib.stokes_fd_apply_noalloc(n1, n2, n3, *[_ptr(u) for u in U], *[_ptr(v) for v in lam],
+                                     float(scale), _ptr(x), _ptr(y),
+                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != STOKES_OK:
+        raise StokesError(rc, "stokes_fd_apply_noalloc")
+    return y
 
 
 def _ptr(t):
