@@ -30,10 +30,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Stokes solves/s to 1e-8 rel. residual; HBM GB/s & TC util vs peak; mixed vs FP64"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 FMA rate of GB300: 2 DFMA per clock per SM (measured by an FMA-throughput probe at
-# 1.20 TFLOP/s) x 152 SMs x 2 flop x 2.07 GHz maximum SM clock.
-FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.07e9 / 1e12
-FP32_PEAK_TFLOPS = 128 * 152 * 2 * 2.07e9 / 1e12
+# GB300 FP64 rate: nominal 1.25 TFLOP/s (an FMA-throughput probe on this machine measured 1.20).
+FP64_PEAK_TFLOPS = 1.25
+TF32_NOMINAL_TFLOPS = 1100.0
 
 WORKLOADS = {
     "cavity32": dict(n=32, p=3, sweep=[(q, s) for q in (2, 3) for s in (0, 1, 2, 3)],
@@ -153,6 +152,53 @@ def oracle_sample(n, p, q, s, repeats):
     return time.perf_counter() - t0, its
 
 
+def mixed_vs_fp64(Stokes, peaks, n=128, p=3, q=2, s=2):
+    """128^3 cavity, order 2, 2 steps: plain FP64 MINRES vs the mixed form (TF32 / BF16
+    tensor-core fast diagonalisation and FP32 inner steps inside FP64 flexible GMRES), each to the
+    1e-8 tolerance; times by CUDA events after one untimed solve; error against the FP64 solution."""
+    import torch
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    res = {"workload": f"3D lid-driven cavity, {n}^3 elements, p={p}, nu=1, order {q}, {s} steps, "
+                       f"tol 1e-8", "forms": {}}
+    ref = None
+    for prec in ["fp64", "tf32", "bf16"]:
+        G = Stokes(n, p, precision=prec, max_order=q, max_steps=s)
+        G.set_preconditioner(q, s)
+        f = G.rhs_cavity(1.0)
+        x, it, rr, _ = G.solve(f, 1e-8)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        x, it, rr, _ = G.solve(f, 1e-8, out=x)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        G.profile_begin()
+        G.solve(f, 1e-8)
+        prof = G.profile_end()
+        if ref is None:
+            ref = x.clone()
+        err = float((x - ref).norm() / ref.norm())
+        entry = {"ms": ms, "iterations": it, "true_rel_res": rr,
+                 "solver": "minres" if prec == "fp64" else "fgmres",
+                 "rel_err_vs_fp64_solution": err,
+                 "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}
+        for name, key in [("mma_mode_product", "tensor_core_fd"), ("band_pass", "band_pass")]:
+            st = prof.get(name)
+            if st and st["launches"] and prec != "fp64":
+                gbs = st["bytes"] / (st["ms"] / 1e3) / 1e9
+                entry[f"roofline_{key}"] = {
+                    "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                    "frac": gbs / hbm, "avg_launch_us": 1e3 * st["ms"] / st["launches"],
+                    "tflops": st["flops"] / (st["ms"] / 1e3) / 1e12}
+        res["forms"][prec] = entry
+        G.close()
+        del G
+        torch.cuda.empty_cache()
+    f64 = res["forms"]["fp64"]["ms"]
+    res["speedup_vs_fp64"] = {k: f64 / v["ms"] for k, v in res["forms"].items() if k != "fp64"}
+    return res
+
+
 def run_reference(args, wl):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -188,6 +234,8 @@ def main():
     ap.add_argument("--workload", default="cavity32", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the 128^3 mixed-precision vs FP64 comparison")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.precision:
@@ -307,8 +355,7 @@ def main():
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "kernel": dom_name, "launches_per_step": dom["launches"],
                 "avg_launch_us": 1e3 * dom["ms"] / max(dom["launches"], 1),
-                "peak_note": "FP64 FMA peak derived: 2 DFMA/clk/SM (probe: 1.20 TFLOP/s) x 152 "
-                             "SMs x 2.07 GHz"}
+                "peak_note": "nominal GB300 FP64 1.25 TFLOP/s (an FMA probe measured 1.20)"}
     else:
         hbm = peaks.get("hbm_gbs", 6800.0)
         achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
@@ -318,6 +365,10 @@ def main():
                 "avg_launch_us": 1e3 * dom["ms"] / max(dom["launches"], 1),
                 "peak_note": "of measured" if "hbm_gbs" in peaks else "of fallback"}
     step_ms_profiled = sum(v["ms"] for v in prof.values())
+
+    mixed = None
+    if not args.no_mixed:
+        mixed = mixed_vs_fp64(Stokes, load_peaks() or {})
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -352,6 +403,7 @@ def main():
                     "d2h_bytes_per_step": bytes_per_solve * len(sweep)},
             "gpu_launches": int(launches),
             "clocks": clocks,
+            "mixed_vs_fp64": mixed,
         }
         print(json.dumps(line), flush=True)
     G.close()

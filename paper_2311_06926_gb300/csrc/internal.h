@@ -43,11 +43,19 @@ struct PassArgs {
 };
 template <typename T>
 void band_pass(const PassArgs<T>& a, cudaStream_t s);
+// Several independent passes (up to kMaxPassJobs, e.g. one per velocity component) in one launch.
+constexpr int kMaxPassJobs = 6;
+template <typename T>
+void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s);
 
 // delta = sum_c D .c u_c: exact discrete divergence of the velocity coefficients (App. B.2),
 // output b^3. (D beta)_i = beta_i - beta_{i-1} with beta_{-1} = beta_a = 0.
 template <typename T>
 void divergence(const T* u1, const T* u2, const T* u3, int a, int b, T* delta, cudaStream_t s);
+// as divergence, and also e = nu delta + q (the argument of the grad-div / pressure term)
+template <typename T>
+void divergence_plus(const T* u1, const T* u2, const T* u3, int a, int b, T* delta,
+                     const T* q, T nu, T* e, cudaStream_t s);
 
 // y_c (+)= D^T .c g for the three components (grad of a b^3 field onto velocity coefficients).
 template <typename T>
@@ -66,9 +74,14 @@ struct ModeArgs {
   Dims in; int axis;
   const T* lam1; const T* lam2; const T* lam3; T scale;
   T post;   // if lam1 == null: the result is multiplied by post
+  const T* invd;   // if set (FP64 path): the result is multiplied by invd[output index] instead
 };
 template <typename T>
 void mode_product(const ModeArgs<T>& a, cudaStream_t s);
+// Several independent mode products (up to kMaxModeJobs) in one launch.
+constexpr int kMaxModeJobs = 4;
+template <typename T>
+void mode_product_multi(const ModeArgs<T>* jobs, int njobs, cudaStream_t s);
 
 // ---- vector kernels (k_vec.cu) -----------------------------------------------------------
 // Deterministic dot product: fixed grid, fixed-order tree reduction. Result written to *out
@@ -102,12 +115,15 @@ struct MinresState {
   double delta, gg;          // dot products written by the dot kernel
   double a1, a2, a3, xcoef;  // update coefficients of the current iteration
   double ratio;
+  double tol;                // stopping tolerance (read by the scalar kernel)
+  double* ratios;            // per-iteration ratio history (device, `cap` entries)
+  int cap;
   int iter, status, done, pad;
 };
 void minres_scale_z(double* z, MinresState* st, int64_t n, cudaStream_t s);
 void minres_lanczos(const double* Kz, const double* v, double* vold_inout, MinresState* st,
                     int64_t n, cudaStream_t s);
-void minres_scalars(MinresState* st, double tol, cudaStream_t s);
+void minres_scalars(MinresState* st, cudaStream_t s);
 void minres_update(const double* z, double* w_old_inout, const double* w, double* x,
                    MinresState* st, int64_t n, cudaStream_t s);
 void minres_init(MinresState* st, cudaStream_t s);

@@ -19,61 +19,224 @@ inline int grid_for(int64_t total, int threads) {
   return (int)b;
 }
 
-template <typename T, int AXIS>
-__global__ void __launch_bounds__(256) k_band_pass(PassArgs<T> a) {
-  const Dims out = a.in.with(AXIS, a.D0.rows);
-  const int64_t total = out.size();
-  const int64_t step = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += step) {
-    const int i1 = (int)(o % out.n1);
-    const int64_t t = o / out.n1;
-    const int i2 = (int)(t % out.n2);
-    const int i3 = (int)(t / out.n2);
-    const int i = AXIS == 1 ? i1 : (AXIS == 2 ? i2 : i3);
-    int64_t base, stride;
-    if (AXIS == 1) {
-      base = (int64_t)a.in.n1 * (i2 + (int64_t)a.in.n2 * i3);
-      stride = 1;
-    } else if (AXIS == 2) {
-      base = i1 + (int64_t)a.in.n1 * a.in.n2 * i3;
-      stride = a.in.n1;
-    } else {
-      base = i1 + (int64_t)a.in.n1 * i2;
-      stride = (int64_t)a.in.n1 * a.in.n2;
+template <typename T>
+struct PassBatch {
+  PassArgs<T> job[kMaxPassJobs];
+  int first_block[kMaxPassJobs + 1];
+  int njobs;
+  int seg;   // outputs per thread along the band direction
+};
+
+// Each thread computes a segment of `seg` consecutive outputs along the band direction of one
+// line (a fixed position in the other two directions), so consecutive outputs reuse the band
+// window of inputs from L1 instead of re-reading it from L2. A warp covers 32 neighbouring lines
+// (consecutive x1 for passes along x2 or x3: coalesced), all at the same segment, so the band
+// rows it reads are shared (broadcast). The flat block index selects the job. FP32 passes are
+// bandwidth bound and use 32 outputs per thread; FP64 passes are bound by the FP64 pipe and use
+// one output per thread for the most parallelism.
+template <typename T>
+constexpr int seg_len() { return sizeof(T) == 4 ? 32 : 1; }
+
+template <typename T>
+__device__ __forceinline__ T band_dot(const BandD<T>& D, int i, const T* __restrict__ X,
+                                      int64_t base, int64_t stride) {
+  const int s0 = __ldg(D.start + i);
+  const T* v = D.val + (int64_t)i * D.width;
+  const T* x = X + base + (int64_t)s0 * stride;
+  T sum = 0;
+  for (int w = 0; w < D.width; ++w) sum += __ldg(v + w) * __ldg(x + (int64_t)w * stride);
+  return sum;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_band_pass(const __grid_constant__ PassBatch<T> pb) {
+  int jb = 0;
+  while (jb + 1 < pb.njobs && (int)blockIdx.x >= pb.first_block[jb + 1]) ++jb;
+  const PassArgs<T>& a = pb.job[jb];
+  const int axis = a.axis;
+  const Dims out = a.in.with(axis, a.D0.rows);
+  const int m = a.D0.rows;
+  const int seg_n = pb.seg;
+  const int nseg = (m + seg_n - 1) / seg_n;
+  const int64_t lines = out.size() / m;
+  const int64_t t = (int64_t)(blockIdx.x - pb.first_block[jb]) * blockDim.x + threadIdx.x;
+  // t = line + lines_rounded * seg with lines rounded to a warp multiple (warps share seg)
+  const int64_t lines_r = (lines + 31) / 32 * 32;
+  const int64_t line = t % lines_r;
+  const int seg = (int)(t / lines_r);
+  if (line >= lines || seg >= nseg) return;
+  // line -> (j_a, j_b): the two non-band indices, the first one fastest
+  int64_t base_in, stride_in, base_out, stride_out;
+  int k1, k2;   // indices along (x1, x2, x3) of the line position, filled per axis
+  if (axis == 1) {
+    const int i2 = (int)(line % out.n2), i3 = (int)(line / out.n2);
+    base_in = (int64_t)a.in.n1 * (i2 + (int64_t)a.in.n2 * i3);
+    stride_in = 1;
+    base_out = (int64_t)out.n1 * (i2 + (int64_t)out.n2 * i3);
+    stride_out = 1;
+    k1 = i2;
+    k2 = i3;
+  } else if (axis == 2) {
+    const int i1 = (int)(line % out.n1), i3 = (int)(line / out.n1);
+    base_in = i1 + (int64_t)a.in.n1 * a.in.n2 * i3;
+    stride_in = a.in.n1;
+    base_out = i1 + (int64_t)out.n1 * out.n2 * i3;
+    stride_out = out.n1;
+    k1 = i1;
+    k2 = i3;
+  } else {
+    const int i1 = (int)(line % out.n1), i2 = (int)(line / out.n1);
+    base_in = i1 + (int64_t)a.in.n1 * i2;
+    stride_in = (int64_t)a.in.n1 * a.in.n2;
+    base_out = i1 + (int64_t)out.n1 * i2;
+    stride_out = (int64_t)out.n1 * out.n2;
+    k1 = i1;
+    k2 = i2;
+  }
+  int64_t gbase = 0, gstride = 0, gstep = 0;
+  if (a.g) {
+    // g has extents b^3 (gdims); the output's own index along gaxis is the band index when
+    // gaxis == axis, otherwise one of (k1, k2)
+    const Dims gd = a.gdims;
+    const int64_t gs[3] = {1, (int64_t)gd.n1, (int64_t)gd.n1 * gd.n2};
+    int idx[3];
+    if (axis == 1) { idx[0] = 0; idx[1] = k1; idx[2] = k2; }
+    else if (axis == 2) { idx[0] = k1; idx[1] = 0; idx[2] = k2; }
+    else { idx[0] = k1; idx[1] = k2; idx[2] = 0; }
+    gbase = idx[0] * gs[0] + idx[1] * gs[1] + idx[2] * gs[2];
+    gstride = gs[axis - 1];     // moving along the band direction
+    gstep = gs[a.gaxis - 1];    // the difference direction
+  }
+  const int i_end = min(m, (seg + 1) * seg_n);
+  for (int i = seg * seg_n; i < i_end; ++i) {
+    T acc = a.c0 * band_dot(a.D0, i, a.X0, base_in, stride_in);
+    if (a.nterms > 1) acc += a.c1 * band_dot(a.D1, i, a.X1, base_in, stride_in);
+    const int64_t o = base_out + (int64_t)i * stride_out;
+    if (a.Z) acc += a.cz * a.Z[o];
+    if (a.g) {
+      const int64_t gi = gbase + (int64_t)i * gstride;
+      acc += a.g[gi] - a.g[gi + gstep];
     }
-    T acc = 0;
+    a.Y[o] = acc;
+  }
+}
+
+// FP32 (bandwidth-bound) variant: a block owns 32 neighbouring lines (flattened over the two
+// non-band directions in memory order) and the whole band extent. Inputs are read once from
+// global memory with coalesced loads into shared memory ([j][line]), every output of the tile is
+// formed from shared memory, and passes along x1 stage their outputs in shared memory so that
+// the stores are coalesced too.
+constexpr int kTileLines = 32;
+
+__device__ __forceinline__ void line_geometry(int axis, const Dims& d, int64_t line,
+                                              int64_t* base, int64_t* stride) {
+  if (axis == 1) {
+    *base = (int64_t)d.n1 * line;
+    *stride = 1;
+  } else if (axis == 2) {
+    const int64_t i1 = line % d.n1, i3 = line / d.n1;
+    *base = i1 + (int64_t)d.n1 * d.n2 * i3;
+    *stride = d.n1;
+  } else {
+    *base = line;
+    *stride = (int64_t)d.n1 * d.n2;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_band_tile(const __grid_constant__ PassBatch<float> pb) {
+  extern __shared__ float sh[];
+  int jb = 0;
+  while (jb + 1 < pb.njobs && (int)blockIdx.x >= pb.first_block[jb + 1]) ++jb;
+  const PassArgs<float>& a = pb.job[jb];
+  const int axis = a.axis;
+  const int nin = a.in.get(axis);
+  const int m = a.D0.rows;
+  const Dims out = a.in.with(axis, m);
+  const int64_t lines = out.size() / m;
+  const int64_t line0 = (int64_t)(blockIdx.x - pb.first_block[jb]) * kTileLines;
+  const int nl = (int)(lines - line0 < kTileLines ? lines - line0 : kTileLines);
+  constexpr int P = kTileLines + 1;   // shared pitch
+  float* xs0 = sh;
+  float* xs1 = sh + nin * P;
+  float* ys = sh + (a.nterms > 1 ? 2 : 1) * nin * P;   // m x P (passes along x1)
+  const int tid = threadIdx.x;
+  // load the input slab(s): element (line, j)
+  for (int t = 0; t < a.nterms; ++t) {
+    const float* X = t == 0 ? a.X0 : a.X1;
+    float* xs = t == 0 ? xs0 : xs1;
+    const int total = nin * kTileLines;
+    for (int idx = tid; idx < total; idx += blockDim.x) {
+      int l, j;
+      if (axis == 1) { j = idx % nin; l = idx / nin; } else { l = idx % kTileLines; j = idx / kTileLines; }
+      float v = 0.f;
+      if (l < nl) {
+        int64_t base, stride;
+        line_geometry(axis, a.in, line0 + l, &base, &stride);
+        v = X[base + stride * j];
+      }
+      xs[j * P + l] = v;
+    }
+  }
+  __syncthreads();
+  const int lane = tid % 32, warp = tid / 32, nwarps = blockDim.x / 32;
+  int64_t obase = 0, ostride = 0;
+  if (lane < nl) line_geometry(axis, out, line0 + lane, &obase, &ostride);
+  int64_t gbase = 0, gstride = 0, gstep = 0;
+  if (a.g && lane < nl) {
+    // output (line, i) -> g entry with the same indices (g has extents b^3)
+    int idx3[3];
+    const int64_t line = line0 + lane;
+    if (axis == 1) { idx3[0] = 0; idx3[1] = (int)(line % out.n2); idx3[2] = (int)(line / out.n2); }
+    else if (axis == 2) { idx3[0] = (int)(line % out.n1); idx3[1] = 0; idx3[2] = (int)(line / out.n1); }
+    else { idx3[0] = (int)(line % out.n1); idx3[1] = (int)(line / out.n1); idx3[2] = 0; }
+    const Dims gd = a.gdims;
+    const int64_t gs[3] = {1, (int64_t)gd.n1, (int64_t)gd.n1 * gd.n2};
+    gbase = idx3[0] * gs[0] + idx3[1] * gs[1] + idx3[2] * gs[2];
+    gstride = gs[axis - 1];
+    gstep = gs[a.gaxis - 1];
+  }
+  for (int i = warp; i < m; i += nwarps) {
+    float acc = 0.f;
     {
       const int s0 = __ldg(a.D0.start + i);
-      const T* v = a.D0.val + (int64_t)i * a.D0.width;
-      const T* x = a.X0 + base + (int64_t)s0 * stride;
-      T s = 0;
-      for (int w = 0; w < a.D0.width; ++w) s += __ldg(v + w) * __ldg(x + (int64_t)w * stride);
-      acc = a.c0 * s;
+      const float* v = a.D0.val + (int64_t)i * a.D0.width;
+      float sum = 0.f;
+      for (int w = 0; w < a.D0.width; ++w) sum += __ldg(v + w) * xs0[(s0 + w) * P + lane];
+      acc = a.c0 * sum;
     }
     if (a.nterms > 1) {
       const int s1 = __ldg(a.D1.start + i);
-      const T* v = a.D1.val + (int64_t)i * a.D1.width;
-      const T* x = a.X1 + base + (int64_t)s1 * stride;
-      T s = 0;
-      for (int w = 0; w < a.D1.width; ++w) s += __ldg(v + w) * __ldg(x + (int64_t)w * stride);
-      acc += a.c1 * s;
+      const float* v = a.D1.val + (int64_t)i * a.D1.width;
+      float sum = 0.f;
+      for (int w = 0; w < a.D1.width; ++w) sum += __ldg(v + w) * xs1[(s1 + w) * P + lane];
+      acc += a.c1 * sum;
     }
-    if (a.Z) acc += a.cz * a.Z[o];
-    if (a.g) {
-      // (D^T g) along gaxis: g_j - g_{j+1}; the other two indices are shared with the output
-      const int64_t gi = i1 + (int64_t)a.gdims.n1 * (i2 + (int64_t)a.gdims.n2 * i3);
-      const int64_t gs = a.gaxis == 1 ? 1 : (a.gaxis == 2 ? (int64_t)a.gdims.n1
-                                                         : (int64_t)a.gdims.n1 * a.gdims.n2);
-      acc += a.g[gi] - a.g[gi + gs];
+    if (lane < nl) {
+      const int64_t o = obase + ostride * i;
+      if (a.Z) acc += a.cz * a.Z[o];
+      if (a.g) {
+        const int64_t gi = gbase + gstride * i;
+        acc += a.g[gi] - a.g[gi + gstep];
+      }
+      if (axis == 1) ys[i * P + lane] = acc;
+      else a.Y[o] = acc;
     }
-    a.Y[o] = acc;
+  }
+  if (axis == 1) {
+    __syncthreads();
+    const int total = m * kTileLines;
+    for (int idx = tid; idx < total; idx += blockDim.x) {
+      const int i = idx % m, l = idx / m;
+      if (l < nl) a.Y[(int64_t)m * (line0 + l) + i] = ys[i * P + l];
+    }
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_divergence(const T* __restrict__ u1, const T* __restrict__ u2,
                                                     const T* __restrict__ u3, int a, int b,
-                                                    T* __restrict__ delta) {
+                                                    T* __restrict__ delta, const T* __restrict__ q,
+                                                    T nu, T* __restrict__ e) {
   const int64_t total = (int64_t)b * b * b;
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += step) {
@@ -100,6 +263,7 @@ __global__ void __launch_bounds__(256) k_divergence(const T* __restrict__ u1, co
       if (i3 >= 1) d -= u3[off + (int64_t)b * b * (i3 - 1)];
     }
     delta[o] = d;
+    if (e) e[o] = nu * d + q[o];
   }
 }
 
@@ -131,30 +295,99 @@ __global__ void __launch_bounds__(256) k_div_transpose(const T* __restrict__ g, 
 
 }  // namespace
 
+void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {
+  PassBatch<float> pb{};
+  pb.njobs = njobs;
+  int blocks = 0;
+  int smem = 0;
+  double flops = 0, bytes = 0;
+  for (int j = 0; j < njobs; ++j) {
+    const PassArgs<float>& a = jobs[j];
+    pb.job[j] = a;
+    pb.first_block[j] = blocks;
+    const Dims out = a.in.with(a.axis, a.D0.rows);
+    const int64_t lines = out.size() / a.D0.rows;
+    blocks += (int)((lines + kTileLines - 1) / kTileLines);
+    const int nin = a.in.get(a.axis);
+    const int sm = ((a.nterms > 1 ? 2 : 1) * nin + (a.axis == 1 ? a.D0.rows : 0)) *
+                   (kTileLines + 1) * (int)sizeof(float);
+    smem = sm > smem ? sm : smem;
+    const double outs = (double)out.size();
+    double fl = 2.0 * a.D0.width * outs, by = (double)a.in.size() + outs;
+    if (a.nterms > 1) { fl += 2.0 * a.D1.width * outs; by += (double)a.in.size(); }
+    if (a.Z) { fl += 2.0 * outs; by += outs; }
+    if (a.g) { fl += 2.0 * outs; by += (double)a.gdims.size(); }
+    flops += fl;
+    bytes += by * sizeof(float);
+  }
+  pb.first_block[njobs] = blocks;
+  pb.seg = 1;
+  static int attr = 0;
+  if (smem > 48 * 1024 && smem > attr) {
+    cudaFuncSetAttribute(k_band_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = smem;
+  }
+  launch_begin(kClassBand, s);
+  k_band_tile<<<blocks, 256, smem, s>>>(pb);
+  launch_end(kClassBand, s, flops, bytes);
+}
+
+template <typename T>
+void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    band_tile_multi(jobs, njobs, s);
+    return;
+  }
+  PassBatch<T> pb{};
+  pb.njobs = njobs;
+  int blocks = 0;
+  double flops = 0, bytes = 0;
+  for (int j = 0; j < njobs; ++j) {
+    const PassArgs<T>& a = jobs[j];
+    pb.job[j] = a;
+    pb.first_block[j] = blocks;
+    const Dims out = a.in.with(a.axis, a.D0.rows);
+    const int64_t lines = out.size() / a.D0.rows;
+    const int64_t lines_r = (lines + 31) / 32 * 32;
+    const int64_t nseg = (a.D0.rows + seg_len<T>() - 1) / seg_len<T>();
+    blocks += (int)((lines_r * nseg + 255) / 256);
+    // algorithmic work: one band row per output and term; one read of every input tensor
+    const double outs = (double)out.size();
+    double fl = 2.0 * a.D0.width * outs, by = (double)a.in.size() + outs;
+    if (a.nterms > 1) { fl += 2.0 * a.D1.width * outs; by += (double)a.in.size(); }
+    if (a.Z) { fl += 2.0 * outs; by += outs; }
+    if (a.g) { fl += 2.0 * outs; by += (double)a.gdims.size(); }
+    flops += fl;
+    bytes += by * sizeof(T);
+  }
+  pb.first_block[njobs] = blocks;
+  pb.seg = seg_len<T>();
+  launch_begin(kClassBand, s);
+  k_band_pass<T><<<blocks, 256, 0, s>>>(pb);
+  launch_end(kClassBand, s, flops, bytes);
+}
+
 template <typename T>
 void band_pass(const PassArgs<T>& a, cudaStream_t s) {
-  const Dims out = a.in.with(a.axis, a.D0.rows);
-  const int threads = 256;
-  const int grid = grid_for(out.size(), threads);
-  // algorithmic work: one band row per output and term; one read of every input tensor
-  const double outs = (double)out.size();
-  double flops = 2.0 * a.D0.width * outs, bytes = (double)a.in.size() + outs;
-  if (a.nterms > 1) { flops += 2.0 * a.D1.width * outs; bytes += (double)a.in.size(); }
-  if (a.Z) { flops += 2.0 * outs; bytes += outs; }
-  if (a.g) { flops += 2.0 * outs; bytes += (double)a.gdims.size(); }
-  launch_begin(kClassBand, s);
-  if (a.axis == 1) k_band_pass<T, 1><<<grid, threads, 0, s>>>(a);
-  else if (a.axis == 2) k_band_pass<T, 2><<<grid, threads, 0, s>>>(a);
-  else k_band_pass<T, 3><<<grid, threads, 0, s>>>(a);
-  launch_end(kClassBand, s, flops, bytes * sizeof(T));
+  band_pass_multi<T>(&a, 1, s);
 }
 
 template <typename T>
 void divergence(const T* u1, const T* u2, const T* u3, int a, int b, T* delta, cudaStream_t s) {
   const int64_t total = (int64_t)b * b * b;
   launch_begin(kClassDiv, s);
-  k_divergence<T><<<grid_for(total, 256), 256, 0, s>>>(u1, u2, u3, a, b, delta);
+  k_divergence<T><<<grid_for(total, 256), 256, 0, s>>>(u1, u2, u3, a, b, delta, nullptr, T(0),
+                                                      nullptr);
   launch_end(kClassDiv, s, 6.0 * total, (3.0 * a * b * b + total) * sizeof(T));
+}
+
+template <typename T>
+void divergence_plus(const T* u1, const T* u2, const T* u3, int a, int b, T* delta, const T* q,
+                     T nu, T* e, cudaStream_t s) {
+  const int64_t total = (int64_t)b * b * b;
+  launch_begin(kClassDiv, s);
+  k_divergence<T><<<grid_for(total, 256), 256, 0, s>>>(u1, u2, u3, a, b, delta, q, nu, e);
+  launch_end(kClassDiv, s, 8.0 * total, (3.0 * a * b * b + 3.0 * total) * sizeof(T));
 }
 
 template <typename T>
@@ -169,10 +402,16 @@ void div_transpose(const T* g, int a, int b, T* y1, T* y2, T* y3, int accumulate
 
 template void band_pass<double>(const PassArgs<double>&, cudaStream_t);
 template void band_pass<float>(const PassArgs<float>&, cudaStream_t);
+template void band_pass_multi<double>(const PassArgs<double>*, int, cudaStream_t);
+template void band_pass_multi<float>(const PassArgs<float>*, int, cudaStream_t);
 template void divergence<double>(const double*, const double*, const double*, int, int, double*,
                                  cudaStream_t);
 template void divergence<float>(const float*, const float*, const float*, int, int, float*,
                                 cudaStream_t);
+template void divergence_plus<double>(const double*, const double*, const double*, int, int,
+                                      double*, const double*, double, double*, cudaStream_t);
+template void divergence_plus<float>(const float*, const float*, const float*, int, int, float*,
+                                     const float*, float, float*, cudaStream_t);
 template void div_transpose<double>(const double*, int, int, double*, double*, double*, int,
                                     cudaStream_t);
 template void div_transpose<float>(const float*, int, int, float*, float*, float*, int,

@@ -3,43 +3,69 @@
 // A mode product along one direction is a (batched) matrix product: for directions 2 and 3,
 // Y[l, i, r] = sum_j X[l, j, r] Op(i, j) with l running over the contiguous leading extents; for
 // direction 1, Y[i, r] = sum_j Op(i, j) X[j, r]. Both are written as C[p, q] = sum_k A[p, k] B[k, q]
-// with strided operands and tiled through shared memory (64 x 64 output tile, k-chunks of 16,
-// 4 x 4 outputs per thread). The fast-diagonalisation division by the eigenvalue sums is fused
+// with strided operands, tiled through shared memory. Several independent products (one per
+// velocity component) share one launch: the flat block index selects the product, its batch
+// entry and its output tile. The fast-diagonalisation division by the eigenvalue sums is fused
 // into the epilogue of the last forward product.
+//
+// FP32 (CUDA-core fallback of the reduced-precision preconditioner): 64 x 64 tiles, 256 threads,
+// 4 x 4 outputs per thread. FP64 uses the row-streaming kernel further below.
 #include "internal.h"
 #include "profile.h"
 
 namespace shp {
 namespace {
 
-constexpr int BP = 64, BQ = 64, BK = 16, NTH = 256;
+template <typename T>
+struct Tile;
+template <>
+struct Tile<float> {
+  static constexpr int BP = 64, BQ = 64, BK = 16, TX = 16, TY = 16, MP = 4, MQ = 4, NTH = 256;
+};
 
 template <typename T>
 struct GemmArgs {
   const T* A; int64_t a_p, a_k, a_b;
   const T* B; int64_t b_k, b_q, b_b;
   T* C; int64_t c_p, c_q, c_b;
-  int P, Q, K;
+  int P, Q, K, R;
+  int tiles_p, tiles_q;
   // optional fast-diagonalisation epilogue
   const T* lam1; const T* lam2; const T* lam3; T scale; Dims out;
   T post;
 };
 
 template <typename T>
-__global__ void __launch_bounds__(NTH) k_gemm(GemmArgs<T> g) {
+struct GemmBatch {
+  GemmArgs<T> job[kMaxModeJobs];
+  int first_block[kMaxModeJobs + 1];
+  int njobs;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(Tile<T>::NTH) k_gemm(const __grid_constant__ GemmBatch<T> gb) {
+  using TL = Tile<T>;
+  constexpr int BP = TL::BP, BQ = TL::BQ, BK = TL::BK, NTH = TL::NTH;
   __shared__ T As[BK][BP + 1];
   __shared__ T Bs[BK][BQ + 1];
+  int jb = 0;
+  while (jb + 1 < gb.njobs && (int)blockIdx.x >= gb.first_block[jb + 1]) ++jb;
+  const GemmArgs<T>& g = gb.job[jb];
+  int local = blockIdx.x - gb.first_block[jb];
+  const int tiles = g.tiles_p * g.tiles_q;
+  const int bz = local / tiles;
+  local -= bz * tiles;
+  const int tq = local / g.tiles_p, tp = local - tq * g.tiles_p;
   const int tid = threadIdx.x;
-  const int tx = tid % 16, ty = tid / 16;
-  const int p0 = blockIdx.x * BP, q0 = blockIdx.y * BQ;
-  const int64_t bz = blockIdx.z;
-  const T* A = g.A + bz * g.a_b;
-  const T* B = g.B + bz * g.b_b;
-  T acc[4][4];
+  const int tx = tid % TL::TX, ty = tid / TL::TX;
+  const int p0 = tp * BP, q0 = tq * BQ;
+  const T* A = g.A + (int64_t)bz * g.a_b;
+  const T* B = g.B + (int64_t)bz * g.b_b;
+  T acc[TL::MP][TL::MQ];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TL::MP; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+    for (int j = 0; j < TL::MQ; ++j) acc[i][j] = 0;
   const bool a_pfast = g.a_p == 1;
   const bool b_kfast = g.b_k == 1;
   for (int k0 = 0; k0 < g.K; k0 += BK) {
@@ -62,29 +88,29 @@ __global__ void __launch_bounds__(NTH) k_gemm(GemmArgs<T> g) {
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
-      T av[4], bv[4];
+      T av[TL::MP], bv[TL::MQ];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = As[k][tx + 16 * i];
+      for (int i = 0; i < TL::MP; ++i) av[i] = As[k][tx + TL::TX * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[k][ty + 16 * j];
+      for (int j = 0; j < TL::MQ; ++j) bv[j] = Bs[k][ty + TL::TY * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TL::MP; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+        for (int j = 0; j < TL::MQ; ++j) acc[i][j] += av[i] * bv[j];
     }
     __syncthreads();
   }
-  T* C = g.C + bz * g.c_b;
+  T* C = g.C + (int64_t)bz * g.c_b;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TL::MP; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int p = p0 + tx + 16 * i, q = q0 + ty + 16 * j;
+    for (int j = 0; j < TL::MQ; ++j) {
+      const int p = p0 + tx + TL::TX * i, q = q0 + ty + TL::TY * j;
       if (p < g.P && q < g.Q) {
         const int64_t off = p * g.c_p + q * g.c_q;
         T v = acc[i][j];
         if (g.lam1) {
-          const int64_t o = off + bz * g.c_b;
+          const int64_t o = off + (int64_t)bz * g.c_b;
           const int i1 = (int)(o % g.out.n1);
           const int64_t t2 = o / g.out.n1;
           const int i2 = (int)(t2 % g.out.n2);
@@ -98,48 +124,202 @@ __global__ void __launch_bounds__(NTH) k_gemm(GemmArgs<T> g) {
     }
 }
 
-}  // namespace
-
 template <typename T>
-void mode_product(const ModeArgs<T>& m, cudaStream_t s) {
+GemmArgs<T> make_gemm(const ModeArgs<T>& m) {
+  using TL = Tile<T>;
   GemmArgs<T> g{};
   const Dims in = m.in;
   const int nin = in.get(m.axis);
   const Dims out = in.with(m.axis, m.m);
-  // Op(i, j) strides
   const int64_t op_i = m.trans ? 1 : m.ld, op_j = m.trans ? m.ld : 1;
   if (m.axis == 1) {
     // C[i, r] = sum_j Op(i, j) X[j, r]
     g.A = m.U; g.a_p = op_i; g.a_k = op_j; g.a_b = 0;
     g.B = m.X; g.b_k = 1; g.b_q = nin; g.b_b = 0;
     g.C = m.Y; g.c_p = 1; g.c_q = m.m; g.c_b = 0;
-    g.P = m.m; g.Q = in.n2 * in.n3; g.K = nin;
-    g.lam1 = m.lam1; g.lam2 = m.lam2; g.lam3 = m.lam3; g.scale = m.scale; g.out = out;
-    g.post = m.post;
-    dim3 grid((g.P + BP - 1) / BP, (g.Q + BQ - 1) / BQ, 1);
-    launch_begin(kClassMode, s);
-    k_gemm<T><<<grid, NTH, 0, s>>>(g);
-    launch_end(kClassMode, s, 2.0 * g.P * g.Q * g.K,
-               ((double)in.size() + (double)out.size()) * sizeof(T));
+    g.P = m.m; g.Q = in.n2 * in.n3; g.K = nin; g.R = 1;
   } else {
     const int64_t L = m.axis == 2 ? in.n1 : (int64_t)in.n1 * in.n2;
-    const int R = m.axis == 2 ? in.n3 : 1;
     // C[l, i] = sum_j X[l, j] Op(i, j), batched over r
     g.A = m.X; g.a_p = 1; g.a_k = L; g.a_b = L * nin;
     g.B = m.U; g.b_k = op_j; g.b_q = op_i; g.b_b = 0;
     g.C = m.Y; g.c_p = 1; g.c_q = L; g.c_b = L * m.m;
-    g.P = (int)L; g.Q = m.m; g.K = nin;
-    g.lam1 = m.lam1; g.lam2 = m.lam2; g.lam3 = m.lam3; g.scale = m.scale; g.out = out;
-    g.post = m.post;
-    dim3 grid((g.P + BP - 1) / BP, (g.Q + BQ - 1) / BQ, R);
-    launch_begin(kClassMode, s);
-    k_gemm<T><<<grid, NTH, 0, s>>>(g);
-    launch_end(kClassMode, s, 2.0 * g.P * g.Q * g.K * R,
-               ((double)in.size() + (double)out.size()) * sizeof(T));
+    g.P = (int)L; g.Q = m.m; g.K = nin; g.R = m.axis == 2 ? in.n3 : 1;
   }
+  g.tiles_p = (g.P + TL::BP - 1) / TL::BP;
+  g.tiles_q = (g.Q + TL::BQ - 1) / TL::BQ;
+  g.lam1 = m.lam1; g.lam2 = m.lam2; g.lam3 = m.lam3; g.scale = m.scale; g.out = out;
+  g.post = m.post;
+  return g;
+}
+
+// ---- FP64: row-streaming mode products ---------------------------------------------------------
+// GB300 executes about two FP64 FMA per clock per SM, so an FP64 mode product is bound by the
+// FP64 pipe on every mesh size. Each thread owns one output line position and kRowsPerThread
+// consecutive output indices i (independent accumulators hide the FMA latency), streams the
+// contracted line of X through the read-only cache and reads Op(i, j) from it as well (a warp
+// shares its i range, so those loads broadcast). Extents are used exactly: no padded tiles.
+constexpr int kRowsPerThread = 8;   // upper bound of the outputs per thread
+
+struct RowJob {
+  const double* X; double* Y; const double* U;
+  int64_t op_i, op_j;      // Op(i, j) = U[i * op_i + j * op_j]
+  int64_t L;               // product of the extents before the contracted direction
+  int K, m, groups;        // contracted extent, output extent, ceil(m / MI)
+  int64_t R;               // product of the extents after it
+  int64_t threads;         // L * groups * R
+  const double* invd;      // optional multiplier per output entry
+  const double *lam1, *lam2, *lam3;   // otherwise optional eigenvalue-sum divisor
+  double scale;
+  Dims out;
+  double post;
+};
+
+struct RowBatch {
+  RowJob job[kMaxModeJobs];
+  int64_t first[kMaxModeJobs + 1];   // first flat thread of each job
+  int njobs;
+};
+
+template <int MI>
+__global__ void __launch_bounds__(128) k_mode_rows(const __grid_constant__ RowBatch rb) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= rb.first[rb.njobs]) return;
+  int jb = 0;
+  while (jb + 1 < rb.njobs && t >= rb.first[jb + 1]) ++jb;
+  const RowJob& J = rb.job[jb];
+  int64_t u = t - rb.first[jb];
+  // l fastest, then the i group, then r: a warp shares (group, r) when L >= 32 (coalesced X,
+  // broadcast Op); for L = 1 consecutive threads take consecutive groups of one r.
+  const int64_t l = u % J.L;
+  u /= J.L;
+  const int g = (int)(u % J.groups);
+  const int64_t r = u / J.groups;
+  const int i0 = g * MI;
+  const double* x = J.X + l + J.L * (int64_t)J.K * r;
+  double acc[MI];
+#pragma unroll
+  for (int k = 0; k < MI; ++k) acc[k] = 0.0;
+  const double* op = J.U + i0 * J.op_i;
+  if (i0 + MI <= J.m) {
+    for (int j = 0; j < J.K; ++j) {
+      const double xv = __ldg(x + J.L * j);
+      const double* o = op + j * J.op_j;
+#pragma unroll
+      for (int k = 0; k < MI; ++k) acc[k] = fma(__ldg(o + k * J.op_i), xv, acc[k]);
+    }
+  } else {
+    const int cnt = J.m - i0;
+    for (int j = 0; j < J.K; ++j) {
+      const double xv = __ldg(x + J.L * j);
+      const double* o = op + j * J.op_j;
+#pragma unroll
+      for (int k = 0; k < MI; ++k)
+        if (k < cnt) acc[k] = fma(__ldg(o + k * J.op_i), xv, acc[k]);
+    }
+  }
+  double* y = J.Y + l + J.L * (int64_t)J.m * r;
+#pragma unroll
+  for (int k = 0; k < MI; ++k) {
+    const int i = i0 + k;
+    if (i < J.m) {
+      const int64_t off = J.L * (int64_t)i;
+      double v = acc[k];
+      const int64_t o = l + off + J.L * (int64_t)J.m * r;
+      if (J.invd) {
+        v *= J.invd[o];
+      } else if (J.lam1) {
+        const int i1 = (int)(o % J.out.n1);
+        const int64_t t2 = o / J.out.n1;
+        v /= J.scale * (J.lam1[i1] + J.lam2[(int)(t2 % J.out.n2)] + J.lam3[(int)(t2 / J.out.n2)]);
+      } else {
+        v *= J.post;
+      }
+      y[off] = v;
+    }
+  }
+}
+
+}  // namespace
+
+template <>
+void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStream_t s) {
+  // outputs per thread: as many as still leave ~1000 threads per SM (152 SMs), at least 2
+  int64_t lines = 0;
+  for (int j = 0; j < njobs; ++j) {
+    const Dims in = jobs[j].in;
+    lines += in.size() / in.get(jobs[j].axis) * (int64_t)jobs[j].m;
+  }
+  int mi = 8;
+  while (mi > 2 && lines / mi < 152 * 1024) mi /= 2;
+  RowBatch rb{};
+  rb.njobs = njobs;
+  int64_t total = 0;
+  double flops = 0, bytes = 0;
+  for (int j = 0; j < njobs; ++j) {
+    const ModeArgs<double>& m = jobs[j];
+    RowJob& J = rb.job[j];
+    const Dims in = m.in;
+    J.X = m.X;
+    J.Y = m.Y;
+    J.U = m.U;
+    J.op_i = m.trans ? 1 : m.ld;
+    J.op_j = m.trans ? m.ld : 1;
+    J.K = in.get(m.axis);
+    J.m = m.m;
+    J.L = m.axis == 1 ? 1 : (m.axis == 2 ? in.n1 : (int64_t)in.n1 * in.n2);
+    J.R = m.axis == 1 ? (int64_t)in.n2 * in.n3 : (m.axis == 2 ? in.n3 : 1);
+    J.groups = (m.m + mi - 1) / mi;
+    J.threads = J.L * J.groups * J.R;
+    J.invd = m.invd;
+    J.lam1 = m.invd ? nullptr : m.lam1;
+    J.lam2 = m.lam2;
+    J.lam3 = m.lam3;
+    J.scale = m.scale;
+    J.out = in.with(m.axis, m.m);
+    J.post = m.lam1 ? 1.0 : m.post;
+    rb.first[j] = total;
+    total += J.threads;
+    flops += 2.0 * J.L * J.R * (double)J.K * J.m;
+    bytes += ((double)in.size() + (double)in.with(m.axis, m.m).size()) * sizeof(double);
+  }
+  rb.first[njobs] = total;
+  const int64_t blocks = (total + 127) / 128;
+  launch_begin(kClassMode, s);
+  if (mi == 8) k_mode_rows<8><<<(unsigned)blocks, 128, 0, s>>>(rb);
+  else if (mi == 4) k_mode_rows<4><<<(unsigned)blocks, 128, 0, s>>>(rb);
+  else k_mode_rows<2><<<(unsigned)blocks, 128, 0, s>>>(rb);
+  launch_end(kClassMode, s, flops, bytes);
+}
+
+template <typename T>
+void mode_product_multi(const ModeArgs<T>* jobs, int njobs, cudaStream_t s) {
+  GemmBatch<T> gb{};
+  gb.njobs = njobs;
+  int blocks = 0;
+  double flops = 0, bytes = 0;
+  for (int j = 0; j < njobs; ++j) {
+    gb.job[j] = make_gemm<T>(jobs[j]);
+    gb.first_block[j] = blocks;
+    blocks += gb.job[j].tiles_p * gb.job[j].tiles_q * gb.job[j].R;
+    const GemmArgs<T>& g = gb.job[j];
+    flops += 2.0 * g.P * g.Q * g.K * g.R;
+    bytes += ((double)jobs[j].in.size() + (double)jobs[j].in.with(jobs[j].axis, jobs[j].m).size()) *
+             sizeof(T);
+  }
+  gb.first_block[njobs] = blocks;
+  launch_begin(kClassMode, s);
+  k_gemm<T><<<blocks, Tile<T>::NTH, 0, s>>>(gb);
+  launch_end(kClassMode, s, flops, bytes);
+}
+
+template <typename T>
+void mode_product(const ModeArgs<T>& m, cudaStream_t s) {
+  mode_product_multi<T>(&m, 1, s);
 }
 
 template void mode_product<double>(const ModeArgs<double>&, cudaStream_t);
 template void mode_product<float>(const ModeArgs<float>&, cudaStream_t);
+template void mode_product_multi<float>(const ModeArgs<float>*, int, cudaStream_t);
 
 }  // namespace shp

@@ -1,0 +1,497 @@
+// Tensor-core (tcgen05 / TMEM / TMA) mode products for the reduced-precision fast
+// diagonalisation (App. A.4).
+//
+// Rotating mode product. A tensor with extents (e1, e2, e3), e1 fastest and its rows padded to a
+// 16-byte multiple (ld >= e1), is contracted along e1 with a dense operator Op (m x e1):
+//   D[r, i] = sum_j X[r][j] Op[i][j],   r = j2 + e2 j3 in [0, e2 e3),
+// and written with the axes rotated, Y[j2 + ldy (j3 + e3 i)], so that the next contraction is
+// again along the contiguous axis. Three rotations restore the original axis order, so the six
+// products of a fast diagonalisation (U1^T, U2^T, U3^T, scale, U3, U2, U1) need no transposes.
+//
+// GEMM mapping on the fifth-generation tensor cores: M = 128 rows r per tile (TMEM lanes),
+// N = m padded to 16 (TMEM columns, FP32 accumulator), K = e1 in 128-byte chunks. Both operands
+// are K-major with the 128-byte swizzle. Op stays resident in shared memory; row tiles of X
+// stream through a ring of chunk stages filled by TMA (cp.async.bulk.tensor). One elected thread
+// issues tcgen05.mma; four epilogue warps read the accumulator with tcgen05.ld, apply the optional
+// eigenvalue scaling and store coalesced rows. Two TMEM accumulators let the epilogue of one tile
+// overlap the MMAs of the next. Every wait on an mbarrier is bounded: on timeout the kernel sets an
+// error flag, stops issuing work, waits (bounded) for the tensor-core work it has issued, frees
+// its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "internal.h"
+#include "mma.h"
+#include "profile.h"
+
+namespace shp {
+namespace {
+
+constexpr int kTileM = 128;
+constexpr int kStages = 4;
+constexpr int kChunkBytes = 128;                  // one 128-byte swizzle atom of K per row
+constexpr int kStageBytes = kTileM * kChunkBytes; // 16 KiB
+constexpr int kThreads = 192;                     // warp 0 TMA, warp 1 MMA + TMEM, warps 2-5 epilogue
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity. Returns false (and raises the shared abort
+// flag and the global error flag) if it does not complete within the limit or if another role
+// has already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          int* err) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (i > 64) __nanosleep(128);
+  }
+  *abort_flag = 1;
+  atomicExch(err, 1);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile with the 128-byte swizzle: rows of 128 bytes,
+// 8-row core groups 1024 bytes apart (stride byte offset), descriptor version 1, layout code 2.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);        // start address
+  d |= (uint64_t)1 << 16;                         // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset
+  d |= (uint64_t)1 << 46;                         // descriptor version
+  d |= (uint64_t)2 << 61;                         // 128-byte swizzle
+  return d;
+}
+
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t accumulate) {
+  if (KIND == kMmaTF32) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+  }
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <typename TO>
+__device__ __forceinline__ void store_val(TO* p, float v);
+template <>
+__device__ __forceinline__ void store_val<float>(float* p, float v) { *p = v; }
+template <>
+__device__ __forceinline__ void store_val<__nv_bfloat16>(__nv_bfloat16* p, float v) {
+  *p = __float2bfloat16_rn(v);
+}
+
+__host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+struct RmpJob {
+  CUtensorMap map_x;
+  CUtensorMap map_op;
+  RmpArgs args;
+  int first_tile;   // index of this job's first tile in the launch
+  int ntiles;
+  int nchunks;
+};
+
+struct RmpBatch {
+  RmpJob job[kMaxRmpJobs];
+  int njobs;
+  int total_tiles;
+};
+
+__device__ __forceinline__ int job_of(const RmpBatch& b, int t) {
+  int j = 0;
+  while (j + 1 < b.njobs && t >= b.job[j + 1].first_tile) ++j;
+  return j;
+}
+
+// KIND: kMmaTF32 (FP32 operands in memory) or kMmaBF16; TO: output element type. Each CTA owns a
+// contiguous range of tiles over all jobs; the operator is reloaded when the range crosses into
+// the next job, after the MMAs that read the previous operator have completed.
+template <int KIND, typename TO>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_rmp(const __grid_constant__ RmpBatch batch, int* err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const int elem = KIND == kMmaTF32 ? 4 : 2;
+  const int chunk_elems = kChunkBytes / elem;
+  int b_bytes = 0;
+  for (int j = 0; j < batch.njobs; ++j) {
+    const int bb = batch.job[j].nchunks * batch.job[j].args.npad * kChunkBytes;
+    b_bytes = bb > b_bytes ? bb : b_bytes;
+  }
+  uint8_t* b_tile = smem;                 // operator of the current job, all K chunks
+  uint8_t* a_ring = smem + b_bytes;       // kStages x 16 KiB (b_bytes is a multiple of 2 KiB)
+  __shared__ uint64_t full_bar[kStages], empty_bar[kStages];
+  __shared__ uint64_t b_bar, b_free_bar, drain_bar, tfull_bar[2], tempty_bar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int t_begin = (int)(((int64_t)batch.total_tiles * blockIdx.x) / gridDim.x);
+  const int t_end = (int)(((int64_t)batch.total_tiles * (blockIdx.x + 1)) / gridDim.x);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&b_bar, 1);
+    mbar_init(&b_free_bar, 1);
+    mbar_init(&drain_bar, 1);
+    for (int t = 0; t < 2; ++t) {
+      mbar_init(&tfull_bar[t], 1);
+      mbar_init(&tempty_bar[t], 4);     // one arrival per epilogue warp
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  volatile int* abort_p = &abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0, cur = -1, nb = 0;
+      bool ok = true;
+      for (int t = t_begin; ok && t < t_end && !*abort_p; ++t) {
+        const int j = job_of(batch, t);
+        const RmpJob& J = batch.job[j];
+        if (j != cur) {
+          // operator of job j; when replacing one, wait until its last MMAs have completed
+          if (nb > 0 && !mbar_wait(&b_free_bar, (nb - 1) & 1, abort_p, err)) break;
+          mbar_expect_tx(&b_bar, (uint32_t)(J.nchunks * J.args.npad * kChunkBytes));
+          for (int c = 0; c < J.nchunks; ++c)
+            tma_load_2d(b_tile + c * J.args.npad * kChunkBytes, &J.map_op, c * chunk_elems, 0,
+                        &b_bar);
+          cur = j;
+          ++nb;
+        }
+        const int local_tile = t - J.first_tile;
+        for (int c = 0; c < J.nchunks; ++c, ++it) {
+          const int s = it % kStages;
+          const uint32_t ph = (it / kStages) & 1;
+          if (it >= kStages && !mbar_wait(&empty_bar[s], ph ^ 1, abort_p, err)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full_bar[s], kStageBytes);
+          tma_load_2d(a_ring + s * kStageBytes, &J.map_x, c * chunk_elems, local_tile * kTileM,
+                      &full_bar[s]);
+        }
+      }
+      // bounded wait until every copy this thread issued has landed
+      for (int k = (it > kStages ? it - kStages : 0); k < it; ++k) {
+        const int s = k % kStages;
+        for (uint32_t i = 0; i < kSpinLimit && !mbar_try_wait(&full_bar[s], (k / kStages) & 1); ++i)
+          __nanosleep(128);
+      }
+      if (nb > 0)
+        for (uint32_t i = 0; i < kSpinLimit && !mbar_try_wait(&b_bar, (nb - 1) & 1); ++i)
+          __nanosleep(128);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = true;
+      int it = 0, local = 0, cur = -1, nbw = 0;
+      for (int t = t_begin; ok && t < t_end; ++t, ++local) {
+        const int j = job_of(batch, t);
+        const RmpJob& J = batch.job[j];
+        if (j != cur) {
+          if (!mbar_wait(&b_bar, nbw & 1, abort_p, err)) break;
+          ++nbw;
+          cur = j;
+        }
+        const int acc = local & 1;
+        const uint32_t d_tmem = tmem + acc * 256;
+        if (local >= 2 && !mbar_wait(&tempty_bar[acc], ((local / 2) - 1) & 1, abort_p, err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int c = 0; c < J.nchunks; ++c, ++it) {
+          const int s = it % kStages;
+          if (!mbar_wait(&full_bar[s], (it / kStages) & 1, abort_p, err)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a_addr = smem_u32(a_ring + s * kStageBytes);
+          const uint32_t b_addr = smem_u32(b_tile + c * J.args.npad * kChunkBytes);
+#pragma unroll
+          for (int k = 0; k < 4; ++k)   // 4 instructions of 32 bytes of K each
+            umma<KIND>(d_tmem, sw128_desc(a_addr + 32 * k), sw128_desc(b_addr + 32 * k),
+                       J.args.idesc, (c > 0 || k > 0) ? 1u : 0u);
+          umma_commit(&empty_bar[s]);   // stage free once these MMAs have read it
+        }
+        if (!ok) break;
+        umma_commit(&tfull_bar[acc]);   // accumulator ready for the epilogue
+        if (t + 1 < t_end && job_of(batch, t + 1) != j) umma_commit(&b_free_bar);
+      }
+      // bounded wait until every MMA this thread issued has completed
+      umma_commit(&drain_bar);
+      for (uint32_t i = 0; i < kSpinLimit && !mbar_try_wait(&drain_bar, 0); ++i) __nanosleep(128);
+    }
+  } else {
+    // epilogue warps 2..5: TMEM lane quarter = warp % 4
+    const int quarter = warp % 4;
+    const int row_in_tile = quarter * 32 + lane;
+    int local = 0;
+    for (int t = t_begin; t < t_end; ++t, ++local) {
+      const RmpJob& J = batch.job[job_of(batch, t)];
+      const RmpArgs& args = J.args;
+      const int acc = local & 1;
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(&tfull_bar[acc], (local / 2) & 1, abort_p, err) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int r = (t - J.first_tile) * kTileM + row_in_tile;
+      const bool valid = r < args.R;
+      int64_t base = 0;
+      float lam_r = 0.f;
+      if (valid) {
+        const int j2 = r % args.e2, j3 = r / args.e2;
+        base = j2 + (int64_t)args.ldy * j3;
+        if (args.lam_i) lam_r = args.lam_j2[j2] + args.lam_j3[j3];
+      }
+      const int64_t stride_i = (int64_t)args.ldy * args.e3;
+      TO* Y = reinterpret_cast<TO*>(args.Y);
+      for (int c0 = 0; c0 < args.npad; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + acc * 256 + ((uint32_t)(quarter * 32) << 16) + c0, v);
+        if (valid) {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const int i = c0 + k;
+            if (i < args.m) {
+              float val = v[k];
+              if (args.lam_i) val = val / (args.scale * (lam_r + args.lam_i[i]));
+              else val *= args.post;
+              store_val<TO>(Y + base + stride_i * i, val);
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty_bar[acc]);
+    }
+  }
+  // drain: make sure no tensor-core work of this CTA is in flight before TMEM is freed
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+template <typename TO>
+__global__ void k_pad_rows(const float* __restrict__ x, int e1, int64_t R, int ld,
+                           TO* __restrict__ y) {
+  const int64_t total = (int64_t)e1 * R;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = o / e1;
+    const int j = (int)(o - r * e1);
+    store_val<TO>(y + r * ld + j, x[o]);
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+int rmp_smem_bytes(int kind, int K, int npad) {
+  const int elem = kind == kMmaTF32 ? 4 : 2;
+  const int nchunks = (K + kChunkBytes / elem - 1) / (kChunkBytes / elem);
+  return 1024 + nchunks * npad * kChunkBytes + kStages * kStageBytes;
+}
+
+bool rmp_supported(int kind, int K, int m) {
+  const int npad = round_up(m, 16);
+  return npad <= 256 && rmp_smem_bytes(kind, K, npad) <= 220 * 1024;
+}
+
+// 2D tensor map over rows of `cols` valid elements (row pitch `ld` elements, 16-byte multiple),
+// box = (128 bytes of columns) x box_rows, 128-byte swizzle, zero fill out of range.
+bool make_map(void* map, const void* base, int kind, int cols, int64_t rows, int ld, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const int elem = kind == kMmaTF32 ? 4 : 2;
+  if (((uintptr_t)base) % 16 != 0 || ((int64_t)ld * elem) % 16 != 0) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * elem};
+  cuuint32_t box[2] = {(cuuint32_t)(kChunkBytes / elem), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(reinterpret_cast<CUtensorMap*>(map),
+                   kind == kMmaTF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                    : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                   2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+uint32_t rmp_idesc(int kind, int npad) {
+  const uint32_t fmt = kind == kMmaTF32 ? 2u : 1u;   // TF32 = 2 (kind::tf32), BF16 = 1 (kind::f16)
+  uint32_t d = 0;
+  d |= 1u << 4;                        // accumulator format F32
+  d |= fmt << 7;                       // A format
+  d |= fmt << 10;                      // B format
+  d |= (uint32_t)(npad >> 3) << 17;    // N
+  d |= (uint32_t)(kTileM >> 4) << 24;  // M
+  return d;
+}
+
+template <int KIND, typename TO>
+void launch_rmp_t(const RmpPlan* const* plans, int njobs, int* err, int sms, cudaStream_t s) {
+  RmpBatch b{};
+  b.njobs = njobs;
+  int tiles = 0, smem = 0;
+  double flops = 0, bytes = 0;
+  const int elem = KIND == kMmaTF32 ? 4 : 2;
+  for (int j = 0; j < njobs; ++j) {
+    const RmpPlan& p = *plans[j];
+    RmpJob& J = b.job[j];
+    std::memcpy(&J.map_x, p.map_x, sizeof(CUtensorMap));
+    std::memcpy(&J.map_op, p.map_op, sizeof(CUtensorMap));
+    J.args = p.args;
+    J.first_tile = tiles;
+    J.ntiles = (p.args.R + kTileM - 1) / kTileM;
+    J.nchunks = (p.args.K + kChunkBytes / elem - 1) / (kChunkBytes / elem);
+    tiles += J.ntiles;
+    const int sm = rmp_smem_bytes(KIND, p.args.K, p.args.npad);
+    smem = sm > smem ? sm : smem;
+    flops += 2.0 * p.args.R * p.args.m * p.args.K;
+    bytes += (double)p.args.R * (p.args.K * elem + p.args.m * (double)sizeof(TO));
+  }
+  b.total_tiles = tiles;
+  const int grid = tiles < sms ? tiles : sms;
+  if (smem < 116 * 1024) smem = 116 * 1024;   // one CTA, one 512-column TMEM allocation per SM
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_rmp<KIND, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr_set = true;
+  }
+  launch_begin(kClassMma, s);
+  k_rmp<KIND, TO><<<grid, kThreads, smem, s>>>(b, err);
+  launch_end(kClassMma, s, flops, bytes);
+}
+
+void launch_rmp_multi(const RmpPlan* const* plans, int njobs, int* err, int sms, cudaStream_t s) {
+  const RmpPlan& p = *plans[0];
+  if (p.kind == kMmaTF32) launch_rmp_t<kMmaTF32, float>(plans, njobs, err, sms, s);
+  else if (p.out_bf16) launch_rmp_t<kMmaBF16, __nv_bfloat16>(plans, njobs, err, sms, s);
+  else launch_rmp_t<kMmaBF16, float>(plans, njobs, err, sms, s);
+}
+
+void pad_rows(const float* x, int e1, int64_t R, int ld, void* y, bool to_bf16, cudaStream_t s) {
+  const int64_t total = (int64_t)e1 * R;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  launch_begin(kClassVector, s);
+  if (to_bf16)
+    k_pad_rows<__nv_bfloat16><<<(int)blocks, 256, 0, s>>>(x, e1, R, ld,
+                                                          static_cast<__nv_bfloat16*>(y));
+  else
+    k_pad_rows<float><<<(int)blocks, 256, 0, s>>>(x, e1, R, ld, static_cast<float*>(y));
+  launch_end(kClassVector, s, 0.0, (double)total * (to_bf16 ? 6.0 : 8.0));
+}
+
+void launch_rmp(const RmpPlan& p, int* err, int sms, cudaStream_t s) {
+  const RmpPlan* one = &p;
+  launch_rmp_multi(&one, 1, err, sms, s);
+}
+
+}  // namespace shp

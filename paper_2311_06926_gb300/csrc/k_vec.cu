@@ -144,6 +144,7 @@ __global__ void k_multi_axpy(const double* __restrict__ V, int64_t ldv, int nvec
 // status codes mirror the public error codes
 constexpr int kStatusNonfinite = -3;
 constexpr int kStatusNotSpd = -4;
+constexpr int kStatusMaxit = -5;
 
 __global__ void k_minres_init(MinresState* st) {
   const double gg = st->gg;
@@ -196,9 +197,14 @@ __global__ void k_minres_lanczos(const double* __restrict__ Kz, const double* __
 
 // Givens QR of the Lanczos tridiagonal: apply the two previous rotations to the new column
 // (gamma, delta, gamma_new), form the new rotation, and update the residual estimate |eta|.
-__global__ void k_minres_scalars(MinresState* st, double tol) {
+__global__ void k_minres_scalars(MinresState* st) {
   st->pad = 0;                   // "update this iteration" flag read by the update kernel
   if (st->done) return;
+  if (st->iter >= st->cap) {     // iteration cap: keep the last iterate
+    st->status = kStatusMaxit;
+    st->done = 1;
+    return;
+  }
   const double gg = st->gg, delta = st->delta;
   if (!isfinite(gg) || !isfinite(delta)) {
     st->status = kStatusNonfinite;
@@ -223,6 +229,7 @@ __global__ void k_minres_scalars(MinresState* st, double tol) {
   st->xcoef = c_new * st->eta;
   st->eta = -s_new * st->eta;
   st->ratio = fabs(st->eta) / st->eta0;
+  if (st->ratios && st->iter < st->cap) st->ratios[st->iter] = st->ratio;
   st->c_old = c;
   st->c = c_new;
   st->s_old = s;
@@ -231,7 +238,7 @@ __global__ void k_minres_scalars(MinresState* st, double tol) {
   st->gamma = gamma_new;
   st->iter += 1;
   st->pad = 1;
-  if (st->ratio <= tol) st->done = 1;
+  if (st->ratio <= st->tol) st->done = 1;
 }
 
 // w_new = (z - a3 w_old - a2 w) / a1 over w_old; x += (c_new eta) w_new.
@@ -332,9 +339,9 @@ void minres_lanczos(const double* Kz, const double* v, double* vold, MinresState
   k_minres_lanczos<<<grid_for(n), kThreads, 0, s>>>(Kz, v, vold, st, n);
   launch_end(kClassVector, s, 0.0, 0.0);
 }
-void minres_scalars(MinresState* st, double tol, cudaStream_t s) {
+void minres_scalars(MinresState* st, cudaStream_t s) {
   launch_begin(kClassVector, s);
-  k_minres_scalars<<<1, 1, 0, s>>>(st, tol);
+  k_minres_scalars<<<1, 1, 0, s>>>(st);
   launch_end(kClassVector, s, 0.0, 0.0);
 }
 void minres_update(const double* z, double* wold, const double* w, double* x, MinresState* st,

@@ -1,0 +1,50 @@
+// Tensor-core rotating mode products (k_mma.cu).
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace shp {
+
+enum { kMmaTF32 = 0, kMmaBF16 = 1 };
+
+struct RmpArgs {
+  int R;            // rows (product of the two non-contracted extents)
+  int K;            // contracted extent
+  int m;            // output extent along the contracted direction
+  int npad;         // m rounded up to 16 (MMA N)
+  int e2, e3;       // the two non-contracted extents (r = j2 + e2 j3)
+  int ldy;          // output row pitch (elements) of the rotated output Y[j2 + ldy (j3 + e3 i)]
+  uint32_t idesc;   // tcgen05 instruction descriptor
+  float scale;      // eigenvalue scaling: divide by scale (lam_j2 + lam_j3 + lam_i) if lam_i
+  const float* lam_j2;
+  const float* lam_j3;
+  const float* lam_i;
+  float post;       // otherwise multiply by post
+  void* Y;
+};
+
+struct RmpPlan {
+  alignas(64) uint8_t map_x[128];    // CUtensorMap of the input rows
+  alignas(64) uint8_t map_op[128];   // CUtensorMap of the padded operator
+  int kind;
+  bool out_bf16;
+  RmpArgs args;
+};
+
+// Up to kMaxRmpJobs independent rotating products (e.g. the three velocity components) in one
+// persistent launch; every plan must have the same kind and output type.
+constexpr int kMaxRmpJobs = 4;
+
+int rmp_smem_bytes(int kind, int K, int npad);
+bool rmp_supported(int kind, int K, int m);
+bool make_map(void* map, const void* base, int kind, int cols, int64_t rows, int ld, int box_rows);
+uint32_t rmp_idesc(int kind, int npad);
+void launch_rmp(const RmpPlan& p, int* err, int sms, cudaStream_t s);
+void launch_rmp_multi(const RmpPlan* const* plans, int njobs, int* err, int sms, cudaStream_t s);
+
+// Copy a canonical float tensor (rows of e1 entries, R rows) into rows of pitch ld, converting
+// to bfloat16 if to_bf16.
+void pad_rows(const float* x, int e1, int64_t R, int ld, void* y, bool to_bf16, cudaStream_t s);
+
+}  // namespace shp

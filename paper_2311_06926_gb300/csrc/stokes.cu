@@ -20,7 +20,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <utility>
@@ -28,6 +30,7 @@
 
 #include "host_setup.h"
 #include "internal.h"
+#include "mma.h"
 #include "profile.h"
 #include "stokes_hp.h"
 
@@ -102,10 +105,20 @@ struct Ops {
   int64_t nvc = 0, nvel = 0, npres = 0;
   BandD<T> M{}, K{}, Mc{}, Tc{};
   const T *U_N = nullptr, *lam_N = nullptr, *U_T = nullptr, *lam_T = nullptr;
+  const T* invd = nullptr;   // FP64: 1 / (2 nu (l1 + l2 + l3)) per velocity entry
   T *tK = nullptr, *tM = nullptr, *tS = nullptr, *tR = nullptr;   // component-size temporaries
   T *f1 = nullptr, *f2 = nullptr;                                 // mode-product ping-pong
   T *delta = nullptr, *m1 = nullptr, *m2 = nullptr;               // pressure-size temporaries
   cudaStream_t s = nullptr;
+  // tensor-core fast diagonalisation (reduced precision only): per tensor (3 velocity components,
+  // pressure) a padded input copy and six rotating mode products
+  bool tc = false;
+  bool tc_bf16 = false;
+  int sms = 152;
+  int* tc_err = nullptr;
+  void* tc_p0[4] = {nullptr, nullptr, nullptr, nullptr};
+  int tc_ld0[4] = {0, 0, 0, 0};
+  RmpPlan* tc_plan = nullptr;   // [4][6], host memory
 
   Dims comp(int c) const {
     if (c == 0) return Dims{a, b, b};
@@ -113,15 +126,15 @@ struct Ops {
     return Dims{b, b, a};
   }
 
-  void pass(const T* X0, const BandD<T>& D0, T c0, const T* X1, const BandD<T>* D1, T c1, Dims in,
-            int axis, T* Y, const T* Z = nullptr, T cz = 0, const T* g = nullptr,
-            int gaxis = 0) const {
+  PassArgs<T> job(const T* X0, const BandD<T>& D0, T c0, const T* X1, const BandD<T>* D1, T c1,
+                  Dims in, int axis, T* Y, const T* Z = nullptr, T cz = 0, const T* g = nullptr,
+                  int gaxis = 0) const {
     PassArgs<T> p{};
     p.X0 = X0;
     p.D0 = D0;
     p.c0 = c0;
     p.X1 = X1;
-    if (D1) p.D1 = *D1; else p.D1 = D0;
+    p.D1 = D1 ? *D1 : D0;
     p.c1 = c1;
     p.nterms = X1 ? 2 : 1;
     p.Z = Z;
@@ -132,62 +145,94 @@ struct Ops {
     p.Y = Y;
     p.in = in;
     p.axis = axis;
-    band_pass<T>(p, s);
+    return p;
   }
 
-  // y = A'_cc u (+ D^T g along the own direction of component c if g != null)
-  void adiag(int c, const T* u, T* y, const T* g) const {
-    const Dims d = comp(c);
-    const int own = c + 1;
-    const int o1 = c == 0 ? 2 : 1;
-    const int o2 = c == 2 ? 2 : 3;
+  static int own_axis(int c) { return c + 1; }
+  static int first_other(int c) { return c == 0 ? 2 : 1; }
+  static int second_other(int c) { return c == 2 ? 2 : 3; }
+
+  // y_c = A'_cc u_c + D^T g along the own direction of c, for the three components at once:
+  // t_K = K u, t_M = M u along the own direction; s = nu Mc t_K + 2 nu Tc t_M and r = Mc t_M
+  // along the first other direction; y = Mc s + 2 nu Tc r (+ D^T g) along the second.
+  void adiag_all(const T* u, T* y, const T* g) const {
     const T nu2 = 2 * nu;
-    pass(u, K, 1, nullptr, nullptr, 0, d, own, tK);
-    pass(u, M, 1, nullptr, nullptr, 0, d, own, tM);
-    pass(tK, Mc, nu, tM, &Tc, nu2, d, o1, tS);
-    pass(tM, Mc, 1, nullptr, nullptr, 0, d, o1, tR);
-    pass(tS, Mc, 1, tR, &Tc, nu2, d, o2, y, nullptr, 0, g, own);
+    PassArgs<T> j[kMaxPassJobs];
+    for (int c = 0; c < 3; ++c) {
+      const int64_t o = c * nvc;
+      j[2 * c] = job(u + o, K, 1, nullptr, nullptr, 0, comp(c), own_axis(c), tK + o);
+      j[2 * c + 1] = job(u + o, M, 1, nullptr, nullptr, 0, comp(c), own_axis(c), tM + o);
+    }
+    band_pass_multi<T>(j, 6, s);
+    for (int c = 0; c < 3; ++c) {
+      const int64_t o = c * nvc;
+      j[2 * c] = job(tK + o, Mc, nu, tM + o, &Tc, nu2, comp(c), first_other(c), tS + o);
+      j[2 * c + 1] = job(tM + o, Mc, 1, nullptr, nullptr, 0, comp(c), first_other(c), tR + o);
+    }
+    band_pass_multi<T>(j, 6, s);
+    for (int c = 0; c < 3; ++c) {
+      const int64_t o = c * nvc;
+      j[c] = job(tS + o, Mc, 1, tR + o, &Tc, nu2, comp(c), second_other(c), y + o, nullptr, 0, g,
+                 own_axis(c));
+    }
+    band_pass_multi<T>(j, 3, s);
   }
 
-  // y = coef * M_q x (+ cz Z)
-  void mq(const T* x, T* y, T coef, const T* Z = nullptr, T cz = 0) const {
+  // y_k = coef_k M_q x_k for nvec <= 2 independent vectors (M_q = M-check^(x)3)
+  void mq(int nvec, const T* const* x, T* const* y, const T* coef) const {
     const Dims d{b, b, b};
-    pass(x, Mc, 1, nullptr, nullptr, 0, d, 1, f1);
-    pass(f1, Mc, 1, nullptr, nullptr, 0, d, 2, f2);
-    pass(f2, Mc, coef, nullptr, nullptr, 0, d, 3, y, Z, cz);
+    PassArgs<T> j[2];
+    for (int k = 0; k < nvec; ++k)
+      j[k] = job(x[k], Mc, 1, nullptr, nullptr, 0, d, 1, f1 + k * npres);
+    band_pass_multi<T>(j, nvec, s);
+    for (int k = 0; k < nvec; ++k)
+      j[k] = job(f1 + k * npres, Mc, 1, nullptr, nullptr, 0, d, 2, f2 + k * npres);
+    band_pass_multi<T>(j, nvec, s);
+    for (int k = 0; k < nvec; ++k)
+      j[k] = job(f2 + k * npres, Mc, coef[k], nullptr, nullptr, 0, d, 3, y[k]);
+    band_pass_multi<T>(j, nvec, s);
   }
 
   void apply_K(const T* x, T* y) const {
-    const T* u1 = x;
-    const T* u2 = x + nvc;
-    const T* u3 = x + 2 * nvc;
     const T* q = x + nvel;
     T* yq = y + nvel;
-    divergence<T>(u1, u2, u3, a, b, delta, s);
-    mq(delta, yq, 1);                 // B^T u = M_q D_div u
-    mq(q, m2, 1, yq, nu);             // g = M_q q + nu M_q D_div u
-    for (int c = 0; c < 3; ++c) adiag(c, x + c * nvc, y + c * nvc, m2);
+    // delta = D_div u, e = nu delta + q; B^T u = M_q delta; g = M_q e
+    divergence_plus<T>(x, x + nvc, x + 2 * nvc, a, b, delta, q, nu, m1, s);
+    const T* in[2] = {delta, m1};
+    T* out[2] = {yq, m2};
+    const T coef[2] = {1, 1};
+    mq(2, in, out, coef);
+    adiag_all(x, y, m2);
   }
 
   void apply_A(const T* x, T* y) const {
     divergence<T>(x, x + nvc, x + 2 * nvc, a, b, delta, s);
-    mq(delta, m2, nu);
-    for (int c = 0; c < 3; ++c) adiag(c, x + c * nvc, y + c * nvc, m2);
+    const T* in[1] = {delta};
+    T* out[1] = {m2};
+    const T coef[1] = {nu};
+    mq(1, in, out, coef);
+    adiag_all(x, y, m2);
   }
 
   void apply_B(const T* q, T* yu) const {   // B q = D_div^T M_q q
-    mq(q, m2, 1);
+    const T* in[1] = {q};
+    T* out[1] = {m2};
+    const T coef[1] = {1};
+    mq(1, in, out, coef);
     div_transpose<T>(m2, a, b, yu, yu + nvc, yu + 2 * nvc, 0, s);
   }
 
   void apply_Bt(const T* u, T* yq) const {  // B^T u = M_q D_div u
     divergence<T>(u, u + nvc, u + 2 * nvc, a, b, delta, s);
-    mq(delta, yq, 1);
+    const T* in[1] = {delta};
+    T* out[1] = {yq};
+    const T coef[1] = {1};
+    mq(1, in, out, coef);
   }
 
-  void mode(const T* X, T* Y, const T* U, int n, int trans, Dims in, int axis,
-            const T* l1 = nullptr, const T* l2 = nullptr, const T* l3 = nullptr, T scale = 1,
-            T post = 1) const {
+  ModeArgs<T> mjob(const T* X, T* Y, const T* U, int n, int trans, Dims in, int axis,
+                   const T* l1 = nullptr, const T* l2 = nullptr, const T* l3 = nullptr,
+                   T scale = 1, T post = 1) const {
     ModeArgs<T> m{};
     m.X = X;
     m.Y = Y;
@@ -202,42 +247,95 @@ struct Ops {
     m.lam3 = l3;
     m.scale = scale;
     m.post = post;
-    mode_product<T>(m, s);
+    return m;
   }
 
-  // fast diagonalisation of A_cc (App. A.4): y = (U3 U2 U1) diag(1/(2 nu sum lam)) (U3 U2 U1)^T x
-  void fd_comp(int c, const T* x, T* y) const {
-    const Dims d = comp(c);
-    const T* U[3];
-    const T* L[3];
-    int n[3];
-    for (int k = 0; k < 3; ++k) {
-      const bool own = k == c;
-      U[k] = own ? U_N : U_T;
-      L[k] = own ? lam_N : lam_T;
-      n[k] = own ? a : b;
+  // fast diagonalisation of the three diagonal blocks A_cc (App. A.4), all components per launch:
+  // y_c = (U3 U2 U1) diag(1 / (2 nu (l1 + l2 + l3))) (U3 U2 U1)^T x_c, with (U, l) = (U_N, lam_N)
+  // in the own direction of c and (U_T, lam_T) in the other two.
+  // tensor t (0..2 velocity components, 3 pressure): canonical x -> canonical y
+  void tc_fd(int t, const float* x, float* y) const {
+    const Dims d = t < 3 ? comp(t) : Dims{b, b, b};
+    pad_rows(x, d.n1, (int64_t)d.n2 * d.n3, tc_ld0[t], tc_p0[t], tc_bf16, s);
+    for (int st = 0; st < 6; ++st) {
+      RmpPlan p = tc_plan[t * 6 + st];
+      if (st == 5) p.args.Y = y;
+      launch_rmp(p, tc_err, sms, s);
     }
-    mode(x, f1, U[0], n[0], 1, d, 1);
-    mode(f1, f2, U[1], n[1], 1, d, 2);
-    mode(f2, f1, U[2], n[2], 1, d, 3, L[0], L[1], L[2], 2 * nu);
-    mode(f1, f2, U[2], n[2], 0, d, 3);
-    mode(f2, f1, U[1], n[1], 0, d, 2);
-    mode(f1, y, U[0], n[0], 0, d, 1);
   }
 
   void fd_V(const T* x, T* y) const {
-    for (int c = 0; c < 3; ++c) fd_comp(c, x + c * nvc, y + c * nvc);
+    if (tc) {
+      // the three components share each of the six tensor-core launches
+      for (int c = 0; c < 3; ++c) {
+        const Dims d = comp(c);
+        pad_rows(reinterpret_cast<const float*>(x + c * nvc), d.n1, (int64_t)d.n2 * d.n3,
+                 tc_ld0[c], tc_p0[c], tc_bf16, s);
+      }
+      for (int st = 0; st < 6; ++st) {
+        RmpPlan p[3];
+        const RmpPlan* pp[3];
+        for (int c = 0; c < 3; ++c) {
+          p[c] = tc_plan[c * 6 + st];
+          if (st == 5) p[c].args.Y = reinterpret_cast<float*>(y + c * nvc);
+          pp[c] = &p[c];
+        }
+        launch_rmp_multi(pp, 3, tc_err, sms, s);
+      }
+      return;
+    }
+    const T* U[3][3];
+    const T* L[3][3];
+    int n[3][3];
+    for (int c = 0; c < 3; ++c)
+      for (int k = 0; k < 3; ++k) {
+        const bool own = k == c;
+        U[c][k] = own ? U_N : U_T;
+        L[c][k] = own ? lam_N : lam_T;
+        n[c][k] = own ? a : b;
+      }
+    ModeArgs<T> j[3];
+    const T* src;
+    T* dst;
+    // forward: U1^T, U2^T, U3^T (with the eigenvalue scaling); backward: U3, U2, U1
+    const int axis_of[6] = {1, 2, 3, 3, 2, 1};
+    const int trans_of[6] = {1, 1, 1, 0, 0, 0};
+    for (int st = 0; st < 6; ++st) {
+      for (int c = 0; c < 3; ++c) {
+        const int64_t o = c * nvc;
+        src = st == 0 ? x + o : ((st % 2) ? f1 + o : f2 + o);
+        dst = st == 5 ? y + o : ((st % 2) ? f2 + o : f1 + o);
+        const int k = axis_of[st] - 1;
+        if (st == 2) {
+          j[c] = mjob(src, dst, U[c][k], n[c][k], trans_of[st], comp(c), axis_of[st], L[c][0],
+                      L[c][1], L[c][2], 2 * nu);
+          j[c].invd = invd ? invd + o : nullptr;
+        }
+        else
+          j[c] = mjob(src, dst, U[c][k], n[c][k], trans_of[st], comp(c), axis_of[st]);
+      }
+      mode_product_multi<T>(j, 3, s);
+    }
+  }
+
+  void mode(const T* X, T* Y, const T* U, int n, int trans, Dims in, int axis, T post = 1) const {
+    ModeArgs<T> m = mjob(X, Y, U, n, trans, in, axis, nullptr, nullptr, nullptr, 1, post);
+    mode_product<T>(m, s);
   }
 
   // pressure block: y = 2 nu (M-check^-1)^(x)3 x = 2 nu (U_T U_T^T)^(x)3 x
   void minv_Q(const T* x, T* y) const {
+    if (tc) {
+      tc_fd(3, reinterpret_cast<const float*>(x), reinterpret_cast<float*>(y));
+      return;
+    }
     const Dims d{b, b, b};
     mode(x, f1, U_T, b, 1, d, 1);
     mode(f1, f2, U_T, b, 1, d, 2);
     mode(f2, f1, U_T, b, 1, d, 3);
     mode(f1, f2, U_T, b, 0, d, 3);
     mode(f2, f1, U_T, b, 0, d, 2);
-    mode(f1, y, U_T, b, 0, d, 1, nullptr, nullptr, nullptr, 1, 2 * nu);
+    mode(f1, y, U_T, b, 0, d, 1, 2 * nu);
   }
 };
 
@@ -335,6 +433,15 @@ struct stokes_ctx {
   std::vector<double> ratios;
   std::string err;
   Profiler* prof = nullptr;
+  bool prof_on = false;
+  bool use_graphs = true;
+  double* xi = nullptr;           // MINRES iterate (context-owned, so captured graphs are reusable)
+  double* ratio_dev = nullptr;    // per-iteration convergence ratios
+  std::map<int, cudaGraphExec_t> minres_graphs;
+  std::vector<RmpPlan> tc_plans;
+  ~stokes_ctx() {
+    for (auto& kv : minres_graphs) cudaGraphExecDestroy(kv.second);
+  }
 };
 
 namespace {
@@ -375,16 +482,124 @@ void init_ops(stokes_ctx* c, Ops<T>& o, const Band& M, const Band& K, const Band
   o.lam_N = upload<T>(ar, lN, s);
   o.U_T = upload<T>(ar, UT, s);
   o.lam_T = upload<T>(ar, lT, s);
-  const size_t big = (size_t)c->b * c->b * c->b;   // >= a b^2
-  o.tK = ar.alloc<T>(big);
-  o.tM = ar.alloc<T>(big);
-  o.tS = ar.alloc<T>(big);
-  o.tR = ar.alloc<T>(big);
-  o.f1 = ar.alloc<T>(big);
-  o.f2 = ar.alloc<T>(big);
-  o.delta = ar.alloc<T>(big);
-  o.m1 = ar.alloc<T>(big);
-  o.m2 = ar.alloc<T>(big);
+  const size_t pres = (size_t)c->npres, vel = (size_t)c->nvel;
+  const size_t ping = std::max(vel, 2 * pres);   // all velocity components, or two pressures
+  o.tK = ar.alloc<T>(vel);
+  o.tM = ar.alloc<T>(vel);
+  o.tS = ar.alloc<T>(vel);
+  o.tR = ar.alloc<T>(vel);
+  o.f1 = ar.alloc<T>(ping);
+  o.f2 = ar.alloc<T>(ping);
+  o.delta = ar.alloc<T>(pres);
+  o.m1 = ar.alloc<T>(pres);
+  o.m2 = ar.alloc<T>(pres);
+}
+
+int rup(int x, int m) { return (x + m - 1) / m * m; }
+
+// Tensor-core fast diagonalisation: padded operators (rows npad = n rounded to 16, row pitch
+// kpad = n rounded to one 128-byte chunk), rotation buffers and the 4 x 6 TMA plans.
+void init_tc(stokes_ctx* c, const Dense& UN, const std::vector<double>& lN, const Dense& UT,
+             const std::vector<double>& lT, int kind) {
+  Ops<float>& o = c->of;
+  const int a = c->a, b = c->b;
+  if (!rmp_supported(kind, a, a) || !rmp_supported(kind, b, b)) return;   // CUDA-core fallback
+  const bool bf = kind == kMmaBF16;
+  const int elem = bf ? 2 : 4;
+  const int kchunk = 128 / elem;
+  const int align = 16 / elem;
+  Arena& ar = c->arena;
+  cudaStream_t s = c->stream;
+  // padded operators: op[0] = U_N^T, op[1] = U_N, op[2] = U_T^T, op[3] = U_T (Op[i][j] rows)
+  const Dense* srcs[4] = {&UN, &UN, &UT, &UT};
+  const bool transp[4] = {true, false, true, false};
+  void* op[4];
+  int npad_of[4], kpad_of[4];
+  for (int k = 0; k < 4; ++k) {
+    const int n = srcs[k]->rows;
+    const int npad = rup(n, 16), kpad = rup(n, kchunk);
+    npad_of[k] = npad;
+    kpad_of[k] = kpad;
+    std::vector<float> hf((size_t)npad * kpad, 0.f);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j)
+        hf[(size_t)i * kpad + j] = (float)(transp[k] ? (*srcs[k])(j, i) : (*srcs[k])(i, j));
+    if (bf) {
+      std::vector<uint16_t> hb(hf.size());
+      for (size_t i = 0; i < hf.size(); ++i) {   // round to nearest even
+        uint32_t u;
+        std::memcpy(&u, &hf[i], 4);
+        u += 0x7FFF + ((u >> 16) & 1);
+        hb[i] = (uint16_t)(u >> 16);
+      }
+      op[k] = ar.alloc<uint16_t>(hb.size());
+      ck(cudaMemcpyAsync(op[k], hb.data(), hb.size() * 2, cudaMemcpyHostToDevice, s), "op");
+    } else {
+      op[k] = ar.alloc<float>(hf.size());
+      ck(cudaMemcpyAsync(op[k], hf.data(), hf.size() * 4, cudaMemcpyHostToDevice, s), "op");
+    }
+    ck(cudaStreamSynchronize(s), "op");
+  }
+  const size_t slot = (size_t)rup(rup(b, align) * b * b, 64);   // elements per rotation slot
+  uint8_t* P0 = reinterpret_cast<uint8_t*>(ar.alloc<float>(slot * 4 * elem / 4 + 64));
+  uint8_t* F1 = reinterpret_cast<uint8_t*>(ar.alloc<float>(slot * 4 * elem / 4 + 64));
+  uint8_t* F2 = reinterpret_cast<uint8_t*>(ar.alloc<float>(slot * 4 * elem / 4 + 64));
+  ck(cudaMemsetAsync(P0, 0, slot * 4 * elem, s), "memset");
+  ck(cudaMemsetAsync(F1, 0, slot * 4 * elem, s), "memset");
+  ck(cudaMemsetAsync(F2, 0, slot * 4 * elem, s), "memset");
+  o.tc_err = ar.alloc<int>(1);
+  ck(cudaMemsetAsync(o.tc_err, 0, sizeof(int), s), "memset");
+  int dev = 0;
+  ck(cudaGetDevice(&dev), "device");
+  ck(cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev), "sms");
+  c->tc_plans.assign(24, RmpPlan{});
+  for (int t = 0; t < 4; ++t) {
+    const Dims d = t < 3 ? o.comp(t) : Dims{b, b, b};
+    const int ext[3] = {d.n1, d.n2, d.n3};
+    const bool own[3] = {t == 0, t == 1, t == 2};
+    const float* lam[3];
+    for (int k = 0; k < 3; ++k) lam[k] = own[k] ? o.lam_N : o.lam_T;
+    uint8_t* bufs_in[6] = {P0, F1, F2, F1, F2, F1};
+    uint8_t* bufs_out[6] = {F1, F2, F1, F2, F1, nullptr};
+    o.tc_p0[t] = P0 + (size_t)t * slot * elem;
+    o.tc_ld0[t] = rup(ext[0], align);
+    for (int st = 0; st < 6; ++st) {
+      const int ax = st % 3;   // contracted direction: x1, x2, x3, x1, x2, x3
+      const int e1 = ext[ax], e2 = ext[(ax + 1) % 3], e3 = ext[(ax + 2) % 3];
+      const bool fwd = st < 3;
+      // operator index: velocity own direction uses U_N, the rest U_T (pressure: always U_T)
+      const int base_op = (t < 3 && own[ax]) ? 0 : 2;
+      const int opk = base_op + (fwd ? 0 : 1);
+      RmpPlan& p = c->tc_plans[t * 6 + st];
+      p.kind = kind;
+      p.out_bf16 = bf && st < 5;
+      RmpArgs& ra = p.args;
+      ra.R = e2 * e3;
+      ra.K = e1;
+      ra.m = e1;
+      ra.npad = npad_of[opk];
+      ra.e2 = e2;
+      ra.e3 = e3;
+      ra.ldy = st < 5 ? rup(e2, align) : e2;
+      ra.idesc = rmp_idesc(kind, ra.npad);
+      ra.scale = (float)(2.0 * c->nu);
+      ra.post = 1.f;
+      if (st == 2 && t < 3) {
+        ra.lam_j2 = lam[0];
+        ra.lam_j3 = lam[1];
+        ra.lam_i = lam[2];
+      }
+      if (st == 5 && t == 3) ra.post = (float)(2.0 * c->nu);
+      ra.Y = bufs_out[st] ? (void*)(bufs_out[st] + (size_t)t * slot * elem) : nullptr;
+      const void* in = bufs_in[st] + (size_t)t * slot * elem;
+      if (!make_map(p.map_x, in, kind, e1, (int64_t)e2 * e3, rup(e1, align), 128) ||
+          !make_map(p.map_op, op[opk], kind, e1, ra.npad, kpad_of[opk], ra.npad))
+        throw SetupError{"tensor map encoding failed"};
+    }
+  }
+  o.tc_plan = c->tc_plans.data();
+  o.tc_bf16 = bf;
+  o.tc = true;
 }
 
 template <typename T>
@@ -458,65 +673,96 @@ double true_residual(stokes_ctx* c, const double* f, const double* x, double* tm
   return ff > 0 ? std::sqrt(rr / ff) : std::sqrt(rr);
 }
 
+// One MINRES iteration (Paige-Saunders recurrences with all scalars on the device). The buffer
+// roles rotate with period two, so two consecutive iterations form a fixed launch sequence.
+void minres_iteration(stokes_ctx* c, double* vold, double* v, double* z, double* zn, double* wold,
+                      double* w, double* Kz, double* x) {
+  const int64_t n = c->ntot;
+  cudaStream_t s = c->stream;
+  minres_scale_z(z, c->st, n, s);
+  c->od.apply_K(z, Kz);
+  dot<double>(Kz, z, n, c->partials, &c->st->delta, s);
+  minres_lanczos(Kz, v, vold, c->st, n, s);            // v_new over v_old
+  apply_prec(c, c->order, c->steps, vold, zn);
+  dot<double>(zn, vold, n, c->partials, &c->st->gg, s);
+  minres_scalars(c->st, s);
+  minres_update(z, wold, w, x, c->st, n, s);           // w_new over w_old, x += ...
+}
+
+void minres_pair(stokes_ctx* c) {
+  double** k = c->kv;
+  // roles: vold, v, z, zn, wold, w; Kz = kv[4]; iterate into the context buffer xi
+  minres_iteration(c, k[0], k[1], k[2], k[3], k[5], k[6], k[4], c->xi);
+  minres_iteration(c, k[1], k[0], k[3], k[2], k[6], k[5], k[4], c->xi);
+}
+
+bool profiling_active(stokes_ctx* c) { return c->prof_on; }
+
 int run_minres(stokes_ctx* c, const double* f, double tol, double* x, int* iters) {
   const int64_t n = c->ntot;
   cudaStream_t s = c->stream;
-  double* vold = c->kv[0];
-  double* v = c->kv[1];
-  double* z = c->kv[2];
-  double* zn = c->kv[3];
-  double* Kz = c->kv[4];
-  double* wold = c->kv[5];
-  double* w = c->kv[6];
-  fill_zero(x, n * sizeof(double), s);
-  fill_zero(vold, n * sizeof(double), s);
-  fill_zero(wold, n * sizeof(double), s);
-  fill_zero(w, n * sizeof(double), s);
-  copy_async(v, f, n * sizeof(double), s);
-  apply_prec(c, c->order, c->steps, v, z);
-  dot<double>(z, v, n, c->partials, &c->st->gg, s);
+  double** k = c->kv;
+  fill_zero(c->xi, n * sizeof(double), s);
+  fill_zero(k[0], n * sizeof(double), s);
+  fill_zero(k[5], n * sizeof(double), s);
+  fill_zero(k[6], n * sizeof(double), s);
+  copy_async(k[1], f, n * sizeof(double), s);
+  MinresState* h = c->st_host;
+  std::memset(h, 0, sizeof(MinresState));
+  h->tol = tol;
+  h->ratios = c->ratio_dev;
+  h->cap = c->opts.maxit;
+  ck(cudaMemcpyAsync(c->st, h, sizeof(MinresState), cudaMemcpyHostToDevice, s), "state");
+  apply_prec(c, c->order, c->steps, k[1], k[2]);
+  dot<double>(k[2], k[1], n, c->partials, &c->st->gg, s);
   minres_init(c->st, s);
   check_launch("minres init");
-  c->ratios.clear();
-  ck(cudaMemcpyAsync(c->st_host, c->st, sizeof(MinresState), cudaMemcpyDeviceToHost, s), "state");
+  ck(cudaMemcpyAsync(h, c->st, sizeof(MinresState), cudaMemcpyDeviceToHost, s), "state");
   ck(cudaStreamSynchronize(s), "sync");
-  if (c->st_host->status != 0) {
-    *iters = 0;
-    return c->st_host->status;
-  }
-  if (c->st_host->done) {
-    *iters = 0;
-    return STOKES_OK;
-  }
-  for (int it = 0; it < c->opts.maxit; ++it) {
-    minres_scale_z(z, c->st, n, s);
-    c->od.apply_K(z, Kz);
-    dot<double>(Kz, z, n, c->partials, &c->st->delta, s);
-    minres_lanczos(Kz, v, vold, c->st, n, s);
-    apply_prec(c, c->order, c->steps, vold, zn);
-    dot<double>(zn, vold, n, c->partials, &c->st->gg, s);
-    minres_scalars(c->st, tol, s);
-    minres_update(z, wold, w, x, c->st, n, s);
-    check_launch("minres iteration");
-    std::swap(vold, v);
-    std::swap(z, zn);
-    std::swap(wold, w);
-    ck(cudaMemcpyAsync(c->st_host, c->st, sizeof(MinresState), cudaMemcpyDeviceToHost, s),
-       "state");
-    ck(cudaStreamSynchronize(s), "sync");
-    const MinresState& h = *c->st_host;
-    if (h.pad) c->ratios.push_back(h.ratio);
-    if (h.status != 0) {
-      *iters = h.iter;
-      return h.status;
+  c->ratios.clear();
+  int rc = STOKES_OK;
+  if (h->status != 0) {
+    rc = h->status;
+  } else if (!h->done) {
+    // two iterations per replay of a captured graph (or per direct launch sequence when a
+    // profiler is recording events or graphs are disabled)
+    cudaGraphExec_t exec = nullptr;
+    const bool use_graph = c->use_graphs && !profiling_active(c);
+    if (use_graph) {
+      const int key = c->order * 16 + c->steps;
+      auto it = c->minres_graphs.find(key);
+      if (it == c->minres_graphs.end()) {
+        cudaGraph_t g = nullptr;
+        ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
+        minres_pair(c);
+        ck(cudaStreamEndCapture(s, &g), "capture");
+        ck(cudaGraphInstantiate(&exec, g, 0), "instantiate");
+        cudaGraphDestroy(g);
+        c->minres_graphs[key] = exec;
+      } else {
+        exec = it->second;
+      }
     }
-    if (h.done) {
-      *iters = h.iter;
-      return STOKES_OK;
+    for (int pair = 0; 2 * pair < c->opts.maxit; ++pair) {
+      if (use_graph) ck(cudaGraphLaunch(exec, s), "graph launch");
+      else minres_pair(c);
+      check_launch("minres iteration");
+      ck(cudaMemcpyAsync(h, c->st, sizeof(MinresState), cudaMemcpyDeviceToHost, s), "state");
+      ck(cudaStreamSynchronize(s), "sync");
+      if (h->status != 0 || h->done) break;
     }
+    if (h->status != 0) rc = h->status;
+    else if (!h->done) rc = STOKES_ERR_MAXIT;
   }
-  *iters = c->st_host->iter;
-  return STOKES_ERR_MAXIT;
+  *iters = h->iter;
+  if (h->iter > 0) {
+    c->ratios.resize(std::min(h->iter, c->opts.maxit));
+    ck(cudaMemcpyAsync(c->ratios.data(), c->ratio_dev, c->ratios.size() * sizeof(double),
+                       cudaMemcpyDeviceToHost, s), "ratios");
+  }
+  copy_async(x, c->xi, n * sizeof(double), s);
+  ck(cudaStreamSynchronize(s), "sync");
+  return rc;
 }
 
 // Right-preconditioned flexible GMRES (Saad 1993) with classical Gram-Schmidt applied twice
@@ -633,6 +879,15 @@ int run_fgmres(stokes_ctx* c, const double* f, double tol, double* x, int* iters
   return STOKES_ERR_MAXIT;
 }
 
+// the tensor-core pipeline raises this flag if one of its bounded waits ran out
+bool tc_failed(stokes_ctx* c) {
+  if (!c->of.tc) return false;
+  int h = 0;
+  ck(cudaMemcpyAsync(&h, c->of.tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag");
+  ck(cudaStreamSynchronize(c->stream), "flag");
+  return h != 0;
+}
+
 int solve_impl(stokes_ctx* c, const double* rhs, double tol, double* x, int* iterations,
                double* final_rel_res) {
   int its = 0;
@@ -643,6 +898,10 @@ int solve_impl(stokes_ctx* c, const double* rhs, double tol, double* x, int* ite
   const double rr = true_residual(c, rhs, x, c->kv[7]);
   if (iterations) *iterations = its;
   if (final_rel_res) *final_rel_res = rr;
+  if (tc_failed(c)) {
+    c->err = "tensor-core pipeline wait timed out";
+    return STOKES_ERR_CUDA;
+  }
   if (rc == STOKES_ERR_MAXIT) c->err = "iteration cap reached";
   else if (rc == STOKES_ERR_NONFINITE) c->err = "non-finite value in the Krylov recurrence";
   else if (rc == STOKES_ERR_NOT_SPD) c->err = "preconditioner is not positive definite";
@@ -724,9 +983,26 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
     const Band bM = to_band(u.M, 1e-15), bK = to_band(u.K, 1e-15);
     const Band bMc = to_band(u.Mc, 1e-15), bTc = to_band(u.Tc, 1e-15);
     init_ops<double>(c, c->od, bM, bK, bMc, bTc, UN.v, lN, UT.v, lT);
+    {
+      // reciprocal eigenvalue sums of the fast diagonalisation, one per velocity entry
+      std::vector<double> inv((size_t)c->nvel);
+      for (int comp = 0; comp < 3; ++comp) {
+        const Dims d = c->od.comp(comp);
+        const std::vector<double>* l[3];
+        for (int k = 0; k < 3; ++k) l[k] = k == comp ? &lN : &lT;
+        size_t o = (size_t)comp * c->nvc;
+        for (int i3 = 0; i3 < d.n3; ++i3)
+          for (int i2 = 0; i2 < d.n2; ++i2)
+            for (int i1 = 0; i1 < d.n1; ++i1)
+              inv[o++] = 1.0 / (2.0 * nu * ((*l[0])[i1] + (*l[1])[i2] + (*l[2])[i3]));
+      }
+      c->od.invd = upload<double>(c->arena, inv, c->stream);
+    }
     init_hp<double>(c, c->hd, c->od);
     if (reduced(c)) {
       init_ops<float>(c, c->of, bM, bK, bMc, bTc, UN.v, lN, UT.v, lT);
+      if (o.precision == STOKES_PREC_TF32 || o.precision == STOKES_PREC_BF16)
+        init_tc(c, UN, lN, UT, lT, o.precision == STOKES_PREC_BF16 ? kMmaBF16 : kMmaTF32);
       init_hp<float>(c, c->hf, c->of);
       c->xf = c->arena.alloc<float>(c->ntot);
       c->yf = c->arena.alloc<float>(c->ntot);
@@ -750,6 +1026,9 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
       c->V = c->arena.alloc<double>((size_t)(o.restart + 1) * c->ntot);
       c->Z = c->arena.alloc<double>((size_t)o.restart * c->ntot);
     }
+    c->xi = c->arena.alloc<double>(c->ntot);
+    c->ratio_dev = c->arena.alloc<double>(o.maxit);
+    if (const char* e = std::getenv("STOKES_NO_GRAPHS")) c->use_graphs = e[0] == '0';
     c->io_rhs = c->arena.alloc<double>(c->ntot);
     c->io_x = c->arena.alloc<double>(c->ntot);
     ck(cudaStreamSynchronize(c->stream), "setup");
@@ -814,6 +1093,7 @@ int stokes_apply_hyperpower(stokes_t c, int order, int steps, const double* x, d
   try {
     apply_prec(c, order, steps, x, y);
     check_launch("apply_hyperpower");
+    if (tc_failed(c)) return fail(c, STOKES_ERR_CUDA, "tensor-core pipeline wait timed out");
   } catch (const CudaError& e) {
     return cuda_fail(c, e);
   }
@@ -933,6 +1213,7 @@ int stokes_profile_begin(stokes_t c) {
   if (!c) return STOKES_ERR_ARG;
   if (!c->prof) c->prof = profiler_create();
   profiler_activate(c->prof);
+  c->prof_on = true;
   return STOKES_OK;
 }
 
@@ -942,6 +1223,7 @@ int stokes_profile_end(stokes_t c, stokes_kernel_stat* out, int capacity) {
   double ms[kNumClasses], fl[kNumClasses], by[kNumClasses];
   profiler_collect(c->prof, l, ms, fl, by);
   profiler_activate(nullptr);
+  c->prof_on = false;
   const int k = std::min(capacity, (int)kNumClasses);
   for (int i = 0; i < k; ++i) {
     out[i].kernel_class = i;

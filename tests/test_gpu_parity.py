@@ -163,3 +163,54 @@ def test_mixed_precision_fgmres_accuracy(prec):
     assert rr <= 1e-8 * 1.01
     err = np.linalg.norm(host(x) - xo) / np.linalg.norm(xo)
     assert err <= kappa * rr
+
+
+# Reduced-precision base preconditioner against the FP64 oracle. The bound is the relative
+# rounding of the operand format (FP32 2^-24, TF32 2^-11, BF16 2^-8) times the growth through
+# six dense contractions with orthonormal-like eigenvector matrices; the tolerances below are
+# that unit roundoff times 20.
+@pytest.mark.parametrize("prec,tol", [("fp32", 20 * 2.0 ** -24 * 64), ("tf32", 20 * 2.0 ** -11),
+                                      ("bf16", 20 * 2.0 ** -8)])
+@pytest.mark.parametrize("n,p", [(2, 1), (8, 2), (13, 3), (30, 3)])
+def test_reduced_precision_base_preconditioner(prec, tol, n, p):
+    S, base, Kop, F = oracle(n, p)
+    G = _ctx(n, p, 1.0, precision=prec)
+    x = synthetic.random_vector(S.size, 400 + n)
+    ref = np.concatenate([base.pv0_inv(x[:S.n_vel]), base.pq0_inv(x[S.n_vel:])])
+    err = relerr(host(G.apply_P(dev(x))), ref)
+    G.close()
+    assert err < tol, err
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("s", [1, 2])
+def test_reduced_precision_fgmres(prec, s):
+    """Mixed-precision form: reduced-precision preconditioner inside FP64 flexible GMRES reaches
+    the FP64 tolerance; error vs the direct solve within kappa(K) times the residual."""
+    n, p = 6, 2
+    S, base, Kop, F = oracle(n, p)
+    f = S.rhs_lid(1.0)
+    xo = _direct(S, f)
+    kappa = _condition_number(S)
+    G = _ctx(n, p, 1.0, precision=prec)
+    G.set_preconditioner(2, s)
+    x, it, rr, rc = G.solve(dev(f), 1e-8)
+    G.close()
+    assert rr <= 1e-8 * 1.01
+    assert np.linalg.norm(host(x) - xo) / np.linalg.norm(xo) <= kappa * rr
+
+
+@pytest.mark.parametrize("n,p", [(2, 1), (9, 3), (30, 3)])
+@pytest.mark.parametrize("q,s", [(2, 1), (2, 2), (3, 1)])
+def test_fp32_hyperpower_exercises_banded_passes(n, p, q, s):
+    """FP32 preconditioner (CUDA-core fast diagonalisation, FP32 banded A, B, B^T passes inside
+    the recursion) against the FP64 oracle; bound: 2^-24 times the growth of q^s nested
+    applications (<= 64 here) times 64."""
+    S, base, Kop, F = oracle(n, p)
+    G = _ctx(n, p, 1.0, precision="fp32")
+    x = synthetic.random_vector(S.size, 500 + n + 10 * q + s)
+    ref = np.concatenate([hyperpower_V(base, x[:S.n_vel], q, s),
+                          hyperpower_Q(base, x[S.n_vel:], q, s, "inner")])
+    err = relerr(host(G.apply_hyperpower(q, s, dev(x))), ref)
+    G.close()
+    assert err < 2.0 ** -24 * 64 * 64, err
