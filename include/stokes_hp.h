@@ -118,6 +118,22 @@ int stokes_rhs_cavity(stokes_t ctx, double lid_speed, double* f);
 int stokes_rhs_body(stokes_t ctx, int n_modes, const double* coef, const int* waves,
                     int accumulate, double* f);
 
+/* f = Nitsche load (Sec. 3.1, sigma with boundary data; the cavity lid of Sec. 5 generalised to
+ * a profile) of a lid velocity (g(x1), 0, 0) on the face x2 = 1 with g = sum_k theta[k] S_k, S_k
+ * the ncoef >= 4 cubic B-splines of an open uniform knot vector on [0, 1]. theta: HOST array of
+ * ncoef entries. theta = (U, ..., U) gives stokes_rhs_cavity(U). If accumulate != 0 the load is
+ * added to f. f: device, n_vel + n_pres. */
+int stokes_rhs_lid_profile(stokes_t ctx, int ncoef, const double* theta, int accumulate,
+                           double* f);
+
+/* y = M_V x, the L2 Gram (mass) matrix of the velocity basis (App. B.3 mass matrices, one
+ * Kronecker product per component). x, y: device, n_vel. */
+int stokes_apply_mass(stokes_t ctx, const double* x, double* y);
+
+/* *result (HOST) = <x, y> over n float64 entries of device vectors, by the deterministic
+ * fixed-order reduction of the solver. Synchronizes the context's stream. */
+int stokes_dot(stokes_t ctx, const double* x, const double* y, int64_t n, double* result);
+
 /* Solve K x = rhs with the selected preconditioner and solver to relative tolerance tol
  * (MINRES: ||r||_{P^-1} / ||rhs||_{P^-1}; FGMRES: ||r||_2 / ||rhs||_2), starting from x = 0,
  * then shift the pressure to zero mean. iterations and final_rel_res (the true

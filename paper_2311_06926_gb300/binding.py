@@ -66,6 +66,9 @@ def load_library(path=None):
         "stokes_apply_hyperpower": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp]),
         "stokes_rhs_cavity": (ctypes.c_int, [vp, ctypes.c_double, vp]),
         "stokes_rhs_body": (ctypes.c_int, [vp, ctypes.c_int, dp, ip, ctypes.c_int, vp]),
+        "stokes_rhs_lid_profile": (ctypes.c_int, [vp, ctypes.c_int, dp, ctypes.c_int, vp]),
+        "stokes_apply_mass": (ctypes.c_int, [vp, vp, vp]),
+        "stokes_dot": (ctypes.c_int, [vp, vp, vp, ctypes.c_int64, dp]),
         "stokes_solve": (ctypes.c_int, [vp, vp, ctypes.c_double, vp, ip, dp]),
         "stokes_solve_host": (ctypes.c_int, [vp, vp, ctypes.c_double, vp, ip, dp]),
         "stokes_last_ratios": (ctypes.c_int, [vp, dp, ctypes.c_int]),
@@ -212,6 +215,32 @@ class Stokes:
             waves.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(accumulate),
             _ptr(self._vec(f, self.size))))
         return f
+
+    def rhs_lid_profile(self, theta, accumulate=False, out=None):
+        import numpy as np
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        f = out if out is not None else self.empty()
+        self._check(self._call(self.lib.stokes_rhs_lid_profile, self.h, int(th.size),
+                               th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(accumulate),
+                               _ptr(self._vec(f, self.size))))
+        return f
+
+    def apply_mass(self, x, out=None):
+        y = out if out is not None else self.empty(self.n_vel)
+        self._check(self._call(self.lib.stokes_apply_mass, self.h, _ptr(self._vec(x, self.n_vel)),
+                               _ptr(self._vec(y, self.n_vel))))
+        return y
+
+    def dot(self, x, y):
+        if x.numel() != y.numel():
+            raise ValueError("dot: size mismatch")
+        r = ctypes.c_double()
+        for t in (x, y):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ValueError("dot: expected contiguous float64 CUDA tensors")
+        self._check(self._call(self.lib.stokes_dot, self.h, _ptr(x), _ptr(y), x.numel(),
+                               ctypes.byref(r)))
+        return r.value
 
     def solve(self, rhs, tol=1e-8, out=None, raise_on_error=True):
         """Returns (x, iterations, true relative residual, status code)."""

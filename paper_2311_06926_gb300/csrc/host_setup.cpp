@@ -347,6 +347,31 @@ std::vector<double> sine_load(const Univariate& u, int k, bool use_N) {
 }  // namespace
 
 std::vector<double> sine_load_N(const Univariate& u, int k) { return sine_load(u, k, true); }
+
+Dense lid_profile_matrix(const Univariate& u, int ncoef) {
+  const int n = u.n, p = u.p, nel = ncoef - 3;
+  const std::vector<double> tN = open_knots(n, p + 1), tS = open_knots(nel, 3);
+  std::vector<double> brk;
+  for (int e = 0; e <= n; ++e) brk.push_back((double)e / n);
+  for (int e = 0; e <= nel; ++e) brk.push_back((double)e / nel);
+  std::sort(brk.begin(), brk.end());
+  std::vector<double> uniq;
+  for (double x : brk)
+    if (uniq.empty() || x - uniq.back() > 1e-14) uniq.push_back(x);
+  std::vector<double> g, gw;
+  gauss_legendre(p + 6, g, gw);
+  Dense G(u.a, ncoef);
+  for (size_t e = 0; e + 1 < uniq.size(); ++e) {
+    const double lo = uniq[e], hi = uniq[e + 1];
+    for (size_t q = 0; q < g.size(); ++q) {
+      const double x = 0.5 * (lo + hi) + 0.5 * (hi - lo) * g[q], w = 0.5 * (hi - lo) * gw[q];
+      const std::vector<double> Nv = bspline_values(tN, p + 1, x), Sv = bspline_values(tS, 3, x);
+      for (int i = 0; i < u.a; ++i)
+        for (int k = 0; k < ncoef; ++k) G(i, k) += w * Nv[i + 1] * Sv[k];
+    }
+  }
+  return G;
+}
 std::vector<double> sine_load_M(const Univariate& u, int k) { return sine_load(u, k, false); }
 
 }  // namespace shp

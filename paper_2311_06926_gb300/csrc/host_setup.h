@@ -45,4 +45,9 @@ Band to_band(const Dense& D, double drop_tol);
 std::vector<double> sine_load_N(const Univariate& u, int k);
 std::vector<double> sine_load_M(const Univariate& u, int k);
 
+// G[i][k] = int_0^1 N_i(x) S_k(x) dx for the a interior N-splines and the ncoef cubic B-splines
+// S_k of an open uniform knot vector (ncoef - 3 elements), by Gauss quadrature on the union of the
+// two breakpoint sets (exact for these piecewise polynomials). Row-major a x ncoef.
+Dense lid_profile_matrix(const Univariate& u, int ncoef);
+
 }  // namespace shp

@@ -83,6 +83,12 @@ constexpr int kMaxModeJobs = 4;
 template <typename T>
 void mode_product_multi(const ModeArgs<T>* jobs, int njobs, cudaStream_t s);
 
+// In-place banded Cholesky solves along one direction of a (b, b, b) tensor: x <- post (L L^T)^-1 x
+// with L lower triangular of bandwidth p stored as rows lb[i * (p + 1) + (k - i + p)] for
+// k in [i - p, i], and inv_diag[i] = 1 / L[i][i] (pressure mass inverse, FP64 path).
+void chol_solve_axis(double* x, int b, int p, int axis, const double* lb, const double* inv_diag,
+                     double post, cudaStream_t s);
+
 // ---- vector kernels (k_vec.cu) -----------------------------------------------------------
 // Deterministic dot product: fixed grid, fixed-order tree reduction. Result written to *out
 // (device). `partials` holds kDotBlocks values.

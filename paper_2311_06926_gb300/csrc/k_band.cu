@@ -160,25 +160,27 @@ __global__ void __launch_bounds__(256) k_band_tile(const __grid_constant__ PassB
   float* xs1 = sh + nin * P;
   float* ys = sh + (a.nterms > 1 ? 2 : 1) * nin * P;   // m x P (passes along x1)
   const int tid = threadIdx.x;
-  // load the input slab(s): element (line, j)
+  const int lane = tid % 32, warp = tid / 32, nwarps = blockDim.x / 32;
+  // per-lane line geometry, computed once: input base and stride along the band direction
+  int64_t ibase = 0, istride = 0;
+  if (lane < nl) line_geometry(axis, a.in, line0 + lane, &ibase, &istride);
+  // load the input slab(s) into shared memory as [j][line]
   for (int t = 0; t < a.nterms; ++t) {
     const float* X = t == 0 ? a.X0 : a.X1;
     float* xs = t == 0 ? xs0 : xs1;
-    const int total = nin * kTileLines;
-    for (int idx = tid; idx < total; idx += blockDim.x) {
-      int l, j;
-      if (axis == 1) { j = idx % nin; l = idx / nin; } else { l = idx % kTileLines; j = idx / kTileLines; }
-      float v = 0.f;
-      if (l < nl) {
-        int64_t base, stride;
-        line_geometry(axis, a.in, line0 + l, &base, &stride);
-        v = X[base + stride * j];
+    if (axis == 1) {
+      // lines are rows of x1: one warp per line, lanes along j (coalesced)
+      for (int l = warp; l < kTileLines; l += nwarps) {
+        const float* row = X + (int64_t)a.in.n1 * (line0 + l);
+        for (int j = lane; j < nin; j += 32) xs[j * P + l] = l < nl ? row[j] : 0.f;
       }
-      xs[j * P + l] = v;
+    } else {
+      // lanes along neighbouring lines (consecutive x1: coalesced), warps along j
+      for (int j = warp; j < nin; j += nwarps)
+        xs[j * P + lane] = lane < nl ? X[ibase + istride * j] : 0.f;
     }
   }
   __syncthreads();
-  const int lane = tid % 32, warp = tid / 32, nwarps = blockDim.x / 32;
   int64_t obase = 0, ostride = 0;
   if (lane < nl) line_geometry(axis, out, line0 + lane, &obase, &ostride);
   int64_t gbase = 0, gstride = 0, gstep = 0;
@@ -224,10 +226,9 @@ __global__ void __launch_bounds__(256) k_band_tile(const __grid_constant__ PassB
   }
   if (axis == 1) {
     __syncthreads();
-    const int total = m * kTileLines;
-    for (int idx = tid; idx < total; idx += blockDim.x) {
-      const int i = idx % m, l = idx / m;
-      if (l < nl) a.Y[(int64_t)m * (line0 + l) + i] = ys[i * P + l];
+    for (int l = warp; l < nl; l += nwarps) {
+      float* row = a.Y + (int64_t)m * (line0 + l);
+      for (int i = lane; i < m; i += 32) row[i] = ys[i * P + l];
     }
   }
 }
@@ -293,7 +294,51 @@ __global__ void __launch_bounds__(256) k_div_transpose(const T* __restrict__ g, 
   }
 }
 
+// One thread per line: forward substitution with L, then backward substitution with L^T, in
+// place. Earlier results of the line are re-read from the output (L1 hits).
+__global__ void __launch_bounds__(128) k_chol_line(double* __restrict__ x, int b, int p, int axis,
+                                                   const double* __restrict__ lb,
+                                                   const double* __restrict__ inv, double post) {
+  const int64_t line = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (line >= (int64_t)b * b) return;
+  int64_t base, stride;
+  if (axis == 1) {
+    base = (int64_t)b * line;
+    stride = 1;
+  } else if (axis == 2) {
+    base = (line % b) + (int64_t)b * b * (line / b);
+    stride = b;
+  } else {
+    base = line;
+    stride = (int64_t)b * b;
+  }
+  double* v = x + base;
+  const int w = p + 1;
+  for (int i = 0; i < b; ++i) {
+    double acc = v[i * stride];
+    const int k0 = i - p < 0 ? 0 : i - p;
+    for (int k = k0; k < i; ++k) acc = fma(-lb[i * w + (k - i + p)], v[k * stride], acc);
+    v[i * stride] = acc * inv[i];
+  }
+  for (int i = b - 1; i >= 0; --i) {
+    double acc = v[i * stride];
+    const int k1 = i + p > b - 1 ? b - 1 : i + p;
+    for (int k = i + 1; k <= k1; ++k) acc = fma(-lb[k * w + (i - k + p)], v[k * stride], acc);
+    v[i * stride] = acc * inv[i];
+  }
+  if (post != 1.0)
+    for (int i = 0; i < b; ++i) v[i * stride] *= post;
+}
+
 }  // namespace
+
+void chol_solve_axis(double* x, int b, int p, int axis, const double* lb, const double* inv_diag,
+                     double post, cudaStream_t s) {
+  const int64_t lines = (int64_t)b * b;
+  launch_begin(kClassBand, s);
+  k_chol_line<<<(unsigned)((lines + 127) / 128), 128, 0, s>>>(x, b, p, axis, lb, inv_diag, post);
+  launch_end(kClassBand, s, 4.0 * (p + 1) * lines * b, 2.0 * lines * b * sizeof(double));
+}
 
 void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {
   PassBatch<float> pb{};

@@ -240,22 +240,117 @@ __global__ void __launch_bounds__(128) k_mode_rows(const __grid_constant__ RowBa
   }
 }
 
+// Shared-memory staged variant: a block owns kLinesPerBlock neighbouring lines of one job and all
+// m outputs. The lines' inputs (K x lines) are loaded once, coalesced, into shared memory; each of
+// the 128 threads computes every 8th output index of one line, 4 at a time, reading its inputs
+// from shared memory and Op(i, j) through the read-only cache (two distinct i per warp). Outputs
+// of products along x1 are staged in shared memory for coalesced stores.
+constexpr int kLinesPerBlock = 16;
+constexpr int kGroups = 8;          // 128 threads = 16 lines x 8 output groups
+
+__global__ void __launch_bounds__(128) k_mode_tile(const __grid_constant__ RowBatch rb) {
+  extern __shared__ double shd[];
+  int jb = 0;
+  while (jb + 1 < rb.njobs && (int64_t)blockIdx.x >= rb.first[jb + 1]) ++jb;
+  const RowJob& J = rb.job[jb];
+  const int64_t lines = J.L * J.R;
+  const int64_t line0 = ((int64_t)blockIdx.x - rb.first[jb]) * kLinesPerBlock;
+  const int nl = (int)(lines - line0 < kLinesPerBlock ? lines - line0 : kLinesPerBlock);
+  const int K = J.K, m = J.m;
+  constexpr int P = kLinesPerBlock + 1;
+  double* xs = shd;                 // [K][P]
+  double* ys = shd + K * P;         // [m][P] (x1 products only)
+  const int tid = threadIdx.x;
+  // load: line -> (l, r); input X[l + L (j + K r)]
+  if (J.L == 1) {
+    // x1 products: each line is a contiguous row of K entries
+    for (int idx = tid; idx < K * kLinesPerBlock; idx += 128) {
+      const int l = idx / K, j = idx - l * K;
+      xs[j * P + l] = l < nl ? J.X[(int64_t)K * (line0 + l) + j] : 0.0;
+    }
+  } else {
+    for (int idx = tid; idx < K * kLinesPerBlock; idx += 128) {
+      const int l = idx % kLinesPerBlock, j = idx / kLinesPerBlock;
+      double v = 0.0;
+      if (l < nl) {
+        const int64_t line = line0 + l;
+        const int64_t ll = line % J.L, r = line / J.L;
+        v = J.X[ll + J.L * (j + (int64_t)K * r)];
+      }
+      xs[j * P + l] = v;
+    }
+  }
+  __syncthreads();
+  const int l = tid % kLinesPerBlock, grp = tid / kLinesPerBlock;
+  const bool valid = l < nl;
+  int64_t ybase = 0, ll = 0, r = 0;
+  if (valid && J.L > 1) {
+    const int64_t line = line0 + l;
+    ll = line % J.L;
+    r = line / J.L;
+    ybase = ll + J.L * (int64_t)m * r;
+  }
+  const double* xcol = xs + l;
+  for (int i0 = grp * 4; i0 < m; i0 += kGroups * 4) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const int cnt = m - i0 < 4 ? m - i0 : 4;
+    const double* op = J.U + i0 * J.op_i;
+    if (cnt == 4) {
+      for (int j = 0; j < K; ++j) {
+        const double xv = xcol[j * P];
+        const double* o = op + j * J.op_j;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k] = fma(__ldg(o + k * J.op_i), xv, acc[k]);
+      }
+    } else {
+      for (int j = 0; j < K; ++j) {
+        const double xv = xcol[j * P];
+        const double* o = op + j * J.op_j;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (k < cnt) acc[k] = fma(__ldg(o + k * J.op_i), xv, acc[k]);
+      }
+    }
+    if (!valid) continue;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (k >= cnt) break;
+      const int i = i0 + k;
+      double v = acc[k];
+      int64_t o;
+      if (J.L == 1) o = (int64_t)m * (line0 + l) + i;
+      else o = ybase + J.L * (int64_t)i;
+      if (J.invd) {
+        v *= J.invd[o];
+      } else if (J.lam1) {
+        const int i1 = (int)(o % J.out.n1);
+        const int64_t t2 = o / J.out.n1;
+        v /= J.scale * (J.lam1[i1] + J.lam2[(int)(t2 % J.out.n2)] + J.lam3[(int)(t2 / J.out.n2)]);
+      } else {
+        v *= J.post;
+      }
+      if (J.L == 1) ys[i * P + l] = v;
+      else J.Y[o] = v;
+    }
+  }
+  if (J.L == 1) {
+    __syncthreads();
+    for (int idx = tid; idx < m * kLinesPerBlock; idx += 128) {
+      const int lo = idx / m, i = idx - lo * m;
+      if (lo < nl) J.Y[(int64_t)m * (line0 + lo) + i] = ys[i * P + lo];
+    }
+  }
+}
+
 }  // namespace
 
 template <>
 void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStream_t s) {
-  // outputs per thread: as many as still leave ~1000 threads per SM (152 SMs), at least 2
-  int64_t lines = 0;
-  for (int j = 0; j < njobs; ++j) {
-    const Dims in = jobs[j].in;
-    lines += in.size() / in.get(jobs[j].axis) * (int64_t)jobs[j].m;
-  }
-  int mi = 8;
-  while (mi > 2 && lines / mi < 152 * 1024) mi /= 2;
   RowBatch rb{};
   rb.njobs = njobs;
-  int64_t total = 0;
+  int blocks = 0, smem = 0;
   double flops = 0, bytes = 0;
+  int first_block[kMaxModeJobs + 1];
   for (int j = 0; j < njobs; ++j) {
     const ModeArgs<double>& m = jobs[j];
     RowJob& J = rb.job[j];
@@ -269,8 +364,8 @@ void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStr
     J.m = m.m;
     J.L = m.axis == 1 ? 1 : (m.axis == 2 ? in.n1 : (int64_t)in.n1 * in.n2);
     J.R = m.axis == 1 ? (int64_t)in.n2 * in.n3 : (m.axis == 2 ? in.n3 : 1);
-    J.groups = (m.m + mi - 1) / mi;
-    J.threads = J.L * J.groups * J.R;
+    J.groups = 1;
+    J.threads = 0;
     J.invd = m.invd;
     J.lam1 = m.invd ? nullptr : m.lam1;
     J.lam2 = m.lam2;
@@ -278,17 +373,23 @@ void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStr
     J.scale = m.scale;
     J.out = in.with(m.axis, m.m);
     J.post = m.lam1 ? 1.0 : m.post;
-    rb.first[j] = total;
-    total += J.threads;
+    first_block[j] = blocks;
+    blocks += (int)((J.L * J.R + kLinesPerBlock - 1) / kLinesPerBlock);
+    // the kernel stages outputs in shared memory whenever the lines are contiguous (L == 1)
+    const int sm = (J.K + (J.L == 1 ? J.m : 0)) * (kLinesPerBlock + 1) * (int)sizeof(double);
+    smem = sm > smem ? sm : smem;
     flops += 2.0 * J.L * J.R * (double)J.K * J.m;
     bytes += ((double)in.size() + (double)in.with(m.axis, m.m).size()) * sizeof(double);
   }
-  rb.first[njobs] = total;
-  const int64_t blocks = (total + 127) / 128;
+  first_block[njobs] = blocks;
+  for (int j = 0; j <= njobs; ++j) rb.first[j] = first_block[j];
+  static int attr = 0;
+  if (smem > 48 * 1024 && smem > attr) {
+    cudaFuncSetAttribute(k_mode_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = smem;
+  }
   launch_begin(kClassMode, s);
-  if (mi == 8) k_mode_rows<8><<<(unsigned)blocks, 128, 0, s>>>(rb);
-  else if (mi == 4) k_mode_rows<4><<<(unsigned)blocks, 128, 0, s>>>(rb);
-  else k_mode_rows<2><<<(unsigned)blocks, 128, 0, s>>>(rb);
+  k_mode_tile<<<blocks, 128, smem, s>>>(rb);
   launch_end(kClassMode, s, flops, bytes);
 }
 

@@ -34,7 +34,8 @@ constexpr int kTileM = 128;
 constexpr int kStages = 4;
 constexpr int kChunkBytes = 128;                  // one 128-byte swizzle atom of K per row
 constexpr int kStageBytes = kTileM * kChunkBytes; // 16 KiB
-constexpr int kThreads = 192;                     // warp 0 TMA, warp 1 MMA + TMEM, warps 2-5 epilogue
+constexpr int kEpiWarps = 8;                      // two per TMEM lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;     // warp 0 TMA, warp 1 MMA + TMEM, the rest epilogue
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(&drain_bar, 1);
     for (int t = 0; t < 2; ++t) {
       mbar_init(&tfull_bar[t], 1);
-      mbar_init(&tempty_bar[t], 4);     // one arrival per epilogue warp
+      mbar_init(&tempty_bar[t], kEpiWarps);   // one arrival per epilogue warp
     }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -305,8 +306,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (uint32_t i = 0; i < kSpinLimit && !mbar_try_wait(&drain_bar, 0); ++i) __nanosleep(128);
     }
   } else {
-    // epilogue warps 2..5: TMEM lane quarter = warp % 4
+    // epilogue warps: TMEM lane quarter = warp % 4; the two warps of a quarter take alternate
+    // 32-column chunks of the accumulator
     const int quarter = warp % 4;
+    const int half = (warp - 2) / 4;
     const int row_in_tile = quarter * 32 + lane;
     int local = 0;
     for (int t = t_begin; t < t_end; ++t, ++local) {
@@ -320,27 +323,33 @@ __global__ void __launch_bounds__(kThreads, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int r = (t - J.first_tile) * kTileM + row_in_tile;
       const bool valid = r < args.R;
-      int64_t base = 0;
+      TO* yrow = reinterpret_cast<TO*>(args.Y);
       float lam_r = 0.f;
       if (valid) {
         const int j2 = r % args.e2, j3 = r / args.e2;
-        base = j2 + (int64_t)args.ldy * j3;
+        yrow += j2 + (int64_t)args.ldy * j3;
         if (args.lam_i) lam_r = args.lam_j2[j2] + args.lam_j3[j3];
       }
       const int64_t stride_i = (int64_t)args.ldy * args.e3;
-      TO* Y = reinterpret_cast<TO*>(args.Y);
-      for (int c0 = 0; c0 < args.npad; c0 += 32) {
+      const float post = args.post, scale = args.scale;
+      for (int c0 = half * 32; c0 < args.npad; c0 += 64) {
         float v[32];
         tmem_ld32(tmem + acc * 256 + ((uint32_t)(quarter * 32) << 16) + c0, v);
-        if (valid) {
+        if (valid && c0 < args.m) {
+          const int kmax = args.m - c0 < 32 ? args.m - c0 : 32;
+          TO* yp = yrow + stride_i * c0;
+          if (args.lam_i) {
+            const float* li = args.lam_i + c0;
 #pragma unroll
-          for (int k = 0; k < 32; ++k) {
-            const int i = c0 + k;
-            if (i < args.m) {
-              float val = v[k];
-              if (args.lam_i) val = val / (args.scale * (lam_r + args.lam_i[i]));
-              else val *= args.post;
-              store_val<TO>(Y + base + stride_i * i, val);
+            for (int k = 0; k < 32; ++k) {
+              if (k < kmax) store_val<TO>(yp, __fdividef(v[k], scale * (lam_r + li[k])));
+              yp += stride_i;
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+              if (k < kmax) store_val<TO>(yp, v[k] * post);
+              yp += stride_i;
             }
           }
         }

@@ -106,6 +106,9 @@ struct Ops {
   BandD<T> M{}, K{}, Mc{}, Tc{};
   const T *U_N = nullptr, *lam_N = nullptr, *U_T = nullptr, *lam_T = nullptr;
   const T* invd = nullptr;   // FP64: 1 / (2 nu (l1 + l2 + l3)) per velocity entry
+  const double* chol_lb = nullptr;     // FP64 pressure block: banded Cholesky factor of M-check
+  const double* chol_inv = nullptr;
+  int chol_p = 0;
   T *tK = nullptr, *tM = nullptr, *tS = nullptr, *tR = nullptr;   // component-size temporaries
   T *f1 = nullptr, *f2 = nullptr;                                 // mode-product ping-pong
   T *delta = nullptr, *m1 = nullptr, *m2 = nullptr;               // pressure-size temporaries
@@ -212,6 +215,21 @@ struct Ops {
     const T coef[1] = {nu};
     mq(1, in, out, coef);
     adiag_all(x, y, m2);
+  }
+
+  // y = M_V x: L2 Gram matrix of the velocity basis, per component (mass (x) mass (x) mass with
+  // the interior N-spline mass in the own direction)
+  void mass_V(const T* x, T* y) const {
+    PassArgs<T> j[3];
+    for (int c = 0; c < 3; ++c)
+      j[c] = job(x + c * nvc, M, 1, nullptr, nullptr, 0, comp(c), own_axis(c), tK + c * nvc);
+    band_pass_multi<T>(j, 3, s);
+    for (int c = 0; c < 3; ++c)
+      j[c] = job(tK + c * nvc, Mc, 1, nullptr, nullptr, 0, comp(c), first_other(c), tS + c * nvc);
+    band_pass_multi<T>(j, 3, s);
+    for (int c = 0; c < 3; ++c)
+      j[c] = job(tS + c * nvc, Mc, 1, nullptr, nullptr, 0, comp(c), second_other(c), y + c * nvc);
+    band_pass_multi<T>(j, 3, s);
   }
 
   void apply_B(const T* q, T* yu) const {   // B q = D_div^T M_q q
@@ -325,6 +343,16 @@ struct Ops {
 
   // pressure block: y = 2 nu (M-check^-1)^(x)3 x = 2 nu (U_T U_T^T)^(x)3 x
   void minv_Q(const T* x, T* y) const {
+    if (chol_lb) {
+      // 2 nu (M-check^-1)^(x)3 by banded Cholesky solves along each direction (exact; far fewer
+      // FP64 flops than the dense eigenvector route)
+      copy_async(y, x, npres * sizeof(T), s);
+      double* yd = reinterpret_cast<double*>(y);
+      chol_solve_axis(yd, b, chol_p, 1, chol_lb, chol_inv, 1.0, s);
+      chol_solve_axis(yd, b, chol_p, 2, chol_lb, chol_inv, 1.0, s);
+      chol_solve_axis(yd, b, chol_p, 3, chol_lb, chol_inv, 2.0 * (double)nu, s);
+      return;
+    }
     if (tc) {
       tc_fd(3, reinterpret_cast<const float*>(x), reinterpret_cast<float*>(y));
       return;
@@ -997,6 +1025,29 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
               inv[o++] = 1.0 / (2.0 * nu * ((*l[0])[i1] + (*l[1])[i2] + (*l[2])[i3]));
       }
       c->od.invd = upload<double>(c->arena, inv, c->stream);
+      // banded Cholesky factor of M-check (bandwidth p) for the FP64 pressure block
+      const int b = c->b, p = degree_p, w = p + 1;
+      const Dense& Mc = u.Mc;
+      Dense L(b, b);
+      for (int j = 0; j < b; ++j) {
+        double d = Mc(j, j);
+        for (int k = 0; k < j; ++k) d -= L(j, k) * L(j, k);
+        if (!(d > 0.0)) throw SetupError{"pressure mass matrix is not positive definite"};
+        L(j, j) = std::sqrt(d);
+        for (int i = j + 1; i < b; ++i) {
+          double t = Mc(i, j);
+          for (int k = 0; k < j; ++k) t -= L(i, k) * L(j, k);
+          L(i, j) = t / L(j, j);
+        }
+      }
+      std::vector<double> lb((size_t)b * w, 0.0), ld(b);
+      for (int i = 0; i < b; ++i) {
+        ld[i] = 1.0 / L(i, i);
+        for (int k = std::max(0, i - p); k <= i; ++k) lb[(size_t)i * w + (k - i + p)] = L(i, k);
+      }
+      c->od.chol_lb = upload<double>(c->arena, lb, c->stream);
+      c->od.chol_inv = upload<double>(c->arena, ld, c->stream);
+      c->od.chol_p = p;
     }
     init_hp<double>(c, c->hd, c->od);
     if (reduced(c)) {
@@ -1167,6 +1218,66 @@ int stokes_rhs_body(stokes_t c, int n_modes, const double* coef, const int* wave
     }
     check_launch("rhs_body");
     ck(cudaStreamSynchronize(c->stream), "rhs");
+  } catch (const CudaError& e) {
+    return cuda_fail(c, e);
+  }
+  return STOKES_OK;
+}
+
+int stokes_rhs_lid_profile(stokes_t c, int ncoef, const double* theta, int accumulate,
+                           double* f) {
+  if (!c || !f || !theta || ncoef < 4 || ncoef > 4096)
+    return c ? fail(c, STOKES_ERR_ARG, "invalid lid-profile arguments") : STOKES_ERR_ARG;
+  // Nitsche load of g = (sum_k theta_k S_k(x1), 0, 0) on x2 = 1:
+  // f1[i1, i2, i3] = nu (2 alpha M_i2(1) - M'_i2(1)) (int g N_i1) (int M_i3), int M = 1.
+  const Univariate& u = c->uv;
+  const Dense G = lid_profile_matrix(u, ncoef);
+  std::vector<double> P((size_t)c->a, 0.0);
+  for (int i = 0; i < c->a; ++i)
+    for (int k = 0; k < ncoef; ++k) P[i] += G(i, k) * theta[k];
+  const double alpha = c->c_pen / u.h;
+  std::vector<double> f1((size_t)c->nvc);
+  for (int i3 = 0; i3 < c->b; ++i3)
+    for (int i2 = 0; i2 < c->b; ++i2) {
+      const double g2 = c->nu * (2.0 * alpha * u.M_at_1[i2] - u.dM_at_1[i2]);
+      for (int i1 = 0; i1 < c->a; ++i1)
+        f1[(size_t)i1 + (size_t)c->a * (i2 + (size_t)c->b * i3)] = g2 * P[i1];
+    }
+  try {
+    double* tmp = c->kv[7];
+    ck(cudaMemcpyAsync(tmp, f1.data(), f1.size() * sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream), "rhs upload");
+    if (accumulate) {
+      axpby<double>(1.0, tmp, 1.0, f, c->nvc, c->stream);
+    } else {
+      fill_zero(f, c->ntot * sizeof(double), c->stream);
+      copy_async(f, tmp, c->nvc * sizeof(double), c->stream);
+    }
+    check_launch("rhs_lid_profile");
+    ck(cudaStreamSynchronize(c->stream), "rhs");
+  } catch (const CudaError& e) {
+    return cuda_fail(c, e);
+  }
+  return STOKES_OK;
+}
+
+int stokes_apply_mass(stokes_t c, const double* x, double* y) {
+  if (!c || !x || !y) return c ? fail(c, STOKES_ERR_ARG, "null vector") : STOKES_ERR_ARG;
+  try {
+    c->od.mass_V(x, y);
+    check_launch("apply_mass");
+  } catch (const CudaError& e) {
+    return cuda_fail(c, e);
+  }
+  return STOKES_OK;
+}
+
+int stokes_dot(stokes_t c, const double* x, const double* y, int64_t n, double* result) {
+  if (!c || !x || !y || !result || n < 0)
+    return c ? fail(c, STOKES_ERR_ARG, "invalid dot arguments") : STOKES_ERR_ARG;
+  try {
+    dot<double>(x, y, n, c->partials, c->dsc + 12, c->stream);
+    *result = read_scalar(c, c->dsc + 12);
   } catch (const CudaError& e) {
     return cuda_fail(c, e);
   }

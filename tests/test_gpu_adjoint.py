@@ -1,0 +1,110 @@
+"""Differentiation through the solve (adjoint): parity of the new loads and operators with the
+oracle, gradients against the oracle's direct adjoint, and central finite differences."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import dev, host, oracle, relerr
+from oracle.adjoint import objective_and_gradients, rhs_lid_profile, velocity_mass
+from oracle.stokes import StokesSystem
+from paper_2311_06926_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(n, p, nu, **kw):
+    from paper_2311_06926_gb300 import Stokes
+    return Stokes(n, p, nu=nu, **kw)
+
+
+@pytest.mark.parametrize("n,p,nu", [(1, 1, 1.0), (4, 2, 0.6), (9, 3, 1.0)])
+def test_lid_profile_mass_dot(n, p, nu):
+    S = StokesSystem(n, p, nu=nu)
+    G = _ctx(n, p, nu)
+    theta = np.random.default_rng(n).uniform(0.5, 1.5, 16)
+    assert relerr(host(G.rhs_lid_profile(theta)), rhs_lid_profile(S, theta)) < 1e-13
+    x = synthetic.random_vector(S.n_vel, 7)
+    assert relerr(host(G.apply_mass(dev(x))), velocity_mass(S) @ x) < 1e-13
+    y = synthetic.random_vector(S.n_vel, 8)
+    assert G.dot(dev(x), dev(y)) == pytest.approx(float(x @ y), rel=1e-13)
+    G.close()
+
+
+def _problem(n, p, seed=3):
+    rng = np.random.default_rng(seed)
+    theta = rng.uniform(0.5, 1.5, 16)
+    coef, waves = synthetic.forcing_modes(seed, n_modes=8)
+    S = StokesSystem(n, p, assemble=False)
+    ut = synthetic.random_vector(S.n_vel, 1000) * 0.01
+    return theta, coef, waves, ut
+
+
+def _gpu_grads(n, p, nu, theta, coef, waves, ut, tol=1e-12, steps=1):
+    from paper_2311_06926_gb300.adjoint import cavity_solve, mass_misfit
+    G = _ctx(n, p, nu, maxit=5000)
+    G.set_preconditioner(2, steps)
+    th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+    cf = torch.tensor(coef, dtype=torch.float64, requires_grad=True)
+    nu_t = torch.tensor(nu, dtype=torch.float64, requires_grad=True)
+    x = cavity_solve(G, th, cf, nu_t, waves, tol)
+    J = mass_misfit(G, x, dev(ut))
+    J.backward()
+    out = (float(J), th.grad.numpy().copy(), cf.grad.numpy().copy(), float(nu_t.grad))
+    G.close()
+    return out
+
+
+def test_gradients_match_oracle_adjoint_8cubed():
+    """cfg5 check at 8^3: GPU adjoint (MINRES to 1e-12) against the oracle's direct adjoint."""
+    n, p, nu = 8, 2, 1.0
+    theta, coef, waves, ut = _problem(n, p)
+    J, gt, gc, gn = _gpu_grads(n, p, nu, theta, coef, waves, ut)
+    Jo, gto, gco, gno = objective_and_gradients(n, p, nu, theta, coef, waves, ut)
+    assert J == pytest.approx(Jo, rel=1e-8)
+    assert np.abs(gt - gto).max() <= 1e-7 * np.abs(gto).max()
+    assert np.abs(gc - gco).max() <= 1e-7 * np.abs(gco).max()
+    assert gn == pytest.approx(gno, rel=1e-6)
+
+
+def _J_gpu(G, theta, coef, waves, ut, tol):
+    from paper_2311_06926_gb300.adjoint import cavity_solve, mass_misfit
+    x = cavity_solve(G, torch.tensor(theta), torch.tensor(coef), torch.tensor(G.nu), waves, tol)
+    return float(mass_misfit(G, x, dev(ut)))
+
+
+def _fd_check(n, p, nu, tol=1e-12):
+    theta, coef, waves, ut = _problem(n, p, seed=11)
+    J, gt, gc, gn = _gpu_grads(n, p, nu, theta, coef, waves, ut, tol=tol)
+    G = _ctx(n, p, nu, maxit=5000)
+    G.set_preconditioner(2, 1)
+    h = 1e-6
+    k = 5
+    e = np.zeros(16)
+    e[k] = h
+    fd = (_J_gpu(G, theta + e, coef, waves, ut, tol) - _J_gpu(G, theta - e, coef, waves, ut, tol)) / (2 * h)
+    assert fd == pytest.approx(gt[k], rel=1e-4)
+    c1, c2 = coef.copy(), coef.copy()
+    c1[1, 3] += h
+    c2[1, 3] -= h
+    fd = (_J_gpu(G, theta, c1, waves, ut, tol) - _J_gpu(G, theta, c2, waves, ut, tol)) / (2 * h)
+    assert fd == pytest.approx(gc[1, 3], rel=1e-4, abs=1e-6 * np.abs(gc).max())
+    G.close()
+    Gp = _ctx(n, p, nu + h, maxit=5000)
+    Gm = _ctx(n, p, nu - h, maxit=5000)
+    for Gx in (Gp, Gm):
+        Gx.set_preconditioner(2, 1)
+    fd = (_J_gpu(Gp, theta, coef, waves, ut, tol) - _J_gpu(Gm, theta, coef, waves, ut, tol)) / (2 * h)
+    assert fd == pytest.approx(gn, rel=1e-4)
+    Gp.close()
+    Gm.close()
+
+
+def test_central_differences_16cubed():
+    """Central differences (step 1e-6) of J computed by GPU solves against the adjoint gradient."""
+    _fd_check(16, 3, 1.0)
+
+
+@pytest.mark.slow
+def test_central_differences_64cubed_p3():
+    """cfg5 size: 64^3 elements, p = 3."""
+    _fd_check(64, 3, 1.0)
