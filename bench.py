@@ -46,7 +46,24 @@ WORKLOADS = {
     "cavity128": dict(n=128, p=3, sweep=[(2, 2)], precision="fp64",
                       desc="3D lid-driven cavity, 128^3 elements, p=3, nu=1, FP64 MINRES to 1e-8, "
                            "order 2, 2 steps"),
+    "cavity96": dict(n=96, p=3, sweep=[(2, 2)], precision="fp64",
+                     desc="3D lid-driven cavity, 96^3 elements, p=3, nu=1, order 2, 2 steps"),
 }
+
+
+def aggregate(ms_local, units_local, dist=None):
+    """Whole-job throughput of independent replicas: the slowest rank's time (max over ranks)
+    and the units all ranks processed. Returns (units per second, max ms). With ``dist`` (an
+    initialised torch.distributed) the reduction runs over the default group."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return units_local / (ms_local / 1e3), ms_local
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
+    u = torch.tensor([units_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / (float(t.item()) / 1e3), float(t.item())
 
 
 def dist_env():
@@ -199,6 +216,24 @@ def mixed_vs_fp64(Stokes, peaks, n=128, p=3, q=2, s=2):
     return res
 
 
+def run_probe(args, wl):
+    import torch
+    from paper_2311_06926_gb300 import Stokes
+    G = Stokes(wl["n"], wl["p"], precision=wl["precision"], max_order=2, max_steps=1)
+    x = torch.randn(G.size, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        G.apply_hyperpower(2, 1, x)
+    torch.cuda.synchronize()
+    G.profile_begin()
+    for _ in range(args.steps):
+        G.apply_hyperpower(2, 1, x)
+    prof = G.profile_end()
+    print(json.dumps({"probe": wl["desc"], "precision": wl["precision"], "applications": args.steps,
+                      "kernel_classes": prof}), flush=True)
+    G.close()
+    return 0
+
+
 def run_reference(args, wl):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -236,6 +271,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the 128^3 mixed-precision vs FP64 comparison")
+    ap.add_argument("--probe", action="store_true",
+                    help="kernel probe for ncu: only apply the order-2, 1-step hyper-power "
+                         "preconditioner K times on the workload's mesh in --precision (no "
+                         "Krylov bases, small device footprint); prints per-kernel-class times")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.precision:
@@ -244,6 +283,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args, wl)
+    if args.probe:
+        return run_probe(args, wl)
 
     import torch
     import torch.distributed as dist
@@ -298,12 +339,8 @@ def main():
     clocks = sampler.stop()
     launches = kernel_launches() - launches0
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    value, ms_max = aggregate(ms, len(sweep) * args.steps, dist if ws > 1 else None)
     solves = len(sweep) * args.steps * ws
-    value = solves / (ms_max / 1e3)
 
     # per-preconditioner solve times (one solve each, not part of the headline)
     per = {}
@@ -336,10 +373,8 @@ def main():
         step_e2e()
     torch.cuda.synchronize()
     barrier()
-    e2e_s = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
-    e2e_value = solves / float(e2e_s.item())
+    e2e_value, _ = aggregate(1e3 * (time.perf_counter() - t0), len(sweep) * args.steps,
+                             dist if ws > 1 else None)
     bytes_per_solve = G.size * 8
 
     # profiled pass: per-kernel-class event timing over one step

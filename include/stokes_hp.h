@@ -148,6 +148,14 @@ int stokes_solve(stokes_t ctx, const double* rhs, double tol, double* x, int* it
 int stokes_solve_host(stokes_t ctx, const double* rhs_host, double tol, double* x_host,
                       int* iterations, double* final_rel_res);
 
+/* Solve `count` independent systems at once: ctxs[i] (distinct contexts, any meshes, degrees,
+ * precisions and solvers) with rhs[i] -> x[i] (device pointers of that context's size). Each
+ * solve runs on its own context's stream, driven by its own host thread, so the solves execute
+ * concurrently on the GPU. iterations, final_rel_res and status (per-problem return codes) may
+ * be NULL. Returns STOKES_OK or the first nonzero per-problem code. */
+int stokes_solve_batch(stokes_t* ctxs, int count, const double* const* rhs, double tol,
+                       double* const* x, int* iterations, double* final_rel_res, int* status);
+
 /* Per-iteration convergence ratios of the last solve: copies min(capacity, iterations) values
  * into the host array ratios and returns the number copied (or a negative error). */
 int stokes_last_ratios(stokes_t ctx, double* ratios, int capacity);

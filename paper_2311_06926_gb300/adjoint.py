@@ -30,6 +30,8 @@ class CavitySolve(torch.autograd.Function):
         x, it, rr, _ = G.solve(f, tol)
         ctx.G, ctx.waves, ctx.tol = G, np.asarray(waves), tol
         ctx.shapes = (th.shape, cf.shape)
+        ctx.devices = (theta.device, coef.device,
+                       nu.device if isinstance(nu, torch.Tensor) else torch.device("cpu"))
         ctx.save_for_backward(x, f_lid)
         return x
 
@@ -56,9 +58,9 @@ class CavitySolve(torch.autograd.Function):
                     grad_coef[c, m] = G.dot(lam, G.rhs_body(unit, ctx.waves))
         Ax = G.apply_A(x[:G.n_vel].contiguous())
         grad_nu = (G.dot(lam, f_lid) - G.dot(lam[:G.n_vel].contiguous(), Ax)) / G.nu
-        dev = gx.device
-        return (torch.from_numpy(grad_theta).to(dev), torch.from_numpy(grad_coef).to(dev),
-                torch.tensor(grad_nu, dtype=torch.float64, device=dev), None, None, None)
+        d_th, d_cf, d_nu = ctx.devices
+        return (torch.from_numpy(grad_theta).to(d_th), torch.from_numpy(grad_coef).to(d_cf),
+                torch.tensor(grad_nu, dtype=torch.float64, device=d_nu), None, None, None)
 
 
 class MassMisfit(torch.autograd.Function):

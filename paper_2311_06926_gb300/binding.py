@@ -72,6 +72,9 @@ def load_library(path=None):
         "stokes_solve": (ctypes.c_int, [vp, vp, ctypes.c_double, vp, ip, dp]),
         "stokes_solve_host": (ctypes.c_int, [vp, vp, ctypes.c_double, vp, ip, dp]),
         "stokes_last_ratios": (ctypes.c_int, [vp, dp, ctypes.c_int]),
+        "stokes_solve_batch": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int,
+                                              ctypes.POINTER(vp), ctypes.c_double,
+                                              ctypes.POINTER(vp), ip, dp, ip]),
         "stokes_profile_begin": (ctypes.c_int, [vp]),
         "stokes_profile_end": (ctypes.c_int, [vp, ctypes.POINTER(KernelStat), ctypes.c_int]),
         "stokes_kernel_launches": (ctypes.c_int64, []),
@@ -86,6 +89,33 @@ def load_library(path=None):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def solve_batch(contexts, rhs, tol=1e-8, outs=None):
+    """Solve len(contexts) independent systems concurrently (stokes_solve_batch). contexts:
+    distinct Stokes objects; rhs: matching float64 CUDA tensors. Returns (xs, iterations,
+    true relative residuals, status codes)."""
+    lib = load_library()
+    n = len(contexts)
+    if len(rhs) != n:
+        raise ValueError("one right-hand side per context")
+    xs = outs if outs is not None else [G.empty() for G in contexts]
+    for G, f, x in zip(contexts, rhs, xs):
+        G._vec(f, G.size)
+        G._vec(x, G.size)
+    cur = torch.cuda.current_stream()
+    for G in contexts:
+        G.stream.wait_stream(cur)
+    H = (ctypes.c_void_p * n)(*[G.h.value for G in contexts])
+    R = (ctypes.c_void_p * n)(*[f.data_ptr() for f in rhs])
+    X = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    it = (ctypes.c_int * n)()
+    rr = (ctypes.c_double * n)()
+    st = (ctypes.c_int * n)()
+    lib.stokes_solve_batch(H, n, R, float(tol), X, it, rr, st)
+    for G in contexts:
+        cur.wait_stream(G.stream)
+    return xs, list(it), list(rr), list(st)
 
 
 def kernel_launches():

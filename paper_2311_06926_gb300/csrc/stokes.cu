@@ -25,6 +25,7 @@
 #include <map>
 #include <new>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -1311,6 +1312,31 @@ int stokes_solve_host(stokes_t c, const double* rhs_host, double tol, double* x_
   } catch (const CudaError& e) {
     return cuda_fail(c, e);
   }
+}
+
+int stokes_solve_batch(stokes_t* ctxs, int count, const double* const* rhs, double tol,
+                       double* const* x, int* iterations, double* final_rel_res, int* status) {
+  if (!ctxs || !rhs || !x || count < 0) return STOKES_ERR_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i] || !rhs[i] || !x[i]) return STOKES_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(ctxs[i], STOKES_ERR_ARG, "contexts must be distinct");
+  }
+  std::vector<int> st(count, STOKES_OK);
+  std::vector<std::thread> workers;
+  workers.reserve(count);
+  for (int i = 0; i < count; ++i)
+    workers.emplace_back([&, i] {
+      st[i] = stokes_solve(ctxs[i], rhs[i], tol, x[i], iterations ? iterations + i : nullptr,
+                           final_rel_res ? final_rel_res + i : nullptr);
+    });
+  for (auto& w : workers) w.join();
+  int rc = STOKES_OK;
+  for (int i = 0; i < count; ++i) {
+    if (status) status[i] = st[i];
+    if (rc == STOKES_OK) rc = st[i];
+  }
+  return rc;
 }
 
 int stokes_last_ratios(stokes_t c, double* ratios, int capacity) {
