@@ -37,18 +37,24 @@ struct PassBatch {
 template <typename T>
 constexpr int seg_len() { return sizeof(T) == 4 ? 32 : 1; }
 
-template <typename T>
+template <int W, typename T>
 __device__ __forceinline__ T band_dot(const BandD<T>& D, int i, const T* __restrict__ X,
                                       int64_t base, int64_t stride) {
   const int s0 = __ldg(D.start + i);
-  const T* v = D.val + (int64_t)i * D.width;
   const T* x = X + base + (int64_t)s0 * stride;
   T sum = 0;
-  for (int w = 0; w < D.width; ++w) sum += __ldg(v + w) * __ldg(x + (int64_t)w * stride);
+  if (W > 0) {
+    const T* v = D.val + (int64_t)i * W;
+#pragma unroll
+    for (int w = 0; w < W; ++w) sum = fma(__ldg(v + w), __ldg(x + (int64_t)w * stride), sum);
+  } else {
+    const T* v = D.val + (int64_t)i * D.width;
+    for (int w = 0; w < D.width; ++w) sum = fma(__ldg(v + w), __ldg(x + (int64_t)w * stride), sum);
+  }
   return sum;
 }
 
-template <typename T>
+template <typename T, int W>
 __global__ void __launch_bounds__(256) k_band_pass(const __grid_constant__ PassBatch<T> pb) {
   int jb = 0;
   while (jb + 1 < pb.njobs && (int)blockIdx.x >= pb.first_block[jb + 1]) ++jb;
@@ -109,8 +115,8 @@ __global__ void __launch_bounds__(256) k_band_pass(const __grid_constant__ PassB
   }
   const int i_end = min(m, (seg + 1) * seg_n);
   for (int i = seg * seg_n; i < i_end; ++i) {
-    T acc = a.c0 * band_dot(a.D0, i, a.X0, base_in, stride_in);
-    if (a.nterms > 1) acc += a.c1 * band_dot(a.D1, i, a.X1, base_in, stride_in);
+    T acc = a.c0 * band_dot<W>(a.D0, i, a.X0, base_in, stride_in);
+    if (a.nterms > 1) acc += a.c1 * band_dot<W>(a.D1, i, a.X1, base_in, stride_in);
     const int64_t o = base_out + (int64_t)i * stride_out;
     if (a.Z) acc += a.cz * a.Z[o];
     if (a.g) {
@@ -143,39 +149,56 @@ __device__ __forceinline__ void line_geometry(int axis, const Dims& d, int64_t l
   }
 }
 
+// W: band width of every term of the launch (0: runtime width, generic loop).
+template <int W>
 __global__ void __launch_bounds__(256) k_band_tile(const __grid_constant__ PassBatch<float> pb) {
-  extern __shared__ float sh[];
+  extern __shared__ __align__(16) float sh[];
   int jb = 0;
   while (jb + 1 < pb.njobs && (int)blockIdx.x >= pb.first_block[jb + 1]) ++jb;
   const PassArgs<float>& a = pb.job[jb];
   const int axis = a.axis;
   const int nin = a.in.get(axis);
   const int m = a.D0.rows;
+  const int nt = a.nterms;
+  // band width of each term (the terms of a pass may differ on tiny meshes, where some 1D
+  // matrices are exactly diagonal); W > 0 means every term of the launch has width W
+  const int wt0 = W > 0 ? W : a.D0.width;
+  const int wt1 = W > 0 ? W : (nt > 1 ? a.D1.width : 0);
+  const int wp = ((wt0 > wt1 ? wt0 : wt1) + 3) & ~3;   // coefficient row pitch (float4 loads)
   const Dims out = a.in.with(axis, m);
   const int64_t lines = out.size() / m;
   const int64_t line0 = (int64_t)(blockIdx.x - pb.first_block[jb]) * kTileLines;
   const int nl = (int)(lines - line0 < kTileLines ? lines - line0 : kTileLines);
-  constexpr int P = kTileLines + 1;   // shared pitch
+  constexpr int P = kTileLines + 1;   // shared pitch of the input slabs
   float* xs0 = sh;
   float* xs1 = sh + nin * P;
-  float* ys = sh + (a.nterms > 1 ? 2 : 1) * nin * P;   // m x P (passes along x1)
+  float* ys = sh + nt * nin * P;                       // m x P (passes along x1)
+  // nt x m x wp coefficients, offset rounded up to 4 floats for the 16-byte float4 loads
+  float* cf = sh + ((nt * nin * P + (axis == 1 ? m * P : 0) + 3) & ~3);
+  int* st = reinterpret_cast<int*>(cf + nt * m * wp);  // nt x m band starts
   const int tid = threadIdx.x;
   const int lane = tid % 32, warp = tid / 32, nwarps = blockDim.x / 32;
-  // per-lane line geometry, computed once: input base and stride along the band direction
+  // band coefficients and starts of this launch's operator(s)
+  for (int t = 0; t < nt; ++t) {
+    const BandD<float>& D = t == 0 ? a.D0 : a.D1;
+    const int width = t == 0 ? wt0 : wt1;
+    for (int idx = tid; idx < m * wp; idx += blockDim.x) {
+      const int i = idx / wp, w = idx - i * wp;
+      cf[t * m * wp + idx] = w < width ? D.val[(int64_t)i * width + w] : 0.f;
+    }
+    for (int i = tid; i < m; i += blockDim.x) st[t * m + i] = D.start[i];
+  }
   int64_t ibase = 0, istride = 0;
   if (lane < nl) line_geometry(axis, a.in, line0 + lane, &ibase, &istride);
-  // load the input slab(s) into shared memory as [j][line]
-  for (int t = 0; t < a.nterms; ++t) {
+  for (int t = 0; t < nt; ++t) {
     const float* X = t == 0 ? a.X0 : a.X1;
     float* xs = t == 0 ? xs0 : xs1;
     if (axis == 1) {
-      // lines are rows of x1: one warp per line, lanes along j (coalesced)
       for (int l = warp; l < kTileLines; l += nwarps) {
         const float* row = X + (int64_t)a.in.n1 * (line0 + l);
         for (int j = lane; j < nin; j += 32) xs[j * P + l] = l < nl ? row[j] : 0.f;
       }
     } else {
-      // lanes along neighbouring lines (consecutive x1: coalesced), warps along j
       for (int j = warp; j < nin; j += nwarps)
         xs[j * P + lane] = lane < nl ? X[ibase + istride * j] : 0.f;
     }
@@ -185,7 +208,6 @@ __global__ void __launch_bounds__(256) k_band_tile(const __grid_constant__ PassB
   if (lane < nl) line_geometry(axis, out, line0 + lane, &obase, &ostride);
   int64_t gbase = 0, gstride = 0, gstep = 0;
   if (a.g && lane < nl) {
-    // output (line, i) -> g entry with the same indices (g has extents b^3)
     int idx3[3];
     const int64_t line = line0 + lane;
     if (axis == 1) { idx3[0] = 0; idx3[1] = (int)(line % out.n2); idx3[2] = (int)(line / out.n2); }
@@ -199,19 +221,25 @@ __global__ void __launch_bounds__(256) k_band_tile(const __grid_constant__ PassB
   }
   for (int i = warp; i < m; i += nwarps) {
     float acc = 0.f;
-    {
-      const int s0 = __ldg(a.D0.start + i);
-      const float* v = a.D0.val + (int64_t)i * a.D0.width;
+    for (int t = 0; t < nt; ++t) {
+      const float* xs = (t == 0 ? xs0 : xs1) + st[t * m + i] * P + lane;
+      const float4* c4 = reinterpret_cast<const float4*>(cf + (t * m + i) * wp);
       float sum = 0.f;
-      for (int w = 0; w < a.D0.width; ++w) sum += __ldg(v + w) * xs0[(s0 + w) * P + lane];
-      acc = a.c0 * sum;
-    }
-    if (a.nterms > 1) {
-      const int s1 = __ldg(a.D1.start + i);
-      const float* v = a.D1.val + (int64_t)i * a.D1.width;
-      float sum = 0.f;
-      for (int w = 0; w < a.D1.width; ++w) sum += __ldg(v + w) * xs1[(s1 + w) * P + lane];
-      acc += a.c1 * sum;
+      if (W > 0) {
+#pragma unroll
+        for (int w4 = 0; w4 < (W + 3) / 4; ++w4) {
+          const float4 c = c4[w4];
+          if (4 * w4 + 0 < W) sum = fmaf(c.x, xs[(4 * w4 + 0) * P], sum);
+          if (4 * w4 + 1 < W) sum = fmaf(c.y, xs[(4 * w4 + 1) * P], sum);
+          if (4 * w4 + 2 < W) sum = fmaf(c.z, xs[(4 * w4 + 2) * P], sum);
+          if (4 * w4 + 3 < W) sum = fmaf(c.w, xs[(4 * w4 + 3) * P], sum);
+        }
+      } else {
+        const float* c1 = cf + (t * m + i) * wp;
+        const int width = t == 0 ? wt0 : wt1;
+        for (int w = 0; w < width; ++w) sum = fmaf(c1[w], xs[w * P], sum);
+      }
+      acc = fmaf(t == 0 ? a.c0 : a.c1, sum, acc);
     }
     if (lane < nl) {
       const int64_t o = obase + ostride * i;
@@ -294,14 +322,24 @@ __global__ void __launch_bounds__(256) k_div_transpose(const T* __restrict__ g, 
   }
 }
 
-// One thread per line: forward substitution with L, then backward substitution with L^T, in
-// place. Earlier results of the line are re-read from the output (L1 hits).
-__global__ void __launch_bounds__(128) k_chol_line(double* __restrict__ x, int b, int p, int axis,
-                                                   const double* __restrict__ lb,
-                                                   const double* __restrict__ inv, double post) {
-  const int64_t line = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (line >= (int64_t)b * b) return;
-  int64_t base, stride;
+// One thread per line: the block's lines are first copied into shared memory (coalesced), then
+// each thread runs forward substitution with L and backward substitution with L^T on its own
+// column of shared memory, and the block writes the lines back.
+constexpr int kCholLines = 32;
+
+__global__ void __launch_bounds__(kCholLines) k_chol_line(double* __restrict__ x, int b, int p,
+                                                          int axis,
+                                                          const double* __restrict__ lb,
+                                                          const double* __restrict__ inv,
+                                                          double post) {
+  extern __shared__ double cs[];
+  constexpr int P = kCholLines + 1;
+  const int64_t lines = (int64_t)b * b;
+  const int64_t line0 = (int64_t)blockIdx.x * kCholLines;
+  const int nl = (int)(lines - line0 < kCholLines ? lines - line0 : kCholLines);
+  const int l = threadIdx.x;
+  int64_t base = 0, stride = 0;
+  const int64_t line = line0 + l;
   if (axis == 1) {
     base = (int64_t)b * line;
     stride = 1;
@@ -312,22 +350,41 @@ __global__ void __launch_bounds__(128) k_chol_line(double* __restrict__ x, int b
     base = line;
     stride = (int64_t)b * b;
   }
-  double* v = x + base;
-  const int w = p + 1;
-  for (int i = 0; i < b; ++i) {
-    double acc = v[i * stride];
-    const int k0 = i - p < 0 ? 0 : i - p;
-    for (int k = k0; k < i; ++k) acc = fma(-lb[i * w + (k - i + p)], v[k * stride], acc);
-    v[i * stride] = acc * inv[i];
+  if (axis == 1) {
+    // rows of x1: lanes along the row
+    for (int r = 0; r < nl; ++r) {
+      const double* row = x + (int64_t)b * (line0 + r);
+      for (int j = l; j < b; j += kCholLines) cs[j * P + r] = row[j];
+    }
+  } else if (l < nl) {
+    for (int j = 0; j < b; ++j) cs[j * P + l] = x[base + stride * j];
   }
-  for (int i = b - 1; i >= 0; --i) {
-    double acc = v[i * stride];
-    const int k1 = i + p > b - 1 ? b - 1 : i + p;
-    for (int k = i + 1; k <= k1; ++k) acc = fma(-lb[k * w + (i - k + p)], v[k * stride], acc);
-    v[i * stride] = acc * inv[i];
+  __syncthreads();
+  if (l < nl) {
+    double* v = cs + l;
+    const int w = p + 1;
+    for (int i = 0; i < b; ++i) {
+      double acc = v[i * P];
+      const int k0 = i - p < 0 ? 0 : i - p;
+      for (int k = k0; k < i; ++k) acc = fma(-lb[i * w + (k - i + p)], v[k * P], acc);
+      v[i * P] = acc * inv[i];
+    }
+    for (int i = b - 1; i >= 0; --i) {
+      double acc = v[i * P];
+      const int k1 = i + p > b - 1 ? b - 1 : i + p;
+      for (int k = i + 1; k <= k1; ++k) acc = fma(-lb[k * w + (i - k + p)], v[k * P], acc);
+      v[i * P] = acc * inv[i];
+    }
   }
-  if (post != 1.0)
-    for (int i = 0; i < b; ++i) v[i * stride] *= post;
+  __syncthreads();
+  if (axis == 1) {
+    for (int r = 0; r < nl; ++r) {
+      double* row = x + (int64_t)b * (line0 + r);
+      for (int j = l; j < b; j += kCholLines) row[j] = cs[j * P + r] * post;
+    }
+  } else if (l < nl) {
+    for (int j = 0; j < b; ++j) x[base + stride * j] = cs[j * P + l] * post;
+  }
 }
 
 }  // namespace
@@ -335,8 +392,15 @@ __global__ void __launch_bounds__(128) k_chol_line(double* __restrict__ x, int b
 void chol_solve_axis(double* x, int b, int p, int axis, const double* lb, const double* inv_diag,
                      double post, cudaStream_t s) {
   const int64_t lines = (int64_t)b * b;
+  const int smem = b * (kCholLines + 1) * (int)sizeof(double);
+  static int attr = 0;
+  if (smem > 48 * 1024 && smem > attr) {
+    cudaFuncSetAttribute(k_chol_line, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = smem;
+  }
   launch_begin(kClassBand, s);
-  k_chol_line<<<(unsigned)((lines + 127) / 128), 128, 0, s>>>(x, b, p, axis, lb, inv_diag, post);
+  k_chol_line<<<(unsigned)((lines + kCholLines - 1) / kCholLines), kCholLines, smem, s>>>(
+      x, b, p, axis, lb, inv_diag, post);
   launch_end(kClassBand, s, 4.0 * (p + 1) * lines * b, 2.0 * lines * b * sizeof(double));
 }
 
@@ -354,8 +418,11 @@ void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {
     const int64_t lines = out.size() / a.D0.rows;
     blocks += (int)((lines + kTileLines - 1) / kTileLines);
     const int nin = a.in.get(a.axis);
-    const int sm = ((a.nterms > 1 ? 2 : 1) * nin + (a.axis == 1 ? a.D0.rows : 0)) *
-                   (kTileLines + 1) * (int)sizeof(float);
+    const int nt = a.nterms > 1 ? 2 : 1;
+    const int wmax = nt > 1 && a.D1.width > a.D0.width ? a.D1.width : a.D0.width;
+    const int wp = (wmax + 3) & ~3;
+    const int sm = (nt * nin + (a.axis == 1 ? a.D0.rows : 0)) * (kTileLines + 1) * (int)sizeof(float) +
+                   16 + nt * a.D0.rows * (wp * (int)sizeof(float) + (int)sizeof(int));
     smem = sm > smem ? sm : smem;
     const double outs = (double)out.size();
     double fl = 2.0 * a.D0.width * outs, by = (double)a.in.size() + outs;
@@ -367,13 +434,34 @@ void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {
   }
   pb.first_block[njobs] = blocks;
   pb.seg = 1;
-  static int attr = 0;
-  if (smem > 48 * 1024 && smem > attr) {
-    cudaFuncSetAttribute(k_band_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr = smem;
-  }
+  // one band width per launch (all terms of all jobs); unrolled kernels for the common widths
+  int W = jobs[0].D0.width;
+  for (int j = 0; j < njobs; ++j)
+    if (jobs[j].D0.width != W || (jobs[j].nterms > 1 && jobs[j].D1.width != W)) W = 0;
   launch_begin(kClassBand, s);
-  k_band_tile<<<blocks, 256, smem, s>>>(pb);
+  switch (W) {
+#define SHP_TILE_W(w)                                                                         \
+  case w: {                                                                                   \
+    static int attr = 0;                                                                      \
+    if (smem > 48 * 1024 && smem > attr) {                                                    \
+      cudaFuncSetAttribute(k_band_tile<w>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+      attr = smem;                                                                            \
+    }                                                                                         \
+    k_band_tile<w><<<blocks, 256, smem, s>>>(pb);                                             \
+    break;                                                                                    \
+  }
+    SHP_TILE_W(3) SHP_TILE_W(5) SHP_TILE_W(7) SHP_TILE_W(9) SHP_TILE_W(11) SHP_TILE_W(13)
+    SHP_TILE_W(15) SHP_TILE_W(17) SHP_TILE_W(19) SHP_TILE_W(21)
+    default: {
+      static int attr = 0;
+      if (smem > 48 * 1024 && smem > attr) {
+        cudaFuncSetAttribute(k_band_tile<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = smem;
+      }
+      k_band_tile<0><<<blocks, 256, smem, s>>>(pb);
+    }
+#undef SHP_TILE_W
+  }
   launch_end(kClassBand, s, flops, bytes);
 }
 
@@ -407,8 +495,19 @@ void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s) {
   }
   pb.first_block[njobs] = blocks;
   pb.seg = seg_len<T>();
+  int W = jobs[0].D0.width;
+  for (int j = 0; j < njobs; ++j)
+    if (jobs[j].D0.width != W || (jobs[j].nterms > 1 && jobs[j].D1.width != W)) W = 0;
   launch_begin(kClassBand, s);
-  k_band_pass<T><<<blocks, 256, 0, s>>>(pb);
+  switch (W) {
+    case 3: k_band_pass<T, 3><<<blocks, 256, 0, s>>>(pb); break;
+    case 5: k_band_pass<T, 5><<<blocks, 256, 0, s>>>(pb); break;
+    case 7: k_band_pass<T, 7><<<blocks, 256, 0, s>>>(pb); break;
+    case 9: k_band_pass<T, 9><<<blocks, 256, 0, s>>>(pb); break;
+    case 11: k_band_pass<T, 11><<<blocks, 256, 0, s>>>(pb); break;
+    case 13: k_band_pass<T, 13><<<blocks, 256, 0, s>>>(pb); break;
+    default: k_band_pass<T, 0><<<blocks, 256, 0, s>>>(pb);
+  }
   launch_end(kClassBand, s, flops, bytes);
 }
 

@@ -177,8 +177,9 @@ struct RowJob {
 
 struct RowBatch {
   RowJob job[kMaxModeJobs];
-  int64_t first[kMaxModeJobs + 1];   // first flat thread of each job
+  int64_t first[kMaxModeJobs + 1];   // first block of each job
   int njobs;
+  int isplit;                        // blocks sharing one line tile (each takes a range of i)
 };
 
 template <int MI>
@@ -251,12 +252,18 @@ constexpr int kGroups = 8;          // 128 threads = 16 lines x 8 output groups
 __global__ void __launch_bounds__(128) k_mode_tile(const __grid_constant__ RowBatch rb) {
   extern __shared__ double shd[];
   int jb = 0;
-  while (jb + 1 < rb.njobs && (int64_t)blockIdx.x >= rb.first[jb + 1]) ++jb;
+  const int64_t bidx = blockIdx.x / rb.isplit;
+  const int part = blockIdx.x % rb.isplit;
+  while (jb + 1 < rb.njobs && bidx >= rb.first[jb + 1]) ++jb;
   const RowJob& J = rb.job[jb];
   const int64_t lines = J.L * J.R;
-  const int64_t line0 = ((int64_t)blockIdx.x - rb.first[jb]) * kLinesPerBlock;
+  const int64_t line0 = (bidx - rb.first[jb]) * kLinesPerBlock;
   const int nl = (int)(lines - line0 < kLinesPerBlock ? lines - line0 : kLinesPerBlock);
   const int K = J.K, m = J.m;
+  // this block's output range [ilo, ihi), a multiple of 4 wide
+  const int chunk = ((m + rb.isplit - 1) / rb.isplit + 3) & ~3;
+  const int ilo = part * chunk;
+  const int ihi = ilo + chunk < m ? ilo + chunk : m;
   constexpr int P = kLinesPerBlock + 1;
   double* xs = shd;                 // [K][P]
   double* ys = shd + K * P;         // [m][P] (x1 products only)
@@ -291,9 +298,9 @@ __global__ void __launch_bounds__(128) k_mode_tile(const __grid_constant__ RowBa
     ybase = ll + J.L * (int64_t)m * r;
   }
   const double* xcol = xs + l;
-  for (int i0 = grp * 4; i0 < m; i0 += kGroups * 4) {
+  for (int i0 = ilo + grp * 4; i0 < ihi; i0 += kGroups * 4) {
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    const int cnt = m - i0 < 4 ? m - i0 : 4;
+    const int cnt = ihi - i0 < 4 ? ihi - i0 : 4;
     const double* op = J.U + i0 * J.op_i;
     if (cnt == 4) {
       for (int j = 0; j < K; ++j) {
@@ -333,10 +340,11 @@ __global__ void __launch_bounds__(128) k_mode_tile(const __grid_constant__ RowBa
       else J.Y[o] = v;
     }
   }
-  if (J.L == 1) {
+  if (J.L == 1 && ihi > ilo) {
     __syncthreads();
-    for (int idx = tid; idx < m * kLinesPerBlock; idx += 128) {
-      const int lo = idx / m, i = idx - lo * m;
+    const int w = ihi - ilo;
+    for (int idx = tid; idx < w * kLinesPerBlock; idx += 128) {
+      const int lo = idx / w, i = ilo + (idx - lo * w);
       if (lo < nl) J.Y[(int64_t)m * (line0 + lo) + i] = ys[i * P + lo];
     }
   }
@@ -383,13 +391,16 @@ void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStr
   }
   first_block[njobs] = blocks;
   for (int j = 0; j <= njobs; ++j) rb.first[j] = first_block[j];
+  // too few line tiles to keep every SM busy: several blocks share a tile, each a range of i
+  rb.isplit = 1;
+  while (rb.isplit < 4 && (int64_t)blocks * rb.isplit < 4 * 152) rb.isplit *= 2;
   static int attr = 0;
   if (smem > 48 * 1024 && smem > attr) {
     cudaFuncSetAttribute(k_mode_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr = smem;
   }
   launch_begin(kClassMode, s);
-  k_mode_tile<<<blocks, 128, smem, s>>>(rb);
+  k_mode_tile<<<blocks * rb.isplit, 128, smem, s>>>(rb);
   launch_end(kClassMode, s, flops, bytes);
 }
 

@@ -68,7 +68,8 @@ def test_gradients_match_oracle_adjoint_8cubed():
 
 def _J_gpu(G, theta, coef, waves, ut, tol):
     from paper_2311_06926_gb300.adjoint import cavity_solve, mass_misfit
-    x = cavity_solve(G, torch.tensor(theta), torch.tensor(coef), torch.tensor(G.nu), waves, tol)
+    x = cavity_solve(G, torch.tensor(theta), torch.tensor(coef),
+                     torch.tensor(G.nu, dtype=torch.float64), waves, tol)
     return float(mass_misfit(G, x, dev(ut)))
 
 
