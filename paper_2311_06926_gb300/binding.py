@@ -37,7 +37,8 @@ class KernelStat(ctypes.Structure):
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
-KERNEL_CLASSES = ["band_pass", "mode_product", "divergence", "vector", "mma_mode_product"]
+KERNEL_CLASSES = ["band_pass", "mode_product", "divergence", "vector", "mma_mode_product",
+                  "line_solve"]
 
 _lib = None
 

@@ -290,6 +290,58 @@ bool generalized_eigh(const Dense& K, const Dense& M, std::vector<double>& lam, 
   return true;
 }
 
+bool generalized_eigh_parity(const Dense& K, const Dense& M, std::vector<double>& lam, Dense& U,
+                             int* he_out) {
+  const int n = K.rows, h = n / 2, he = n - h;
+  // Q_e: columns (e_k + e_{n-1-k}) / sqrt(2) for k < h, plus e_h when n is odd;
+  // Q_o: columns (e_k - e_{n-1-k}) / sqrt(2) for k < h.
+  const double r = 1.0 / std::sqrt(2.0);
+  auto project = [&](const Dense& A, bool even) {
+    const int m = even ? he : h;
+    Dense R(m, m);
+    for (int a = 0; a < m; ++a)
+      for (int b = 0; b < m; ++b) {
+        // R_ab = q_a^T A q_b
+        auto q = [&](int c, int j) -> double {   // entry j of basis vector c
+          if (even && c == h && (n % 2)) return j == h ? 1.0 : 0.0;
+          if (j == c) return r;
+          if (j == n - 1 - c) return even ? r : -r;
+          return 0.0;
+        };
+        double sum = 0.0;
+        const int ja[2] = {a, n - 1 - a}, jb[2] = {b, n - 1 - b};
+        const int na = (even && a == h && (n % 2)) ? 1 : 2, nb = (even && b == h && (n % 2)) ? 1 : 2;
+        for (int x = 0; x < na; ++x)
+          for (int y = 0; y < nb; ++y) sum += q(a, ja[x]) * A(ja[x], jb[y]) * q(b, jb[y]);
+        R(a, b) = sum;
+      }
+    return R;
+  };
+  std::vector<double> le, lo;
+  Dense Ve, Vo;
+  if (!generalized_eigh(project(K, true), project(M, true), le, Ve)) return false;
+  if (h > 0 && !generalized_eigh(project(K, false), project(M, false), lo, Vo)) return false;
+  lam.assign(n, 0.0);
+  U = Dense(n, n);
+  for (int i = 0; i < he; ++i) {
+    lam[i] = le[i];
+    for (int k = 0; k < h; ++k) {
+      U(k, i) = r * Ve(k, i);
+      U(n - 1 - k, i) = r * Ve(k, i);
+    }
+    if (n % 2) U(h, i) = Ve(h, i);
+  }
+  for (int i = 0; i < h; ++i) {
+    lam[he + i] = lo[i];
+    for (int k = 0; k < h; ++k) {
+      U(k, he + i) = r * Vo(k, i);
+      U(n - 1 - k, he + i) = -r * Vo(k, i);
+    }
+  }
+  *he_out = he;
+  return true;
+}
+
 Band to_band(const Dense& D, double drop_tol) {
   Band B;
   B.rows = D.rows;

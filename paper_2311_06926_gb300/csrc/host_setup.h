@@ -39,6 +39,13 @@ Univariate build_univariate(int n, int p, double c_pen);
 // not positive definite.
 bool generalized_eigh(const Dense& K, const Dense& M, std::vector<double>& lam, Dense& U);
 
+// The same eigenpairs for a centrosymmetric pencil (K and M unchanged under reversing the index
+// order, as every 1D matrix on a uniform open knot vector is): the problem splits into one on
+// even vectors (u_k = u_{n-1-k}) and one on odd vectors (u_k = -u_{n-1-k}), solved separately.
+// Columns of U are ordered [even modes (he = ceil(n/2)); odd modes], each exactly even or odd.
+bool generalized_eigh_parity(const Dense& K, const Dense& M, std::vector<double>& lam, Dense& U,
+                             int* he);
+
 Band to_band(const Dense& D, double drop_tol);
 
 // 1D load of a sine mode against the interior N functions (own direction) or the M functions.

@@ -75,6 +75,7 @@ struct ModeArgs {
   const T* lam1; const T* lam2; const T* lam3; T scale;
   T post;   // if lam1 == null: the result is multiplied by post
   const T* invd;   // if set (FP64 path): the result is multiplied by invd[output index] instead
+  int eo_he;       // FP64 path: U's columns are [he even; n - he odd] eigenvectors (0: generic)
 };
 template <typename T>
 void mode_product(const ModeArgs<T>& a, cudaStream_t s);

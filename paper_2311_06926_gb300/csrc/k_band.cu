@@ -44,9 +44,15 @@ __device__ __forceinline__ T band_dot(const BandD<T>& D, int i, const T* __restr
   const T* x = X + base + (int64_t)s0 * stride;
   T sum = 0;
   if (W > 0) {
+    // two interleaved partial sums halve the dependent FMA chain
     const T* v = D.val + (int64_t)i * W;
+    T s1 = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) sum = fma(__ldg(v + w), __ldg(x + (int64_t)w * stride), sum);
+    for (int w = 0; w < W; ++w) {
+      if (w % 2 == 0) sum = fma(__ldg(v + w), __ldg(x + (int64_t)w * stride), sum);
+      else s1 = fma(__ldg(v + w), __ldg(x + (int64_t)w * stride), s1);
+    }
+    sum += s1;
   } else {
     const T* v = D.val + (int64_t)i * D.width;
     for (int w = 0; w < D.width; ++w) sum = fma(__ldg(v + w), __ldg(x + (int64_t)w * stride), sum);
@@ -398,10 +404,10 @@ void chol_solve_axis(double* x, int b, int p, int axis, const double* lb, const 
     cudaFuncSetAttribute(k_chol_line, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr = smem;
   }
-  launch_begin(kClassBand, s);
+  launch_begin(kClassLine, s);
   k_chol_line<<<(unsigned)((lines + kCholLines - 1) / kCholLines), kCholLines, smem, s>>>(
       x, b, p, axis, lb, inv_diag, post);
-  launch_end(kClassBand, s, 4.0 * (p + 1) * lines * b, 2.0 * lines * b * sizeof(double));
+  launch_end(kClassLine, s, 4.0 * (p + 1) * lines * b, 2.0 * lines * b * sizeof(double));
 }
 
 void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {

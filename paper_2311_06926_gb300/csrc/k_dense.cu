@@ -10,6 +10,8 @@
 //
 // FP32 (CUDA-core fallback of the reduced-precision preconditioner): 64 x 64 tiles, 256 threads,
 // 4 x 4 outputs per thread. FP64 uses the row-streaming kernel further below.
+#include <algorithm>
+
 #include "internal.h"
 #include "profile.h"
 
@@ -173,6 +175,8 @@ struct RowJob {
   double scale;
   Dims out;
   double post;
+  int eo;     // > 0: number of even modes (even/odd eigenvector split); 0: generic
+  int fwd;    // 1: Op(i, j) = U[j][i] (forward, to mode space); 0: Op(i, j) = U[i][j]
 };
 
 struct RowBatch {
@@ -241,43 +245,35 @@ __global__ void __launch_bounds__(128) k_mode_rows(const __grid_constant__ RowBa
   }
 }
 
-// Shared-memory staged variant: a block owns kLinesPerBlock neighbouring lines of one job and all
-// m outputs. The lines' inputs (K x lines) are loaded once, coalesced, into shared memory; each of
-// the 128 threads computes every 8th output index of one line, 4 at a time, reading its inputs
-// from shared memory and Op(i, j) through the read-only cache (two distinct i per warp). Outputs
-// of products along x1 are staged in shared memory for coalesced stores.
-constexpr int kLinesPerBlock = 16;
-constexpr int kGroups = 8;          // 128 threads = 16 lines x 8 output groups
-
-__global__ void __launch_bounds__(128) k_mode_tile(const __grid_constant__ RowBatch rb) {
+// Shared-memory staged FP64 variant. GB300's FP64 pipe reaches its rate only with many resident
+// warps, so every thread computes exactly one output (line, i): a block owns lb neighbouring lines
+// of one job and all m outputs of each (lb * m threads, lb about 512 / m). The lines' inputs
+// (K x lb) are loaded once, coalesced, into shared memory; Op(i, j) is read through the
+// read-only cache. Outputs of products along contiguous lines (L = 1) are staged in shared memory
+// for coalesced stores.
+__global__ void __launch_bounds__(512) k_mode_tile(const __grid_constant__ RowBatch rb) {
   extern __shared__ double shd[];
   int jb = 0;
-  const int64_t bidx = blockIdx.x / rb.isplit;
-  const int part = blockIdx.x % rb.isplit;
-  while (jb + 1 < rb.njobs && bidx >= rb.first[jb + 1]) ++jb;
+  while (jb + 1 < rb.njobs && (int64_t)blockIdx.x >= rb.first[jb + 1]) ++jb;
   const RowJob& J = rb.job[jb];
-  const int64_t lines = J.L * J.R;
-  const int64_t line0 = (bidx - rb.first[jb]) * kLinesPerBlock;
-  const int nl = (int)(lines - line0 < kLinesPerBlock ? lines - line0 : kLinesPerBlock);
   const int K = J.K, m = J.m;
-  // this block's output range [ilo, ihi), a multiple of 4 wide
-  const int chunk = ((m + rb.isplit - 1) / rb.isplit + 3) & ~3;
-  const int ilo = part * chunk;
-  const int ihi = ilo + chunk < m ? ilo + chunk : m;
-  constexpr int P = kLinesPerBlock + 1;
+  const int lb = J.groups;                       // lines per block for this job
+  const int64_t lines = J.L * J.R;
+  const int64_t line0 = ((int64_t)blockIdx.x - rb.first[jb]) * lb;
+  const int nl = (int)(lines - line0 < lb ? lines - line0 : lb);
+  const int P = lb + 1;
   double* xs = shd;                 // [K][P]
-  double* ys = shd + K * P;         // [m][P] (x1 products only)
+  double* ys = shd + K * P;         // [m][P] (L == 1 only)
   const int tid = threadIdx.x;
-  // load: line -> (l, r); input X[l + L (j + K r)]
+  const int nth = blockDim.x;
   if (J.L == 1) {
-    // x1 products: each line is a contiguous row of K entries
-    for (int idx = tid; idx < K * kLinesPerBlock; idx += 128) {
+    for (int idx = tid; idx < K * lb; idx += nth) {
       const int l = idx / K, j = idx - l * K;
       xs[j * P + l] = l < nl ? J.X[(int64_t)K * (line0 + l) + j] : 0.0;
     }
   } else {
-    for (int idx = tid; idx < K * kLinesPerBlock; idx += 128) {
-      const int l = idx % kLinesPerBlock, j = idx / kLinesPerBlock;
+    for (int idx = tid; idx < K * lb; idx += nth) {
+      const int l = idx % lb, j = idx / lb;
       double v = 0.0;
       if (l < nl) {
         const int64_t line = line0 + l;
@@ -288,64 +284,88 @@ __global__ void __launch_bounds__(128) k_mode_tile(const __grid_constant__ RowBa
     }
   }
   __syncthreads();
-  const int l = tid % kLinesPerBlock, grp = tid / kLinesPerBlock;
-  const bool valid = l < nl;
-  int64_t ybase = 0, ll = 0, r = 0;
-  if (valid && J.L > 1) {
+  auto out_index = [&](int l, int i) -> int64_t {
+    if (J.L == 1) return (int64_t)m * (line0 + l) + i;
     const int64_t line = line0 + l;
-    ll = line % J.L;
-    r = line / J.L;
-    ybase = ll + J.L * (int64_t)m * r;
-  }
-  const double* xcol = xs + l;
-  for (int i0 = ilo + grp * 4; i0 < ihi; i0 += kGroups * 4) {
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    const int cnt = ihi - i0 < 4 ? ihi - i0 : 4;
-    const double* op = J.U + i0 * J.op_i;
-    if (cnt == 4) {
-      for (int j = 0; j < K; ++j) {
-        const double xv = xcol[j * P];
-        const double* o = op + j * J.op_j;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[k] = fma(__ldg(o + k * J.op_i), xv, acc[k]);
-      }
+    const int64_t ll = line % J.L, r = line / J.L;
+    return ll + J.L * ((int64_t)i + (int64_t)m * r);
+  };
+  auto emit = [&](int l, int i, double v) {
+    const int64_t o = out_index(l, i);
+    if (J.invd) {
+      v *= J.invd[o];
+    } else if (J.lam1) {
+      const int i1 = (int)(o % J.out.n1);
+      const int64_t t2 = o / J.out.n1;
+      v /= J.scale * (J.lam1[i1] + J.lam2[(int)(t2 % J.out.n2)] + J.lam3[(int)(t2 / J.out.n2)]);
     } else {
-      for (int j = 0; j < K; ++j) {
-        const double xv = xcol[j * P];
-        const double* o = op + j * J.op_j;
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (k < cnt) acc[k] = fma(__ldg(o + k * J.op_i), xv, acc[k]);
+      v *= J.post;
+    }
+    if (J.L == 1) ys[i * P + l] = v;
+    else J.Y[o] = v;
+  };
+  if (J.eo == 0) {
+    // generic: thread -> (line l, output i), consecutive threads take consecutive i of one line
+    for (int q = tid; q < lb * m; q += nth) {
+      const int l = q / m, i = q - l * m;
+      if (l >= nl) continue;
+      double acc = 0.0;
+      const double* xcol = xs + l;
+      const double* op = J.U + i * J.op_i;
+      for (int j = 0; j < K; ++j) acc = fma(__ldg(op + j * J.op_j), xcol[j * P], acc);
+      emit(l, i, acc);
+    }
+  } else if (J.fwd) {
+    // even/odd forward: fold each line once (x_k + x_{K-1-k} | x_k - x_{K-1-k}), then every mode
+    // is a half-length dot with the top rows of U
+    const int he = J.eo, h = K - he;
+    double* xf = ys + (J.L == 1 ? m * P : 0);     // [K][P]
+    for (int idx = tid; idx < he * lb; idx += nth) {
+      const int l = idx % lb, k = idx / lb;
+      if (k < h) {
+        const double a = xs[k * P + l], b = xs[(K - 1 - k) * P + l];
+        xf[k * P + l] = a + b;
+        xf[(he + k) * P + l] = a - b;
+      } else {
+        xf[k * P + l] = xs[k * P + l];           // middle entry of an odd-length line
       }
     }
-    if (!valid) continue;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (k >= cnt) break;
-      const int i = i0 + k;
-      double v = acc[k];
-      int64_t o;
-      if (J.L == 1) o = (int64_t)m * (line0 + l) + i;
-      else o = ybase + J.L * (int64_t)i;
-      if (J.invd) {
-        v *= J.invd[o];
-      } else if (J.lam1) {
-        const int i1 = (int)(o % J.out.n1);
-        const int64_t t2 = o / J.out.n1;
-        v /= J.scale * (J.lam1[i1] + J.lam2[(int)(t2 % J.out.n2)] + J.lam3[(int)(t2 / J.out.n2)]);
+    __syncthreads();
+    for (int q = tid; q < lb * m; q += nth) {
+      const int l = q / m, i = q - l * m;
+      if (l >= nl) continue;
+      const int len = i < he ? he : h;
+      const double* xcol = xf + (i < he ? 0 : he * P) + l;
+      const double* op = J.U + i;                 // U[k][i], k < len
+      double acc = 0.0;
+      for (int k = 0; k < len; ++k) acc = fma(__ldg(op + (int64_t)k * J.op_j), xcol[k * P], acc);
+      emit(l, i, acc);
+    }
+  } else {
+    // even/odd backward: thread -> (line l, mirrored pair k); a_e over the even modes, a_o over
+    // the odd ones; outputs k = a_e + a_o and K-1-k = a_e - a_o
+    const int he = J.eo, h = K - he;
+    for (int q = tid; q < lb * he; q += nth) {
+      const int l = q / he, k = q - l * he;
+      if (l >= nl) continue;
+      const double* xcol = xs + l;
+      const double* row = J.U + (int64_t)k * J.op_i;   // U[k][j]
+      double ae = 0.0, ao = 0.0;
+      for (int j = 0; j < he; ++j) ae = fma(__ldg(row + j), xcol[j * P], ae);
+      if (k < h) {
+        for (int j = 0; j < h; ++j) ao = fma(__ldg(row + he + j), xcol[(he + j) * P], ao);
+        emit(l, k, ae + ao);
+        emit(l, K - 1 - k, ae - ao);
       } else {
-        v *= J.post;
+        emit(l, k, ae);
       }
-      if (J.L == 1) ys[i * P + l] = v;
-      else J.Y[o] = v;
     }
   }
-  if (J.L == 1 && ihi > ilo) {
+  if (J.L == 1) {
     __syncthreads();
-    const int w = ihi - ilo;
-    for (int idx = tid; idx < w * kLinesPerBlock; idx += 128) {
-      const int lo = idx / w, i = ilo + (idx - lo * w);
-      if (lo < nl) J.Y[(int64_t)m * (line0 + lo) + i] = ys[i * P + lo];
+    for (int idx = tid; idx < m * nl; idx += nth) {
+      const int lo = idx / m, io = idx - lo * m;
+      J.Y[(int64_t)m * (line0 + lo) + io] = ys[io * P + lo];
     }
   }
 }
@@ -356,7 +376,7 @@ template <>
 void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStream_t s) {
   RowBatch rb{};
   rb.njobs = njobs;
-  int blocks = 0, smem = 0;
+  int blocks = 0, smem = 0, threads = 32;
   double flops = 0, bytes = 0;
   int first_block[kMaxModeJobs + 1];
   for (int j = 0; j < njobs; ++j) {
@@ -372,7 +392,11 @@ void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStr
     J.m = m.m;
     J.L = m.axis == 1 ? 1 : (m.axis == 2 ? in.n1 : (int64_t)in.n1 * in.n2);
     J.R = m.axis == 1 ? (int64_t)in.n2 * in.n3 : (m.axis == 2 ? in.n3 : 1);
-    J.groups = 1;
+    J.eo = m.eo_he;
+    J.fwd = m.trans ? 1 : 0;
+    // threads per line: one per output, or one per mirrored output pair (even/odd backward)
+    const int tpl = (J.eo && !J.fwd) ? J.eo : m.m;
+    J.groups = tpl >= 512 ? 1 : 512 / tpl;        // lines per block
     J.threads = 0;
     J.invd = m.invd;
     J.lam1 = m.invd ? nullptr : m.lam1;
@@ -382,25 +406,31 @@ void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStr
     J.out = in.with(m.axis, m.m);
     J.post = m.lam1 ? 1.0 : m.post;
     first_block[j] = blocks;
-    blocks += (int)((J.L * J.R + kLinesPerBlock - 1) / kLinesPerBlock);
-    // the kernel stages outputs in shared memory whenever the lines are contiguous (L == 1)
-    const int sm = (J.K + (J.L == 1 ? J.m : 0)) * (kLinesPerBlock + 1) * (int)sizeof(double);
+    blocks += (int)((J.L * J.R + J.groups - 1) / J.groups);
+    threads = std::max(threads, std::min(512, ((J.groups * tpl + 31) / 32) * 32));
+    // inputs [K][P]; outputs staged when the lines are contiguous (L == 1); folded inputs
+    // (even/odd forward)
+    const int sm = (J.K + (J.L == 1 ? J.m : 0) + ((J.eo && J.fwd) ? J.K : 0)) * (J.groups + 1) *
+                   (int)sizeof(double);
     smem = sm > smem ? sm : smem;
-    flops += 2.0 * J.L * J.R * (double)J.K * J.m;
+    if (J.eo) {   // even/odd split: two half-size products per line
+      const double he = J.eo, ho = J.K - J.eo;
+      flops += 2.0 * J.L * J.R * (he * he + ho * ho);
+    } else {
+      flops += 2.0 * J.L * J.R * (double)J.K * J.m;
+    }
     bytes += ((double)in.size() + (double)in.with(m.axis, m.m).size()) * sizeof(double);
   }
   first_block[njobs] = blocks;
   for (int j = 0; j <= njobs; ++j) rb.first[j] = first_block[j];
-  // too few line tiles to keep every SM busy: several blocks share a tile, each a range of i
   rb.isplit = 1;
-  while (rb.isplit < 4 && (int64_t)blocks * rb.isplit < 4 * 152) rb.isplit *= 2;
   static int attr = 0;
   if (smem > 48 * 1024 && smem > attr) {
     cudaFuncSetAttribute(k_mode_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr = smem;
   }
   launch_begin(kClassMode, s);
-  k_mode_tile<<<blocks * rb.isplit, 128, smem, s>>>(rb);
+  k_mode_tile<<<blocks, threads, smem, s>>>(rb);
   launch_end(kClassMode, s, flops, bytes);
 }
 

@@ -14,7 +14,8 @@ enum KernelClass {
   kClassDiv = 2,       // discrete divergence and its transpose
   kClassVector = 3,    // Krylov vector kernels, dot products, conversions
   kClassMma = 4,       // tensor-core mode products
-  kNumClasses = 5
+  kClassLine = 5,      // banded Cholesky line solves (FP64 pressure block)
+  kNumClasses = 6
 };
 
 void launch_begin(int cls, cudaStream_t s);

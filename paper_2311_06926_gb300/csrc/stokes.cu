@@ -107,6 +107,7 @@ struct Ops {
   BandD<T> M{}, K{}, Mc{}, Tc{};
   const T *U_N = nullptr, *lam_N = nullptr, *U_T = nullptr, *lam_T = nullptr;
   const T* invd = nullptr;   // FP64: 1 / (2 nu (l1 + l2 + l3)) per velocity entry
+  int eo_N = 0, eo_T = 0;    // FP64: even-mode counts of the parity-split eigenvectors
   const double* chol_lb = nullptr;     // FP64 pressure block: banded Cholesky factor of M-check
   const double* chol_inv = nullptr;
   int chol_p = 0;
@@ -329,22 +330,27 @@ struct Ops {
           j[c] = mjob(src, dst, U[c][k], n[c][k], trans_of[st], comp(c), axis_of[st], L[c][0],
                       L[c][1], L[c][2], 2 * nu);
           j[c].invd = invd ? invd + o : nullptr;
-        }
-        else
+        } else {
           j[c] = mjob(src, dst, U[c][k], n[c][k], trans_of[st], comp(c), axis_of[st]);
+        }
+        j[c].eo_he = (k == c) ? eo_N : eo_T;
       }
       mode_product_multi<T>(j, 3, s);
     }
   }
 
-  void mode(const T* X, T* Y, const T* U, int n, int trans, Dims in, int axis, T post = 1) const {
+  void mode(const T* X, T* Y, const T* U, int n, int trans, Dims in, int axis, T post = 1,
+            int eo = 0) const {
     ModeArgs<T> m = mjob(X, Y, U, n, trans, in, axis, nullptr, nullptr, nullptr, 1, post);
+    m.eo_he = eo;
     mode_product<T>(m, s);
   }
 
   // pressure block: y = 2 nu (M-check^-1)^(x)3 x = 2 nu (U_T U_T^T)^(x)3 x
   void minv_Q(const T* x, T* y) const {
-    if (chol_lb) {
+    // FP64: banded Cholesky line solves for large b (few FP64 flops, enough lines in parallel);
+    // for small b their sequential recurrence is latency-bound and the dense route is faster
+    if (chol_lb && b >= 64) {
       // 2 nu (M-check^-1)^(x)3 by banded Cholesky solves along each direction (exact; far fewer
       // FP64 flops than the dense eigenvector route)
       copy_async(y, x, npres * sizeof(T), s);
@@ -359,12 +365,12 @@ struct Ops {
       return;
     }
     const Dims d{b, b, b};
-    mode(x, f1, U_T, b, 1, d, 1);
-    mode(f1, f2, U_T, b, 1, d, 2);
-    mode(f2, f1, U_T, b, 1, d, 3);
-    mode(f1, f2, U_T, b, 0, d, 3);
-    mode(f2, f1, U_T, b, 0, d, 2);
-    mode(f1, y, U_T, b, 0, d, 1, 2 * nu);
+    mode(x, f1, U_T, b, 1, d, 1, 1, eo_T);
+    mode(f1, f2, U_T, b, 1, d, 2, 1, eo_T);
+    mode(f2, f1, U_T, b, 1, d, 3, 1, eo_T);
+    mode(f1, f2, U_T, b, 0, d, 3, 1, eo_T);
+    mode(f2, f1, U_T, b, 0, d, 2, 1, eo_T);
+    mode(f1, y, U_T, b, 0, d, 1, 2 * nu, eo_T);
   }
 };
 
@@ -1001,9 +1007,12 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
     const Univariate& u = c->uv;
     std::vector<double> lN, lT;
     Dense UN, UT;
-    if (!generalized_eigh(u.K, u.M, lN, UN))
+    int heN = 0, heT = 0;
+    // every 1D matrix on the uniform open knot vector is centrosymmetric: split each generalised
+    // eigenproblem into its even and odd halves (exact parity of the eigenvectors)
+    if (!generalized_eigh_parity(u.K, u.M, lN, UN, &heN))
       throw SetupError{"mass matrix of the N basis is not positive definite"};
-    if (!generalized_eigh(u.Tc, u.Mc, lT, UT))
+    if (!generalized_eigh_parity(u.Tc, u.Mc, lT, UT, &heT))
       throw SetupError{"pressure mass matrix is not positive definite"};
     for (double l : lT)
       if (!(l > 0.0)) throw SetupError{"T-check is not positive definite (raise C_pen)"};
@@ -1012,6 +1021,8 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
     const Band bM = to_band(u.M, 1e-15), bK = to_band(u.K, 1e-15);
     const Band bMc = to_band(u.Mc, 1e-15), bTc = to_band(u.Tc, 1e-15);
     init_ops<double>(c, c->od, bM, bK, bMc, bTc, UN.v, lN, UT.v, lT);
+    c->od.eo_N = heN;
+    c->od.eo_T = heT;
     {
       // reciprocal eigenvalue sums of the fast diagonalisation, one per velocity entry
       std::vector<double> inv((size_t)c->nvel);

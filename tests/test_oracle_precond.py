@@ -162,3 +162,27 @@ def test_schur_sequence_spectra():
     X2i = _dense_op(lambda v: hyperpower_Q(base, v, 2, 2, "inner"), S.n_pres)
     ref = 2 * X1 - X1 @ AQ2 @ X1
     assert np.abs(X2i - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+def test_schur_sequences_condition_numbers():
+    """Sec. 5.2 / Fig. 5 (qualitative): with inner updates (Eq. 4.5) the preconditioned Schur
+    condition number decreases at every step; without (Eq. 4.6) it stops improving, because that
+    sequence converges to the inverse of B^T P_V0^-1 B instead of the Schur complement."""
+    S = StokesSystem(2, 2)
+    base = BasePreconditioner(S)
+    A, B = S.A.toarray(), S.B.toarray()
+    Sch = B.T @ np.linalg.solve(A, B)
+
+    def kappa(schur, k):
+        X = _dense_op(lambda v: hyperpower_Q(base, v, 2, k, schur), S.n_pres)
+        ev = np.sort(np.abs(sla.eigvals(X @ Sch).real))[1:]      # drop the constant null mode
+        return ev[-1] / ev[0]
+
+    inner = [kappa("inner", k) for k in range(5)]
+    none = [kappa("none", k) for k in range(5)]
+    assert all(inner[k + 1] < inner[k] for k in range(4))          # keeps improving
+    assert inner[4] < 1.2
+    # without inner updates only the first three updates help (Sec. 5.2): it stalls above 1.4
+    assert all(none[k + 1] < none[k] for k in range(3))
+    assert abs(none[4] - none[3]) < 0.1 and none[4] > 1.4
+    assert inner[4] < none[4]
