@@ -49,13 +49,13 @@ def _gpu_grads(n, p, nu, theta, coef, waves, ut, tol=1e-12, steps=1):
     x = cavity_solve(G, th, cf, nu_t, waves, tol)
     J = mass_misfit(G, x, dev(ut))
     J.backward()
-    out = (float(J), th.grad.numpy().copy(), cf.grad.numpy().copy(), float(nu_t.grad))
+    out = (float(J.detach()), th.grad.numpy().copy(), cf.grad.numpy().copy(), float(nu_t.grad))
     G.close()
     return out
 
 
 def test_gradients_match_oracle_adjoint_8cubed():
-    """cfg5 check at 8^3: GPU adjoint (MINRES to 1e-12) against the oracle's direct adjoint."""
+    """At 8^3: GPU adjoint (MINRES to 1e-12) against the oracle's direct adjoint."""
     n, p, nu = 8, 2, 1.0
     theta, coef, waves, ut = _problem(n, p)
     J, gt, gc, gn = _gpu_grads(n, p, nu, theta, coef, waves, ut)
@@ -73,39 +73,57 @@ def _J_gpu(G, theta, coef, waves, ut, tol):
     return float(mass_misfit(G, x, dev(ut)))
 
 
-def _fd_check(n, p, nu, tol=1e-12):
+def _central(G_or_pair, theta, coef, waves, ut, tol, which, h):
+    """Central difference of J along one parameter: theta[5], coef[1, 3] or nu."""
+    if which == "theta":
+        e = np.zeros(16)
+        e[5] = h
+        return (_J_gpu(G_or_pair, theta + e, coef, waves, ut, tol)
+                - _J_gpu(G_or_pair, theta - e, coef, waves, ut, tol)) / (2 * h)
+    if which == "coef":
+        c1, c2 = coef.copy(), coef.copy()
+        c1[1, 3] += h
+        c2[1, 3] -= h
+        return (_J_gpu(G_or_pair, theta, c1, waves, ut, tol)
+                - _J_gpu(G_or_pair, theta, c2, waves, ut, tol)) / (2 * h)
+    Gp, Gm = G_or_pair
+    return (_J_gpu(Gp, theta, coef, waves, ut, tol) - _J_gpu(Gm, theta, coef, waves, ut, tol)) / (2 * h)
+
+
+def _fd_check(n, p, nu, rel_small, tol=1e-12):
+    """Central differences of J against the adjoint gradient, at two steps.
+
+    Step 1e-6 (the workload's): the quotient carries the solves' error in J (each solve reaches
+    a relative residual of 1e-12, amplified by the condition number) divided by 2h, which sets
+    rel_small. Step 0.1 for theta and the force coefficients: the load is linear in them and the
+    solve is linear, so J is quadratic in them and a central difference is exact at any step;
+    the larger step shrinks the solve noise by 1e5 and allows a tight tolerance. nu enters the
+    operator, J is only smooth in it, so its second check uses step 1e-4 (truncation error
+    O(h^2))."""
     theta, coef, waves, ut = _problem(n, p, seed=11)
     J, gt, gc, gn = _gpu_grads(n, p, nu, theta, coef, waves, ut, tol=tol)
     G = _ctx(n, p, nu, maxit=5000)
     G.set_preconditioner(2, 1)
-    h = 1e-6
-    k = 5
-    e = np.zeros(16)
-    e[k] = h
-    fd = (_J_gpu(G, theta + e, coef, waves, ut, tol) - _J_gpu(G, theta - e, coef, waves, ut, tol)) / (2 * h)
-    assert fd == pytest.approx(gt[k], rel=1e-4)
-    c1, c2 = coef.copy(), coef.copy()
-    c1[1, 3] += h
-    c2[1, 3] -= h
-    fd = (_J_gpu(G, theta, c1, waves, ut, tol) - _J_gpu(G, theta, c2, waves, ut, tol)) / (2 * h)
-    assert fd == pytest.approx(gc[1, 3], rel=1e-4, abs=1e-6 * np.abs(gc).max())
+    for h, rel in ((1e-6, rel_small), (0.1, 1e-6)):
+        assert _central(G, theta, coef, waves, ut, tol, "theta", h) == pytest.approx(gt[5], rel=rel)
+        fd = _central(G, theta, coef, waves, ut, tol, "coef", h)
+        assert fd == pytest.approx(gc[1, 3], rel=rel, abs=rel * 1e-2 * np.abs(gc).max())
     G.close()
-    Gp = _ctx(n, p, nu + h, maxit=5000)
-    Gm = _ctx(n, p, nu - h, maxit=5000)
-    for Gx in (Gp, Gm):
-        Gx.set_preconditioner(2, 1)
-    fd = (_J_gpu(Gp, theta, coef, waves, ut, tol) - _J_gpu(Gm, theta, coef, waves, ut, tol)) / (2 * h)
-    assert fd == pytest.approx(gn, rel=1e-4)
-    Gp.close()
-    Gm.close()
+    for h, rel in ((1e-6, rel_small), (1e-4, 1e-5)):
+        pair = (_ctx(n, p, nu + h, maxit=5000), _ctx(n, p, nu - h, maxit=5000))
+        for Gx in pair:
+            Gx.set_preconditioner(2, 1)
+        assert _central(pair, theta, coef, waves, ut, tol, "nu", h) == pytest.approx(gn, rel=rel)
+        for Gx in pair:
+            Gx.close()
 
 
 def test_central_differences_16cubed():
-    """Central differences (step 1e-6) of J computed by GPU solves against the adjoint gradient."""
-    _fd_check(16, 3, 1.0)
+    """Central differences of J computed by GPU solves against the adjoint gradient."""
+    _fd_check(16, 3, 1.0, rel_small=1e-4)
 
 
 @pytest.mark.slow
 def test_central_differences_64cubed_p3():
-    """cfg5 size: 64^3 elements, p = 3."""
-    _fd_check(64, 3, 1.0)
+    """The differentiation workload size: 64^3 elements, p = 3."""
+    _fd_check(64, 3, 1.0, rel_small=2e-3)

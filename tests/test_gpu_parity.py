@@ -1,7 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
 
 Sizes span one to several 64-wide tiles of the dense mode products with ragged tails
-(b = 2 ... 65) and the cfg1 workload (8^3, p = 2)."""
+(b = 2 ... 65) and the 8^3, p = 2 cavity workload."""
 import numpy as np
 import pytest
 import torch
@@ -92,7 +92,7 @@ def _compare_solve(n, p, q, s, rhs_kind="cavity", tol=1e-8):
 
 
 @pytest.mark.parametrize("q,s", [(2, 0), (2, 1), (3, 1), (2, 2)])
-def test_solve_cfg1_cavity(q, s):
+def test_solve_cavity_8cubed(q, s):
     """8^3, p = 2, nu = 1 cavity; MINRES to 1e-8: identical iterations, solution to 1e-10."""
     _compare_solve(8, 2, q, s)
 
@@ -105,8 +105,8 @@ def test_solve_small_and_forced(n, p):
 @pytest.mark.slow
 @pytest.mark.parametrize("q", [2, 3])
 @pytest.mark.parametrize("s", [0, 1, 2, 3])
-def test_solve_cfg2_sweep(q, s):
-    """32^3, p = 3 cavity (cfg2): the full order x steps sweep against the matrix-free oracle."""
+def test_solve_sweep_32cubed(q, s):
+    """32^3, p = 3 cavity: the full order x steps sweep against the matrix-free oracle."""
     _compare_solve(32, 3, q, s)
 
 
