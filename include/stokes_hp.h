@@ -178,7 +178,8 @@ typedef struct stokes_kernel_stat {
 } stokes_kernel_stat;
 int stokes_profile_begin(stokes_t ctx);
 int stokes_profile_end(stokes_t ctx, stokes_kernel_stat* out, int capacity);
-/* Number of kernels this library has launched in this process (all contexts and threads). */
+/* Number of kernels this library has launched in this process (all contexts and threads). Kernels
+ * of a captured CUDA graph are counted each time the graph is replayed, not when it is captured. */
 int64_t stokes_kernel_launches(void);
 
 /* ---- allocation-free variant (no counterpart in the paper) --------------------------------

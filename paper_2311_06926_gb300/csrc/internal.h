@@ -6,11 +6,19 @@
 namespace shp {
 
 // Banded 1D matrix on the device: D(i, start[i] + w) = val[i * width + w].
+// Square matrices whose nonzeros all lie within |i - j| <= half also carry a centred copy:
+// D(i, i - half + k) = cval[i * cpitch + k] for k < 2 half + 1 (zero where i - half + k is out of
+// range), cpitch = (2 half + 4) & ~3 (16-byte rows), rows padded with zeros to a multiple of 8.
+// cval is null when the matrix is not of that form. Rows tlo <= i < thi of the centred copy are
+// identical (the Toeplitz interior of a matrix on a uniform knot vector); tlo = thi = 0 if none.
 template <typename T>
 struct BandD {
   int rows, cols, width;
   const int* start;
   const T* val;
+  const T* cval;
+  int half, cpitch;
+  int tlo, thi;
 };
 
 // Extents of a 3D tensor, x1 fastest: index = i1 + n1 * (i2 + n2 * i3).

@@ -267,6 +267,211 @@ __global__ void __launch_bounds__(256) k_band_tile(const __grid_constant__ PassB
   }
 }
 
+// Asynchronous global -> shared copies (cp.async): a thread issues all of its copies before it
+// waits, so a block keeps its whole slab in flight instead of one load per warp.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// FP32 pass for centred band matrices (every term of the launch has the centred width
+// W = 2H + 1). Tiles as k_band_tile: 32 neighbouring lines per block, the whole band extent.
+// - The input slabs (stored with H zero rows above and below, so row i of the output reads slab
+//   rows i .. i + W - 1 with no clamping) and the centred coefficients are copied with cp.async,
+//   all copies in flight at once.
+// - Each lane forms kSlideR consecutive outputs of its line from one register window of
+//   kSlideR + W - 1 inputs: (kSlideR + W - 1) / kSlideR shared loads per output instead of W.
+// - Interior rows of a matrix on a uniform knot vector are identical (Toeplitz); chunks of rows
+//   inside that range take their coefficients from registers, the few boundary chunks from
+//   shared memory.
+// - Index arithmetic is 32-bit (the launcher only takes tensors below 2^31 entries).
+constexpr int kSlideR = 8;
+
+__host__ __device__ constexpr int slide_rows(int m) { return (m + kSlideR - 1) / kSlideR * kSlideR; }
+
+__device__ __forceinline__ void line_geometry32(int axis, const Dims& d, int line, int* base,
+                                                int* stride) {
+  if (axis == 1) {
+    *base = d.n1 * line;
+    *stride = 1;
+  } else if (axis == 2) {
+    const int i3 = line / d.n1, i1 = line - i3 * d.n1;
+    *base = i1 + d.n1 * d.n2 * i3;
+    *stride = d.n1;
+  } else {
+    *base = line;
+    *stride = d.n1 * d.n2;
+  }
+}
+
+template <int W, int R>
+__device__ __forceinline__ void slide_term(const float* xs, const float* cf_rows, bool interior,
+                                           const float (&creg)[W], float ct, float (&acc)[R]) {
+  constexpr int P = kTileLines + 1;
+  constexpr int CP = (W + 3) & ~3;
+  float v[R + W - 1];
+#pragma unroll
+  for (int k = 0; k < R + W - 1; ++k) v[k] = xs[k * P];
+  if (interior) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        if (k % 2 == 0) s0 = fmaf(creg[k], v[r + k], s0);
+        else s1 = fmaf(creg[k], v[r + k], s1);
+      }
+      acc[r] = fmaf(ct, s0 + s1, acc[r]);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float4* c4 = reinterpret_cast<const float4*>(cf_rows + r * CP);
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int w4 = 0; w4 < CP / 4; ++w4) {
+        const float4 c = c4[w4];
+        if (4 * w4 + 0 < W) s0 = fmaf(c.x, v[r + 4 * w4 + 0], s0);
+        if (4 * w4 + 1 < W) s1 = fmaf(c.y, v[r + 4 * w4 + 1], s1);
+        if (4 * w4 + 2 < W) s0 = fmaf(c.z, v[r + 4 * w4 + 2], s0);
+        if (4 * w4 + 3 < W) s1 = fmaf(c.w, v[r + 4 * w4 + 3], s1);
+      }
+      acc[r] = fmaf(ct, s0 + s1, acc[r]);
+    }
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(256, 3) k_band_slide(const __grid_constant__ PassBatch<float> pb) {
+  constexpr int H = (W - 1) / 2;
+  constexpr int CP = (W + 3) & ~3;
+  constexpr int R = kSlideR;
+  constexpr int P = kTileLines + 1;
+  extern __shared__ __align__(16) float sh[];
+  int jb = 0;
+  while (jb + 1 < pb.njobs && (int)blockIdx.x >= pb.first_block[jb + 1]) ++jb;
+  const PassArgs<float>& a = pb.job[jb];
+  const int axis = a.axis;
+  const int m = a.D0.rows;   // square: output extent = input extent along the axis
+  const int mr = slide_rows(m);
+  const int rs = mr + 2 * H;   // slab rows
+  const int nt = a.nterms;
+  const Dims out = a.in;
+  const int lines = (int)(out.size() / m);
+  const int line0 = ((int)blockIdx.x - pb.first_block[jb]) * kTileLines;
+  const int nl = lines - line0 < kTileLines ? lines - line0 : kTileLines;
+  float* ys = sh + nt * rs * P;                                          // m x P (passes along x1)
+  float* cf = sh + ((nt * rs * P + (axis == 1 ? m * P : 0) + 3) & ~3);   // nt x mr x CP
+  const int tid = threadIdx.x;
+  const int lane = tid % 32, warp = tid / 32, nwarps = blockDim.x / 32;
+  for (int t = 0; t < nt; ++t) {
+    const float* src = (t == 0 ? a.D0 : a.D1).cval;
+    for (int q = tid; q < mr * CP / 4; q += blockDim.x) cp_async16(cf + t * mr * CP + 4 * q, src + 4 * q);
+  }
+  int base = 0, stride = 0;
+  if (lane < nl) line_geometry32(axis, a.in, line0 + lane, &base, &stride);
+  for (int t = 0; t < nt; ++t) {
+    const float* X = t == 0 ? a.X0 : a.X1;
+    float* xs = sh + t * rs * P;
+    // zero rows: H above, H + (mr - m) below
+    for (int q = tid; q < H * P; q += blockDim.x) xs[q] = 0.f;
+    for (int q = tid; q < (rs - H - m) * P; q += blockDim.x) xs[(H + m) * P + q] = 0.f;
+    if (axis == 1) {
+      for (int l = warp; l < kTileLines; l += nwarps) {
+        const float* row = X + a.in.n1 * (line0 + l);
+        float* dst = xs + H * P + l;
+        if (l < nl) {
+          for (int j = lane; j < m; j += 32) cp_async4(dst + j * P, row + j);
+        } else {
+          for (int j = lane; j < m; j += 32) dst[j * P] = 0.f;
+        }
+      }
+    } else {
+      float* dst = xs + (H + warp) * P + lane;
+      if (lane < nl) {
+        const float* src = X + base + warp * stride;
+        for (int j = warp; j < m; j += nwarps, dst += nwarps * P, src += nwarps * stride)
+          cp_async4(dst, src);
+      } else {
+        for (int j = warp; j < m; j += nwarps, dst += nwarps * P) *dst = 0.f;
+      }
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  int gbase = 0, gstride = 0, gstep = 0;
+  if (a.g && lane < nl) {
+    const int line = line0 + lane;
+    int idx3[3];
+    if (axis == 1) { idx3[0] = 0; idx3[2] = line / out.n2; idx3[1] = line - idx3[2] * out.n2; }
+    else if (axis == 2) { idx3[2] = line / out.n1; idx3[0] = line - idx3[2] * out.n1; idx3[1] = 0; }
+    else { idx3[1] = line / out.n1; idx3[0] = line - idx3[1] * out.n1; idx3[2] = 0; }
+    const int g1 = a.gdims.n1, g12 = a.gdims.n1 * a.gdims.n2;
+    gbase = idx3[0] + g1 * idx3[1] + g12 * idx3[2];
+    gstride = axis == 1 ? 1 : (axis == 2 ? g1 : g12);
+    gstep = a.gaxis == 1 ? 1 : (a.gaxis == 2 ? g1 : g12);
+  }
+  // interior (Toeplitz) rows shared by every term, and their coefficients in registers
+  int tlo = a.D0.tlo, thi = a.D0.thi;
+  if (nt > 1) {
+    tlo = max(tlo, a.D1.tlo);
+    thi = min(thi, a.D1.thi);
+  }
+  float creg0[W], creg1[W];
+  const int trow = tlo < thi ? tlo : 0;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    creg0[k] = cf[trow * CP + k];
+    creg1[k] = nt > 1 ? cf[mr * CP + trow * CP + k] : 0.f;
+  }
+  const float c0 = a.c0, c1 = a.c1;
+  const float* Z = a.Z;
+  const float* g = a.g;
+  const float cz = a.cz;
+  float* Y = a.Y;
+  for (int i0 = warp * R; i0 < mr; i0 += nwarps * R) {
+    float acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0.f;
+    const bool interior = i0 >= tlo && i0 + R <= thi;
+    slide_term<W, R>(sh + i0 * P + lane, cf + i0 * CP, interior, creg0, c0, acc);
+    if (nt > 1)
+      slide_term<W, R>(sh + rs * P + i0 * P + lane, cf + (mr + i0) * CP, interior, creg1, c1, acc);
+    if (lane < nl) {
+      const int o0 = base + stride * i0;
+      const int g0 = gbase + gstride * i0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (i0 + r < m) {
+          float val = acc[r];
+          const int o = o0 + stride * r;
+          if (Z) val = fmaf(cz, Z[o], val);
+          if (g) {
+            const int gi = g0 + gstride * r;
+            val += g[gi] - g[gi + gstep];
+          }
+          if (axis == 1) ys[(i0 + r) * P + lane] = val;
+          else Y[o] = val;
+        }
+      }
+    }
+  }
+  if (axis == 1) {
+    __syncthreads();
+    for (int l = warp; l < nl; l += nwarps) {
+      float* row = Y + m * (line0 + l);
+      for (int i = lane; i < m; i += 32) row[i] = ys[i * P + l];
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_divergence(const T* __restrict__ u1, const T* __restrict__ u2,
                                                     const T* __restrict__ u3, int a, int b,
@@ -440,6 +645,52 @@ void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {
   }
   pb.first_block[njobs] = blocks;
   pb.seg = 1;
+  // centred kernel when every term of every job is square with a centred copy of one width
+  int Wc = 2 * jobs[0].D0.half + 1;
+  int smem_c = 0;
+  for (int j = 0; j < njobs && Wc > 0; ++j) {
+    const PassArgs<float>& a = jobs[j];
+    const int nt = a.nterms > 1 ? 2 : 1;
+    for (int t = 0; t < nt; ++t) {
+      const BandD<float>& D = t == 0 ? a.D0 : a.D1;
+      if (!D.cval || D.rows != D.cols || D.rows != a.in.get(a.axis) || 2 * D.half + 1 != Wc ||
+          D.cpitch != ((Wc + 3) & ~3))
+        Wc = 0;
+    }
+    if (Wc == 0) break;
+    if (a.in.size() >= ((int64_t)1 << 31) || (a.g && a.gdims.size() >= ((int64_t)1 << 31))) {
+      Wc = 0;   // 32-bit indexing only
+      break;
+    }
+    const int mr = slide_rows(a.D0.rows);
+    const int rs = mr + Wc - 1;
+    const int sm = ((nt * rs + (a.axis == 1 ? a.D0.rows : 0)) * (kTileLines + 1) + 3) / 4 * 4 *
+                       (int)sizeof(float) +
+                   nt * mr * ((Wc + 3) & ~3) * (int)sizeof(float);
+    smem_c = sm > smem_c ? sm : smem_c;
+  }
+  if (Wc < 3 || Wc > 21) Wc = 0;   // the instantiated centred widths
+  if (Wc > 0) {
+    launch_begin(kClassBand, s);
+    switch (Wc) {
+#define SHP_SLIDE_W(w)                                                                          \
+  case w: {                                                                                     \
+    static int attr = 0;                                                                        \
+    if (smem_c > 48 * 1024 && smem_c > attr) {                                                  \
+      cudaFuncSetAttribute(k_band_slide<w>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c); \
+      attr = smem_c;                                                                            \
+    }                                                                                           \
+    k_band_slide<w><<<blocks, 256, smem_c, s>>>(pb);                                            \
+    break;                                                                                      \
+  }
+      SHP_SLIDE_W(3) SHP_SLIDE_W(5) SHP_SLIDE_W(7) SHP_SLIDE_W(9) SHP_SLIDE_W(11) SHP_SLIDE_W(13)
+      SHP_SLIDE_W(15) SHP_SLIDE_W(17) SHP_SLIDE_W(19) SHP_SLIDE_W(21)
+#undef SHP_SLIDE_W
+      default: break;
+    }
+    launch_end(kClassBand, s, flops, bytes);
+    return;
+  }
   // one band width per launch (all terms of all jobs); unrolled kernels for the common widths
   int W = jobs[0].D0.width;
   for (int j = 0; j < njobs; ++j)

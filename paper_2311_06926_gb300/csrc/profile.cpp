@@ -69,6 +69,8 @@ void launch_end(int cls, cudaStream_t s, double flops, double bytes) {
 
 int64_t launch_count() { return g_launches.load(); }
 
+void launch_add(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 void profiler_collect(Profiler* p, int64_t* launches, double* ms, double* flops, double* bytes) {
   for (int c = 0; c < kNumClasses; ++c) {
     launches[c] = 0;

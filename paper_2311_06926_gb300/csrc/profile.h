@@ -21,6 +21,8 @@ enum KernelClass {
 void launch_begin(int cls, cudaStream_t s);
 void launch_end(int cls, cudaStream_t s, double flops, double bytes);
 int64_t launch_count();
+// Adjusts the counter by n (kernels of a captured graph: counted on replay, not on capture).
+void launch_add(int64_t n);
 
 struct Profiler;
 Profiler* profiler_create();

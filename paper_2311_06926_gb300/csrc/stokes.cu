@@ -83,9 +83,58 @@ BandD<T> upload_band(Arena& ar, const Band& b, cudaStream_t s) {
      "upload band");
   ck(cudaMemcpyAsync(v, tv.data(), tv.size() * sizeof(T), cudaMemcpyHostToDevice, s),
      "upload band");
-  ck(cudaStreamSynchronize(s), "upload band");
   d.start = st;
   d.val = v;
+  d.cval = nullptr;
+  d.half = 0;
+  d.cpitch = 0;
+  d.tlo = d.thi = 0;
+  // centred copy for square matrices (every matrix of the operator applies is one)
+  std::vector<T> cv;
+  if (b.rows == b.cols) {
+    int half = 0;
+    for (int i = 0; i < b.rows; ++i)
+      for (int w = 0; w < b.width; ++w)
+        if (b.val[(size_t)i * b.width + w] != 0.0) half = std::max(half, std::abs(b.start[i] + w - i));
+    const int pitch = (2 * half + 4) & ~3;
+    const int rows8 = (b.rows + 7) / 8 * 8;
+    cv.assign((size_t)rows8 * pitch, T(0));
+    for (int i = 0; i < b.rows; ++i)
+      for (int w = 0; w < b.width; ++w) {
+        const int k = b.start[i] + w - i + half;
+        if (k >= 0 && k <= 2 * half && b.start[i] + w < b.cols)
+          cv[(size_t)i * pitch + k] = (T)b.val[(size_t)i * b.width + w];
+      }
+    // Toeplitz interior: rows equal to the middle row. In FP32 an interior entry may round to a
+    // neighbouring float of the middle row's (the FP64 entries agree to rounding only); entries
+    // within 2 float ulps of the middle row's are set to it, so one coefficient set serves every
+    // interior row.
+    d.tlo = d.thi = 0;
+    if (sizeof(T) == 4 && b.rows >= 8) {
+      const int mid = b.rows / 2;
+      auto same = [&](int i) {
+        for (int k = 0; k < pitch; ++k) {
+          const double x = (double)cv[(size_t)i * pitch + k], y = (double)cv[(size_t)mid * pitch + k];
+          if (std::fabs(x - y) > 2.0 * 1.1920928955078125e-07 * std::fabs(y)) return false;
+        }
+        return true;
+      };
+      int lo = mid, hi = mid + 1;
+      while (lo > 0 && same(lo - 1)) --lo;
+      while (hi < b.rows && same(hi)) ++hi;
+      for (int i = lo; i < hi; ++i)
+        for (int k = 0; k < pitch; ++k) cv[(size_t)i * pitch + k] = cv[(size_t)mid * pitch + k];
+      d.tlo = lo;
+      d.thi = hi;
+    }
+    T* c = ar.alloc<T>(cv.size());
+    ck(cudaMemcpyAsync(c, cv.data(), cv.size() * sizeof(T), cudaMemcpyHostToDevice, s),
+       "upload band");
+    d.cval = c;
+    d.half = half;
+    d.cpitch = pitch;
+  }
+  ck(cudaStreamSynchronize(s), "upload band");
   return d;
 }
 
@@ -378,30 +427,40 @@ struct Ops {
 template <typename T>
 struct HyperPower {
   const Ops<T>* op = nullptr;
+  // Optional second operator set (own workspace, own stream) for the pressure block. P_k is block
+  // diagonal (Eq. 4.4, 4.5), so the velocity and pressure recursions are independent: apply()
+  // runs them as two concurrent branches joined by events. Both branches launch the same kernels
+  // on disjoint buffers, so the result is bit-identical to running them one after the other.
+  const Ops<T>* opq = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool serial = false;   // run the branches one after the other (per-launch profiling)
   int order = 2;
   int schur = STOKES_SCHUR_INNER;
-  std::vector<T*> vr, vacc, vt, vu;   // velocity buffers per level 1..max_steps
+  struct VLevels {
+    std::vector<T*> r, acc, t, u;   // velocity buffers per level 1..max_steps
+  };
+  VLevels vmain, vq;                  // velocity recursion; velocity solves inside the Schur block
   std::vector<T*> qr, qacc, qt, qu;   // pressure buffers per level
   T *bv = nullptr, *hv = nullptr;     // velocity buffers of the Schur approximation
   int64_t counts[4] = {0, 0, 0, 0};   // fd_V, minv_Q, A, (B + B^T)
 
-  void V(int s, const T* x, T* y) {
-    const int64_t n = op->nvel;
+  void V(const Ops<T>& o, const VLevels& L, int s, const T* x, T* y) {
+    const int64_t n = o.nvel;
     if (s == 0) {
-      op->fd_V(x, y);
+      o.fd_V(x, y);
       ++counts[0];
       return;
     }
-    T *r = vr[s], *acc = vacc[s], *t = vt[s], *u = vu[s];
-    copy_async(r, x, n * sizeof(T), op->s);
-    copy_async(acc, x, n * sizeof(T), op->s);
+    T *r = L.r[s], *acc = L.acc[s], *t = L.t[s], *u = L.u[s];
+    copy_async(r, x, n * sizeof(T), o.s);
+    copy_async(acc, x, n * sizeof(T), o.s);
     for (int j = 1; j < order; ++j) {
-      V(s - 1, r, t);
-      op->apply_A(t, u);
+      V(o, L, s - 1, r, t);
+      o.apply_A(t, u);
       ++counts[2];
-      hp_update<T>(r, u, acc, n, op->s);
+      hp_update<T>(r, u, acc, n, o.s);
     }
-    V(s - 1, acc, y);
+    V(o, L, s - 1, acc, y);
   }
 
   int level_of(int m) const {
@@ -409,31 +468,40 @@ struct HyperPower {
     return m == 1 ? 0 : m;
   }
 
-  void Q(int m, const T* x, T* y) {
-    const int64_t n = op->npres;
+  void Q(const Ops<T>& o, const VLevels& L, int m, const T* x, T* y) {
+    const int64_t n = o.npres;
     if (m == 0) {
-      op->minv_Q(x, y);
+      o.minv_Q(x, y);
       ++counts[1];
       return;
     }
     T *r = qr[m], *acc = qacc[m], *t = qt[m], *u = qu[m];
     const int l = level_of(m);
-    copy_async(r, x, n * sizeof(T), op->s);
-    copy_async(acc, x, n * sizeof(T), op->s);
+    copy_async(r, x, n * sizeof(T), o.s);
+    copy_async(acc, x, n * sizeof(T), o.s);
     for (int j = 1; j < order; ++j) {
-      Q(m - 1, r, t);
-      op->apply_B(t, bv);          // A~_Q t = B^T P_{V,l}^-1 B t
-      V(l, bv, hv);
-      op->apply_Bt(hv, u);
+      Q(o, L, m - 1, r, t);
+      o.apply_B(t, bv);          // A~_Q t = B^T P_{V,l}^-1 B t
+      V(o, L, l, bv, hv);
+      o.apply_Bt(hv, u);
       ++counts[3];
-      hp_update<T>(r, u, acc, n, op->s);
+      hp_update<T>(r, u, acc, n, o.s);
     }
-    Q(m - 1, acc, y);
+    Q(o, L, m - 1, acc, y);
   }
 
   void apply(int steps, const T* x, T* y) {
-    V(steps, x, y);
-    Q(steps, x + op->nvel, y + op->nvel);
+    if (!opq || serial) {
+      V(*op, vmain, steps, x, y);
+      Q(*op, vmain, steps, x + op->nvel, y + op->nvel);
+      return;
+    }
+    ck(cudaEventRecord(ev_fork, op->s), "fork");
+    ck(cudaStreamWaitEvent(opq->s, ev_fork, 0), "fork");
+    V(*op, vmain, steps, x, y);
+    Q(*opq, vq, steps, x + op->nvel, y + op->nvel);
+    ck(cudaEventRecord(ev_join, opq->s), "join");
+    ck(cudaStreamWaitEvent(op->s, ev_join, 0), "join");
   }
 };
 
@@ -452,6 +520,8 @@ struct stokes_ctx {
   Arena arena;
   Univariate uv;
   Ops<double> od;
+  Ops<double> odq;                       // FP64 operators of the concurrent pressure branch
+  cudaStream_t stream_q = nullptr;       // its stream (owned)
   Ops<float> of;
   HyperPower<double> hd;
   HyperPower<float> hf;
@@ -473,9 +543,12 @@ struct stokes_ctx {
   double* xi = nullptr;           // MINRES iterate (context-owned, so captured graphs are reusable)
   double* ratio_dev = nullptr;    // per-iteration convergence ratios
   std::map<int, cudaGraphExec_t> minres_graphs;
+  std::map<int, int64_t> minres_graph_kernels;   // kernels per replay of each graph
   std::vector<RmpPlan> tc_plans;
   ~stokes_ctx() {
     for (auto& kv : minres_graphs) cudaGraphExecDestroy(kv.second);
+    if (hd.ev_fork) cudaEventDestroy(hd.ev_fork);
+    if (hd.ev_join) cudaEventDestroy(hd.ev_join);
   }
 };
 
@@ -495,6 +568,9 @@ int cuda_fail(stokes_ctx* c, const CudaError& e) {
 void check_launch(const char* what) {
   ck(cudaGetLastError(), what);
 }
+
+template <typename T>
+void alloc_workspace(stokes_ctx* c, Ops<T>& o);
 
 template <typename T>
 void init_ops(stokes_ctx* c, Ops<T>& o, const Band& M, const Band& K, const Band& Mc,
@@ -517,6 +593,13 @@ void init_ops(stokes_ctx* c, Ops<T>& o, const Band& M, const Band& K, const Band
   o.lam_N = upload<T>(ar, lN, s);
   o.U_T = upload<T>(ar, UT, s);
   o.lam_T = upload<T>(ar, lT, s);
+  alloc_workspace(c, o);
+}
+
+// temporaries of one operator set (a second set lets a second stream run the same operators)
+template <typename T>
+void alloc_workspace(stokes_ctx* c, Ops<T>& o) {
+  Arena& ar = c->arena;
   const size_t pres = (size_t)c->npres, vel = (size_t)c->nvel;
   const size_t ping = std::max(vel, 2 * pres);   // all velocity components, or two pressures
   o.tK = ar.alloc<T>(vel);
@@ -638,24 +721,39 @@ void init_tc(stokes_ctx* c, const Dense& UN, const std::vector<double>& lN, cons
 }
 
 template <typename T>
-void init_hp(stokes_ctx* c, HyperPower<T>& h, const Ops<T>& o) {
+void alloc_levels(stokes_ctx* c, typename HyperPower<T>::VLevels& L) {
+  const int n = c->opts.max_steps;
+  L.r.assign(n + 1, nullptr);
+  L.acc.assign(n + 1, nullptr);
+  L.t.assign(n + 1, nullptr);
+  L.u.assign(n + 1, nullptr);
+  for (int l = 1; l <= n; ++l) {
+    L.r[l] = c->arena.alloc<T>(c->nvel);
+    L.acc[l] = c->arena.alloc<T>(c->nvel);
+    L.t[l] = c->arena.alloc<T>(c->nvel);
+    L.u[l] = c->arena.alloc<T>(c->nvel);
+  }
+}
+
+// opq: operator set of the concurrent pressure branch, or null (one stream)
+template <typename T>
+void init_hp(stokes_ctx* c, HyperPower<T>& h, const Ops<T>& o, const Ops<T>* opq) {
   Arena& ar = c->arena;
   h.op = &o;
+  h.opq = opq;
   h.schur = c->opts.schur;
   const int L = c->opts.max_steps;
-  h.vr.assign(L + 1, nullptr);
-  h.vacc.assign(L + 1, nullptr);
-  h.vt.assign(L + 1, nullptr);
-  h.vu.assign(L + 1, nullptr);
+  alloc_levels<T>(c, h.vmain);
+  if (opq) {
+    alloc_levels<T>(c, h.vq);
+    ck(cudaEventCreateWithFlags(&h.ev_fork, cudaEventDisableTiming), "event");
+    ck(cudaEventCreateWithFlags(&h.ev_join, cudaEventDisableTiming), "event");
+  }
   h.qr.assign(L + 1, nullptr);
   h.qacc.assign(L + 1, nullptr);
   h.qt.assign(L + 1, nullptr);
   h.qu.assign(L + 1, nullptr);
   for (int l = 1; l <= L; ++l) {
-    h.vr[l] = ar.alloc<T>(c->nvel);
-    h.vacc[l] = ar.alloc<T>(c->nvel);
-    h.vt[l] = ar.alloc<T>(c->nvel);
-    h.vu[l] = ar.alloc<T>(c->nvel);
     h.qr[l] = ar.alloc<T>(c->npres);
     h.qacc[l] = ar.alloc<T>(c->npres);
     h.qt[l] = ar.alloc<T>(c->npres);
@@ -768,19 +866,29 @@ int run_minres(stokes_ctx* c, const double* f, double tol, double* x, int* iters
       auto it = c->minres_graphs.find(key);
       if (it == c->minres_graphs.end()) {
         cudaGraph_t g = nullptr;
+        const int64_t before = launch_count();
         ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
         minres_pair(c);
         ck(cudaStreamEndCapture(s, &g), "capture");
+        // captured kernels run only when the graph is replayed: count them there
+        const int64_t k = launch_count() - before;
+        launch_add(-k);
         ck(cudaGraphInstantiate(&exec, g, 0), "instantiate");
         cudaGraphDestroy(g);
         c->minres_graphs[key] = exec;
+        c->minres_graph_kernels[key] = k;
       } else {
         exec = it->second;
       }
     }
+    const int64_t graph_kernels = use_graph ? c->minres_graph_kernels[c->order * 16 + c->steps] : 0;
     for (int pair = 0; 2 * pair < c->opts.maxit; ++pair) {
-      if (use_graph) ck(cudaGraphLaunch(exec, s), "graph launch");
-      else minres_pair(c);
+      if (use_graph) {
+        ck(cudaGraphLaunch(exec, s), "graph launch");
+        launch_add(graph_kernels);
+      } else {
+        minres_pair(c);
+      }
       check_launch("minres iteration");
       ck(cudaMemcpyAsync(h, c->st, sizeof(MinresState), cudaMemcpyDeviceToHost, s), "state");
       ck(cudaStreamSynchronize(s), "sync");
@@ -1061,12 +1169,21 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
       c->od.chol_inv = upload<double>(c->arena, ld, c->stream);
       c->od.chol_p = p;
     }
-    init_hp<double>(c, c->hd, c->od);
+    const Ops<double>* odq = nullptr;
+    if (!reduced(c)) {
+      // FP64 preconditioner: the pressure recursion gets its own operator set and stream
+      ck(cudaStreamCreateWithFlags(&c->stream_q, cudaStreamNonBlocking), "stream");
+      c->odq = c->od;
+      c->odq.s = c->stream_q;
+      alloc_workspace<double>(c, c->odq);
+      odq = &c->odq;
+    }
+    init_hp<double>(c, c->hd, c->od, odq);
     if (reduced(c)) {
       init_ops<float>(c, c->of, bM, bK, bMc, bTc, UN.v, lN, UT.v, lT);
       if (o.precision == STOKES_PREC_TF32 || o.precision == STOKES_PREC_BF16)
         init_tc(c, UN, lN, UT, lT, o.precision == STOKES_PREC_BF16 ? kMmaBF16 : kMmaTF32);
-      init_hp<float>(c, c->hf, c->of);
+      init_hp<float>(c, c->hf, c->of, nullptr);
       c->xf = c->arena.alloc<float>(c->ntot);
       c->yf = c->arena.alloc<float>(c->ntot);
     }
@@ -1362,6 +1479,7 @@ int stokes_profile_begin(stokes_t c) {
   if (!c->prof) c->prof = profiler_create();
   profiler_activate(c->prof);
   c->prof_on = true;
+  c->hd.serial = true;   // per-launch event timing: no concurrent branches
   return STOKES_OK;
 }
 
@@ -1372,6 +1490,7 @@ int stokes_profile_end(stokes_t c, stokes_kernel_stat* out, int capacity) {
   profiler_collect(c->prof, l, ms, fl, by);
   profiler_activate(nullptr);
   c->prof_on = false;
+  c->hd.serial = false;
   const int k = std::min(capacity, (int)kNumClasses);
   for (int i = 0; i < k; ++i) {
     out[i].kernel_class = i;
@@ -1391,9 +1510,12 @@ void stokes_destroy(stokes_t c) {
   if (c->prof) profiler_destroy(c->prof);
   if (c->st_host) cudaFreeHost(c->st_host);
   if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->stream_q) cudaStreamSynchronize(c->stream_q);
   cudaStream_t s = c->own_stream ? c->stream : nullptr;
+  cudaStream_t sq = c->stream_q;
   delete c;   // frees the arena
   if (s) cudaStreamDestroy(s);
+  if (sq) cudaStreamDestroy(sq);
 }
 
 const char* stokes_last_error(stokes_t c) {

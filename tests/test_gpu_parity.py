@@ -214,3 +214,28 @@ def test_fp32_hyperpower_exercises_banded_passes(n, p, q, s):
     err = relerr(host(G.apply_hyperpower(q, s, dev(x))), ref)
     G.close()
     assert err < 2.0 ** -24 * 64 * 64, err
+
+
+@pytest.mark.parametrize("n,p,q,s", [(5, 2, 2, 1), (13, 3, 2, 2), (20, 3, 3, 2)])
+def test_concurrent_branches_bit_identical(n, p, q, s):
+    """The FP64 preconditioner runs its velocity and pressure recursions (Eq. 4.4, 4.5) as two
+    concurrent branches on disjoint buffers; per-launch profiling runs them one after the
+    other. Both orders must give the same bits, on repeated applications and inside solves."""
+    S, base, Kop, F = oracle(n, p)
+    G = _ctx(n, p, 1.0, max_order=q, max_steps=s)
+    x = dev(synthetic.random_vector(S.size, 900 + n))
+    conc = [G.apply_hyperpower(q, s, x) for _ in range(3)]
+    G.profile_begin()
+    ser = G.apply_hyperpower(q, s, x)
+    G.profile_end()
+    for y in conc:
+        assert torch.equal(y, ser)
+    G.set_preconditioner(q, s)
+    f = dev(S.rhs_lid(1.0))
+    x1, it1, rr1, _ = G.solve(f, 1e-10)
+    G.profile_begin()
+    x2, it2, rr2, _ = G.solve(f, 1e-10)
+    G.profile_end()
+    G.close()
+    assert it1 == it2 and rr1 == rr2
+    assert torch.equal(x1, x2)
