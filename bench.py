@@ -34,6 +34,28 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 1.25
 TF32_NOMINAL_TFLOPS = 1100.0
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the
+# captured launches) of a dominant kernel class on a workload, from one ncu capture, with the
+# SHA-256 of the kernel's source file when it was taken. roofline.traffic reports it only while
+# that source is unchanged, and null otherwise.
+TRAFFIC = {}
+
+
+def traffic_for(kernel_class, precision, workload):
+    import hashlib
+    t = TRAFFIC.get((kernel_class, precision, workload))
+    if not t:
+        return None, None
+    src = os.path.join(ROOT, "paper_2311_06926_gb300", "csrc", t["source"])
+    try:
+        with open(src, "rb") as fh:
+            digest = hashlib.sha256(fh.read()).hexdigest()
+    except OSError:
+        return None, None
+    if digest != t["sha256"]:
+        return None, None
+    return t["bytes_per_launch"], t["profile"]
+
 WORKLOADS = {
     "cavity32": dict(n=32, p=3, sweep=[(q, s) for q in (2, 3) for s in (0, 1, 2, 3)],
                      precision="fp64",
@@ -450,6 +472,10 @@ def main():
                 "launches_per_step": dom["launches"],
                 "avg_launch_us": 1e3 * dom["ms"] / max(dom["launches"], 1),
                 "peak_note": "of measured" if "hbm_gbs" in peaks else "of fallback"}
+    traffic, traffic_src = traffic_for(dom_name, prec, args.workload)
+    roof["traffic"] = traffic
+    if traffic is not None:
+        roof["traffic_source"] = traffic_src
     step_ms_profiled = sum(v["ms"] for v in prof.values())
 
     mixed = None

@@ -5,6 +5,35 @@
 
 namespace shp {
 
+// ---- programmatic dependent launch ---------------------------------------------------------------
+// Every kernel of the library is launched with programmatic stream serialization: the next kernel
+// in a stream is scheduled as soon as every block of the current one has exited, before the grid
+// has formally completed, so part of its launch latency overlaps the end of the previous kernel.
+// Each kernel therefore begins with pdl_begin(): griddepcontrol.wait blocks until the preceding
+// grid has completed and its memory operations are visible, so no read or write of a kernel races
+// with its predecessor. (No kernel triggers its dependents early: blocks of a waiting grid would
+// hold warp slots and shared memory that a concurrent stream's kernel could use.) For a kernel
+// launched without the attribute the wait returns immediately.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
+template <typename... P, typename... A>
+inline void launch_k(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     A... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
+
 // Banded 1D matrix on the device: D(i, start[i] + w) = val[i * width + w].
 // Square matrices whose nonzeros all lie within |i - j| <= half also carry a centred copy:
 // D(i, i - half + k) = cval[i * cpitch + k] for k < 2 half + 1 (zero where i - half + k is out of
@@ -52,7 +81,7 @@ struct PassArgs {
 template <typename T>
 void band_pass(const PassArgs<T>& a, cudaStream_t s);
 // Several independent passes (up to kMaxPassJobs, e.g. one per velocity component) in one launch.
-constexpr int kMaxPassJobs = 6;
+constexpr int kMaxPassJobs = 8;
 template <typename T>
 void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s);
 
@@ -102,6 +131,8 @@ void chol_solve_axis(double* x, int b, int p, int axis, const double* lb, const 
 // Deterministic dot product: fixed grid, fixed-order tree reduction. Result written to *out
 // (device). `partials` holds kDotBlocks values.
 constexpr int kDotBlocks = 512;
+// grid of the multi-vector dot products (fixed, so their reductions are deterministic)
+constexpr int kMultiDotBlocks = 152 * 4;   // one resident wave (4 blocks per SM)
 template <typename T>
 void dot(const T* x, const T* y, int64_t n, T* partials, T* out, cudaStream_t s);
 // y = a x + b y with a, b from host
@@ -114,7 +145,7 @@ void copy_async(void* dst, const void* src, size_t bytes, cudaStream_t s);
 // y += sign * (*alpha) * x with alpha in device memory
 void axpy_dev(const double* alpha, double sign, const double* x, double* y, int64_t n,
               cudaStream_t s);
-// y[k] = <V_k, w> for k < nvec (V_k = V + k * ldv); deterministic, partials: nvec * kDotBlocks
+// y[k] = <V_k, w> for k < nvec (V_k = V + k * ldv); deterministic, partials: nvec * kMultiDotBlocks
 void multi_dot(const double* V, int64_t ldv, int nvec, const double* w, int64_t n,
                double* partials, double* out, cudaStream_t s);
 // w += sign * sum_k h[k] V_k (h in device memory)

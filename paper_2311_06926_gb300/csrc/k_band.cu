@@ -24,7 +24,8 @@ struct PassBatch {
   PassArgs<T> job[kMaxPassJobs];
   int first_block[kMaxPassJobs + 1];
   int njobs;
-  int seg;   // outputs per thread along the band direction
+  int seg;     // outputs per thread along the band direction
+  int flat1;   // FP64: passes along x1 enumerate (line, row) with the row fastest
 };
 
 // Each thread computes a segment of `seg` consecutive outputs along the band direction of one
@@ -60,12 +61,74 @@ __device__ __forceinline__ T band_dot(const BandD<T>& D, int i, const T* __restr
   return sum;
 }
 
+// Passes along x1 with flat1 set: threads enumerate (line, row) with the row fastest, so a warp
+// reads a contiguous stretch of the input and writes a contiguous stretch of the output; the band
+// coefficients of the job are staged in shared memory transposed ([term][w][row]) so that lanes
+// with consecutive rows read consecutive words.
+template <typename T, int W>
+__device__ __forceinline__ void band_pass_flat_x1(const PassArgs<T>& a, int64_t t, T* csh) {
+  const int m = a.D0.rows;
+  const Dims out = a.in.with(1, m);
+  if (t >= out.size()) return;
+  const int64_t line = t / m;
+  const int i = (int)(t - line * m);
+  const T* cs = csh + i;
+  const int64_t base_in = (int64_t)a.in.n1 * line;
+  const T* x0 = a.X0 + base_in + __ldg(a.D0.start + i);
+  T s0 = 0, s1 = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    if (w % 2 == 0) s0 = fma(cs[w * m], __ldg(x0 + w), s0);
+    else s1 = fma(cs[w * m], __ldg(x0 + w), s1);
+  }
+  T acc = a.c0 * (s0 + s1);
+  if (a.nterms > 1) {
+    const T* x1 = a.X1 + base_in + __ldg(a.D1.start + i);
+    T u0 = 0, u1 = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      if (w % 2 == 0) u0 = fma(cs[(W + w) * m], __ldg(x1 + w), u0);
+      else u1 = fma(cs[(W + w) * m], __ldg(x1 + w), u1);
+    }
+    acc += a.c1 * (u0 + u1);
+  }
+  const int64_t o = (int64_t)m * line + i;
+  if (a.Z) acc += a.cz * a.Z[o];
+  if (a.g) {
+    // g has extents b^3; along x1 the output's own index is i, the line is (i2, i3)
+    const Dims gd = a.gdims;
+    const int64_t i3 = line / out.n2, i2 = line - i3 * out.n2;
+    const int64_t gi = i + (int64_t)gd.n1 * (i2 + (int64_t)gd.n2 * i3);
+    const int64_t gstep = a.gaxis == 1 ? 1 : (a.gaxis == 2 ? (int64_t)gd.n1 : (int64_t)gd.n1 * gd.n2);
+    acc += a.g[gi] - a.g[gi + gstep];
+  }
+  a.Y[o] = acc;
+}
+
 template <typename T, int W>
 __global__ void __launch_bounds__(256) k_band_pass(const __grid_constant__ PassBatch<T> pb) {
+  pdl_begin();
   int jb = 0;
   while (jb + 1 < pb.njobs && (int)blockIdx.x >= pb.first_block[jb + 1]) ++jb;
   const PassArgs<T>& a = pb.job[jb];
   const int axis = a.axis;
+  if constexpr (W > 0) {
+    if (pb.flat1 && axis == 1) {
+      extern __shared__ __align__(16) unsigned char band_smem[];
+      T* csh = reinterpret_cast<T*>(band_smem);
+      const int m = a.D0.rows;
+      const int nt = a.nterms > 1 ? 2 : 1;
+      for (int idx = threadIdx.x; idx < nt * W * m; idx += blockDim.x) {
+        const int tt = idx / (W * m), r = idx - tt * (W * m);
+        const int w = r / m, i = r - w * m;
+        csh[idx] = (tt == 0 ? a.D0 : a.D1).val[(int64_t)i * W + w];
+      }
+      __syncthreads();
+      band_pass_flat_x1<T, W>(a, (int64_t)(blockIdx.x - pb.first_block[jb]) * blockDim.x + threadIdx.x,
+                              csh);
+      return;
+    }
+  }
   const Dims out = a.in.with(axis, a.D0.rows);
   const int m = a.D0.rows;
   const int seg_n = pb.seg;
@@ -158,6 +221,7 @@ __device__ __forceinline__ void line_geometry(int axis, const Dims& d, int64_t l
 // W: band width of every term of the launch (0: runtime width, generic loop).
 template <int W>
 __global__ void __launch_bounds__(256) k_band_tile(const __grid_constant__ PassBatch<float> pb) {
+  pdl_begin();
   extern __shared__ __align__(16) float sh[];
   int jb = 0;
   while (jb + 1 < pb.njobs && (int)blockIdx.x >= pb.first_block[jb + 1]) ++jb;
@@ -348,8 +412,10 @@ __device__ __forceinline__ void slide_term(const float* xs, const float* cf_rows
   }
 }
 
-template <int W>
+// HAS_G: every job of the launch adds the difference term of g (none has a Z term).
+template <int W, bool HAS_G>
 __global__ void __launch_bounds__(256, 3) k_band_slide(const __grid_constant__ PassBatch<float> pb) {
+  pdl_begin();
   constexpr int H = (W - 1) / 2;
   constexpr int CP = (W + 3) & ~3;
   constexpr int R = kSlideR;
@@ -388,6 +454,7 @@ __global__ void __launch_bounds__(256, 3) k_band_slide(const __grid_constant__ P
         const float* row = X + a.in.n1 * (line0 + l);
         float* dst = xs + H * P + l;
         if (l < nl) {
+#pragma unroll 4
           for (int j = lane; j < m; j += 32) cp_async4(dst + j * P, row + j);
         } else {
           for (int j = lane; j < m; j += 32) dst[j * P] = 0.f;
@@ -397,6 +464,7 @@ __global__ void __launch_bounds__(256, 3) k_band_slide(const __grid_constant__ P
       float* dst = xs + (H + warp) * P + lane;
       if (lane < nl) {
         const float* src = X + base + warp * stride;
+#pragma unroll 4
         for (int j = warp; j < m; j += nwarps, dst += nwarps * P, src += nwarps * stride)
           cp_async4(dst, src);
       } else {
@@ -407,7 +475,7 @@ __global__ void __launch_bounds__(256, 3) k_band_slide(const __grid_constant__ P
   cp_async_wait_all();
   __syncthreads();
   int gbase = 0, gstride = 0, gstep = 0;
-  if (a.g && lane < nl) {
+  if (HAS_G && lane < nl) {
     const int line = line0 + lane;
     int idx3[3];
     if (axis == 1) { idx3[0] = 0; idx3[2] = line / out.n2; idx3[1] = line - idx3[2] * out.n2; }
@@ -432,10 +500,9 @@ __global__ void __launch_bounds__(256, 3) k_band_slide(const __grid_constant__ P
     creg1[k] = nt > 1 ? cf[mr * CP + trow * CP + k] : 0.f;
   }
   const float c0 = a.c0, c1 = a.c1;
-  const float* Z = a.Z;
   const float* g = a.g;
-  const float cz = a.cz;
   float* Y = a.Y;
+  const bool ax1 = axis == 1;
   for (int i0 = warp * R; i0 < mr; i0 += nwarps * R) {
     float acc[R];
 #pragma unroll
@@ -444,22 +511,31 @@ __global__ void __launch_bounds__(256, 3) k_band_slide(const __grid_constant__ P
     slide_term<W, R>(sh + i0 * P + lane, cf + i0 * CP, interior, creg0, c0, acc);
     if (nt > 1)
       slide_term<W, R>(sh + rs * P + i0 * P + lane, cf + (mr + i0) * CP, interior, creg1, c1, acc);
-    if (lane < nl) {
-      const int o0 = base + stride * i0;
+    if (HAS_G && lane < nl) {
       const int g0 = gbase + gstride * i0;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if (i0 + r < m) {
-          float val = acc[r];
-          const int o = o0 + stride * r;
-          if (Z) val = fmaf(cz, Z[o], val);
-          if (g) {
-            const int gi = g0 + gstride * r;
-            val += g[gi] - g[gi + gstep];
-          }
-          if (axis == 1) ys[(i0 + r) * P + lane] = val;
-          else Y[o] = val;
-        }
+      for (int r = 0; r < R; ++r)
+        if (i0 + r < m) acc[r] += g[g0 + gstride * r] - g[g0 + gstride * r + gstep];
+    }
+    if (ax1) {
+      float* yr = ys + i0 * P + lane;
+      if (i0 + R <= m) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) yr[r * P] = acc[r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (i0 + r < m) yr[r * P] = acc[r];
+      }
+    } else if (lane < nl) {
+      float* yo = Y + base + stride * i0;
+      if (i0 + R <= m) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) yo[stride * r] = acc[r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (i0 + r < m) yo[stride * r] = acc[r];
       }
     }
   }
@@ -477,6 +553,7 @@ __global__ void __launch_bounds__(256) k_divergence(const T* __restrict__ u1, co
                                                     const T* __restrict__ u3, int a, int b,
                                                     T* __restrict__ delta, const T* __restrict__ q,
                                                     T nu, T* __restrict__ e) {
+  pdl_begin();
   const int64_t total = (int64_t)b * b * b;
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += step) {
@@ -510,6 +587,7 @@ __global__ void __launch_bounds__(256) k_divergence(const T* __restrict__ u1, co
 template <typename T>
 __global__ void __launch_bounds__(256) k_div_transpose(const T* __restrict__ g, int a, int b, T* y1,
                                                        T* y2, T* y3, int accumulate) {
+  pdl_begin();
   const int64_t nc = (int64_t)a * b * b;
   const int64_t total = 3 * nc;
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
@@ -543,6 +621,7 @@ __global__ void __launch_bounds__(kCholLines) k_chol_line(double* __restrict__ x
                                                           const double* __restrict__ lb,
                                                           const double* __restrict__ inv,
                                                           double post) {
+  pdl_begin();
   extern __shared__ double cs[];
   constexpr int P = kCholLines + 1;
   const int64_t lines = (int64_t)b * b;
@@ -610,7 +689,7 @@ void chol_solve_axis(double* x, int b, int p, int axis, const double* lb, const 
     attr = smem;
   }
   launch_begin(kClassLine, s);
-  k_chol_line<<<(unsigned)((lines + kCholLines - 1) / kCholLines), kCholLines, smem, s>>>(
+  launch_k(k_chol_line, (unsigned)((lines + kCholLines - 1) / kCholLines), kCholLines, smem, s, 
       x, b, p, axis, lb, inv_diag, post);
   launch_end(kClassLine, s, 4.0 * (p + 1) * lines * b, 2.0 * lines * b * sizeof(double));
 }
@@ -670,6 +749,10 @@ void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {
     smem_c = sm > smem_c ? sm : smem_c;
   }
   if (Wc < 3 || Wc > 21) Wc = 0;   // the instantiated centred widths
+  // the slide kernel has no Z term, and either every job or none adds the g term
+  bool has_g = jobs[0].g != nullptr;
+  for (int j = 0; j < njobs && Wc > 0; ++j)
+    if (jobs[j].Z || (jobs[j].g != nullptr) != has_g) Wc = 0;
   if (Wc > 0) {
     launch_begin(kClassBand, s);
     switch (Wc) {
@@ -677,10 +760,14 @@ void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {
   case w: {                                                                                     \
     static int attr = 0;                                                                        \
     if (smem_c > 48 * 1024 && smem_c > attr) {                                                  \
-      cudaFuncSetAttribute(k_band_slide<w>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c); \
+      cudaFuncSetAttribute(k_band_slide<w, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                           smem_c);                                                             \
+      cudaFuncSetAttribute(k_band_slide<w, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                           smem_c);                                                             \
       attr = smem_c;                                                                            \
     }                                                                                           \
-    k_band_slide<w><<<blocks, 256, smem_c, s>>>(pb);                                            \
+    if (has_g) launch_k(k_band_slide<w, true>, blocks, 256, smem_c, s, pb);                      \
+    else launch_k(k_band_slide<w, false>, blocks, 256, smem_c, s, pb);                          \
     break;                                                                                      \
   }
       SHP_SLIDE_W(3) SHP_SLIDE_W(5) SHP_SLIDE_W(7) SHP_SLIDE_W(9) SHP_SLIDE_W(11) SHP_SLIDE_W(13)
@@ -704,7 +791,7 @@ void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {
       cudaFuncSetAttribute(k_band_tile<w>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
       attr = smem;                                                                            \
     }                                                                                         \
-    k_band_tile<w><<<blocks, 256, smem, s>>>(pb);                                             \
+    launch_k(k_band_tile<w>, blocks, 256, smem, s, pb);                                             \
     break;                                                                                    \
   }
     SHP_TILE_W(3) SHP_TILE_W(5) SHP_TILE_W(7) SHP_TILE_W(9) SHP_TILE_W(11) SHP_TILE_W(13)
@@ -715,7 +802,7 @@ void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {
         cudaFuncSetAttribute(k_band_tile<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = smem;
       }
-      k_band_tile<0><<<blocks, 256, smem, s>>>(pb);
+      launch_k(k_band_tile<0>, blocks, 256, smem, s, pb);
     }
 #undef SHP_TILE_W
   }
@@ -730,6 +817,21 @@ void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s) {
   }
   PassBatch<T> pb{};
   pb.njobs = njobs;
+  int W = jobs[0].D0.width;
+  for (int j = 0; j < njobs; ++j)
+    if (jobs[j].D0.width != W || (jobs[j].nterms > 1 && jobs[j].D1.width != W)) W = 0;
+  // x1 passes with the flat (line, row) layout when the band width is a compiled one and the
+  // transposed coefficients fit in shared memory
+  int smem = 0;
+  pb.flat1 = W > 0 && W <= 13;
+  for (int j = 0; j < njobs && pb.flat1; ++j)
+    if (jobs[j].axis == 1) {
+      const int nt = jobs[j].nterms > 1 ? 2 : 1;
+      const int sm = nt * W * jobs[j].D0.rows * (int)sizeof(T);
+      if (sm > 96 * 1024) pb.flat1 = 0;
+      smem = sm > smem ? sm : smem;
+    }
+  if (!pb.flat1) smem = 0;
   int blocks = 0;
   double flops = 0, bytes = 0;
   for (int j = 0; j < njobs; ++j) {
@@ -740,7 +842,8 @@ void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s) {
     const int64_t lines = out.size() / a.D0.rows;
     const int64_t lines_r = (lines + 31) / 32 * 32;
     const int64_t nseg = (a.D0.rows + seg_len<T>() - 1) / seg_len<T>();
-    blocks += (int)((lines_r * nseg + 255) / 256);
+    if (pb.flat1 && a.axis == 1) blocks += (int)((out.size() + 255) / 256);
+    else blocks += (int)((lines_r * nseg + 255) / 256);
     // algorithmic work: one band row per output and term; one read of every input tensor
     const double outs = (double)out.size();
     double fl = 2.0 * a.D0.width * outs, by = (double)a.in.size() + outs;
@@ -752,18 +855,22 @@ void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s) {
   }
   pb.first_block[njobs] = blocks;
   pb.seg = seg_len<T>();
-  int W = jobs[0].D0.width;
-  for (int j = 0; j < njobs; ++j)
-    if (jobs[j].D0.width != W || (jobs[j].nterms > 1 && jobs[j].D1.width != W)) W = 0;
   launch_begin(kClassBand, s);
   switch (W) {
-    case 3: k_band_pass<T, 3><<<blocks, 256, 0, s>>>(pb); break;
-    case 5: k_band_pass<T, 5><<<blocks, 256, 0, s>>>(pb); break;
-    case 7: k_band_pass<T, 7><<<blocks, 256, 0, s>>>(pb); break;
-    case 9: k_band_pass<T, 9><<<blocks, 256, 0, s>>>(pb); break;
-    case 11: k_band_pass<T, 11><<<blocks, 256, 0, s>>>(pb); break;
-    case 13: k_band_pass<T, 13><<<blocks, 256, 0, s>>>(pb); break;
-    default: k_band_pass<T, 0><<<blocks, 256, 0, s>>>(pb);
+#define SHP_PASS_W(w)                                                                     \
+  case w: {                                                                               \
+    static int attr = 0;                                                                  \
+    if (smem > 48 * 1024 && smem > attr) {                                                \
+      cudaFuncSetAttribute(k_band_pass<T, w>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                           smem);                                                         \
+      attr = smem;                                                                        \
+    }                                                                                     \
+    launch_k(k_band_pass<T, w>, blocks, 256, smem, s, pb);                                      \
+    break;                                                                                \
+  }
+    SHP_PASS_W(3) SHP_PASS_W(5) SHP_PASS_W(7) SHP_PASS_W(9) SHP_PASS_W(11) SHP_PASS_W(13)
+#undef SHP_PASS_W
+    default: launch_k(k_band_pass<T, 0>, blocks, 256, 0, s, pb);
   }
   launch_end(kClassBand, s, flops, bytes);
 }
@@ -777,7 +884,7 @@ template <typename T>
 void divergence(const T* u1, const T* u2, const T* u3, int a, int b, T* delta, cudaStream_t s) {
   const int64_t total = (int64_t)b * b * b;
   launch_begin(kClassDiv, s);
-  k_divergence<T><<<grid_for(total, 256), 256, 0, s>>>(u1, u2, u3, a, b, delta, nullptr, T(0),
+  launch_k(k_divergence<T>, grid_for(total, 256), 256, 0, s, u1, u2, u3, a, b, delta, nullptr, T(0),
                                                       nullptr);
   launch_end(kClassDiv, s, 6.0 * total, (3.0 * a * b * b + total) * sizeof(T));
 }
@@ -787,7 +894,7 @@ void divergence_plus(const T* u1, const T* u2, const T* u3, int a, int b, T* del
                      T nu, T* e, cudaStream_t s) {
   const int64_t total = (int64_t)b * b * b;
   launch_begin(kClassDiv, s);
-  k_divergence<T><<<grid_for(total, 256), 256, 0, s>>>(u1, u2, u3, a, b, delta, q, nu, e);
+  launch_k(k_divergence<T>, grid_for(total, 256), 256, 0, s, u1, u2, u3, a, b, delta, q, nu, e);
   launch_end(kClassDiv, s, 8.0 * total, (3.0 * a * b * b + 3.0 * total) * sizeof(T));
 }
 
@@ -796,7 +903,7 @@ void div_transpose(const T* g, int a, int b, T* y1, T* y2, T* y3, int accumulate
                    cudaStream_t s) {
   const int64_t total = 3 * (int64_t)a * b * b;
   launch_begin(kClassDiv, s);
-  k_div_transpose<T><<<grid_for(total, 256), 256, 0, s>>>(g, a, b, y1, y2, y3, accumulate);
+  launch_k(k_div_transpose<T>, grid_for(total, 256), 256, 0, s, g, a, b, y1, y2, y3, accumulate);
   launch_end(kClassDiv, s, (accumulate ? 2.0 : 1.0) * total,
              ((double)b * b * b + (accumulate ? 2.0 : 1.0) * total) * sizeof(T));
 }

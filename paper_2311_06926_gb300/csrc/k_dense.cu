@@ -46,6 +46,7 @@ struct GemmBatch {
 
 template <typename T>
 __global__ void __launch_bounds__(Tile<T>::NTH) k_gemm(const __grid_constant__ GemmBatch<T> gb) {
+  pdl_begin();
   using TL = Tile<T>;
   constexpr int BP = TL::BP, BQ = TL::BQ, BK = TL::BK, NTH = TL::NTH;
   __shared__ T As[BK][BP + 1];
@@ -188,6 +189,7 @@ struct RowBatch {
 
 template <int MI>
 __global__ void __launch_bounds__(128) k_mode_rows(const __grid_constant__ RowBatch rb) {
+  pdl_begin();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= rb.first[rb.njobs]) return;
   int jb = 0;
@@ -252,6 +254,7 @@ __global__ void __launch_bounds__(128) k_mode_rows(const __grid_constant__ RowBa
 // read-only cache. Outputs of products along contiguous lines (L = 1) are staged in shared memory
 // for coalesced stores.
 __global__ void __launch_bounds__(512) k_mode_tile(const __grid_constant__ RowBatch rb) {
+  pdl_begin();
   extern __shared__ double shd[];
   int jb = 0;
   while (jb + 1 < rb.njobs && (int64_t)blockIdx.x >= rb.first[jb + 1]) ++jb;
@@ -430,7 +433,7 @@ void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStr
     attr = smem;
   }
   launch_begin(kClassMode, s);
-  k_mode_tile<<<blocks, threads, smem, s>>>(rb);
+  launch_k(k_mode_tile, blocks, threads, smem, s, rb);
   launch_end(kClassMode, s, flops, bytes);
 }
 
@@ -451,7 +454,7 @@ void mode_product_multi(const ModeArgs<T>* jobs, int njobs, cudaStream_t s) {
   }
   gb.first_block[njobs] = blocks;
   launch_begin(kClassMode, s);
-  k_gemm<T><<<blocks, Tile<T>::NTH, 0, s>>>(gb);
+  launch_k(k_gemm<T>, blocks, Tile<T>::NTH, 0, s, gb);
   launch_end(kClassMode, s, flops, bytes);
 }
 

@@ -181,6 +181,7 @@ __device__ __forceinline__ int job_of(const RmpBatch& b, int t) {
 template <int KIND, typename TO>
 __global__ void __launch_bounds__(kThreads, 1)
     k_rmp(const __grid_constant__ RmpBatch batch, int* err) {
+  pdl_begin();
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int elem = KIND == kMmaTF32 ? 4 : 2;
@@ -372,6 +373,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 template <typename TO>
 __global__ void k_pad_rows(const float* __restrict__ x, int e1, int64_t R, int ld,
                            TO* __restrict__ y) {
+  pdl_begin();
   const int64_t total = (int64_t)e1 * R;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
        o += (int64_t)gridDim.x * blockDim.x) {
@@ -474,7 +476,7 @@ void launch_rmp_t(const RmpPlan* const* plans, int njobs, int* err, int sms, cud
     attr_set = true;
   }
   launch_begin(kClassMma, s);
-  k_rmp<KIND, TO><<<grid, kThreads, smem, s>>>(b, err);
+  launch_k(k_rmp<KIND, TO>, grid, kThreads, smem, s, b, err);
   launch_end(kClassMma, s, flops, bytes);
 }
 
@@ -491,10 +493,10 @@ void pad_rows(const float* x, int e1, int64_t R, int ld, void* y, bool to_bf16, 
   if (blocks > 152 * 32) blocks = 152 * 32;
   launch_begin(kClassVector, s);
   if (to_bf16)
-    k_pad_rows<__nv_bfloat16><<<(int)blocks, 256, 0, s>>>(x, e1, R, ld,
+    launch_k(k_pad_rows<__nv_bfloat16>, (int)blocks, 256, 0, s, x, e1, R, ld,
                                                           static_cast<__nv_bfloat16*>(y));
   else
-    k_pad_rows<float><<<(int)blocks, 256, 0, s>>>(x, e1, R, ld, static_cast<float*>(y));
+    launch_k(k_pad_rows<float>, (int)blocks, 256, 0, s, x, e1, R, ld, static_cast<float*>(y));
   launch_end(kClassVector, s, 0.0, (double)total * (to_bf16 ? 6.0 : 8.0));
 }
 

@@ -34,6 +34,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_dot_partial(const T* __restrict__ x,
                                                           const T* __restrict__ y, int64_t n,
                                                           T* __restrict__ partials) {
+  pdl_begin();
   __shared__ T sh[kThreads];
   T s = 0;
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
@@ -47,6 +48,7 @@ __global__ void __launch_bounds__(kThreads) k_dot_partial(const T* __restrict__ 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_dot_final(const T* __restrict__ partials, int np,
                                                         T* __restrict__ out) {
+  pdl_begin();
   __shared__ T sh[kThreads];
   T s = 0;
   for (int i = threadIdx.x; i < np; i += kThreads) s += partials[i];
@@ -56,6 +58,7 @@ __global__ void __launch_bounds__(kThreads) k_dot_final(const T* __restrict__ pa
 
 template <typename T>
 __global__ void k_axpby(T a, const T* __restrict__ x, T b, T* __restrict__ y, int64_t n) {
+  pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     y[i] = a * x[i] + b * y[i];
@@ -64,6 +67,7 @@ __global__ void k_axpby(T a, const T* __restrict__ x, T b, T* __restrict__ y, in
 template <typename T>
 __global__ void k_hp_update(T* __restrict__ r, const T* __restrict__ u, T* __restrict__ acc,
                             int64_t n) {
+  pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const T ri = r[i] - u[i];
@@ -73,12 +77,14 @@ __global__ void k_hp_update(T* __restrict__ r, const T* __restrict__ u, T* __res
 }
 
 __global__ void k_to_float(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
+  pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     y[i] = (float)x[i];
 }
 
 __global__ void k_to_double(const float* __restrict__ x, double* __restrict__ y, int64_t n) {
+  pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     y[i] = (double)x[i];
@@ -86,6 +92,7 @@ __global__ void k_to_double(const float* __restrict__ x, double* __restrict__ y,
 
 __global__ void k_axpy_dev(const double* __restrict__ alpha, double sign,
                            const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+  pdl_begin();
   const double a = sign * (*alpha);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -94,6 +101,7 @@ __global__ void k_axpy_dev(const double* __restrict__ alpha, double sign,
 
 __global__ void k_scale_inv_dev(const double* __restrict__ alpha, const double* __restrict__ x,
                                 double* __restrict__ y, int64_t n) {
+  pdl_begin();
   const double a = 1.0 / (*alpha);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -101,26 +109,67 @@ __global__ void k_scale_inv_dev(const double* __restrict__ alpha, const double* 
 }
 
 // Partial dot products of w with nvec vectors: block b handles the same slice for every vector.
-__global__ void __launch_bounds__(kThreads) k_multi_dot_partial(const double* __restrict__ V,
-                                                                int64_t ldv, int nvec,
+// y[k] = <V_k, w>, NG <= kDotGroup vectors per sweep over the index range: each element of w is
+// loaded once per group, every vector has its own accumulator, and a thread handles two
+// elements per step, so 2 (NG + 1) independent loads are in flight per thread. Block b of the
+// fixed grid of kMultiDotBlocks sums its elements in a fixed order, reduces each vector's sums in
+// a fixed tree (warp shuffles, then the warps in order), and stage 2 sums the block partials in a
+// fixed order: the result is deterministic.
+constexpr int kDotGroup = 8;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int NG>
+__global__ void __launch_bounds__(kThreads, 4) k_multi_dot_partial(const double* __restrict__ V,
+                                                                int64_t ldv, int k0,
                                                                 const double* __restrict__ w,
                                                                 int64_t n,
                                                                 double* __restrict__ partials) {
-  __shared__ double sh[kThreads];
-  for (int k = 0; k < nvec; ++k) {
-    const double* v = V + k * ldv;
-    double s = 0;
-    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * kThreads)
-      s += v[i] * w[i];
-    const double tot = block_sum(s, sh);
-    if (threadIdx.x == 0) partials[(int64_t)k * gridDim.x + blockIdx.x] = tot;
-    __syncthreads();
+  pdl_begin();
+  __shared__ double sh[NG][kThreads / 32];
+  double acc[NG];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) acc[g] = 0.0;
+  const double* v0 = V + (int64_t)k0 * ldv;
+  const int64_t step = (int64_t)gridDim.x * kThreads;
+  int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  for (; i + step < n; i += 2 * step) {
+    const double wa = w[i], wb = w[i + step];
+    double va[NG], vb[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      va[g] = v0[g * ldv + i];
+      vb[g] = v0[g * ldv + i + step];
+    }
+#pragma unroll
+    for (int g = 0; g < NG; ++g) acc[g] = fma(vb[g], wb, fma(va[g], wa, acc[g]));
+  }
+  if (i < n) {
+    const double wa = w[i];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) acc[g] = fma(v0[g * ldv + i], wa, acc[g]);
+  }
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    const double t = warp_sum(acc[g]);
+    if (lane == 0) sh[g][warp] = t;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < NG) {
+    double t = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) t += sh[threadIdx.x][k];
+    partials[(int64_t)(k0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
   }
 }
 
 __global__ void __launch_bounds__(kThreads) k_multi_dot_final(const double* __restrict__ partials,
                                                               int np, double* __restrict__ out) {
+  pdl_begin();
   __shared__ double sh[kThreads];
   const double* p = partials + (int64_t)blockIdx.x * np;
   double s = 0;
@@ -129,14 +178,31 @@ __global__ void __launch_bounds__(kThreads) k_multi_dot_final(const double* __re
   if (threadIdx.x == 0) out[blockIdx.x] = tot;
 }
 
-__global__ void k_multi_axpy(const double* __restrict__ V, int64_t ldv, int nvec,
-                             const double* __restrict__ h, double sign, double* __restrict__ w,
-                             int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0;
-    for (int k = 0; k < nvec; ++k) s += h[k] * V[k * ldv + i];
-    w[i] += sign * s;
+// w += sign * sum_k h[k] V_k: coefficients staged in shared memory, four independent partial
+// sums per element so the loads of several vectors are in flight together.
+constexpr int kAxpyMaxVec = 512;   // restart <= 400 (checked at setup)
+
+__global__ void __launch_bounds__(kThreads) k_multi_axpy(const double* __restrict__ V, int64_t ldv,
+                                                         int nvec, const double* __restrict__ h,
+                                                         double sign, double* __restrict__ w,
+                                                         int64_t n) {
+  pdl_begin();
+  __shared__ double hs[kAxpyMaxVec];
+  for (int k = threadIdx.x; k < nvec; k += kThreads) hs[k] = h[k];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads) {
+    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    const double* v = V + i;
+    int k = 0;
+    for (; k + 4 <= nvec; k += 4) {
+      s0 = fma(hs[k], v[k * ldv], s0);
+      s1 = fma(hs[k + 1], v[(k + 1) * ldv], s1);
+      s2 = fma(hs[k + 2], v[(k + 2) * ldv], s2);
+      s3 = fma(hs[k + 3], v[(k + 3) * ldv], s3);
+    }
+    for (; k < nvec; ++k) s0 = fma(hs[k], v[k * ldv], s0);
+    w[i] += sign * ((s0 + s1) + (s2 + s3));
   }
 }
 
@@ -147,6 +213,7 @@ constexpr int kStatusNotSpd = -4;
 constexpr int kStatusMaxit = -5;
 
 __global__ void k_minres_init(MinresState* st) {
+  pdl_begin();
   const double gg = st->gg;
   st->status = 0;
   st->iter = 0;
@@ -177,6 +244,7 @@ __global__ void k_minres_init(MinresState* st) {
 
 __global__ void k_minres_scale_z(double* __restrict__ z, const MinresState* __restrict__ st,
                                  int64_t n) {
+  pdl_begin();
   if (st->done) return;
   const double inv = 1.0 / st->gamma;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -188,6 +256,7 @@ __global__ void k_minres_scale_z(double* __restrict__ z, const MinresState* __re
 __global__ void k_minres_lanczos(const double* __restrict__ Kz, const double* __restrict__ v,
                                  double* __restrict__ vold, const MinresState* __restrict__ st,
                                  int64_t n) {
+  pdl_begin();
   if (st->done) return;
   const double a = st->delta / st->gamma, b = st->gamma / st->gamma_old;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -198,6 +267,7 @@ __global__ void k_minres_lanczos(const double* __restrict__ Kz, const double* __
 // Givens QR of the Lanczos tridiagonal: apply the two previous rotations to the new column
 // (gamma, delta, gamma_new), form the new rotation, and update the residual estimate |eta|.
 __global__ void k_minres_scalars(MinresState* st) {
+  pdl_begin();
   st->pad = 0;                   // "update this iteration" flag read by the update kernel
   if (st->done) return;
   if (st->iter >= st->cap) {     // iteration cap: keep the last iterate
@@ -245,6 +315,7 @@ __global__ void k_minres_scalars(MinresState* st) {
 __global__ void k_minres_update(const double* __restrict__ z, double* __restrict__ wold,
                                 const double* __restrict__ w, double* __restrict__ x,
                                 const MinresState* __restrict__ st, int64_t n) {
+  pdl_begin();
   if (!st->pad) return;
   const double inv = 1.0 / st->a1, a2 = st->a2, a3 = st->a3, xc = st->xcoef;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -260,24 +331,24 @@ __global__ void k_minres_update(const double* __restrict__ z, double* __restrict
 template <typename T>
 void dot(const T* x, const T* y, int64_t n, T* partials, T* out, cudaStream_t s) {
   launch_begin(kClassVector, s);
-  k_dot_partial<T><<<kDotBlocks, kThreads, 0, s>>>(x, y, n, partials);
+  launch_k(k_dot_partial<T>, kDotBlocks, kThreads, 0, s, x, y, n, partials);
   launch_end(kClassVector, s, 0.0, 0.0);
   launch_begin(kClassVector, s);
-  k_dot_final<T><<<1, kThreads, 0, s>>>(partials, kDotBlocks, out);
+  launch_k(k_dot_final<T>, 1, kThreads, 0, s, partials, kDotBlocks, out);
   launch_end(kClassVector, s, 0.0, 0.0);
 }
 
 template <typename T>
 void axpby(T a, const T* x, T b, T* y, int64_t n, cudaStream_t s) {
   launch_begin(kClassVector, s);
-  k_axpby<T><<<grid_for(n), kThreads, 0, s>>>(a, x, b, y, n);
+  launch_k(k_axpby<T>, grid_for(n), kThreads, 0, s, a, x, b, y, n);
   launch_end(kClassVector, s, 0.0, 0.0);
 }
 
 template <typename T>
 void hp_update(T* r, const T* u, T* acc, int64_t n, cudaStream_t s) {
   launch_begin(kClassVector, s);
-  k_hp_update<T><<<grid_for(n), kThreads, 0, s>>>(r, u, acc, n);
+  launch_k(k_hp_update<T>, grid_for(n), kThreads, 0, s, r, u, acc, n);
   launch_end(kClassVector, s, 0.0, 0.0);
 }
 
@@ -289,65 +360,77 @@ void fill_zero(void* dst, size_t bytes, cudaStream_t s) { cudaMemsetAsync(dst, 0
 
 void to_float(const double* x, float* y, int64_t n, cudaStream_t s) {
   launch_begin(kClassVector, s);
-  k_to_float<<<grid_for(n), kThreads, 0, s>>>(x, y, n);
+  launch_k(k_to_float, grid_for(n), kThreads, 0, s, x, y, n);
   launch_end(kClassVector, s, 0.0, 0.0);
 }
 void to_double(const float* x, double* y, int64_t n, cudaStream_t s) {
   launch_begin(kClassVector, s);
-  k_to_double<<<grid_for(n), kThreads, 0, s>>>(x, y, n);
+  launch_k(k_to_double, grid_for(n), kThreads, 0, s, x, y, n);
   launch_end(kClassVector, s, 0.0, 0.0);
 }
 
 void axpy_dev(const double* alpha, double sign, const double* x, double* y, int64_t n,
               cudaStream_t s) {
   launch_begin(kClassVector, s);
-  k_axpy_dev<<<grid_for(n), kThreads, 0, s>>>(alpha, sign, x, y, n);
+  launch_k(k_axpy_dev, grid_for(n), kThreads, 0, s, alpha, sign, x, y, n);
   launch_end(kClassVector, s, 0.0, 0.0);
 }
 void scale_inv_dev(const double* alpha, const double* x, double* y, int64_t n, cudaStream_t s) {
   launch_begin(kClassVector, s);
-  k_scale_inv_dev<<<grid_for(n), kThreads, 0, s>>>(alpha, x, y, n);
+  launch_k(k_scale_inv_dev, grid_for(n), kThreads, 0, s, alpha, x, y, n);
   launch_end(kClassVector, s, 0.0, 0.0);
 }
 void multi_dot(const double* V, int64_t ldv, int nvec, const double* w, int64_t n,
                double* partials, double* out, cudaStream_t s) {
+  for (int k0 = 0; k0 < nvec; k0 += kDotGroup) {
+    const int ng = nvec - k0 < kDotGroup ? nvec - k0 : kDotGroup;
+    launch_begin(kClassVector, s);
+    switch (ng) {
+#define SHP_MDOT(g)                                                                              \
+  case g:                                                                                        \
+    launch_k(k_multi_dot_partial<g>, kMultiDotBlocks, kThreads, 0, s, V, ldv, k0, w, n, partials);     \
+    break;
+      SHP_MDOT(1) SHP_MDOT(2) SHP_MDOT(3) SHP_MDOT(4) SHP_MDOT(5) SHP_MDOT(6) SHP_MDOT(7)
+      SHP_MDOT(8)
+#undef SHP_MDOT
+      default: break;
+    }
+    launch_end(kClassVector, s, 2.0 * (double)n * ng, 8.0 * (double)n * (ng + 1));
+  }
   launch_begin(kClassVector, s);
-  k_multi_dot_partial<<<kDotBlocks, kThreads, 0, s>>>(V, ldv, nvec, w, n, partials);
-  launch_end(kClassVector, s, 0.0, 0.0);
-  launch_begin(kClassVector, s);
-  k_multi_dot_final<<<nvec, kThreads, 0, s>>>(partials, kDotBlocks, out);
+  launch_k(k_multi_dot_final, nvec, kThreads, 0, s, partials, kMultiDotBlocks, out);
   launch_end(kClassVector, s, 0.0, 0.0);
 }
 void multi_axpy(const double* V, int64_t ldv, int nvec, const double* h, double sign, double* w,
                 int64_t n, cudaStream_t s) {
   launch_begin(kClassVector, s);
-  k_multi_axpy<<<grid_for(n), kThreads, 0, s>>>(V, ldv, nvec, h, sign, w, n);
-  launch_end(kClassVector, s, 0.0, 0.0);
+  launch_k(k_multi_axpy, grid_for(n), kThreads, 0, s, V, ldv, nvec, h, sign, w, n);
+  launch_end(kClassVector, s, 2.0 * nvec * (double)n, 8.0 * (double)n * (nvec + 2));
 }
 
 void minres_init(MinresState* st, cudaStream_t s) { launch_begin(kClassVector, s);
-  k_minres_init<<<1, 1, 0, s>>>(st);
+  launch_k(k_minres_init, 1, 1, 0, s, st);
   launch_end(kClassVector, s, 0.0, 0.0); }
 void minres_scale_z(double* z, MinresState* st, int64_t n, cudaStream_t s) {
   launch_begin(kClassVector, s);
-  k_minres_scale_z<<<grid_for(n), kThreads, 0, s>>>(z, st, n);
+  launch_k(k_minres_scale_z, grid_for(n), kThreads, 0, s, z, st, n);
   launch_end(kClassVector, s, 0.0, 0.0);
 }
 void minres_lanczos(const double* Kz, const double* v, double* vold, MinresState* st, int64_t n,
                     cudaStream_t s) {
   launch_begin(kClassVector, s);
-  k_minres_lanczos<<<grid_for(n), kThreads, 0, s>>>(Kz, v, vold, st, n);
+  launch_k(k_minres_lanczos, grid_for(n), kThreads, 0, s, Kz, v, vold, st, n);
   launch_end(kClassVector, s, 0.0, 0.0);
 }
 void minres_scalars(MinresState* st, cudaStream_t s) {
   launch_begin(kClassVector, s);
-  k_minres_scalars<<<1, 1, 0, s>>>(st);
+  launch_k(k_minres_scalars, 1, 1, 0, s, st);
   launch_end(kClassVector, s, 0.0, 0.0);
 }
 void minres_update(const double* z, double* wold, const double* w, double* x, MinresState* st,
                    int64_t n, cudaStream_t s) {
   launch_begin(kClassVector, s);
-  k_minres_update<<<grid_for(n), kThreads, 0, s>>>(z, wold, w, x, st, n);
+  launch_k(k_minres_update, grid_for(n), kThreads, 0, s, z, wold, w, x, st, n);
   launch_end(kClassVector, s, 0.0, 0.0);
 }
 

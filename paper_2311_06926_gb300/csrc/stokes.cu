@@ -70,8 +70,30 @@ struct Arena {
   }
 };
 
+// The same banded matrix stored with a larger band width (zeros in the added slots); rows = 0 when
+// the matrix has fewer columns than the width.
+Band widen(const Band& B, int width) {
+  Band W;
+  if (width <= B.width || B.cols < width) return W;
+  const int d = (width - B.width) / 2;
+  W.rows = B.rows;
+  W.cols = B.cols;
+  W.width = width;
+  W.start.resize(B.rows);
+  W.val.assign((size_t)B.rows * width, 0.0);
+  for (int i = 0; i < B.rows; ++i) {
+    const int s0 = std::max(0, std::min(B.start[i] - d, B.cols - width));
+    W.start[i] = s0;
+    for (int w = 0; w < B.width; ++w)
+      W.val[(size_t)i * width + (B.start[i] + w - s0)] = B.val[(size_t)i * B.width + w];
+  }
+  return W;
+}
+
+// min_half: lower bound of the centred copy's half width (a zero-padded copy keeps the width of
+// the matrices it shares launches with)
 template <typename T>
-BandD<T> upload_band(Arena& ar, const Band& b, cudaStream_t s) {
+BandD<T> upload_band(Arena& ar, const Band& b, cudaStream_t s, int min_half = 0) {
   BandD<T> d;
   d.rows = b.rows;
   d.cols = b.cols;
@@ -92,7 +114,7 @@ BandD<T> upload_band(Arena& ar, const Band& b, cudaStream_t s) {
   // centred copy for square matrices (every matrix of the operator applies is one)
   std::vector<T> cv;
   if (b.rows == b.cols) {
-    int half = 0;
+    int half = min_half;
     for (int i = 0; i < b.rows; ++i)
       for (int w = 0; w < b.width; ++w)
         if (b.val[(size_t)i * b.width + w] != 0.0) half = std::max(half, std::abs(b.start[i] + w - i));
@@ -154,6 +176,7 @@ struct Ops {
   T nu = 0;
   int64_t nvc = 0, nvel = 0, npres = 0;
   BandD<T> M{}, K{}, Mc{}, Tc{};
+  BandD<T> Mc_w{};   // M-check padded with zeros to the band width of K and M (val null: none)
   const T *U_N = nullptr, *lam_N = nullptr, *U_T = nullptr, *lam_T = nullptr;
   const T* invd = nullptr;   // FP64: 1 / (2 nu (l1 + l2 + l3)) per velocity entry
   int eo_N = 0, eo_T = 0;    // FP64: even-mode counts of the parity-split eigenvectors
@@ -209,21 +232,36 @@ struct Ops {
   // y_c = A'_cc u_c + D^T g along the own direction of c, for the three components at once:
   // t_K = K u, t_M = M u along the own direction; s = nu Mc t_K + 2 nu Tc t_M and r = Mc t_M
   // along the first other direction; y = Mc s + 2 nu Tc r (+ D^T g) along the second.
-  void adiag_all(const T* u, T* y, const T* g) const {
+  // With nq > 0 the pressure-mass products g_k = coef_k M_q x_k (k < nq) that feed g are formed in
+  // the same launches: their passes along x1 and x2 ride with the first two velocity passes (the
+  // x1 pass with Mc_w, M-check padded with zeros to the width of K and M, so that every job of a
+  // launch has one band width), their pass along x3 runs alone, then the last velocity pass.
+  void adiag_all(const T* u, T* y, const T* g, int nq = 0, const T* const* qx = nullptr,
+                 T* const* qy = nullptr, const T* qcoef = nullptr) const {
     const T nu2 = 2 * nu;
+    const Dims dq{b, b, b};
     PassArgs<T> j[kMaxPassJobs];
     for (int c = 0; c < 3; ++c) {
       const int64_t o = c * nvc;
       j[2 * c] = job(u + o, K, 1, nullptr, nullptr, 0, comp(c), own_axis(c), tK + o);
       j[2 * c + 1] = job(u + o, M, 1, nullptr, nullptr, 0, comp(c), own_axis(c), tM + o);
     }
-    band_pass_multi<T>(j, 6, s);
+    for (int k = 0; k < nq; ++k)
+      j[6 + k] = job(qx[k], Mc_w, 1, nullptr, nullptr, 0, dq, 1, f1 + k * npres);
+    band_pass_multi<T>(j, 6 + nq, s);
     for (int c = 0; c < 3; ++c) {
       const int64_t o = c * nvc;
       j[2 * c] = job(tK + o, Mc, nu, tM + o, &Tc, nu2, comp(c), first_other(c), tS + o);
       j[2 * c + 1] = job(tM + o, Mc, 1, nullptr, nullptr, 0, comp(c), first_other(c), tR + o);
     }
-    band_pass_multi<T>(j, 6, s);
+    for (int k = 0; k < nq; ++k)
+      j[6 + k] = job(f1 + k * npres, Mc, 1, nullptr, nullptr, 0, dq, 2, f2 + k * npres);
+    band_pass_multi<T>(j, 6 + nq, s);
+    if (nq > 0) {
+      for (int k = 0; k < nq; ++k)
+        j[k] = job(f2 + k * npres, Mc, qcoef[k], nullptr, nullptr, 0, dq, 3, qy[k]);
+      band_pass_multi<T>(j, nq, s);
+    }
     for (int c = 0; c < 3; ++c) {
       const int64_t o = c * nvc;
       j[c] = job(tS + o, Mc, 1, tR + o, &Tc, nu2, comp(c), second_other(c), y + o, nullptr, 0, g,
@@ -255,6 +293,10 @@ struct Ops {
     const T* in[2] = {delta, m1};
     T* out[2] = {yq, m2};
     const T coef[2] = {1, 1};
+    if (Mc_w.val) {
+      adiag_all(x, y, m2, 2, in, out, coef);
+      return;
+    }
     mq(2, in, out, coef);
     adiag_all(x, y, m2);
   }
@@ -264,6 +306,10 @@ struct Ops {
     const T* in[1] = {delta};
     T* out[1] = {m2};
     const T coef[1] = {nu};
+    if (Mc_w.val) {
+      adiag_all(x, y, m2, 1, in, out, coef);
+      return;
+    }
     mq(1, in, out, coef);
     adiag_all(x, y, m2);
   }
@@ -589,6 +635,11 @@ void init_ops(stokes_ctx* c, Ops<T>& o, const Band& M, const Band& K, const Band
   o.K = upload_band<T>(ar, K, s);
   o.Mc = upload_band<T>(ar, Mc, s);
   o.Tc = upload_band<T>(ar, Tc, s);
+  {
+    const Band Mcw = widen(Mc, K.width);
+    if (Mcw.rows > 0 && o.K.cval && o.M.cval && o.K.half == o.M.half && 2 * o.K.half + 1 == K.width)
+      o.Mc_w = upload_band<T>(ar, Mcw, s, o.K.half);
+  }
   o.U_N = upload<T>(ar, UN, s);
   o.lam_N = upload<T>(ar, lN, s);
   o.U_T = upload<T>(ar, UT, s);
@@ -1196,7 +1247,7 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
           z[(size_t)i + (size_t)b * (j + (size_t)b * k)] = u.const_M[i] * u.const_M[j] * u.const_M[k];
     c->zconst = upload<double>(c->arena, z, c->stream);
     c->ones = upload<double>(c->arena, one, c->stream);
-    c->partials = c->arena.alloc<double>((size_t)kDotBlocks * (o.restart + 2));
+    c->partials = c->arena.alloc<double>((size_t)std::max(kDotBlocks, kMultiDotBlocks) * (o.restart + 2));
     c->dsc = c->arena.alloc<double>(16 + 2 * (o.restart + 2));
     c->st = c->arena.alloc<MinresState>(1);
     ck(cudaMallocHost(&c->st_host, sizeof(MinresState)), "pinned");
