@@ -67,6 +67,13 @@ typedef struct stokes_opts {
   int maxit;          /* Krylov iteration cap */
   int restart;        /* FGMRES restart length */
   void* stream;       /* cudaStream_t to run on; NULL: the library creates one */
+  int nrhs;           /* right-hand sides held by the context (<= 1: one). With nrhs > 1 every
+                         vector argument of stokes_apply_K, stokes_apply_P,
+                         stokes_apply_hyperpower and stokes_solve_multi holds nrhs items of
+                         n_vel + n_pres entries one after the other, and each kernel of those
+                         calls processes all items in one launch (the mode products of the fast
+                         diagonalisation become GEMMs with nrhs times the rows). Needs
+                         precision TF32 or BF16 and solver FGMRES. */
 } stokes_opts;
 
 typedef struct stokes_ctx* stokes_t;
@@ -90,7 +97,9 @@ int stokes_sizes(stokes_t ctx, int64_t* n_vel, int64_t* n_pres);
 int stokes_set_preconditioner(stokes_t ctx, int order, int steps);
 
 /* y = A x on the velocity block (x, y: n_vel). A = the 15 Kronecker products of Sec. 3.3 with
- * the weak-form scaling (2 nu on the printed diagonal blocks, nu on the off-diagonal ones). */
+ * the weak-form scaling (2 nu on the printed diagonal blocks, nu on the off-diagonal ones).
+ * One item, also on a context with nrhs > 1 (as stokes_apply_mass, the stokes_rhs_* loads and
+ * stokes_dot). */
 int stokes_apply_A(stokes_t ctx, const double* x, double* y);
 
 /* y = K x on the full saddle-point system (Eq. 3.3; x, y: n_vel + n_pres). */
@@ -143,16 +152,29 @@ int stokes_dot(stokes_t ctx, const double* x, const double* y, int64_t n, double
 int stokes_solve(stokes_t ctx, const double* rhs, double tol, double* x, int* iterations,
                  double* final_rel_res);
 
+/* Solve all nrhs systems of a context (stokes_opts.nrhs): rhs and x hold nrhs items of
+ * n_vel + n_pres entries one after the other (device). Flexible GMRES runs for all items in
+ * lockstep: one Arnoldi step applies the preconditioner and K to every item in the same launches,
+ * while each item keeps its own Krylov basis, Hessenberg matrix, restarts and stopping test, so its
+ * result and iteration count equal those of a context with nrhs = 1 for that item alone.
+ * iterations, final_rel_res and status (per-item return codes) are HOST arrays of nrhs entries and
+ * may be NULL. Returns STOKES_OK or the first nonzero per-item code. (stokes_solve on such a
+ * context solves all items and reports the largest iteration count and residual.) */
+int stokes_solve_multi(stokes_t ctx, const double* rhs, double tol, double* x, int* iterations,
+                       double* final_rel_res, int* status);
+
 /* As stokes_solve with HOST buffers rhs_host and x_host (pinned memory gives full copy speed):
- * the host-to-device copy, the solve and the device-to-host copy all happen inside the call. */
+ * the host-to-device copy, the solve and the device-to-host copy all happen inside the call.
+ * Contexts with nrhs = 1 only (STOKES_ERR_ARG otherwise). */
 int stokes_solve_host(stokes_t ctx, const double* rhs_host, double tol, double* x_host,
                       int* iterations, double* final_rel_res);
 
 /* Solve `count` independent systems at once: ctxs[i] (distinct contexts, any meshes, degrees,
  * precisions and solvers) with rhs[i] -> x[i] (device pointers of that context's size). Each
  * solve runs on its own context's stream, driven by its own host thread, so the solves execute
- * concurrently on the GPU. iterations, final_rel_res and status (per-problem return codes) may
- * be NULL. Returns STOKES_OK or the first nonzero per-problem code. */
+ * concurrently on the GPU. A context with nrhs > 1 solves all its items (as stokes_solve, with
+ * the largest iteration count and residual reported). iterations, final_rel_res and status
+ * (per-context return codes) may be NULL. Returns STOKES_OK or the first nonzero code. */
 int stokes_solve_batch(stokes_t* ctxs, int count, const double* const* rhs, double tol,
                        double* const* x, int* iterations, double* final_rel_res, int* status);
 

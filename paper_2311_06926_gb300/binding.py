@@ -29,7 +29,8 @@ class StokesError(RuntimeError):
 class _Opts(ctypes.Structure):
     _fields_ = [("c_pen", ctypes.c_double), ("schur", ctypes.c_int), ("precision", ctypes.c_int),
                 ("solver", ctypes.c_int), ("max_order", ctypes.c_int), ("max_steps", ctypes.c_int),
-                ("maxit", ctypes.c_int), ("restart", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("maxit", ctypes.c_int), ("restart", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("nrhs", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -72,6 +73,7 @@ def load_library(path=None):
         "stokes_dot": (ctypes.c_int, [vp, vp, vp, ctypes.c_int64, dp]),
         "stokes_solve": (ctypes.c_int, [vp, vp, ctypes.c_double, vp, ip, dp]),
         "stokes_solve_host": (ctypes.c_int, [vp, vp, ctypes.c_double, vp, ip, dp]),
+        "stokes_solve_multi": (ctypes.c_int, [vp, vp, ctypes.c_double, vp, ip, dp, ip]),
         "stokes_last_ratios": (ctypes.c_int, [vp, dp, ctypes.c_int]),
         "stokes_solve_batch": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int,
                                               ctypes.POINTER(vp), ctypes.c_double,
@@ -100,10 +102,10 @@ def solve_batch(contexts, rhs, tol=1e-8, outs=None):
     n = len(contexts)
     if len(rhs) != n:
         raise ValueError("one right-hand side per context")
-    xs = outs if outs is not None else [G.empty() for G in contexts]
+    xs = outs if outs is not None else [G.empty(G.batch_size) for G in contexts]
     for G, f, x in zip(contexts, rhs, xs):
-        G._vec(f, G.size)
-        G._vec(x, G.size)
+        G._vec(f, G.batch_size)
+        G._vec(x, G.batch_size)
     cur = torch.cuda.current_stream()
     for G in contexts:
         G.stream.wait_stream(cur)
@@ -150,7 +152,12 @@ class Stokes:
     """One discretised cavity (n^3 elements, pressure degree p, viscosity nu) on the GPU."""
 
     def __init__(self, n, p, nu=1.0, c_pen=14.0, schur="inner", precision="fp64",
-                 solver=None, max_order=3, max_steps=4, maxit=2000, restart=60, device=None):
+                 solver=None, max_order=3, max_steps=4, maxit=2000, restart=60, device=None,
+                 nrhs=1):
+        """nrhs > 1: the context holds nrhs right-hand sides; apply_K, apply_P,
+        apply_hyperpower, solve and solve_multi then take nrhs stacked vectors of `size` entries
+        each (`batch_size` in all), processed by the same launches (needs precision "tf32" or
+        "bf16")."""
         self.lib = load_library()
         if not torch.cuda.is_available():
             raise RuntimeError("Stokes needs a CUDA device")
@@ -164,6 +171,7 @@ class Stokes:
         o.precision = PRECISION[precision]
         o.solver = SOLVER[solver]
         o.max_order, o.max_steps, o.maxit, o.restart = max_order, max_steps, maxit, restart
+        o.nrhs = nrhs
         with torch.cuda.device(self.device):
             # the library runs on its own stream, ordered against the caller's current stream
             # at every call (inputs ready before, outputs visible after)
@@ -179,6 +187,8 @@ class Stokes:
         self.lib.stokes_sizes(self.h, ctypes.byref(nv), ctypes.byref(npr))
         self.n_vel, self.n_pres = nv.value, npr.value
         self.size = self.n_vel + self.n_pres
+        self.nrhs = max(1, nrhs)
+        self.batch_size = self.nrhs * self.size
         self.a, self.b = n + p - 1, n + p
 
     # -- helpers -------------------------------------------------------------------------------
@@ -212,22 +222,22 @@ class Stokes:
         return y
 
     def apply_K(self, x, out=None):
-        y = out if out is not None else self.empty()
-        self._check(self._call(self.lib.stokes_apply_K, self.h, _ptr(self._vec(x, self.size)),
-                                            _ptr(self._vec(y, self.size))))
+        y = out if out is not None else self.empty(self.batch_size)
+        self._check(self._call(self.lib.stokes_apply_K, self.h, _ptr(self._vec(x, self.batch_size)),
+                                            _ptr(self._vec(y, self.batch_size))))
         return y
 
     def apply_P(self, x, out=None):
-        y = out if out is not None else self.empty()
-        self._check(self._call(self.lib.stokes_apply_P, self.h, _ptr(self._vec(x, self.size)),
-                                            _ptr(self._vec(y, self.size))))
+        y = out if out is not None else self.empty(self.batch_size)
+        self._check(self._call(self.lib.stokes_apply_P, self.h, _ptr(self._vec(x, self.batch_size)),
+                                            _ptr(self._vec(y, self.batch_size))))
         return y
 
     def apply_hyperpower(self, order, steps, x, out=None):
-        y = out if out is not None else self.empty()
+        y = out if out is not None else self.empty(self.batch_size)
         self._check(self._call(self.lib.stokes_apply_hyperpower, self.h, order, steps,
-                                                     _ptr(self._vec(x, self.size)),
-                                                     _ptr(self._vec(y, self.size))))
+                                                     _ptr(self._vec(x, self.batch_size)),
+                                                     _ptr(self._vec(y, self.batch_size))))
         return y
 
     def rhs_cavity(self, lid_speed=1.0, out=None):
@@ -274,16 +284,30 @@ class Stokes:
         return r.value
 
     def solve(self, rhs, tol=1e-8, out=None, raise_on_error=True):
-        """Returns (x, iterations, true relative residual, status code)."""
-        x = out if out is not None else self.empty()
+        """Returns (x, iterations, true relative residual, status code); with nrhs > 1 all items
+        are solved and the largest iteration count and residual are returned."""
+        x = out if out is not None else self.empty(self.batch_size)
         it = ctypes.c_int()
         rr = ctypes.c_double()
-        rc = self._call(self.lib.stokes_solve, self.h, _ptr(self._vec(rhs, self.size)), float(tol),
-                                   _ptr(self._vec(x, self.size)), ctypes.byref(it),
-                                   ctypes.byref(rr))
+        rc = self._call(self.lib.stokes_solve, self.h, _ptr(self._vec(rhs, self.batch_size)),
+                        float(tol), _ptr(self._vec(x, self.batch_size)), ctypes.byref(it),
+                        ctypes.byref(rr))
         if raise_on_error:
             self._check(rc)
         return x, it.value, rr.value, rc
+
+    def solve_multi(self, rhs, tol=1e-8, out=None, raise_on_error=True):
+        """All nrhs systems (rhs: nrhs stacked right-hand sides). Returns (x, per-item
+        iterations, per-item true relative residuals, per-item status codes, return code)."""
+        x = out if out is not None else self.empty(self.batch_size)
+        its = (ctypes.c_int * self.nrhs)()
+        rrs = (ctypes.c_double * self.nrhs)()
+        st = (ctypes.c_int * self.nrhs)()
+        rc = self._call(self.lib.stokes_solve_multi, self.h, _ptr(self._vec(rhs, self.batch_size)),
+                        float(tol), _ptr(self._vec(x, self.batch_size)), its, rrs, st)
+        if raise_on_error:
+            self._check(rc)
+        return x, list(its), list(rrs), list(st), rc
 
     def solve_host(self, rhs_host, x_host, tol=1e-8):
         """Solve with HOST (preferably pinned) float64 tensors; copies happen inside the call."""

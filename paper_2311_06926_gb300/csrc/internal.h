@@ -66,6 +66,8 @@ struct Dims {
 // Y = c0 (D0 .axis X0) [+ c1 (D1 .axis X1)] [+ cz Z] [+ Dt_axis g  (difference transpose along
 // axis `gaxis` of the b^3 tensor g, see k_band.cu)]. X0/X1 have extents `in`; Y has extents
 // in.with(axis, D0.rows). Z (may alias Y) and g may be null.
+// Batches: nb items (nb <= 1: one), item k of every tensor of the job (X0, X1, Z, g, Y) at
+// offset k * bs elements from its pointer.
 template <typename T>
 struct PassArgs {
   const T* X0; const T* X1;
@@ -77,6 +79,8 @@ struct PassArgs {
   Dims in;
   int axis;
   int nterms;
+  int nb;
+  int64_t bs;
 };
 template <typename T>
 void band_pass(const PassArgs<T>& a, cudaStream_t s);
@@ -87,17 +91,19 @@ void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s);
 
 // delta = sum_c D .c u_c: exact discrete divergence of the velocity coefficients (App. B.2),
 // output b^3. (D beta)_i = beta_i - beta_{i-1} with beta_{-1} = beta_a = 0.
+// For these three: nb items, item k of every argument tensor at offset k * bs elements.
 template <typename T>
-void divergence(const T* u1, const T* u2, const T* u3, int a, int b, T* delta, cudaStream_t s);
+void divergence(const T* u1, const T* u2, const T* u3, int a, int b, T* delta, cudaStream_t s,
+                int nb = 1, int64_t bs = 0);
 // as divergence, and also e = nu delta + q (the argument of the grad-div / pressure term)
 template <typename T>
 void divergence_plus(const T* u1, const T* u2, const T* u3, int a, int b, T* delta,
-                     const T* q, T nu, T* e, cudaStream_t s);
+                     const T* q, T nu, T* e, cudaStream_t s, int nb = 1, int64_t bs = 0);
 
 // y_c (+)= D^T .c g for the three components (grad of a b^3 field onto velocity coefficients).
 template <typename T>
 void div_transpose(const T* g, int a, int b, T* y1, T* y2, T* y3, int accumulate,
-                   cudaStream_t s);
+                   cudaStream_t s, int nb = 1, int64_t bs = 0);
 
 // ---- dense mode products (k_dense.cu) ----------------------------------------------------
 // Y[l, i, r] = sum_j Op(i, j) X[l, j, r] along `axis` of X (extents `in`), Op(i, j) =
@@ -138,10 +144,14 @@ void dot(const T* x, const T* y, int64_t n, T* partials, T* out, cudaStream_t s)
 // y = a x + b y with a, b from host
 template <typename T>
 void axpby(T a, const T* x, T b, T* y, int64_t n, cudaStream_t s);
-// r = r - u; acc = acc + r  (one hyper-power Horner step, Eq. 2.1 generalised)
+// r = r - u; acc = acc + r  (one hyper-power Horner step, Eq. 2.1 generalised), on nb rows of
+// n entries with pitch bs
 template <typename T>
-void hp_update(T* r, const T* u, T* acc, int64_t n, cudaStream_t s);
+void hp_update(T* r, const T* u, T* acc, int64_t n, cudaStream_t s, int nb = 1, int64_t bs = 0);
 void copy_async(void* dst, const void* src, size_t bytes, cudaStream_t s);
+// nb rows of row_bytes with the same pitch in source and destination (one 2D copy)
+void copy_rows(void* dst, const void* src, size_t row_bytes, int nb, size_t pitch_bytes,
+               cudaStream_t s);
 // y += sign * (*alpha) * x with alpha in device memory
 void axpy_dev(const double* alpha, double sign, const double* x, double* y, int64_t n,
               cudaStream_t s);

@@ -69,11 +69,15 @@ template <typename T, int W>
 __device__ __forceinline__ void band_pass_flat_x1(const PassArgs<T>& a, int64_t t, T* csh) {
   const int m = a.D0.rows;
   const Dims out = a.in.with(1, m);
-  if (t >= out.size()) return;
-  const int64_t line = t / m;
+  const int nb = a.nb > 1 ? a.nb : 1;
+  if (t >= out.size() * nb) return;
+  const int64_t lines = out.size() / m;
+  int64_t line = t / m;
   const int i = (int)(t - line * m);
+  const int64_t kb = nb > 1 ? (line / lines) * a.bs : 0;   // item offset
+  if (nb > 1) line %= lines;
   const T* cs = csh + i;
-  const int64_t base_in = (int64_t)a.in.n1 * line;
+  const int64_t base_in = kb + (int64_t)a.in.n1 * line;
   const T* x0 = a.X0 + base_in + __ldg(a.D0.start + i);
   T s0 = 0, s1 = 0;
 #pragma unroll
@@ -92,13 +96,13 @@ __device__ __forceinline__ void band_pass_flat_x1(const PassArgs<T>& a, int64_t 
     }
     acc += a.c1 * (u0 + u1);
   }
-  const int64_t o = (int64_t)m * line + i;
+  const int64_t o = kb + (int64_t)m * line + i;
   if (a.Z) acc += a.cz * a.Z[o];
   if (a.g) {
     // g has extents b^3; along x1 the output's own index is i, the line is (i2, i3)
     const Dims gd = a.gdims;
     const int64_t i3 = line / out.n2, i2 = line - i3 * out.n2;
-    const int64_t gi = i + (int64_t)gd.n1 * (i2 + (int64_t)gd.n2 * i3);
+    const int64_t gi = kb + i + (int64_t)gd.n1 * (i2 + (int64_t)gd.n2 * i3);
     const int64_t gstep = a.gaxis == 1 ? 1 : (a.gaxis == 2 ? (int64_t)gd.n1 : (int64_t)gd.n1 * gd.n2);
     acc += a.g[gi] - a.g[gi + gstep];
   }
@@ -133,13 +137,17 @@ __global__ void __launch_bounds__(256) k_band_pass(const __grid_constant__ PassB
   const int m = a.D0.rows;
   const int seg_n = pb.seg;
   const int nseg = (m + seg_n - 1) / seg_n;
-  const int64_t lines = out.size() / m;
+  const int64_t lines1 = out.size() / m;              // lines of one item
+  const int nb = a.nb > 1 ? a.nb : 1;
+  const int64_t lines = lines1 * nb;
   const int64_t t = (int64_t)(blockIdx.x - pb.first_block[jb]) * blockDim.x + threadIdx.x;
   // t = line + lines_rounded * seg with lines rounded to a warp multiple (warps share seg)
   const int64_t lines_r = (lines + 31) / 32 * 32;
-  const int64_t line = t % lines_r;
+  int64_t line = t % lines_r;
   const int seg = (int)(t / lines_r);
   if (line >= lines || seg >= nseg) return;
+  const int64_t kb = nb > 1 ? (line / lines1) * a.bs : 0;   // item offset
+  if (nb > 1) line %= lines1;
   // line -> (j_a, j_b): the two non-band indices, the first one fastest
   int64_t base_in, stride_in, base_out, stride_out;
   int k1, k2;   // indices along (x1, x2, x3) of the line position, filled per axis
@@ -168,6 +176,8 @@ __global__ void __launch_bounds__(256) k_band_pass(const __grid_constant__ PassB
     k1 = i1;
     k2 = i2;
   }
+  base_in += kb;
+  base_out += kb;
   int64_t gbase = 0, gstride = 0, gstep = 0;
   if (a.g) {
     // g has extents b^3 (gdims); the output's own index along gaxis is the band index when
@@ -178,7 +188,7 @@ __global__ void __launch_bounds__(256) k_band_pass(const __grid_constant__ PassB
     if (axis == 1) { idx[0] = 0; idx[1] = k1; idx[2] = k2; }
     else if (axis == 2) { idx[0] = k1; idx[1] = 0; idx[2] = k2; }
     else { idx[0] = k1; idx[1] = k2; idx[2] = 0; }
-    gbase = idx[0] * gs[0] + idx[1] * gs[1] + idx[2] * gs[2];
+    gbase = kb + idx[0] * gs[0] + idx[1] * gs[1] + idx[2] * gs[2];
     gstride = gs[axis - 1];     // moving along the band direction
     gstep = gs[a.gaxis - 1];    // the difference direction
   }
@@ -430,7 +440,9 @@ __global__ void __launch_bounds__(256, 3) k_band_slide(const __grid_constant__ P
   const int rs = mr + 2 * H;   // slab rows
   const int nt = a.nterms;
   const Dims out = a.in;
-  const int lines = (int)(out.size() / m);
+  const int lines1 = (int)(out.size() / m);        // lines of one item
+  const int nb = a.nb > 1 ? a.nb : 1;
+  const int lines = lines1 * nb;
   const int line0 = ((int)blockIdx.x - pb.first_block[jb]) * kTileLines;
   const int nl = lines - line0 < kTileLines ? lines - line0 : kTileLines;
   float* ys = sh + nt * rs * P;                                          // m x P (passes along x1)
@@ -441,8 +453,16 @@ __global__ void __launch_bounds__(256, 3) k_band_slide(const __grid_constant__ P
     const float* src = (t == 0 ? a.D0 : a.D1).cval;
     for (int q = tid; q < mr * CP / 4; q += blockDim.x) cp_async16(cf + t * mr * CP + 4 * q, src + 4 * q);
   }
+  // this lane's line: item k (offset koff) and line l within the item
   int base = 0, stride = 0;
-  if (lane < nl) line_geometry32(axis, a.in, line0 + lane, &base, &stride);
+  int64_t koff = 0;
+  int lline = line0 + lane;
+  if (nb > 1) {
+    const int k = lline / lines1;
+    lline -= k * lines1;
+    koff = (int64_t)k * a.bs;
+  }
+  if (lane < nl) line_geometry32(axis, a.in, lline, &base, &stride);
   for (int t = 0; t < nt; ++t) {
     const float* X = t == 0 ? a.X0 : a.X1;
     float* xs = sh + t * rs * P;
@@ -451,7 +471,12 @@ __global__ void __launch_bounds__(256, 3) k_band_slide(const __grid_constant__ P
     for (int q = tid; q < (rs - H - m) * P; q += blockDim.x) xs[(H + m) * P + q] = 0.f;
     if (axis == 1) {
       for (int l = warp; l < kTileLines; l += nwarps) {
-        const float* row = X + a.in.n1 * (line0 + l);
+        int gl = line0 + l, k = 0;
+        if (nb > 1) {
+          k = gl / lines1;
+          gl -= k * lines1;
+        }
+        const float* row = X + (int64_t)k * a.bs + a.in.n1 * gl;
         float* dst = xs + H * P + l;
         if (l < nl) {
 #pragma unroll 4
@@ -463,7 +488,7 @@ __global__ void __launch_bounds__(256, 3) k_band_slide(const __grid_constant__ P
     } else {
       float* dst = xs + (H + warp) * P + lane;
       if (lane < nl) {
-        const float* src = X + base + warp * stride;
+        const float* src = X + koff + base + warp * stride;
 #pragma unroll 4
         for (int j = warp; j < m; j += nwarps, dst += nwarps * P, src += nwarps * stride)
           cp_async4(dst, src);
@@ -476,7 +501,7 @@ __global__ void __launch_bounds__(256, 3) k_band_slide(const __grid_constant__ P
   __syncthreads();
   int gbase = 0, gstride = 0, gstep = 0;
   if (HAS_G && lane < nl) {
-    const int line = line0 + lane;
+    const int line = lline;
     int idx3[3];
     if (axis == 1) { idx3[0] = 0; idx3[2] = line / out.n2; idx3[1] = line - idx3[2] * out.n2; }
     else if (axis == 2) { idx3[2] = line / out.n1; idx3[0] = line - idx3[2] * out.n1; idx3[1] = 0; }
@@ -500,7 +525,7 @@ __global__ void __launch_bounds__(256, 3) k_band_slide(const __grid_constant__ P
     creg1[k] = nt > 1 ? cf[mr * CP + trow * CP + k] : 0.f;
   }
   const float c0 = a.c0, c1 = a.c1;
-  const float* g = a.g;
+  const float* g = HAS_G ? a.g + koff : nullptr;
   float* Y = a.Y;
   const bool ax1 = axis == 1;
   for (int i0 = warp * R; i0 < mr; i0 += nwarps * R) {
@@ -528,7 +553,7 @@ __global__ void __launch_bounds__(256, 3) k_band_slide(const __grid_constant__ P
           if (i0 + r < m) yr[r * P] = acc[r];
       }
     } else if (lane < nl) {
-      float* yo = Y + base + stride * i0;
+      float* yo = Y + koff + base + stride * i0;
       if (i0 + R <= m) {
 #pragma unroll
         for (int r = 0; r < R; ++r) yo[stride * r] = acc[r];
@@ -542,59 +567,74 @@ __global__ void __launch_bounds__(256, 3) k_band_slide(const __grid_constant__ P
   if (axis == 1) {
     __syncthreads();
     for (int l = warp; l < nl; l += nwarps) {
-      float* row = Y + m * (line0 + l);
+      int gl = line0 + l, k = 0;
+      if (nb > 1) {
+        k = gl / lines1;
+        gl -= k * lines1;
+      }
+      float* row = Y + (int64_t)k * a.bs + m * gl;
       for (int i = lane; i < m; i += 32) row[i] = ys[i * P + l];
     }
   }
 }
 
+// nb items: item k of every tensor argument at offset k * bs elements
 template <typename T>
 __global__ void __launch_bounds__(256) k_divergence(const T* __restrict__ u1, const T* __restrict__ u2,
                                                     const T* __restrict__ u3, int a, int b,
                                                     T* __restrict__ delta, const T* __restrict__ q,
-                                                    T nu, T* __restrict__ e) {
+                                                    T nu, T* __restrict__ e, int nb, int64_t bs) {
   pdl_begin();
-  const int64_t total = (int64_t)b * b * b;
+  const int64_t per = (int64_t)b * b * b;
+  const int64_t total = per * nb;
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += step) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += step) {
+    const int64_t k = nb > 1 ? t / per : 0;
+    const int64_t o = t - k * per;
+    const int64_t kb = k * bs;
     const int i1 = (int)(o % b);
     const int i2 = (int)((o / b) % b);
     const int i3 = (int)(o / ((int64_t)b * b));
     T d = 0;
     // u1 extents (a, b, b)
     {
-      const int64_t row = (int64_t)a * (i2 + (int64_t)b * i3);
+      const int64_t row = kb + (int64_t)a * (i2 + (int64_t)b * i3);
       if (i1 < a) d += u1[row + i1];
       if (i1 >= 1) d -= u1[row + i1 - 1];
     }
     // u2 extents (b, a, b)
     {
-      const int64_t off = i1 + (int64_t)b * a * i3;
+      const int64_t off = kb + i1 + (int64_t)b * a * i3;
       if (i2 < a) d += u2[off + (int64_t)b * i2];
       if (i2 >= 1) d -= u2[off + (int64_t)b * (i2 - 1)];
     }
     // u3 extents (b, b, a)
     {
-      const int64_t off = i1 + (int64_t)b * i2;
+      const int64_t off = kb + i1 + (int64_t)b * i2;
       if (i3 < a) d += u3[off + (int64_t)b * b * i3];
       if (i3 >= 1) d -= u3[off + (int64_t)b * b * (i3 - 1)];
     }
-    delta[o] = d;
-    if (e) e[o] = nu * d + q[o];
+    delta[kb + o] = d;
+    if (e) e[kb + o] = nu * d + q[kb + o];
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_div_transpose(const T* __restrict__ g, int a, int b, T* y1,
-                                                       T* y2, T* y3, int accumulate) {
+                                                       T* y2, T* y3, int accumulate, int nb,
+                                                       int64_t bs) {
   pdl_begin();
   const int64_t nc = (int64_t)a * b * b;
-  const int64_t total = 3 * nc;
+  const int64_t per = 3 * nc;
+  const int64_t total = per * nb;
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += step) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += step) {
+    const int64_t k = nb > 1 ? t / per : 0;
+    const int64_t o = t - k * per;
+    const int64_t kb = k * bs;
     const int c = (int)(o / nc);
     const int64_t r = o - c * nc;
-    T* y = c == 0 ? y1 : (c == 1 ? y2 : y3);
+    T* y = (c == 0 ? y1 : (c == 1 ? y2 : y3)) + kb;
     int i1, i2, i3;
     int64_t gs;
     if (c == 0) {
@@ -605,7 +645,7 @@ __global__ void __launch_bounds__(256) k_div_transpose(const T* __restrict__ g, 
       i1 = (int)(r % b); i2 = (int)((r / b) % b); i3 = (int)(r / ((int64_t)b * b));
       gs = (int64_t)b * b;
     }
-    const int64_t gi = i1 + (int64_t)b * (i2 + (int64_t)b * i3);
+    const int64_t gi = kb + i1 + (int64_t)b * (i2 + (int64_t)b * i3);
     const T v = g[gi] - g[gi + gs];
     y[r] = accumulate ? y[r] + v : v;
   }
@@ -705,7 +745,8 @@ void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {
     pb.job[j] = a;
     pb.first_block[j] = blocks;
     const Dims out = a.in.with(a.axis, a.D0.rows);
-    const int64_t lines = out.size() / a.D0.rows;
+    const int nbj = a.nb > 1 ? a.nb : 1;
+    const int64_t lines = out.size() / a.D0.rows * nbj;
     blocks += (int)((lines + kTileLines - 1) / kTileLines);
     const int nin = a.in.get(a.axis);
     const int nt = a.nterms > 1 ? 2 : 1;
@@ -714,11 +755,11 @@ void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {
     const int sm = (nt * nin + (a.axis == 1 ? a.D0.rows : 0)) * (kTileLines + 1) * (int)sizeof(float) +
                    16 + nt * a.D0.rows * (wp * (int)sizeof(float) + (int)sizeof(int));
     smem = sm > smem ? sm : smem;
-    const double outs = (double)out.size();
-    double fl = 2.0 * a.D0.width * outs, by = (double)a.in.size() + outs;
-    if (a.nterms > 1) { fl += 2.0 * a.D1.width * outs; by += (double)a.in.size(); }
+    const double outs = (double)out.size() * nbj;
+    double fl = 2.0 * a.D0.width * outs, by = (double)a.in.size() * nbj + outs;
+    if (a.nterms > 1) { fl += 2.0 * a.D1.width * outs; by += (double)a.in.size() * nbj; }
     if (a.Z) { fl += 2.0 * outs; by += outs; }
-    if (a.g) { fl += 2.0 * outs; by += (double)a.gdims.size(); }
+    if (a.g) { fl += 2.0 * outs; by += (double)a.gdims.size() * nbj; }
     flops += fl;
     bytes += by * sizeof(float);
   }
@@ -737,8 +778,10 @@ void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {
         Wc = 0;
     }
     if (Wc == 0) break;
-    if (a.in.size() >= ((int64_t)1 << 31) || (a.g && a.gdims.size() >= ((int64_t)1 << 31))) {
-      Wc = 0;   // 32-bit indexing only
+    const int nbj = a.nb > 1 ? a.nb : 1;
+    if (a.in.size() >= ((int64_t)1 << 31) || (a.g && a.gdims.size() >= ((int64_t)1 << 31)) ||
+        a.in.size() / a.in.get(a.axis) * nbj >= ((int64_t)1 << 31)) {
+      Wc = 0;   // 32-bit indexing within an item, 32-bit line count
       break;
     }
     const int mr = slide_rows(a.D0.rows);
@@ -776,6 +819,33 @@ void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {
       default: break;
     }
     launch_end(kClassBand, s, flops, bytes);
+    return;
+  }
+  // The tile kernel has no item index: a batched launch runs its items as separate jobs.
+  bool batched = false;
+  for (int j = 0; j < njobs; ++j) batched = batched || jobs[j].nb > 1;
+  if (batched) {
+    PassArgs<float> items[kMaxPassJobs];
+    int ni = 0;
+    for (int j = 0; j < njobs; ++j) {
+      const int nbj = jobs[j].nb > 1 ? jobs[j].nb : 1;
+      for (int k = 0; k < nbj; ++k) {
+        PassArgs<float> e = jobs[j];
+        const int64_t o = (int64_t)k * e.bs;
+        e.X0 += o;
+        if (e.X1) e.X1 += o;
+        if (e.Z) e.Z += o;
+        if (e.g) e.g += o;
+        e.Y += o;
+        e.nb = 1;
+        items[ni++] = e;
+        if (ni == kMaxPassJobs) {
+          band_tile_multi(items, ni, s);
+          ni = 0;
+        }
+      }
+    }
+    if (ni > 0) band_tile_multi(items, ni, s);
     return;
   }
   // one band width per launch (all terms of all jobs); unrolled kernels for the common widths
@@ -839,17 +909,18 @@ void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s) {
     pb.job[j] = a;
     pb.first_block[j] = blocks;
     const Dims out = a.in.with(a.axis, a.D0.rows);
-    const int64_t lines = out.size() / a.D0.rows;
+    const int nbj = a.nb > 1 ? a.nb : 1;
+    const int64_t lines = out.size() / a.D0.rows * nbj;
     const int64_t lines_r = (lines + 31) / 32 * 32;
     const int64_t nseg = (a.D0.rows + seg_len<T>() - 1) / seg_len<T>();
-    if (pb.flat1 && a.axis == 1) blocks += (int)((out.size() + 255) / 256);
+    if (pb.flat1 && a.axis == 1) blocks += (int)((out.size() * nbj + 255) / 256);
     else blocks += (int)((lines_r * nseg + 255) / 256);
     // algorithmic work: one band row per output and term; one read of every input tensor
-    const double outs = (double)out.size();
-    double fl = 2.0 * a.D0.width * outs, by = (double)a.in.size() + outs;
-    if (a.nterms > 1) { fl += 2.0 * a.D1.width * outs; by += (double)a.in.size(); }
+    const double outs = (double)out.size() * nbj;
+    double fl = 2.0 * a.D0.width * outs, by = (double)a.in.size() * nbj + outs;
+    if (a.nterms > 1) { fl += 2.0 * a.D1.width * outs; by += (double)a.in.size() * nbj; }
     if (a.Z) { fl += 2.0 * outs; by += outs; }
-    if (a.g) { fl += 2.0 * outs; by += (double)a.gdims.size(); }
+    if (a.g) { fl += 2.0 * outs; by += (double)a.gdims.size() * nbj; }
     flops += fl;
     bytes += by * sizeof(T);
   }
@@ -881,31 +952,37 @@ void band_pass(const PassArgs<T>& a, cudaStream_t s) {
 }
 
 template <typename T>
-void divergence(const T* u1, const T* u2, const T* u3, int a, int b, T* delta, cudaStream_t s) {
-  const int64_t total = (int64_t)b * b * b;
+void divergence(const T* u1, const T* u2, const T* u3, int a, int b, T* delta, cudaStream_t s,
+                int nb, int64_t bs) {
+  if (nb < 1) nb = 1;
+  const int64_t total = (int64_t)b * b * b * nb;
   launch_begin(kClassDiv, s);
   launch_k(k_divergence<T>, grid_for(total, 256), 256, 0, s, u1, u2, u3, a, b, delta, nullptr, T(0),
-                                                      nullptr);
-  launch_end(kClassDiv, s, 6.0 * total, (3.0 * a * b * b + total) * sizeof(T));
+           nullptr, nb, bs);
+  launch_end(kClassDiv, s, 6.0 * total, (3.0 * a * b * b * nb + total) * sizeof(T));
 }
 
 template <typename T>
 void divergence_plus(const T* u1, const T* u2, const T* u3, int a, int b, T* delta, const T* q,
-                     T nu, T* e, cudaStream_t s) {
-  const int64_t total = (int64_t)b * b * b;
+                     T nu, T* e, cudaStream_t s, int nb, int64_t bs) {
+  if (nb < 1) nb = 1;
+  const int64_t total = (int64_t)b * b * b * nb;
   launch_begin(kClassDiv, s);
-  launch_k(k_divergence<T>, grid_for(total, 256), 256, 0, s, u1, u2, u3, a, b, delta, q, nu, e);
-  launch_end(kClassDiv, s, 8.0 * total, (3.0 * a * b * b + 3.0 * total) * sizeof(T));
+  launch_k(k_divergence<T>, grid_for(total, 256), 256, 0, s, u1, u2, u3, a, b, delta, q, nu, e, nb,
+           bs);
+  launch_end(kClassDiv, s, 8.0 * total, (3.0 * a * b * b * nb + 3.0 * total) * sizeof(T));
 }
 
 template <typename T>
 void div_transpose(const T* g, int a, int b, T* y1, T* y2, T* y3, int accumulate,
-                   cudaStream_t s) {
-  const int64_t total = 3 * (int64_t)a * b * b;
+                   cudaStream_t s, int nb, int64_t bs) {
+  if (nb < 1) nb = 1;
+  const int64_t total = 3 * (int64_t)a * b * b * nb;
   launch_begin(kClassDiv, s);
-  launch_k(k_div_transpose<T>, grid_for(total, 256), 256, 0, s, g, a, b, y1, y2, y3, accumulate);
+  launch_k(k_div_transpose<T>, grid_for(total, 256), 256, 0, s, g, a, b, y1, y2, y3, accumulate,
+           nb, bs);
   launch_end(kClassDiv, s, (accumulate ? 2.0 : 1.0) * total,
-             ((double)b * b * b + (accumulate ? 2.0 : 1.0) * total) * sizeof(T));
+             ((double)b * b * b * nb + (accumulate ? 2.0 : 1.0) * total) * sizeof(T));
 }
 
 template void band_pass<double>(const PassArgs<double>&, cudaStream_t);
@@ -913,16 +990,17 @@ template void band_pass<float>(const PassArgs<float>&, cudaStream_t);
 template void band_pass_multi<double>(const PassArgs<double>*, int, cudaStream_t);
 template void band_pass_multi<float>(const PassArgs<float>*, int, cudaStream_t);
 template void divergence<double>(const double*, const double*, const double*, int, int, double*,
-                                 cudaStream_t);
+                                 cudaStream_t, int, int64_t);
 template void divergence<float>(const float*, const float*, const float*, int, int, float*,
-                                cudaStream_t);
+                                cudaStream_t, int, int64_t);
 template void divergence_plus<double>(const double*, const double*, const double*, int, int,
-                                      double*, const double*, double, double*, cudaStream_t);
+                                      double*, const double*, double, double*, cudaStream_t, int,
+                                      int64_t);
 template void divergence_plus<float>(const float*, const float*, const float*, int, int, float*,
-                                     const float*, float, float*, cudaStream_t);
+                                     const float*, float, float*, cudaStream_t, int, int64_t);
 template void div_transpose<double>(const double*, int, int, double*, double*, double*, int,
-                                    cudaStream_t);
+                                    cudaStream_t, int, int64_t);
 template void div_transpose<float>(const float*, int, int, float*, float*, float*, int,
-                                   cudaStream_t);
+                                   cudaStream_t, int, int64_t);
 
 }  // namespace shp

@@ -323,12 +323,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int r = (t - J.first_tile) * kTileM + row_in_tile;
-      const bool valid = r < args.R;
+      const int nbi = args.nb > 1 ? args.nb : 1;
+      const bool valid = r < args.R * nbi;
       TO* yrow = reinterpret_cast<TO*>(args.Y);
       float lam_r = 0.f;
       if (valid) {
-        const int j2 = r % args.e2, j3 = r / args.e2;
-        yrow += j2 + (int64_t)args.ldy * j3;
+        const int k = nbi > 1 ? r / args.R : 0;   // item
+        const int rr = r - k * args.R;
+        const int j2 = rr % args.e2, j3 = rr / args.e2;
+        yrow += (int64_t)k * args.ybs + j2 + (int64_t)args.ldy * j3;
         if (args.lam_i) lam_r = args.lam_j2[j2] + args.lam_j3[j3];
       }
       const int64_t stride_i = (int64_t)args.ldy * args.e3;
@@ -372,14 +375,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 template <typename TO>
 __global__ void k_pad_rows(const float* __restrict__ x, int e1, int64_t R, int ld,
-                           TO* __restrict__ y) {
+                           TO* __restrict__ y, int nb, int64_t xbs) {
   pdl_begin();
-  const int64_t total = (int64_t)e1 * R;
+  const int64_t per = (int64_t)e1 * R;
+  const int64_t total = per * nb;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
        o += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = o / e1;
+    const int64_t r = o / e1;                 // row over all items
     const int j = (int)(o - r * e1);
-    store_val<TO>(y + r * ld + j, x[o]);
+    const int64_t k = nb > 1 ? r / R : 0;     // item
+    store_val<TO>(y + r * ld + j, x[o + k * (xbs - per)]);
   }
 }
 
@@ -459,13 +464,14 @@ void launch_rmp_t(const RmpPlan* const* plans, int njobs, int* err, int sms, cud
     std::memcpy(&J.map_op, p.map_op, sizeof(CUtensorMap));
     J.args = p.args;
     J.first_tile = tiles;
-    J.ntiles = (p.args.R + kTileM - 1) / kTileM;
+    const int64_t rows = (int64_t)p.args.R * (p.args.nb > 1 ? p.args.nb : 1);
+    J.ntiles = (int)((rows + kTileM - 1) / kTileM);
     J.nchunks = (p.args.K + kChunkBytes / elem - 1) / (kChunkBytes / elem);
     tiles += J.ntiles;
     const int sm = rmp_smem_bytes(KIND, p.args.K, p.args.npad);
     smem = sm > smem ? sm : smem;
-    flops += 2.0 * p.args.R * p.args.m * p.args.K;
-    bytes += (double)p.args.R * (p.args.K * elem + p.args.m * (double)sizeof(TO));
+    flops += 2.0 * rows * p.args.m * p.args.K;
+    bytes += (double)rows * (p.args.K * elem + p.args.m * (double)sizeof(TO));
   }
   b.total_tiles = tiles;
   const int grid = tiles < sms ? tiles : sms;
@@ -487,16 +493,19 @@ void launch_rmp_multi(const RmpPlan* const* plans, int njobs, int* err, int sms,
   else launch_rmp_t<kMmaBF16, float>(plans, njobs, err, sms, s);
 }
 
-void pad_rows(const float* x, int e1, int64_t R, int ld, void* y, bool to_bf16, cudaStream_t s) {
-  const int64_t total = (int64_t)e1 * R;
+void pad_rows(const float* x, int e1, int64_t R, int ld, void* y, bool to_bf16, cudaStream_t s,
+              int nb, int64_t xbs) {
+  if (nb < 1) nb = 1;
+  const int64_t total = (int64_t)e1 * R * nb;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
   launch_begin(kClassVector, s);
   if (to_bf16)
     launch_k(k_pad_rows<__nv_bfloat16>, (int)blocks, 256, 0, s, x, e1, R, ld,
-                                                          static_cast<__nv_bfloat16*>(y));
+             static_cast<__nv_bfloat16*>(y), nb, xbs);
   else
-    launch_k(k_pad_rows<float>, (int)blocks, 256, 0, s, x, e1, R, ld, static_cast<float*>(y));
+    launch_k(k_pad_rows<float>, (int)blocks, 256, 0, s, x, e1, R, ld, static_cast<float*>(y), nb,
+             xbs);
   launch_end(kClassVector, s, 0.0, (double)total * (to_bf16 ? 6.0 : 8.0));
 }
 

@@ -64,12 +64,16 @@ __global__ void k_axpby(T a, const T* __restrict__ x, T b, T* __restrict__ y, in
     y[i] = a * x[i] + b * y[i];
 }
 
+// nb rows of n entries with pitch bs (nb == 1: one contiguous range)
 template <typename T>
 __global__ void k_hp_update(T* __restrict__ r, const T* __restrict__ u, T* __restrict__ acc,
-                            int64_t n) {
+                            int64_t n, int nb, int64_t bs) {
   pdl_begin();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t total = n * nb;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = nb > 1 ? t / n : 0;
+    const int64_t i = t + k * (bs - n);
     const T ri = r[i] - u[i];
     r[i] = ri;
     acc[i] += ri;
@@ -346,14 +350,24 @@ void axpby(T a, const T* x, T b, T* y, int64_t n, cudaStream_t s) {
 }
 
 template <typename T>
-void hp_update(T* r, const T* u, T* acc, int64_t n, cudaStream_t s) {
+void hp_update(T* r, const T* u, T* acc, int64_t n, cudaStream_t s, int nb, int64_t bs) {
+  if (nb < 1) nb = 1;
   launch_begin(kClassVector, s);
-  launch_k(k_hp_update<T>, grid_for(n), kThreads, 0, s, r, u, acc, n);
+  launch_k(k_hp_update<T>, grid_for(n * nb), kThreads, 0, s, r, u, acc, n, nb, nb > 1 ? bs : n);
   launch_end(kClassVector, s, 0.0, 0.0);
 }
 
 void copy_async(void* dst, const void* src, size_t bytes, cudaStream_t s) {
   cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
+}
+
+void copy_rows(void* dst, const void* src, size_t row_bytes, int nb, size_t pitch_bytes,
+               cudaStream_t s) {
+  if (nb <= 1) {
+    cudaMemcpyAsync(dst, src, row_bytes, cudaMemcpyDeviceToDevice, s);
+    return;
+  }
+  cudaMemcpy2DAsync(dst, pitch_bytes, src, pitch_bytes, row_bytes, nb, cudaMemcpyDeviceToDevice, s);
 }
 
 void fill_zero(void* dst, size_t bytes, cudaStream_t s) { cudaMemsetAsync(dst, 0, bytes, s); }
@@ -438,7 +452,7 @@ template void dot<double>(const double*, const double*, int64_t, double*, double
 template void dot<float>(const float*, const float*, int64_t, float*, float*, cudaStream_t);
 template void axpby<double>(double, const double*, double, double*, int64_t, cudaStream_t);
 template void axpby<float>(float, const float*, float, float*, int64_t, cudaStream_t);
-template void hp_update<double>(double*, const double*, double*, int64_t, cudaStream_t);
-template void hp_update<float>(float*, const float*, float*, int64_t, cudaStream_t);
+template void hp_update<double>(double*, const double*, double*, int64_t, cudaStream_t, int, int64_t);
+template void hp_update<float>(float*, const float*, float*, int64_t, cudaStream_t, int, int64_t);
 
 }  // namespace shp

@@ -22,6 +22,9 @@ struct RmpArgs {
   const float* lam_i;
   float post;       // otherwise multiply by post
   void* Y;
+  int nb;           // items (<= 1: one): the input holds nb * R rows, item k's rows after item
+                    // k - 1's; item k's output starts ybs elements after item k - 1's
+  int64_t ybs;
 };
 
 struct RmpPlan {
@@ -44,7 +47,9 @@ void launch_rmp(const RmpPlan& p, int* err, int sms, cudaStream_t s);
 void launch_rmp_multi(const RmpPlan* const* plans, int njobs, int* err, int sms, cudaStream_t s);
 
 // Copy a canonical float tensor (rows of e1 entries, R rows) into rows of pitch ld, converting
-// to bfloat16 if to_bf16.
-void pad_rows(const float* x, int e1, int64_t R, int ld, void* y, bool to_bf16, cudaStream_t s);
+// to bfloat16 if to_bf16. nb items: item k's tensor starts xbs elements after item k - 1's in x,
+// its rows follow item k - 1's in y.
+void pad_rows(const float* x, int e1, int64_t R, int ld, void* y, bool to_bf16, cudaStream_t s,
+              int nb = 1, int64_t xbs = 0);
 
 }  // namespace shp

@@ -187,6 +187,9 @@ struct Ops {
   T *f1 = nullptr, *f2 = nullptr;                                 // mode-product ping-pong
   T *delta = nullptr, *m1 = nullptr, *m2 = nullptr;               // pressure-size temporaries
   cudaStream_t s = nullptr;
+  // batch: nb items per vector, item k of every tensor bs elements after item k - 1's
+  int nb = 1;
+  int64_t bs = 0;
   // tensor-core fast diagonalisation (reduced precision only): per tensor (3 velocity components,
   // pressure) a padded input copy and six rotating mode products
   bool tc = false;
@@ -222,6 +225,8 @@ struct Ops {
     p.Y = Y;
     p.in = in;
     p.axis = axis;
+    p.nb = nb;
+    p.bs = bs;
     return p;
   }
 
@@ -289,7 +294,7 @@ struct Ops {
     const T* q = x + nvel;
     T* yq = y + nvel;
     // delta = D_div u, e = nu delta + q; B^T u = M_q delta; g = M_q e
-    divergence_plus<T>(x, x + nvc, x + 2 * nvc, a, b, delta, q, nu, m1, s);
+    divergence_plus<T>(x, x + nvc, x + 2 * nvc, a, b, delta, q, nu, m1, s, nb, bs);
     const T* in[2] = {delta, m1};
     T* out[2] = {yq, m2};
     const T coef[2] = {1, 1};
@@ -302,7 +307,7 @@ struct Ops {
   }
 
   void apply_A(const T* x, T* y) const {
-    divergence<T>(x, x + nvc, x + 2 * nvc, a, b, delta, s);
+    divergence<T>(x, x + nvc, x + 2 * nvc, a, b, delta, s, nb, bs);
     const T* in[1] = {delta};
     T* out[1] = {m2};
     const T coef[1] = {nu};
@@ -334,11 +339,11 @@ struct Ops {
     T* out[1] = {m2};
     const T coef[1] = {1};
     mq(1, in, out, coef);
-    div_transpose<T>(m2, a, b, yu, yu + nvc, yu + 2 * nvc, 0, s);
+    div_transpose<T>(m2, a, b, yu, yu + nvc, yu + 2 * nvc, 0, s, nb, bs);
   }
 
   void apply_Bt(const T* u, T* yq) const {  // B^T u = M_q D_div u
-    divergence<T>(u, u + nvc, u + 2 * nvc, a, b, delta, s);
+    divergence<T>(u, u + nvc, u + 2 * nvc, a, b, delta, s, nb, bs);
     const T* in[1] = {delta};
     T* out[1] = {yq};
     const T coef[1] = {1};
@@ -371,10 +376,13 @@ struct Ops {
   // tensor t (0..2 velocity components, 3 pressure): canonical x -> canonical y
   void tc_fd(int t, const float* x, float* y) const {
     const Dims d = t < 3 ? comp(t) : Dims{b, b, b};
-    pad_rows(x, d.n1, (int64_t)d.n2 * d.n3, tc_ld0[t], tc_p0[t], tc_bf16, s);
+    pad_rows(x, d.n1, (int64_t)d.n2 * d.n3, tc_ld0[t], tc_p0[t], tc_bf16, s, nb, bs);
     for (int st = 0; st < 6; ++st) {
       RmpPlan p = tc_plan[t * 6 + st];
-      if (st == 5) p.args.Y = y;
+      if (st == 5) {
+        p.args.Y = y;
+        p.args.ybs = bs;
+      }
       launch_rmp(p, tc_err, sms, s);
     }
   }
@@ -385,14 +393,17 @@ struct Ops {
       for (int c = 0; c < 3; ++c) {
         const Dims d = comp(c);
         pad_rows(reinterpret_cast<const float*>(x + c * nvc), d.n1, (int64_t)d.n2 * d.n3,
-                 tc_ld0[c], tc_p0[c], tc_bf16, s);
+                 tc_ld0[c], tc_p0[c], tc_bf16, s, nb, bs);
       }
       for (int st = 0; st < 6; ++st) {
         RmpPlan p[3];
         const RmpPlan* pp[3];
         for (int c = 0; c < 3; ++c) {
           p[c] = tc_plan[c * 6 + st];
-          if (st == 5) p[c].args.Y = reinterpret_cast<float*>(y + c * nvc);
+          if (st == 5) {
+            p[c].args.Y = reinterpret_cast<float*>(y + c * nvc);
+            p[c].args.ybs = bs;
+          }
           pp[c] = &p[c];
         }
         launch_rmp_multi(pp, 3, tc_err, sms, s);
@@ -498,13 +509,13 @@ struct HyperPower {
       return;
     }
     T *r = L.r[s], *acc = L.acc[s], *t = L.t[s], *u = L.u[s];
-    copy_async(r, x, n * sizeof(T), o.s);
-    copy_async(acc, x, n * sizeof(T), o.s);
+    copy_rows(r, x, n * sizeof(T), o.nb, o.bs * sizeof(T), o.s);
+    copy_rows(acc, x, n * sizeof(T), o.nb, o.bs * sizeof(T), o.s);
     for (int j = 1; j < order; ++j) {
       V(o, L, s - 1, r, t);
       o.apply_A(t, u);
       ++counts[2];
-      hp_update<T>(r, u, acc, n, o.s);
+      hp_update<T>(r, u, acc, n, o.s, o.nb, o.bs);
     }
     V(o, L, s - 1, acc, y);
   }
@@ -523,15 +534,15 @@ struct HyperPower {
     }
     T *r = qr[m], *acc = qacc[m], *t = qt[m], *u = qu[m];
     const int l = level_of(m);
-    copy_async(r, x, n * sizeof(T), o.s);
-    copy_async(acc, x, n * sizeof(T), o.s);
+    copy_rows(r, x, n * sizeof(T), o.nb, o.bs * sizeof(T), o.s);
+    copy_rows(acc, x, n * sizeof(T), o.nb, o.bs * sizeof(T), o.s);
     for (int j = 1; j < order; ++j) {
       Q(o, L, m - 1, r, t);
       o.apply_B(t, bv);          // A~_Q t = B^T P_{V,l}^-1 B t
       V(o, L, l, bv, hv);
       o.apply_Bt(hv, u);
       ++counts[3];
-      hp_update<T>(r, u, acc, n, o.s);
+      hp_update<T>(r, u, acc, n, o.s, o.nb, o.bs);
     }
     Q(o, L, m - 1, acc, y);
   }
@@ -576,11 +587,13 @@ struct stokes_ctx {
   MinresState* st = nullptr;
   MinresState* st_host = nullptr;
   double* pinned = nullptr;              // small pinned host scratch
+  double* pinned_multi = nullptr;        // 2 scalars per item (nrhs > 1)
   // Krylov vectors
   double *kv[8] = {nullptr};
   double *V = nullptr, *Z = nullptr;     // FGMRES bases ((restart + 1) x ntot, restart x ntot)
   double *io_rhs = nullptr, *io_x = nullptr;
   int order = 2, steps = 0;
+  int nb = 1;                     // right-hand sides (items) per vector, item stride ntot
   std::vector<double> ratios;
   std::string err;
   Profiler* prof = nullptr;
@@ -648,20 +661,28 @@ void init_ops(stokes_ctx* c, Ops<T>& o, const Band& M, const Band& K, const Band
 }
 
 // temporaries of one operator set (a second set lets a second stream run the same operators)
+// entries of a buffer holding one item of `per_item` entries per right-hand side, item k at
+// k * ntot (per_item <= ntot)
+size_t bsize(const stokes_ctx* c, int64_t per_item) {
+  return c->nb > 1 ? (size_t)(c->nb - 1) * (size_t)c->ntot + (size_t)per_item : (size_t)per_item;
+}
+
 template <typename T>
 void alloc_workspace(stokes_ctx* c, Ops<T>& o) {
   Arena& ar = c->arena;
-  const size_t pres = (size_t)c->npres, vel = (size_t)c->nvel;
-  const size_t ping = std::max(vel, 2 * pres);   // all velocity components, or two pressures
-  o.tK = ar.alloc<T>(vel);
-  o.tM = ar.alloc<T>(vel);
-  o.tS = ar.alloc<T>(vel);
-  o.tR = ar.alloc<T>(vel);
-  o.f1 = ar.alloc<T>(ping);
-  o.f2 = ar.alloc<T>(ping);
-  o.delta = ar.alloc<T>(pres);
-  o.m1 = ar.alloc<T>(pres);
-  o.m2 = ar.alloc<T>(pres);
+  const int64_t pres = c->npres, vel = c->nvel;
+  const int64_t ping = std::max(vel, 2 * pres);   // all velocity components, or two pressures
+  o.nb = c->nb;
+  o.bs = c->ntot;
+  o.tK = ar.alloc<T>(bsize(c, vel));
+  o.tM = ar.alloc<T>(bsize(c, vel));
+  o.tS = ar.alloc<T>(bsize(c, vel));
+  o.tR = ar.alloc<T>(bsize(c, vel));
+  o.f1 = ar.alloc<T>(bsize(c, ping));
+  o.f2 = ar.alloc<T>(bsize(c, ping));
+  o.delta = ar.alloc<T>(bsize(c, pres));
+  o.m1 = ar.alloc<T>(bsize(c, pres));
+  o.m2 = ar.alloc<T>(bsize(c, pres));
 }
 
 int rup(int x, int m) { return (x + m - 1) / m * m; }
@@ -709,7 +730,9 @@ void init_tc(stokes_ctx* c, const Dense& UN, const std::vector<double>& lN, cons
     }
     ck(cudaStreamSynchronize(s), "op");
   }
-  const size_t slot = (size_t)rup(rup(b, align) * b * b, 64);   // elements per rotation slot
+  // elements per rotation slot: one tensor (the largest rotated layout) of every item
+  const int nb = c->nb;
+  const size_t slot = (size_t)rup(rup(b, align) * b * b, 64) * nb;
   uint8_t* P0 = reinterpret_cast<uint8_t*>(ar.alloc<float>(slot * 4 * elem / 4 + 64));
   uint8_t* F1 = reinterpret_cast<uint8_t*>(ar.alloc<float>(slot * 4 * elem / 4 + 64));
   uint8_t* F2 = reinterpret_cast<uint8_t*>(ar.alloc<float>(slot * 4 * elem / 4 + 64));
@@ -760,8 +783,12 @@ void init_tc(stokes_ctx* c, const Dense& UN, const std::vector<double>& lN, cons
       }
       if (st == 5 && t == 3) ra.post = (float)(2.0 * c->nu);
       ra.Y = bufs_out[st] ? (void*)(bufs_out[st] + (size_t)t * slot * elem) : nullptr;
+      // items: the rotated output of item k follows item k - 1's (e3 * m rows of pitch ldy,
+      // the next step's input rows); the final step's output is canonical (set at launch)
+      ra.nb = nb;
+      ra.ybs = (int64_t)ra.ldy * e3 * ra.m;
       const void* in = bufs_in[st] + (size_t)t * slot * elem;
-      if (!make_map(p.map_x, in, kind, e1, (int64_t)e2 * e3, rup(e1, align), 128) ||
+      if (!make_map(p.map_x, in, kind, e1, (int64_t)e2 * e3 * nb, rup(e1, align), 128) ||
           !make_map(p.map_op, op[opk], kind, e1, ra.npad, kpad_of[opk], ra.npad))
         throw SetupError{"tensor map encoding failed"};
     }
@@ -779,10 +806,10 @@ void alloc_levels(stokes_ctx* c, typename HyperPower<T>::VLevels& L) {
   L.t.assign(n + 1, nullptr);
   L.u.assign(n + 1, nullptr);
   for (int l = 1; l <= n; ++l) {
-    L.r[l] = c->arena.alloc<T>(c->nvel);
-    L.acc[l] = c->arena.alloc<T>(c->nvel);
-    L.t[l] = c->arena.alloc<T>(c->nvel);
-    L.u[l] = c->arena.alloc<T>(c->nvel);
+    L.r[l] = c->arena.alloc<T>(bsize(c, c->nvel));
+    L.acc[l] = c->arena.alloc<T>(bsize(c, c->nvel));
+    L.t[l] = c->arena.alloc<T>(bsize(c, c->nvel));
+    L.u[l] = c->arena.alloc<T>(bsize(c, c->nvel));
   }
 }
 
@@ -805,14 +832,14 @@ void init_hp(stokes_ctx* c, HyperPower<T>& h, const Ops<T>& o, const Ops<T>* opq
   h.qt.assign(L + 1, nullptr);
   h.qu.assign(L + 1, nullptr);
   for (int l = 1; l <= L; ++l) {
-    h.qr[l] = ar.alloc<T>(c->npres);
-    h.qacc[l] = ar.alloc<T>(c->npres);
-    h.qt[l] = ar.alloc<T>(c->npres);
-    h.qu[l] = ar.alloc<T>(c->npres);
+    h.qr[l] = ar.alloc<T>(bsize(c, c->npres));
+    h.qacc[l] = ar.alloc<T>(bsize(c, c->npres));
+    h.qt[l] = ar.alloc<T>(bsize(c, c->npres));
+    h.qu[l] = ar.alloc<T>(bsize(c, c->npres));
   }
   if (L > 0) {
-    h.bv = ar.alloc<T>(c->nvel);
-    h.hv = ar.alloc<T>(c->nvel);
+    h.bv = ar.alloc<T>(bsize(c, c->nvel));
+    h.hv = ar.alloc<T>(bsize(c, c->nvel));
   }
 }
 
@@ -824,10 +851,11 @@ void apply_prec(stokes_ctx* c, int order, int steps, const double* x, double* y)
     c->hd.order = order;
     c->hd.apply(steps, x, y);
   } else {
-    to_float(x, c->xf, c->ntot, c->stream);
+    const int64_t n = (int64_t)c->nb * c->ntot;   // every item
+    to_float(x, c->xf, n, c->stream);
     c->hf.order = order;
     c->hf.apply(steps, c->xf, c->yf);
-    to_double(c->yf, y, c->ntot, c->stream);
+    to_double(c->yf, y, n, c->stream);
   }
 }
 
@@ -1073,6 +1101,223 @@ int run_fgmres(stokes_ctx* c, const double* f, double tol, double* x, int* iters
   return STOKES_ERR_MAXIT;
 }
 
+bool tc_failed(stokes_ctx* c);
+
+// FGMRES for nb right-hand sides in lockstep (contexts with nrhs > 1). Each item follows exactly
+// the steps of run_fgmres (its own Hessenberg matrix, Givens rotations, restarts and stopping
+// test); the preconditioner and K applies of one Arnoldi step run for all items at once, the
+// Gram-Schmidt products and norms per item. Basis vector j holds the items one after the other:
+// item k of V_j at V + j * nb * ntot + k * ntot. An item that has stopped is carried through the
+// batched applies but no longer updated.
+void run_fgmres_multi(stokes_ctx* c, const double* f, double tol, double* x, int* iters,
+                      int* rcs) {
+  const int nb = c->nb;
+  const int64_t n = c->ntot, N = (int64_t)nb * n;
+  cudaStream_t s = c->stream;
+  const int m = c->opts.restart;
+  const int ds = 16 + 2 * (m + 2);   // device scalars per item
+  double* w = c->kv[0];
+  double* r = c->kv[1];
+  auto dsc = [&](int k) { return c->dsc + (size_t)k * ds; };
+  std::vector<double> hs((size_t)nb * ds);
+  auto read_all = [&]() {
+    ck(cudaMemcpyAsync(hs.data(), c->dsc, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, s),
+       "read");
+    ck(cudaStreamSynchronize(s), "sync");
+  };
+  auto put = [&](int k, int slot, double v) {   // one scalar to the device (pinned staging)
+    c->pinned_multi[2 * k + (slot == 5 ? 0 : 1)] = v;
+    ck(cudaMemcpyAsync(dsc(k) + slot, c->pinned_multi + 2 * k + (slot == 5 ? 0 : 1), sizeof(double),
+                       cudaMemcpyHostToDevice, s), "scalar");
+  };
+  fill_zero(x, N * sizeof(double), s);
+  c->ratios.clear();
+  for (int k = 0; k < nb; ++k) dot<double>(f + k * n, f + k * n, n, c->partials, dsc(k) + 3, s);
+  read_all();
+  std::vector<double> fnorm(nb);
+  std::vector<char> done(nb, 0);
+  for (int k = 0; k < nb; ++k) {
+    iters[k] = 0;
+    rcs[k] = STOKES_OK;
+    fnorm[k] = std::sqrt(hs[(size_t)k * ds + 3]);
+    if (!std::isfinite(fnorm[k])) { rcs[k] = STOKES_ERR_NONFINITE; done[k] = 1; }
+    else if (fnorm[k] == 0.0) done[k] = 1;
+  }
+  copy_async(r, f, N * sizeof(double), s);
+  std::vector<std::vector<double>> H(nb, std::vector<double>((size_t)(m + 1) * m));
+  std::vector<std::vector<double>> cs(nb, std::vector<double>(m)), sn(nb, std::vector<double>(m));
+  std::vector<std::vector<double>> g(nb, std::vector<double>(m + 1)), y(nb, std::vector<double>(m));
+  std::vector<int> k_used(nb, 0);
+  std::vector<char> active(nb, 0), stop(nb, 0);
+  auto any = [&](const std::vector<char>& v) {
+    for (char e : v)
+      if (e) return true;
+    return false;
+  };
+  auto all_done = [&]() {
+    for (char e : done)
+      if (!e) return false;
+    return true;
+  };
+  while (!all_done()) {
+    for (int k = 0; k < nb; ++k)
+      if (!done[k]) dot<double>(r + k * n, r + k * n, n, c->partials, dsc(k) + 4, s);
+    read_all();
+    for (int k = 0; k < nb; ++k) {
+      active[k] = 0;
+      stop[k] = 0;
+      k_used[k] = 0;
+      if (done[k]) continue;
+      const double beta = std::sqrt(hs[(size_t)k * ds + 4]);
+      if (!std::isfinite(beta)) { rcs[k] = STOKES_ERR_NONFINITE; done[k] = 1; continue; }
+      if (beta == 0.0) { done[k] = 1; continue; }
+      put(k, 5, beta);
+      scale_inv_dev(dsc(k) + 5, r + k * n, c->V + k * n, n, s);
+      std::fill(H[k].begin(), H[k].end(), 0.0);
+      std::fill(g[k].begin(), g[k].end(), 0.0);
+      g[k][0] = beta;
+      active[k] = 1;
+    }
+    if (!any(active)) break;
+    for (int j = 0; j < m && any(active); ++j) {
+      double* Vj = c->V + (int64_t)j * N;
+      double* Zj = c->Z + (int64_t)j * N;
+      apply_prec(c, c->order, c->steps, Vj, Zj);
+      c->od.apply_K(Zj, w);
+      for (int k = 0; k < nb; ++k) {
+        if (!active[k]) continue;
+        double* hdev = dsc(k) + 8;
+        double* h2dev = dsc(k) + 8 + (m + 2);
+        double* wk = w + k * n;
+        const double* Vk = c->V + k * n;
+        multi_dot(Vk, N, j + 1, wk, n, c->partials, hdev, s);
+        multi_axpy(Vk, N, j + 1, hdev, -1.0, wk, n, s);
+        multi_dot(Vk, N, j + 1, wk, n, c->partials, h2dev, s);
+        multi_axpy(Vk, N, j + 1, h2dev, -1.0, wk, n, s);
+        dot<double>(wk, wk, n, c->partials, dsc(k) + 6, s);
+      }
+      check_launch("fgmres arnoldi");
+      read_all();
+      for (int k = 0; k < nb; ++k) {
+        if (!active[k]) continue;
+        const double* hk = hs.data() + (size_t)k * ds;
+        const double hn = std::sqrt(hk[6]);
+        if (!std::isfinite(hn)) {
+          rcs[k] = STOKES_ERR_NONFINITE;
+          done[k] = 1;
+          active[k] = 0;
+          k_used[k] = 0;
+          continue;
+        }
+        std::vector<double>& Hk = H[k];
+        for (int i = 0; i <= j; ++i) Hk[(size_t)i * m + j] = hk[8 + i] + hk[8 + (m + 2) + i];
+        Hk[(size_t)(j + 1) * m + j] = hn;
+        if (hn > 0.0) {
+          put(k, 7, hn);
+          scale_inv_dev(dsc(k) + 7, w + k * n, c->V + (int64_t)(j + 1) * N + k * n, n, s);
+        }
+        for (int i = 0; i < j; ++i) {
+          const double t = cs[k][i] * Hk[(size_t)i * m + j] + sn[k][i] * Hk[(size_t)(i + 1) * m + j];
+          Hk[(size_t)(i + 1) * m + j] =
+              -sn[k][i] * Hk[(size_t)i * m + j] + cs[k][i] * Hk[(size_t)(i + 1) * m + j];
+          Hk[(size_t)i * m + j] = t;
+        }
+        const double hjj = Hk[(size_t)j * m + j], hj1 = Hk[(size_t)(j + 1) * m + j];
+        const double den = std::hypot(hjj, hj1);
+        if (den == 0.0) {
+          rcs[k] = STOKES_ERR_BREAKDOWN;
+          done[k] = 1;
+          active[k] = 0;
+          k_used[k] = 0;
+          continue;
+        }
+        cs[k][j] = hjj / den;
+        sn[k][j] = hj1 / den;
+        Hk[(size_t)j * m + j] = den;
+        Hk[(size_t)(j + 1) * m + j] = 0.0;
+        g[k][j + 1] = -sn[k][j] * g[k][j];
+        g[k][j] = cs[k][j] * g[k][j];
+        ++iters[k];
+        k_used[k] = j + 1;
+        const double ratio = std::fabs(g[k][j + 1]) / fnorm[k];
+        if (k == 0) c->ratios.push_back(ratio);
+        if (ratio <= tol || iters[k] >= c->opts.maxit || hn == 0.0) {
+          active[k] = 0;
+          stop[k] = 1;
+          rcs[k] = ratio <= tol ? STOKES_OK : STOKES_ERR_MAXIT;
+        }
+      }
+    }
+    // y = H^-1 g (upper triangular), x += Z y, per item
+    for (int k = 0; k < nb; ++k) {
+      if (k_used[k] == 0) continue;
+      const std::vector<double>& Hk = H[k];
+      for (int i = k_used[k] - 1; i >= 0; --i) {
+        double sacc = g[k][i];
+        for (int q = i + 1; q < k_used[k]; ++q) sacc -= Hk[(size_t)i * m + q] * y[k][q];
+        y[k][i] = sacc / Hk[(size_t)i * m + i];
+      }
+      double* hdev = dsc(k) + 8;
+      ck(cudaMemcpyAsync(hdev, y[k].data(), k_used[k] * sizeof(double), cudaMemcpyHostToDevice, s),
+         "y");
+      multi_axpy(c->Z + k * n, N, k_used[k], hdev, 1.0, x + k * n, n, s);
+      ck(cudaStreamSynchronize(s), "sync");   // y[k] is pageable host memory
+    }
+    check_launch("fgmres update");
+    for (int k = 0; k < nb; ++k)
+      if (stop[k]) done[k] = 1;
+    if (all_done()) break;
+    // restart: r = f - K x
+    c->od.apply_K(x, r);
+    for (int k = 0; k < nb; ++k)
+      if (!done[k]) axpby<double>(1.0, f + k * n, -1.0, r + k * n, n, s);
+  }
+  ck(cudaStreamSynchronize(s), "sync");
+}
+
+// solve for every item of a context with nrhs > 1; per-item iterations, true residuals, codes
+int solve_multi_impl(stokes_ctx* c, const double* rhs, double tol, double* x, int* iterations,
+                     double* final_rel_res, int* codes) {
+  const int nb = c->nb;
+  const int64_t n = c->ntot;
+  cudaStream_t s = c->stream;
+  const int ds = 16 + 2 * (c->opts.restart + 2);
+  std::vector<int> its(nb), rcs(nb);
+  run_fgmres_multi(c, rhs, tol, x, its.data(), rcs.data());
+  for (int k = 0; k < nb; ++k) {   // zero-mean pressure per item
+    double* q = x + k * n + c->nvel;
+    dot<double>(q, c->ones, c->npres, c->partials, c->dsc + (size_t)k * ds, s);
+    axpy_dev(c->dsc + (size_t)k * ds, -1.0, c->zconst, q, c->npres, s);
+  }
+  double* tmp = c->kv[7];
+  c->od.apply_K(x, tmp);
+  for (int k = 0; k < nb; ++k) {
+    axpby<double>(1.0, rhs + k * n, -1.0, tmp + k * n, n, s);
+    dot<double>(tmp + k * n, tmp + k * n, n, c->partials, c->dsc + (size_t)k * ds + 1, s);
+    dot<double>(rhs + k * n, rhs + k * n, n, c->partials, c->dsc + (size_t)k * ds + 2, s);
+  }
+  std::vector<double> hs((size_t)nb * ds);
+  ck(cudaMemcpyAsync(hs.data(), c->dsc, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, s),
+     "read");
+  ck(cudaStreamSynchronize(s), "sync");
+  int rc = STOKES_OK;
+  for (int k = 0; k < nb; ++k) {
+    const double rr = hs[(size_t)k * ds + 1], ff = hs[(size_t)k * ds + 2];
+    if (iterations) iterations[k] = its[k];
+    if (final_rel_res) final_rel_res[k] = ff > 0 ? std::sqrt(rr / ff) : std::sqrt(rr);
+    if (codes) codes[k] = rcs[k];
+    if (rc == STOKES_OK && rcs[k] != STOKES_OK) rc = rcs[k];
+  }
+  if (tc_failed(c)) {
+    c->err = "tensor-core pipeline wait timed out";
+    return STOKES_ERR_CUDA;
+  }
+  if (rc == STOKES_ERR_MAXIT) c->err = "iteration cap reached";
+  else if (rc == STOKES_ERR_NONFINITE) c->err = "non-finite value in the Krylov recurrence";
+  else if (rc == STOKES_ERR_BREAKDOWN) c->err = "Krylov breakdown";
+  return rc;
+}
+
 // the tensor-core pipeline raises this flag if one of its bounded waits ran out
 bool tc_failed(stokes_ctx* c) {
   if (!c->of.tc) return false;
@@ -1103,6 +1348,14 @@ int solve_impl(stokes_ctx* c, const double* rhs, double tol, double* x, int* ite
   return rc;
 }
 
+// velocity-only entry points act on one item of a context with nrhs > 1
+struct OneItem {
+  Ops<double>& o;
+  int nb;
+  explicit OneItem(Ops<double>& ops) : o(ops), nb(ops.nb) { o.nb = 1; }
+  ~OneItem() { o.nb = nb; }
+};
+
 }  // namespace
 
 // ============================================================================================
@@ -1121,6 +1374,7 @@ void stokes_default_opts(stokes_opts* o) {
   o->maxit = 2000;
   o->restart = 60;
   o->stream = nullptr;
+  o->nrhs = 1;
 }
 
 int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stokes_opts* opts) {
@@ -1142,6 +1396,12 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
   if (o.solver == STOKES_SOLVER_MINRES && o.precision != STOKES_PREC_FP64)
     return fail(nullptr, STOKES_ERR_ARG,
                 "MINRES needs a fixed SPD preconditioner: use FP64 or the FGMRES solver");
+  if (o.nrhs < 1) o.nrhs = 1;
+  if (o.nrhs > 1024) return fail(nullptr, STOKES_ERR_ARG, "nrhs out of range");
+  if (o.nrhs > 1 && (o.solver != STOKES_SOLVER_FGMRES ||
+                     (o.precision != STOKES_PREC_TF32 && o.precision != STOKES_PREC_BF16)))
+    return fail(nullptr, STOKES_ERR_ARG,
+                "nrhs > 1 needs the tensor-core preconditioner (TF32 or BF16) and FGMRES");
   stokes_ctx* c = new (std::nothrow) stokes_ctx();
   if (!c) return fail(nullptr, STOKES_ERR_SETUP, "out of host memory");
   try {
@@ -1156,6 +1416,7 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
     c->nvel = 3 * c->nvc;
     c->npres = (int64_t)c->b * c->b * c->b;
     c->ntot = c->nvel + c->npres;
+    c->nb = o.nrhs;
     if (o.stream) {
       c->stream = (cudaStream_t)o.stream;
     } else {
@@ -1229,15 +1490,18 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
       alloc_workspace<double>(c, c->odq);
       odq = &c->odq;
     }
-    init_hp<double>(c, c->hd, c->od, odq);
+    if (!reduced(c)) init_hp<double>(c, c->hd, c->od, odq);   // the FP64 preconditioner
     if (reduced(c)) {
       init_ops<float>(c, c->of, bM, bK, bMc, bTc, UN.v, lN, UT.v, lT);
       if (o.precision == STOKES_PREC_TF32 || o.precision == STOKES_PREC_BF16)
         init_tc(c, UN, lN, UT, lT, o.precision == STOKES_PREC_BF16 ? kMmaBF16 : kMmaTF32);
       init_hp<float>(c, c->hf, c->of, nullptr);
-      c->xf = c->arena.alloc<float>(c->ntot);
-      c->yf = c->arena.alloc<float>(c->ntot);
+      c->xf = c->arena.alloc<float>((size_t)c->nb * c->ntot);
+      c->yf = c->arena.alloc<float>((size_t)c->nb * c->ntot);
     }
+    if (c->nb > 1 && !c->of.tc)
+      throw SetupError{"nrhs > 1: the tensor-core fast diagonalisation is not available for this "
+                       "mesh"};
     // constant-pressure coefficients z = c (x) c (x) c
     std::vector<double> z((size_t)c->npres), one((size_t)c->npres, 1.0);
     const int b = c->b;
@@ -1248,14 +1512,15 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
     c->zconst = upload<double>(c->arena, z, c->stream);
     c->ones = upload<double>(c->arena, one, c->stream);
     c->partials = c->arena.alloc<double>((size_t)std::max(kDotBlocks, kMultiDotBlocks) * (o.restart + 2));
-    c->dsc = c->arena.alloc<double>(16 + 2 * (o.restart + 2));
+    c->dsc = c->arena.alloc<double>((size_t)c->nb * (16 + 2 * (o.restart + 2)));
     c->st = c->arena.alloc<MinresState>(1);
     ck(cudaMallocHost(&c->st_host, sizeof(MinresState)), "pinned");
     ck(cudaMallocHost(&c->pinned, 64 * sizeof(double)), "pinned");
-    for (int i = 0; i < 8; ++i) c->kv[i] = c->arena.alloc<double>(c->ntot);
+    ck(cudaMallocHost(&c->pinned_multi, 2 * (size_t)c->nb * sizeof(double)), "pinned");
+    for (int i = 0; i < 8; ++i) c->kv[i] = c->arena.alloc<double>((size_t)c->nb * c->ntot);
     if (o.solver == STOKES_SOLVER_FGMRES) {
-      c->V = c->arena.alloc<double>((size_t)(o.restart + 1) * c->ntot);
-      c->Z = c->arena.alloc<double>((size_t)o.restart * c->ntot);
+      c->V = c->arena.alloc<double>((size_t)(o.restart + 1) * c->nb * c->ntot);
+      c->Z = c->arena.alloc<double>((size_t)o.restart * c->nb * c->ntot);
     }
     c->xi = c->arena.alloc<double>(c->ntot);
     c->ratio_dev = c->arena.alloc<double>(o.maxit);
@@ -1298,6 +1563,7 @@ int stokes_set_preconditioner(stokes_t c, int order, int steps) {
 int stokes_apply_A(stokes_t c, const double* x, double* y) {
   if (!c || !x || !y) return c ? fail(c, STOKES_ERR_ARG, "null vector") : STOKES_ERR_ARG;
   try {
+    OneItem one(c->od);
     c->od.apply_A(x, y);
     check_launch("apply_A");
   } catch (const CudaError& e) {
@@ -1444,6 +1710,7 @@ int stokes_rhs_lid_profile(stokes_t c, int ncoef, const double* theta, int accum
 int stokes_apply_mass(stokes_t c, const double* x, double* y) {
   if (!c || !x || !y) return c ? fail(c, STOKES_ERR_ARG, "null vector") : STOKES_ERR_ARG;
   try {
+    OneItem one(c->od);
     c->od.mass_V(x, y);
     check_launch("apply_mass");
   } catch (const CudaError& e) {
@@ -1470,7 +1737,32 @@ int stokes_solve(stokes_t c, const double* rhs, double tol, double* x, int* iter
   if (!(tol > 0.0) || !(tol < 1.0)) return fail(c, STOKES_ERR_ARG, "tol must be in (0, 1)");
   if (rhs == x) return fail(c, STOKES_ERR_ARG, "rhs and x must not alias");
   try {
+    if (c->nb > 1) {   // all items; the largest iteration count and residual
+      std::vector<int> its(c->nb);
+      std::vector<double> rr(c->nb);
+      const int rc = solve_multi_impl(c, rhs, tol, x, its.data(), rr.data(), nullptr);
+      if (iterations) *iterations = *std::max_element(its.begin(), its.end());
+      if (final_rel_res) *final_rel_res = *std::max_element(rr.begin(), rr.end());
+      return rc;
+    }
     return solve_impl(c, rhs, tol, x, iterations, final_rel_res);
+  } catch (const CudaError& e) {
+    return cuda_fail(c, e);
+  }
+}
+
+int stokes_solve_multi(stokes_t c, const double* rhs, double tol, double* x, int* iterations,
+                       double* final_rel_res, int* status) {
+  if (!c || !rhs || !x) return c ? fail(c, STOKES_ERR_ARG, "null vector") : STOKES_ERR_ARG;
+  if (!(tol > 0.0) || !(tol < 1.0)) return fail(c, STOKES_ERR_ARG, "tol must be in (0, 1)");
+  if (rhs == x) return fail(c, STOKES_ERR_ARG, "rhs and x must not alias");
+  try {
+    if (c->nb == 1) {
+      const int rc = solve_impl(c, rhs, tol, x, iterations, final_rel_res);
+      if (status) status[0] = rc;
+      return rc;
+    }
+    return solve_multi_impl(c, rhs, tol, x, iterations, final_rel_res, status);
   } catch (const CudaError& e) {
     return cuda_fail(c, e);
   }
@@ -1481,6 +1773,7 @@ int stokes_solve_host(stokes_t c, const double* rhs_host, double tol, double* x_
   if (!c || !rhs_host || !x_host)
     return c ? fail(c, STOKES_ERR_ARG, "null vector") : STOKES_ERR_ARG;
   if (!(tol > 0.0) || !(tol < 1.0)) return fail(c, STOKES_ERR_ARG, "tol must be in (0, 1)");
+  if (c->nb > 1) return fail(c, STOKES_ERR_ARG, "stokes_solve_host takes contexts with nrhs = 1");
   try {
     const size_t bytes = c->ntot * sizeof(double);
     ck(cudaMemcpyAsync(c->io_rhs, rhs_host, bytes, cudaMemcpyHostToDevice, c->stream), "h2d");
@@ -1561,6 +1854,7 @@ void stokes_destroy(stokes_t c) {
   if (c->prof) profiler_destroy(c->prof);
   if (c->st_host) cudaFreeHost(c->st_host);
   if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->pinned_multi) cudaFreeHost(c->pinned_multi);
   if (c->stream_q) cudaStreamSynchronize(c->stream_q);
   cudaStream_t s = c->own_stream ? c->stream : nullptr;
   cudaStream_t sq = c->stream_q;
