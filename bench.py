@@ -198,6 +198,23 @@ def oracle_sample(n, p, q, s, repeats):
     return time.perf_counter() - t0, its
 
 
+def oracle_sample_one_thread(n, p, q, s, repeats):
+    """oracle_sample in a child process whose BLAS and OpenMP pools have one thread (the
+    variables are read when NumPy loads). Returns (seconds, iterations), or None on failure."""
+    code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"dt, its = bench.oracle_sample({n}, {p}, {q}, {s}, {repeats}); print(dt, its)")
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True,
+                             text=True, timeout=600)
+        dt, its = out.stdout.strip().split()[-2:]
+        return float(dt), int(its)
+    except Exception:
+        return None
+
+
 def mixed_vs_fp64(Stokes, peaks, n=128, p=3, q=2, s=2):
     """128^3 cavity, order 2, 2 steps: plain FP64 MINRES vs the mixed form (TF32 / BF16
     tensor-core fast diagonalisation and FP32 inner steps inside FP64 flexible GMRES), each to the
@@ -533,6 +550,11 @@ def main():
         cpu = {"value": reps / dt, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
                "sample": f"{reps} oracle FP64 MINRES solve(s) of the {n}^3 p={p} cavity, order "
                          f"{q}, {s} step(s), {its} iterations, matrix-free NumPy"}
+        reps1 = max(1, min(20, int(6.0 * reps / dt)))
+        one = oracle_sample_one_thread(n, p, q, s, reps1)
+        cpu["one_thread"] = ({"value": reps1 / one[0], "unit": "solves/s", "cores": 1,
+                              "sample": f"{reps1} solve(s) as above, BLAS/OpenMP with one thread"}
+                             if one else None)
 
     if rank == 0:
         line = {
@@ -544,7 +566,8 @@ def main():
             "config": {"workload": wl["desc"], "n_elems": n, "degree_p": p,
                        "unknowns": G.size, "precision": prec, "solves_per_step": len(sweep),
                        "tol": 1e-8, "l2": "flushed by a 256 MiB write before every step",
-                       "parallelism": f"replicas x{ws}"},
+                       "parallelism": f"replicas x{ws}",
+                       "fp64_launch_shapes": dict(zip(("mode_block", "band_block"), G.tuning()))},
             "per_preconditioner": per,
             "roofline": roof,
             "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),

@@ -74,6 +74,9 @@ typedef struct stokes_opts {
                          calls processes all items in one launch (the mode products of the fast
                          diagonalisation become GEMMs with nrhs times the rows). Needs
                          precision TF32 or BF16 and solver FGMRES. */
+  int autotune;       /* nonzero (default): time the candidate launch shapes of the FP64 kernels
+                         at setup and keep the fastest (stokes_get_tuning); results do not depend
+                         on the choice. 0: fixed defaults. */
 } stokes_opts;
 
 typedef struct stokes_ctx* stokes_t;
@@ -203,6 +206,14 @@ int stokes_profile_end(stokes_t ctx, stokes_kernel_stat* out, int capacity);
 /* Number of kernels this library has launched in this process (all contexts and threads). Kernels
  * of a captured CUDA graph are counted each time the graph is replayed, not when it is captured. */
 int64_t stokes_kernel_launches(void);
+
+/* Launch shapes of the FP64 kernels (threads per block): mode_block for the fast-diagonalisation
+ * mode products (256, 512 or 1024), band_block for the banded passes (128, 256 or 512). Chosen
+ * at setup by timing when stokes_opts.autotune is set, otherwise 512 and 256. Every output is
+ * computed by one thread in a fixed order whatever the shape, so results do not depend on it.
+ * stokes_set_tuning rejects other values with STOKES_ERR_ARG. */
+int stokes_get_tuning(stokes_t ctx, int* mode_block, int* band_block);
+int stokes_set_tuning(stokes_t ctx, int mode_block, int band_block);
 
 /* ---- allocation-free variant (no counterpart in the paper) --------------------------------
  * For callers that cannot allocate device memory (their allocator is owned by a framework or

@@ -30,7 +30,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("c_pen", ctypes.c_double), ("schur", ctypes.c_int), ("precision", ctypes.c_int),
                 ("solver", ctypes.c_int), ("max_order", ctypes.c_int), ("max_steps", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("restart", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("nrhs", ctypes.c_int)]
+                ("nrhs", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -81,6 +81,8 @@ def load_library(path=None):
         "stokes_profile_begin": (ctypes.c_int, [vp]),
         "stokes_profile_end": (ctypes.c_int, [vp, ctypes.POINTER(KernelStat), ctypes.c_int]),
         "stokes_kernel_launches": (ctypes.c_int64, []),
+        "stokes_get_tuning": (ctypes.c_int, [vp, ip, ip]),
+        "stokes_set_tuning": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
         "stokes_fd_apply_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
                                                    vp, vp, vp, vp, ctypes.c_double, vp, vp, vp]),
         "stokes_destroy": (None, [vp]),
@@ -153,7 +155,7 @@ class Stokes:
 
     def __init__(self, n, p, nu=1.0, c_pen=14.0, schur="inner", precision="fp64",
                  solver=None, max_order=3, max_steps=4, maxit=2000, restart=60, device=None,
-                 nrhs=1):
+                 nrhs=1, autotune=True):
         """nrhs > 1: the context holds nrhs right-hand sides; apply_K, apply_P,
         apply_hyperpower, solve and solve_multi then take nrhs stacked vectors of `size` entries
         each (`batch_size` in all), processed by the same launches (needs precision "tf32" or
@@ -172,6 +174,7 @@ class Stokes:
         o.solver = SOLVER[solver]
         o.max_order, o.max_steps, o.maxit, o.restart = max_order, max_steps, maxit, restart
         o.nrhs = nrhs
+        o.autotune = 1 if autotune else 0
         with torch.cuda.device(self.device):
             # the library runs on its own stream, ordered against the caller's current stream
             # at every call (inputs ready before, outputs visible after)
@@ -212,6 +215,16 @@ class Stokes:
         return torch.empty(n or self.size, dtype=torch.float64, device=self.device)
 
     # -- C ABI ----------------------------------------------------------------------------------
+    def tuning(self):
+        """(mode_block, band_block): threads per block of the FP64 mode products and banded
+        passes (picked by the setup tuner unless autotune=False)."""
+        mb, bb = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.stokes_get_tuning(self.h, ctypes.byref(mb), ctypes.byref(bb)))
+        return mb.value, bb.value
+
+    def set_tuning(self, mode_block, band_block):
+        self._check(self.lib.stokes_set_tuning(self.h, int(mode_block), int(band_block)))
+
     def set_preconditioner(self, order, steps):
         self._check(self.lib.stokes_set_preconditioner(self.h, order, steps))
 

@@ -81,6 +81,7 @@ struct PassArgs {
   int nterms;
   int nb;
   int64_t bs;
+  int block;   // FP64 line kernel: threads per block (<= 0: 256); chosen by the setup tuner
 };
 template <typename T>
 void band_pass(const PassArgs<T>& a, cudaStream_t s);
@@ -119,6 +120,7 @@ struct ModeArgs {
   T post;   // if lam1 == null: the result is multiplied by post
   const T* invd;   // if set (FP64 path): the result is multiplied by invd[output index] instead
   int eo_he;       // FP64 path: U's columns are [he even; n - he odd] eigenvectors (0: generic)
+  int block;       // FP64 path: target threads per block (<= 0: 512); chosen by the setup tuner
 };
 template <typename T>
 void mode_product(const ModeArgs<T>& a, cudaStream_t s);

@@ -5,6 +5,8 @@
 // output entry is a short dot product of the band row with the input line, read through the
 // read-only cache. A pass may sum two such products and add an extra tensor and a difference
 // term, so that a whole Kronecker sum is evaluated in few passes.
+#include <algorithm>
+
 #include "internal.h"
 #include "profile.h"
 
@@ -110,7 +112,7 @@ __device__ __forceinline__ void band_pass_flat_x1(const PassArgs<T>& a, int64_t 
 }
 
 template <typename T, int W>
-__global__ void __launch_bounds__(256) k_band_pass(const __grid_constant__ PassBatch<T> pb) {
+__global__ void __launch_bounds__(512) k_band_pass(const __grid_constant__ PassBatch<T> pb) {
   pdl_begin();
   int jb = 0;
   while (jb + 1 < pb.njobs && (int)blockIdx.x >= pb.first_block[jb + 1]) ++jb;
@@ -887,13 +889,17 @@ void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s) {
   }
   PassBatch<T> pb{};
   pb.njobs = njobs;
+  const int bt = jobs[0].block > 0 ? std::min(jobs[0].block, 512) : 256;   // threads per block
   int W = jobs[0].D0.width;
   for (int j = 0; j < njobs; ++j)
     if (jobs[j].D0.width != W || (jobs[j].nterms > 1 && jobs[j].D1.width != W)) W = 0;
+  // the instantiated widths; any other width (an even width where a band is clamped by a small
+  // matrix) runs the generic kernel, which has no flat layout
+  if (!(W >= 3 && W <= 13 && W % 2 == 1)) W = 0;
   // x1 passes with the flat (line, row) layout when the band width is a compiled one and the
-  // transposed coefficients fit in shared memory
+  // transposed coefficients fit in shared memory (the block counts below depend on this choice)
   int smem = 0;
-  pb.flat1 = W > 0 && W <= 13;
+  pb.flat1 = W > 0;
   for (int j = 0; j < njobs && pb.flat1; ++j)
     if (jobs[j].axis == 1) {
       const int nt = jobs[j].nterms > 1 ? 2 : 1;
@@ -913,8 +919,8 @@ void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s) {
     const int64_t lines = out.size() / a.D0.rows * nbj;
     const int64_t lines_r = (lines + 31) / 32 * 32;
     const int64_t nseg = (a.D0.rows + seg_len<T>() - 1) / seg_len<T>();
-    if (pb.flat1 && a.axis == 1) blocks += (int)((out.size() * nbj + 255) / 256);
-    else blocks += (int)((lines_r * nseg + 255) / 256);
+    if (pb.flat1 && a.axis == 1) blocks += (int)((out.size() * nbj + bt - 1) / bt);
+    else blocks += (int)((lines_r * nseg + bt - 1) / bt);
     // algorithmic work: one band row per output and term; one read of every input tensor
     const double outs = (double)out.size() * nbj;
     double fl = 2.0 * a.D0.width * outs, by = (double)a.in.size() * nbj + outs;
@@ -936,12 +942,12 @@ void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s) {
                            smem);                                                         \
       attr = smem;                                                                        \
     }                                                                                     \
-    launch_k(k_band_pass<T, w>, blocks, 256, smem, s, pb);                                      \
+    launch_k(k_band_pass<T, w>, blocks, bt, smem, s, pb);                                       \
     break;                                                                                \
   }
     SHP_PASS_W(3) SHP_PASS_W(5) SHP_PASS_W(7) SHP_PASS_W(9) SHP_PASS_W(11) SHP_PASS_W(13)
 #undef SHP_PASS_W
-    default: launch_k(k_band_pass<T, 0>, blocks, 256, 0, s, pb);
+    default: launch_k(k_band_pass<T, 0>, blocks, bt, 0, s, pb);
   }
   launch_end(kClassBand, s, flops, bytes);
 }

@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(128) k_mode_rows(const __grid_constant__ RowBa
 // (K x lb) are loaded once, coalesced, into shared memory; Op(i, j) is read through the
 // read-only cache. Outputs of products along contiguous lines (L = 1) are staged in shared memory
 // for coalesced stores.
-__global__ void __launch_bounds__(512) k_mode_tile(const __grid_constant__ RowBatch rb) {
+__global__ void __launch_bounds__(1024) k_mode_tile(const __grid_constant__ RowBatch rb) {
   pdl_begin();
   extern __shared__ double shd[];
   int jb = 0;
@@ -380,6 +380,8 @@ void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStr
   RowBatch rb{};
   rb.njobs = njobs;
   int blocks = 0, smem = 0, threads = 32;
+  // threads per block (target): a block holds target / (threads per line) whole lines
+  const int target = jobs[0].block > 0 ? std::min(jobs[0].block, 1024) : 512;
   double flops = 0, bytes = 0;
   int first_block[kMaxModeJobs + 1];
   for (int j = 0; j < njobs; ++j) {
@@ -399,7 +401,7 @@ void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStr
     J.fwd = m.trans ? 1 : 0;
     // threads per line: one per output, or one per mirrored output pair (even/odd backward)
     const int tpl = (J.eo && !J.fwd) ? J.eo : m.m;
-    J.groups = tpl >= 512 ? 1 : 512 / tpl;        // lines per block
+    J.groups = tpl >= target ? 1 : target / tpl;  // lines per block
     J.threads = 0;
     J.invd = m.invd;
     J.lam1 = m.invd ? nullptr : m.lam1;
@@ -410,7 +412,7 @@ void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStr
     J.post = m.lam1 ? 1.0 : m.post;
     first_block[j] = blocks;
     blocks += (int)((J.L * J.R + J.groups - 1) / J.groups);
-    threads = std::max(threads, std::min(512, ((J.groups * tpl + 31) / 32) * 32));
+    threads = std::max(threads, std::min(target, ((J.groups * tpl + 31) / 32) * 32));
     // inputs [K][P]; outputs staged when the lines are contiguous (L == 1); folded inputs
     // (even/odd forward)
     const int sm = (J.K + (J.L == 1 ? J.m : 0) + ((J.eo && J.fwd) ? J.K : 0)) * (J.groups + 1) *

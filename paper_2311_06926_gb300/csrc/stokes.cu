@@ -190,6 +190,8 @@ struct Ops {
   // batch: nb items per vector, item k of every tensor bs elements after item k - 1's
   int nb = 1;
   int64_t bs = 0;
+  // FP64 launch shapes (threads per block) chosen by the setup tuner
+  int mode_block = 512, band_block = 256;
   // tensor-core fast diagonalisation (reduced precision only): per tensor (3 velocity components,
   // pressure) a padded input copy and six rotating mode products
   bool tc = false;
@@ -227,6 +229,7 @@ struct Ops {
     p.axis = axis;
     p.nb = nb;
     p.bs = bs;
+    p.block = band_block;
     return p;
   }
 
@@ -367,6 +370,7 @@ struct Ops {
     m.lam3 = l3;
     m.scale = scale;
     m.post = post;
+    m.block = mode_block;
     return m;
   }
 
@@ -1356,6 +1360,68 @@ struct OneItem {
   ~OneItem() { o.nb = nb; }
 };
 
+// Setup tuner of the FP64 launch shapes: each candidate threads-per-block of the FP64 mode
+// products (timed on the fast diagonalisation of the velocity block, FP64 preconditioner only)
+// and of the FP64 banded passes (timed on the A apply) runs three times after one warm-up
+// launch, with CUDA events on the context's stream; the fastest is kept. Every output is
+// computed by one thread in a fixed order whatever the block size, so the choice changes timing
+// only, never a result bit.
+constexpr int kModeBlocks[] = {256, 512, 1024};
+constexpr int kBandBlocks[] = {128, 256, 512};
+
+void set_shapes(stokes_ctx* c, int mode_block, int band_block) {
+  c->od.mode_block = c->odq.mode_block = mode_block;
+  c->od.band_block = c->odq.band_block = band_block;
+  // captured graphs hold the previous launch shapes
+  for (auto& kv : c->minres_graphs) cudaGraphExecDestroy(kv.second);
+  c->minres_graphs.clear();
+  c->minres_graph_kernels.clear();
+}
+
+void autotune(stokes_ctx* c) {
+  cudaStream_t s = c->stream;
+  double* x = c->kv[0];
+  double* y = c->kv[1];
+  fill_zero(x, (size_t)c->nb * c->ntot * sizeof(double), s);
+  cudaEvent_t e0, e1;
+  ck(cudaEventCreate(&e0), "event");
+  ck(cudaEventCreate(&e1), "event");
+  auto time3 = [&](auto&& fn) {
+    fn();
+    ck(cudaEventRecord(e0, s), "event");
+    for (int r = 0; r < 3; ++r) fn();
+    ck(cudaEventRecord(e1, s), "event");
+    ck(cudaEventSynchronize(e1), "event");
+    float ms = 0.f;
+    ck(cudaEventElapsedTime(&ms, e0, e1), "event");
+    return ms;
+  };
+  int best_mode = c->od.mode_block, best_band = c->od.band_block;
+  if (!reduced(c)) {
+    float best = 1e30f;
+    for (int mb : kModeBlocks) {
+      c->od.mode_block = mb;
+      const float t = time3([&] { c->od.fd_V(x, y); });
+      if (t < best) { best = t; best_mode = mb; }
+    }
+  }
+  c->od.mode_block = best_mode;
+  {
+    OneItem one(c->od);
+    float best = 1e30f;
+    for (int bb : kBandBlocks) {
+      c->od.band_block = bb;
+      const float t = time3([&] { c->od.apply_A(x, y); });
+      if (t < best) { best = t; best_band = bb; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  check_launch("autotune");
+  set_shapes(c, best_mode, best_band);
+}
+
+
 }  // namespace
 
 // ============================================================================================
@@ -1375,6 +1441,7 @@ void stokes_default_opts(stokes_opts* o) {
   o->restart = 60;
   o->stream = nullptr;
   o->nrhs = 1;
+  o->autotune = 1;
 }
 
 int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stokes_opts* opts) {
@@ -1525,6 +1592,7 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
     c->xi = c->arena.alloc<double>(c->ntot);
     c->ratio_dev = c->arena.alloc<double>(o.maxit);
     if (const char* e = std::getenv("STOKES_NO_GRAPHS")) c->use_graphs = e[0] == '0';
+    if (o.autotune) autotune(c);
     c->io_rhs = c->arena.alloc<double>(c->ntot);
     c->io_x = c->arena.alloc<double>(c->ntot);
     ck(cudaStreamSynchronize(c->stream), "setup");
@@ -1847,6 +1915,23 @@ int stokes_profile_end(stokes_t c, stokes_kernel_stat* out, int capacity) {
 }
 
 int64_t stokes_kernel_launches(void) { return launch_count(); }
+
+int stokes_get_tuning(stokes_t c, int* mode_block, int* band_block) {
+  if (!c) return STOKES_ERR_ARG;
+  if (mode_block) *mode_block = c->od.mode_block;
+  if (band_block) *band_block = c->od.band_block;
+  return STOKES_OK;
+}
+
+int stokes_set_tuning(stokes_t c, int mode_block, int band_block) {
+  if (!c) return STOKES_ERR_ARG;
+  bool ok_m = false, ok_b = false;
+  for (int v : kModeBlocks) ok_m = ok_m || v == mode_block;
+  for (int v : kBandBlocks) ok_b = ok_b || v == band_block;
+  if (!ok_m || !ok_b) return fail(c, STOKES_ERR_ARG, "launch shape not among the candidates");
+  set_shapes(c, mode_block, band_block);
+  return STOKES_OK;
+}
 
 void stokes_destroy(stokes_t c) {
   if (!c) return;

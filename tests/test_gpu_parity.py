@@ -239,3 +239,32 @@ def test_concurrent_branches_bit_identical(n, p, q, s):
     G.close()
     assert it1 == it2 and rr1 == rr2
     assert torch.equal(x1, x2)
+
+
+@pytest.mark.parametrize("n,p", [(7, 2), (20, 3), (5, 4), (7, 4)])
+def test_launch_shapes_do_not_change_results(n, p):
+    """Every candidate launch shape of the FP64 kernels gives the same bits (each output is one
+    thread's fixed-order sum), so the setup tuner's choice affects timing only. (5, 4) and (7, 4):
+    K and M have an even band width there (clamped by the matrix size), which takes the
+    generic-width kernel."""
+    S, base, Kop, F = oracle(n, p)
+    G = _ctx(n, p, 1.0, autotune=False)
+    assert G.tuning() == (512, 256)
+    x = dev(synthetic.random_vector(S.size, 700 + n))
+    ref_K, ref_H = G.apply_K(x), G.apply_hyperpower(2, 1, x)
+    G.set_preconditioner(2, 1)
+    ref_x, ref_it, _, _ = G.solve(dev(S.rhs_lid(1.0)), 1e-8)
+    for mb in (256, 512, 1024):
+        for bb in (128, 256, 512):
+            G.set_tuning(mb, bb)
+            assert G.tuning() == (mb, bb)
+            assert torch.equal(G.apply_K(x), ref_K)
+            assert torch.equal(G.apply_hyperpower(2, 1, x), ref_H)
+    xs, it, _, _ = G.solve(dev(S.rhs_lid(1.0)), 1e-8)
+    assert it == ref_it and torch.equal(xs, ref_x)
+    with pytest.raises(Exception):
+        G.set_tuning(300, 256)
+    G.close()
+    Ga = _ctx(n, p, 1.0)
+    assert Ga.tuning()[0] in (256, 512, 1024) and Ga.tuning()[1] in (128, 256, 512)
+    Ga.close()
