@@ -208,7 +208,7 @@ int stokes_profile_end(stokes_t ctx, stokes_kernel_stat* out, int capacity);
 int64_t stokes_kernel_launches(void);
 
 /* Launch shapes of the FP64 kernels (threads per block): mode_block for the fast-diagonalisation
- * mode products (256, 512 or 1024), band_block for the banded passes (128, 256 or 512). Chosen
+ * mode products (128, 256 or 512), band_block for the banded passes (128, 256 or 512). Chosen
  * at setup by timing when stokes_opts.autotune is set, otherwise 512 and 256. Every output is
  * computed by one thread in a fixed order whatever the shape, so results do not depend on it.
  * stokes_set_tuning rejects other values with STOKES_ERR_ARG. */

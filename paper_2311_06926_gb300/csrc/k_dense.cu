@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(128) k_mode_rows(const __grid_constant__ RowBa
 // (K x lb) are loaded once, coalesced, into shared memory; Op(i, j) is read through the
 // read-only cache. Outputs of products along contiguous lines (L = 1) are staged in shared memory
 // for coalesced stores.
-__global__ void __launch_bounds__(1024) k_mode_tile(const __grid_constant__ RowBatch rb) {
+__global__ void __launch_bounds__(512) k_mode_tile(const __grid_constant__ RowBatch rb) {
   pdl_begin();
   extern __shared__ double shd[];
   int jb = 0;
@@ -381,7 +381,7 @@ void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStr
   rb.njobs = njobs;
   int blocks = 0, smem = 0, threads = 32;
   // threads per block (target): a block holds target / (threads per line) whole lines
-  const int target = jobs[0].block > 0 ? std::min(jobs[0].block, 1024) : 512;
+  const int target = jobs[0].block > 0 ? std::min(jobs[0].block, 512) : 512;
   double flops = 0, bytes = 0;
   int first_block[kMaxModeJobs + 1];
   for (int j = 0; j < njobs; ++j) {

@@ -1366,7 +1366,7 @@ struct OneItem {
 // launch, with CUDA events on the context's stream; the fastest is kept. Every output is
 // computed by one thread in a fixed order whatever the block size, so the choice changes timing
 // only, never a result bit.
-constexpr int kModeBlocks[] = {256, 512, 1024};
+constexpr int kModeBlocks[] = {128, 256, 512};
 constexpr int kBandBlocks[] = {128, 256, 512};
 
 void set_shapes(stokes_ctx* c, int mode_block, int band_block) {
