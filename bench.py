@@ -40,9 +40,9 @@ TF32_NOMINAL_TFLOPS = 1100.0
 # that source is unchanged, and null otherwise.
 TRAFFIC = {
     ("mode_product", "fp64", "cavity32"): {
-        "bytes_per_launch": 1035797,
+        "bytes_per_launch": 1035634,
         "source": "k_dense.cu",
-        "sha256": "6e5b809f1cce78a882a8539f1af7b9e530f6c7212122d0cb89380040dc4c25cc",
+        "sha256": "d05c14c82b258149fb7e1b53760b0abff0cde9339623d5309a23fb8b03d0c98f",
         "profile": "profiles/k_mode_tile_fp64_cavity32.md"},
 }
 
@@ -306,6 +306,10 @@ def run_batch(args, wl):
         G.rhs_body(coef, waves, accumulate=True, out=out)
 
     def timed(ctxs, rhs, xs):
+        # each context solves once alone first: its solver graphs are captured there, one thread
+        # at a time, and the concurrent batch calls replay them
+        for G, f, x in zip(ctxs, rhs, xs):
+            G.solve(f, 1e-8, out=x)
         for _ in range(args.warmup):
             solve_batch(ctxs, rhs, 1e-8, xs)
         torch.cuda.synchronize()

@@ -112,16 +112,33 @@ def schur_level(m, schur):
     raise ValueError(schur)
 
 
+def _exact_A_solve(base):
+    """v -> A^-1 v by a sparse LU factorisation of the assembled velocity block (kept on the base
+    preconditioner; tiny meshes only): the exact inverse of the comparison sequence (Eq. 4.7)."""
+    f = getattr(base, "_A_lu", None)
+    if f is None:
+        import scipy.sparse.linalg as spla
+        f = spla.splu(base.S.A.tocsc())
+        base._A_lu = f
+    return f.solve
+
+
 def hyperpower_V(base, xu, q, s):
     return hyperpower(xu, base.pv0_inv, base.A, q, s)
 
 
 def hyperpower_Q(base, xp, q, s, schur="inner"):
-    """X_{Q,s} x with A~_Q at level m equal to B^T P_{V,l(m)}^-1 B."""
+    """X_{Q,s} x with A~_Q at level m equal to B^T P_{V,l(m)}^-1 B (schur "inner": Eq. 4.5,
+    "none": Eq. 4.6), or to the Schur complement B^T A^-1 B itself (schur "exact": Eq. 4.7, the
+    comparison sequence, assembled systems only)."""
     if s == 0:
         return base.pq0_inv(xp)
-    l = schur_level(s, schur)
-    Aq = lambda v: base.Bt(hyperpower_V(base, base.B(v), q, l))
+    if schur == "exact":
+        solve = _exact_A_solve(base)
+        Aq = lambda v: base.Bt(solve(base.B(v)))
+    else:
+        l = schur_level(s, schur)
+        Aq = lambda v: base.Bt(hyperpower_V(base, base.B(v), q, l))
     prev = lambda v: hyperpower_Q(base, v, q, s - 1, schur)
     r = xp
     acc = xp.copy()

@@ -49,8 +49,12 @@ void profiler_activate(Profiler* p) {
   }
 }
 
+thread_local bool t_capturing = false;
+
+void set_capturing(bool on) { t_capturing = on; }
+
 void launch_begin(int cls, cudaStream_t s) {
-  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (!t_capturing) g_launches.fetch_add(1, std::memory_order_relaxed);
   Profiler* p = t_active;
   if (!p) return;
   p->pending_start = p->take();

@@ -23,6 +23,8 @@ void launch_end(int cls, cudaStream_t s, double flops, double bytes);
 int64_t launch_count();
 // Adjusts the counter by n (kernels of a captured graph: counted on replay, not on capture).
 void launch_add(int64_t n);
+// While set (per host thread), launches are being captured into a graph and are not counted.
+void set_capturing(bool on);
 
 struct Profiler;
 Profiler* profiler_create();

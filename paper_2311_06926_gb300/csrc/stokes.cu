@@ -23,6 +23,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <thread>
@@ -607,9 +608,17 @@ struct stokes_ctx {
   double* ratio_dev = nullptr;    // per-iteration convergence ratios
   std::map<int, cudaGraphExec_t> minres_graphs;
   std::map<int, int64_t> minres_graph_kernels;   // kernels per replay of each graph
+  // FGMRES: one Arnoldi step's P and K applies captured per (order, steps) on fixed buffers
+  std::map<int, cudaGraphExec_t> pk_graphs;
+  std::map<int, int64_t> pk_graph_kernels;
+  double *pk_in = nullptr, *pk_z = nullptr;   // nb * ntot each
+  // set for the duration of stokes_solve_batch: replay existing graphs, capture no new one
+  // (stream capture from the batch's concurrent host threads crashed the host process)
+  bool no_capture = false;
   std::vector<RmpPlan> tc_plans;
   ~stokes_ctx() {
     for (auto& kv : minres_graphs) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : pk_graphs) cudaGraphExecDestroy(kv.second);
     if (hd.ev_fork) cudaEventDestroy(hd.ev_fork);
     if (hd.ev_join) cudaEventDestroy(hd.ev_join);
   }
@@ -914,6 +923,43 @@ void minres_pair(stokes_ctx* c) {
 
 bool profiling_active(stokes_ctx* c) { return c->prof_on; }
 
+// Captures what `record` enqueues on stream s into an instantiated graph and returns it with
+// the number of kernels it replays. One capture at a time in the process (stream capture from
+// several host threads at once crashed the host process, see stokes_solve_batch); the kernels
+// enqueued while capturing are not counted as launches (they run when the graph is replayed).
+std::mutex g_capture_mutex;
+
+template <typename F>
+cudaGraphExec_t capture_graph(cudaStream_t s, F&& record, int64_t* kernels) {
+  std::lock_guard<std::mutex> lock(g_capture_mutex);
+  cudaGraph_t g = nullptr;
+  set_capturing(true);
+  try {
+    ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
+    record();
+    ck(cudaStreamEndCapture(s, &g), "capture");
+  } catch (...) {
+    set_capturing(false);
+    throw;
+  }
+  set_capturing(false);
+  size_t nn = 0;
+  ck(cudaGraphGetNodes(g, nullptr, &nn), "graph nodes");
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (nn) ck(cudaGraphGetNodes(g, nodes.data(), &nn), "graph nodes");
+  int64_t k = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    ck(cudaGraphNodeGetType(nd, &t), "graph node");
+    if (t == cudaGraphNodeTypeKernel) ++k;
+  }
+  cudaGraphExec_t exec = nullptr;
+  ck(cudaGraphInstantiate(&exec, g, 0), "instantiate");
+  cudaGraphDestroy(g);
+  *kernels = k;
+  return exec;
+}
+
 int run_minres(stokes_ctx* c, const double* f, double tol, double* x, int* iters) {
   const int64_t n = c->ntot;
   cudaStream_t s = c->stream;
@@ -943,21 +989,15 @@ int run_minres(stokes_ctx* c, const double* f, double tol, double* x, int* iters
     // two iterations per replay of a captured graph (or per direct launch sequence when a
     // profiler is recording events or graphs are disabled)
     cudaGraphExec_t exec = nullptr;
-    const bool use_graph = c->use_graphs && !profiling_active(c);
+    const int gkey = c->order * 16 + c->steps;
+    const bool use_graph = c->use_graphs && !profiling_active(c) &&
+                           !(c->no_capture && c->minres_graphs.find(gkey) == c->minres_graphs.end());
     if (use_graph) {
-      const int key = c->order * 16 + c->steps;
+      const int key = gkey;
       auto it = c->minres_graphs.find(key);
       if (it == c->minres_graphs.end()) {
-        cudaGraph_t g = nullptr;
-        const int64_t before = launch_count();
-        ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
-        minres_pair(c);
-        ck(cudaStreamEndCapture(s, &g), "capture");
-        // captured kernels run only when the graph is replayed: count them there
-        const int64_t k = launch_count() - before;
-        launch_add(-k);
-        ck(cudaGraphInstantiate(&exec, g, 0), "instantiate");
-        cudaGraphDestroy(g);
+        int64_t k = 0;
+        exec = capture_graph(s, [&] { minres_pair(c); }, &k);
         c->minres_graphs[key] = exec;
         c->minres_graph_kernels[key] = k;
       } else {
@@ -989,6 +1029,40 @@ int run_minres(stokes_ctx* c, const double* f, double tol, double* x, int* iters
   copy_async(x, c->xi, n * sizeof(double), s);
   ck(cudaStreamSynchronize(s), "sync");
   return rc;
+}
+
+// One Arnoldi step's products, for every item: z = P_s^-1 v, then w = K z. With graphs enabled
+// (and no profiler recording) the two applies are captured once per (order, steps) on fixed
+// buffers (v copied in, z copied out, w always the context's first Krylov vector) and replayed,
+// so the host issues three operations instead of every kernel of the recursion. Same kernels in
+// the same order: the result does not depend on the path.
+void pk_apply(stokes_ctx* c, const double* v, double* z, double* w) {
+  cudaStream_t s = c->stream;
+  const size_t bytes = (size_t)c->nb * c->ntot * sizeof(double);
+  const int key = c->order * 16 + c->steps;
+  auto it = c->pk_graphs.find(key);
+  if (!c->use_graphs || profiling_active(c) || !c->pk_in || w != c->kv[0] ||
+      (c->no_capture && it == c->pk_graphs.end())) {
+    apply_prec(c, c->order, c->steps, v, z);
+    c->od.apply_K(z, w);
+    return;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (it == c->pk_graphs.end()) {
+    int64_t k = 0;
+    exec = capture_graph(s, [&] {
+      apply_prec(c, c->order, c->steps, c->pk_in, c->pk_z);
+      c->od.apply_K(c->pk_z, w);
+    }, &k);
+    c->pk_graphs[key] = exec;
+    c->pk_graph_kernels[key] = k;
+  } else {
+    exec = it->second;
+  }
+  copy_async(c->pk_in, v, bytes, s);
+  ck(cudaGraphLaunch(exec, s), "graph launch");
+  launch_add(c->pk_graph_kernels[key]);
+  copy_async(z, c->pk_z, bytes, s);
 }
 
 // Right-preconditioned flexible GMRES (Saad 1993) with classical Gram-Schmidt applied twice
@@ -1033,8 +1107,7 @@ int run_fgmres(stokes_ctx* c, const double* f, double tol, double* x, int* iters
     for (int j = 0; j < m; ++j) {
       double* Vj = c->V + (int64_t)j * n;
       double* Zj = c->Z + (int64_t)j * n;
-      apply_prec(c, c->order, c->steps, Vj, Zj);
-      c->od.apply_K(Zj, w);
+      pk_apply(c, Vj, Zj, w);
       // CGS2: h = V^T w; w -= V h; h2 = V^T w; w -= V h2; h += h2
       multi_dot(c->V, n, j + 1, w, n, c->partials, hdev, s);
       multi_axpy(c->V, n, j + 1, hdev, -1.0, w, n, s);
@@ -1186,8 +1259,7 @@ void run_fgmres_multi(stokes_ctx* c, const double* f, double tol, double* x, int
     for (int j = 0; j < m && any(active); ++j) {
       double* Vj = c->V + (int64_t)j * N;
       double* Zj = c->Z + (int64_t)j * N;
-      apply_prec(c, c->order, c->steps, Vj, Zj);
-      c->od.apply_K(Zj, w);
+      pk_apply(c, Vj, Zj, w);
       for (int k = 0; k < nb; ++k) {
         if (!active[k]) continue;
         double* hdev = dsc(k) + 8;
@@ -1376,6 +1448,9 @@ void set_shapes(stokes_ctx* c, int mode_block, int band_block) {
   for (auto& kv : c->minres_graphs) cudaGraphExecDestroy(kv.second);
   c->minres_graphs.clear();
   c->minres_graph_kernels.clear();
+  for (auto& kv : c->pk_graphs) cudaGraphExecDestroy(kv.second);
+  c->pk_graphs.clear();
+  c->pk_graph_kernels.clear();
 }
 
 void autotune(stokes_ctx* c) {
@@ -1588,6 +1663,8 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
     if (o.solver == STOKES_SOLVER_FGMRES) {
       c->V = c->arena.alloc<double>((size_t)(o.restart + 1) * c->nb * c->ntot);
       c->Z = c->arena.alloc<double>((size_t)o.restart * c->nb * c->ntot);
+      c->pk_in = c->arena.alloc<double>((size_t)c->nb * c->ntot);
+      c->pk_z = c->arena.alloc<double>((size_t)c->nb * c->ntot);
     }
     c->xi = c->arena.alloc<double>(c->ntot);
     c->ratio_dev = c->arena.alloc<double>(o.maxit);
@@ -1863,6 +1940,7 @@ int stokes_solve_batch(stokes_t* ctxs, int count, const double* const* rhs, doub
       if (ctxs[j] == ctxs[i]) return fail(ctxs[i], STOKES_ERR_ARG, "contexts must be distinct");
   }
   std::vector<int> st(count, STOKES_OK);
+  for (int i = 0; i < count; ++i) ctxs[i]->no_capture = true;
   std::vector<std::thread> workers;
   workers.reserve(count);
   for (int i = 0; i < count; ++i)
@@ -1871,6 +1949,7 @@ int stokes_solve_batch(stokes_t* ctxs, int count, const double* const* rhs, doub
                            final_rel_res ? final_rel_res + i : nullptr);
     });
   for (auto& w : workers) w.join();
+  for (int i = 0; i < count; ++i) ctxs[i]->no_capture = false;
   int rc = STOKES_OK;
   for (int i = 0; i < count; ++i) {
     if (status) status[i] = st[i];

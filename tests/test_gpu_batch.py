@@ -36,3 +36,21 @@ def test_batch_equals_individual_solves():
         assert np.array_equal(host(x), xr)           # deterministic kernels: identical bits
     for G, _ in probs:
         G.close()
+
+
+def test_first_solves_inside_a_batch_call():
+    """Contexts that have never solved enter stokes_solve_batch with no captured solver graphs:
+    inside the batch call they capture none (their kernels launch directly), and the results
+    still equal the same solves done alone afterwards (which capture and replay graphs)."""
+    from paper_2311_06926_gb300.binding import solve_batch
+    specs = [(5, 2, "fp64"), (6, 2, "tf32"), (4, 3, "bf16"), (7, 2, "fp64")]
+    probs = [_make(n, p, prec, 40 + seed) for seed, (n, p, prec) in enumerate(specs)]
+    xs, its, rrs, st = solve_batch([G for G, _ in probs], [f for _, f in probs], 1e-9)
+    assert all(s == 0 for s in st)
+    for (G, f), x, it in zip(probs, xs, its):
+        x1, it1, _, _ = G.solve(f, 1e-9)
+        x2, it2, _, _ = G.solve(f, 1e-9)
+        assert it == it1 == it2
+        assert np.array_equal(host(x), host(x1)) and np.array_equal(host(x1), host(x2))
+    for G, _ in probs:
+        G.close()

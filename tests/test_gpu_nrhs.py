@@ -69,3 +69,21 @@ def test_batched_context_options():
     with pytest.raises(StokesError):
         G.solve_host(torch.zeros(G.size, dtype=torch.float64), torch.zeros(G.size, dtype=torch.float64))
     G.close()
+
+
+@pytest.mark.parametrize("nrhs,prec", [(1, "tf32"), (2, "bf16"), (1, "fp32")])
+def test_fgmres_graph_replay_bit_identical(nrhs, prec):
+    """FGMRES replays each Arnoldi step's P and K applies from a captured graph; with a profiler
+    recording the same kernels launch one by one. Both paths must give the same bits."""
+    n, p = 8, 3
+    G = _ctx(n, p, precision=prec, nrhs=nrhs, max_order=2, max_steps=1)
+    G.set_preconditioner(2, 1)
+    F = torch.cat([_rhs(G, 30 + k) for k in range(nrhs)])
+    Xg, its_g, rr_g, _, _ = G.solve_multi(F, 1e-9)
+    Xg2, its_g2, _, _, _ = G.solve_multi(F, 1e-9)
+    G.profile_begin()
+    Xe, its_e, rr_e, _, _ = G.solve_multi(F, 1e-9)
+    G.profile_end()
+    G.close()
+    assert its_g == its_e == its_g2 and rr_g == rr_e
+    assert torch.equal(Xg, Xe) and torch.equal(Xg, Xg2)

@@ -186,3 +186,40 @@ def test_schur_sequences_condition_numbers():
     assert all(none[k + 1] < none[k] for k in range(3))
     assert abs(none[4] - none[3]) < 0.1 and none[4] > 1.4
     assert inner[4] < none[4]
+
+
+def test_exact_schur_sequence():
+    """Eq. 4.7 (the comparison sequence with the exact Schur complement S = B^T A^-1 B): the
+    residual identity E - S X_{k+1} = (E - S X_k)^q holds with S itself, so the spectrum of X_k S
+    follows the order-q map of Cor. 2.2 from that of P_Q0^-1 S. Against it (Sec. 5.2, Fig. 5,
+    qualitative): from level 2 on the sequence with inner updates (Eq. 4.5) tracks the exact one,
+    while the one without (Eq. 4.6) stalls (values at 2^3, degree 3: exact 7.07, 3.90, 2.24, 1.44,
+    1.10; inner 7.07, 3.72, 2.24, 1.44, 1.10; none 7.07, 3.72, 2.32, 1.54, 1.50)."""
+    S = StokesSystem(2, 2)
+    base = BasePreconditioner(S)
+    A, B = S.A.toarray(), S.B.toarray()
+    Sch = B.T @ np.linalg.solve(A, B)
+    E = np.eye(S.n_pres)
+    for q in (2, 3):
+        X = [_dense_op(lambda v, k=k: hyperpower_Q(base, v, q, k, "exact"), S.n_pres)
+             for k in range(4)]
+        for k in range(3):
+            R0, R1 = E - Sch @ X[k], E - Sch @ X[k + 1]
+            assert np.abs(R1 - np.linalg.matrix_power(R0, q)).max() < 1e-9
+        # spectral map: nonzero eigenvalues of X_k S are 1 - (1 - lambda_0)^(q^k)
+        ev0 = np.sort(np.abs(sla.eigvals(X[0] @ Sch).real))[1:]
+        for k in range(1, 4):
+            evk = np.sort(np.abs(sla.eigvals(X[k] @ Sch).real))[1:]
+            pred = np.sort(1.0 - (1.0 - ev0) ** (q ** k))
+            assert np.abs(evk - pred).max() < 1e-8
+
+    def kappa(schur, k):
+        X = _dense_op(lambda v: hyperpower_Q(base, v, 2, k, schur), S.n_pres)
+        ev = np.sort(np.abs(sla.eigvals(X @ Sch).real))[1:]
+        return ev[-1] / ev[0]
+
+    ke = [kappa("exact", k) for k in range(5)]
+    assert all(ke[k + 1] < ke[k] for k in range(4)) and ke[4] < 1.11
+    for k in range(2, 5):
+        assert abs(kappa("inner", k) - ke[k]) < 0.01 * ke[k]
+    assert kappa("none", 4) > 1.3 * ke[4]
