@@ -150,6 +150,11 @@ void axpby(T a, const T* x, T b, T* y, int64_t n, cudaStream_t s);
 // n entries with pitch bs
 template <typename T>
 void hp_update(T* r, const T* u, T* acc, int64_t n, cudaStream_t s, int nb = 1, int64_t bs = 0);
+// first Horner step from r = acc = x: r = x - u; acc = x + r (the same arithmetic as copying x
+// into r and acc and then hp_update), on nb rows of n entries with pitch bs
+template <typename T>
+void hp_first(const T* x, const T* u, T* r, T* acc, int64_t n, cudaStream_t s, int nb = 1,
+              int64_t bs = 0);
 void copy_async(void* dst, const void* src, size_t bytes, cudaStream_t s);
 // nb rows of row_bytes with the same pitch in source and destination (one 2D copy)
 void copy_rows(void* dst, const void* src, size_t row_bytes, int nb, size_t pitch_bytes,

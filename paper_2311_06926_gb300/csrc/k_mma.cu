@@ -374,17 +374,20 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 template <typename TO>
+// One warp per row (rows of all items in order), lanes along the row: coalesced loads and stores,
+// one division per row instead of one per element.
 __global__ void k_pad_rows(const float* __restrict__ x, int e1, int64_t R, int ld,
                            TO* __restrict__ y, int nb, int64_t xbs) {
   pdl_begin();
-  const int64_t per = (int64_t)e1 * R;
-  const int64_t total = per * nb;
-  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total;
-       o += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = o / e1;                 // row over all items
-    const int j = (int)(o - r * e1);
+  const int64_t rows = R * nb;
+  const int lane = threadIdx.x % 32;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+  const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
+  for (int64_t r = w0; r < rows; r += nw) {
     const int64_t k = nb > 1 ? r / R : 0;     // item
-    store_val<TO>(y + r * ld + j, x[o + k * (xbs - per)]);
+    const float* src = x + k * xbs + (r - k * R) * e1;
+    TO* dst = y + r * ld;
+    for (int j = lane; j < e1; j += 32) store_val<TO>(dst + j, src[j]);
   }
 }
 
@@ -497,7 +500,7 @@ void pad_rows(const float* x, int e1, int64_t R, int ld, void* y, bool to_bf16, 
               int nb, int64_t xbs) {
   if (nb < 1) nb = 1;
   const int64_t total = (int64_t)e1 * R * nb;
-  int64_t blocks = (total + 255) / 256;
+  int64_t blocks = (R * nb + 7) / 8;   // 8 warps (rows) per block
   if (blocks > 152 * 32) blocks = 152 * 32;
   launch_begin(kClassVector, s);
   if (to_bf16)

@@ -80,6 +80,22 @@ __global__ void k_hp_update(T* __restrict__ r, const T* __restrict__ u, T* __res
   }
 }
 
+template <typename T>
+__global__ void k_hp_first(const T* __restrict__ x, const T* __restrict__ u, T* __restrict__ r,
+                           T* __restrict__ acc, int64_t n, int nb, int64_t bs) {
+  pdl_begin();
+  const int64_t total = n * nb;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = nb > 1 ? t / n : 0;
+    const int64_t i = t + k * (bs - n);
+    const T xi = x[i];
+    const T ri = xi - u[i];
+    r[i] = ri;
+    acc[i] = xi + ri;
+  }
+}
+
 __global__ void k_to_float(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
   pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -357,6 +373,14 @@ void hp_update(T* r, const T* u, T* acc, int64_t n, cudaStream_t s, int nb, int6
   launch_end(kClassVector, s, 0.0, 0.0);
 }
 
+template <typename T>
+void hp_first(const T* x, const T* u, T* r, T* acc, int64_t n, cudaStream_t s, int nb, int64_t bs) {
+  if (nb < 1) nb = 1;
+  launch_begin(kClassVector, s);
+  launch_k(k_hp_first<T>, grid_for(n * nb), kThreads, 0, s, x, u, r, acc, n, nb, nb > 1 ? bs : n);
+  launch_end(kClassVector, s, 0.0, 0.0);
+}
+
 void copy_async(void* dst, const void* src, size_t bytes, cudaStream_t s) {
   cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
 }
@@ -454,5 +478,9 @@ template void axpby<double>(double, const double*, double, double*, int64_t, cud
 template void axpby<float>(float, const float*, float, float*, int64_t, cudaStream_t);
 template void hp_update<double>(double*, const double*, double*, int64_t, cudaStream_t, int, int64_t);
 template void hp_update<float>(float*, const float*, float*, int64_t, cudaStream_t, int, int64_t);
+template void hp_first<double>(const double*, const double*, double*, double*, int64_t,
+                               cudaStream_t, int, int64_t);
+template void hp_first<float>(const float*, const float*, float*, float*, int64_t, cudaStream_t,
+                              int, int64_t);
 
 }  // namespace shp

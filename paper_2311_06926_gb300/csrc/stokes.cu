@@ -514,13 +514,13 @@ struct HyperPower {
       return;
     }
     T *r = L.r[s], *acc = L.acc[s], *t = L.t[s], *u = L.u[s];
-    copy_rows(r, x, n * sizeof(T), o.nb, o.bs * sizeof(T), o.s);
-    copy_rows(acc, x, n * sizeof(T), o.nb, o.bs * sizeof(T), o.s);
+    // Horner steps from r = acc = x; the first reads x directly
     for (int j = 1; j < order; ++j) {
-      V(o, L, s - 1, r, t);
+      V(o, L, s - 1, j == 1 ? x : r, t);
       o.apply_A(t, u);
       ++counts[2];
-      hp_update<T>(r, u, acc, n, o.s, o.nb, o.bs);
+      if (j == 1) hp_first<T>(x, u, r, acc, n, o.s, o.nb, o.bs);
+      else hp_update<T>(r, u, acc, n, o.s, o.nb, o.bs);
     }
     V(o, L, s - 1, acc, y);
   }
@@ -539,15 +539,15 @@ struct HyperPower {
     }
     T *r = qr[m], *acc = qacc[m], *t = qt[m], *u = qu[m];
     const int l = level_of(m);
-    copy_rows(r, x, n * sizeof(T), o.nb, o.bs * sizeof(T), o.s);
-    copy_rows(acc, x, n * sizeof(T), o.nb, o.bs * sizeof(T), o.s);
+    // Horner steps from r = acc = x; the first reads x directly
     for (int j = 1; j < order; ++j) {
-      Q(o, L, m - 1, r, t);
+      Q(o, L, m - 1, j == 1 ? x : r, t);
       o.apply_B(t, bv);          // A~_Q t = B^T P_{V,l}^-1 B t
       V(o, L, l, bv, hv);
       o.apply_Bt(hv, u);
       ++counts[3];
-      hp_update<T>(r, u, acc, n, o.s, o.nb, o.bs);
+      if (j == 1) hp_first<T>(x, u, r, acc, n, o.s, o.nb, o.bs);
+      else hp_update<T>(r, u, acc, n, o.s, o.nb, o.bs);
     }
     Q(o, L, m - 1, acc, y);
   }

@@ -220,6 +220,8 @@ def test_exact_schur_sequence():
 
     ke = [kappa("exact", k) for k in range(5)]
     assert all(ke[k + 1] < ke[k] for k in range(4)) and ke[4] < 1.11
+    # Sec. 5.2: the updated sequence is slightly better conditioned than the exact one
+    assert kappa("inner", 1) < ke[1]
     for k in range(2, 5):
         assert abs(kappa("inner", k) - ke[k]) < 0.01 * ke[k]
     assert kappa("none", 4) > 1.3 * ke[4]
