@@ -82,7 +82,32 @@ struct PassArgs {
   int nb;
   int64_t bs;
   int block;   // FP64 line kernel: threads per block (<= 0: 256); chosen by the setup tuner
+  // Horner epilogue (one hyper-power step fused into the pass that produces u = A~ t): instead
+  // of writing the result v to Y, hmode 1 sets r = hx - v, acc = hx + r (first step, from
+  // r = acc = hx); hmode 2 sets r = r - v, acc = acc + r. hr, hacc, hx have Y's layout.
+  int hmode;
+  T* hr;
+  T* hacc;
+  const T* hx;
 };
+
+// The Horner epilogue of PassArgs as one store: the same operations as writing Y and then
+// hp_first / hp_update (vector kernels), so the two routes give the same bits.
+template <typename T>
+__device__ __forceinline__ void pass_store(const PassArgs<T>& a, int64_t o, T v) {
+  if (a.hmode == 0) {
+    a.Y[o] = v;
+  } else if (a.hmode == 1) {
+    const T xi = a.hx[o];
+    const T ri = xi - v;
+    a.hr[o] = ri;
+    a.hacc[o] = xi + ri;
+  } else {
+    const T ri = a.hr[o] - v;
+    a.hr[o] = ri;
+    a.hacc[o] += ri;
+  }
+}
 template <typename T>
 void band_pass(const PassArgs<T>& a, cudaStream_t s);
 // Several independent passes (up to kMaxPassJobs, e.g. one per velocity component) in one launch.

@@ -108,7 +108,7 @@ __device__ __forceinline__ void band_pass_flat_x1(const PassArgs<T>& a, int64_t 
     const int64_t gstep = a.gaxis == 1 ? 1 : (a.gaxis == 2 ? (int64_t)gd.n1 : (int64_t)gd.n1 * gd.n2);
     acc += a.g[gi] - a.g[gi + gstep];
   }
-  a.Y[o] = acc;
+  pass_store(a, o, acc);
 }
 
 template <typename T, int W>
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(512) k_band_pass(const __grid_constant__ PassB
       const int64_t gi = gbase + (int64_t)i * gstride;
       acc += a.g[gi] - a.g[gi + gstep];
     }
-    a.Y[o] = acc;
+    pass_store(a, o, acc);
   }
 }
 
@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(256, 3) k_band_slide(const __grid_constant__ P
         k = gl / lines1;
         gl -= k * lines1;
       }
-      float* row = Y + (int64_t)k * a.bs + m * gl;
+      float* row = Y + (int64_t)k * a.bs + (int64_t)m * gl;
       for (int i = lane; i < m; i += 32) row[i] = ys[i * P + l];
     }
   }
@@ -737,6 +737,38 @@ void chol_solve_axis(double* x, int b, int p, int axis, const double* lb, const 
 }
 
 void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {
+  // FP32 passes write Y, then the vector kernel applies a Horner step (in FP32 the separate
+  // streaming kernel measured faster than an epilogue in the banded pass; same operations).
+  bool horner = false;
+  for (int j = 0; j < njobs; ++j) horner = horner || jobs[j].hmode != 0;
+  if (horner) {
+    PassArgs<float> plain[kMaxPassJobs];
+    for (int j = 0; j < njobs; ++j) {
+      plain[j] = jobs[j];
+      plain[j].hmode = 0;
+    }
+    band_tile_multi(plain, njobs, s);
+    // one vector launch when the jobs' outputs (and Horner vectors) follow each other, as the
+    // three velocity components do; otherwise one per job
+    bool contiguous = true;
+    int64_t total = 0;
+    for (int j = 0; j < njobs; ++j) {
+      const PassArgs<float>& a = jobs[j];
+      const PassArgs<float>& a0 = jobs[0];
+      contiguous = contiguous && a.hmode == a0.hmode && a.nb == a0.nb && a.bs == a0.bs &&
+                   a.Y == a0.Y + total && a.hr == a0.hr + total && a.hacc == a0.hacc + total &&
+                   (a.hmode != 1 || a.hx == a0.hx + total);
+      total += a.in.with(a.axis, a.D0.rows).size();
+    }
+    const int np = contiguous ? 1 : njobs;
+    for (int j = 0; j < np; ++j) {
+      const PassArgs<float>& a = jobs[j];
+      const int64_t n = contiguous ? total : a.in.with(a.axis, a.D0.rows).size();
+      if (a.hmode == 1) hp_first<float>(a.hx, a.Y, a.hr, a.hacc, n, s, a.nb, a.bs);
+      else if (a.hmode == 2) hp_update<float>(a.hr, a.Y, a.hacc, n, s, a.nb, a.bs);
+    }
+    return;
+  }
   PassBatch<float> pb{};
   pb.njobs = njobs;
   int blocks = 0;
@@ -839,6 +871,9 @@ void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {
         if (e.Z) e.Z += o;
         if (e.g) e.g += o;
         e.Y += o;
+        if (e.hr) e.hr += o;
+        if (e.hacc) e.hacc += o;
+        if (e.hx) e.hx += o;
         e.nb = 1;
         items[ni++] = e;
         if (ni == kMaxPassJobs) {

@@ -170,6 +170,17 @@ T* upload(Arena& ar, const std::vector<double>& h, cudaStream_t s) {
   return d;
 }
 
+// One hyper-power Horner step applied by the pass that produces A~ t (see PassArgs): mode 1 sets
+// r = x - A~ t, acc = x + r; mode 2 sets r = r - A~ t, acc = acc + r. r, acc, x have the layout of
+// the product.
+template <typename T>
+struct Horner {
+  int mode;
+  T* r;
+  T* acc;
+  const T* x;
+};
+
 // ---- operators in precision T ------------------------------------------------------------------
 template <typename T>
 struct Ops {
@@ -234,6 +245,15 @@ struct Ops {
     return p;
   }
 
+  // the job's result goes through the Horner epilogue h (offset o into its vectors)
+  static void horner(PassArgs<T>& p, const Horner<T>* h, int64_t o) {
+    if (!h) return;
+    p.hmode = h->mode;
+    p.hr = h->r + o;
+    p.hacc = h->acc + o;
+    p.hx = h->x ? h->x + o : nullptr;
+  }
+
   static int own_axis(int c) { return c + 1; }
   static int first_other(int c) { return c == 0 ? 2 : 1; }
   static int second_other(int c) { return c == 2 ? 2 : 3; }
@@ -246,7 +266,8 @@ struct Ops {
   // x1 pass with Mc_w, M-check padded with zeros to the width of K and M, so that every job of a
   // launch has one band width), their pass along x3 runs alone, then the last velocity pass.
   void adiag_all(const T* u, T* y, const T* g, int nq = 0, const T* const* qx = nullptr,
-                 T* const* qy = nullptr, const T* qcoef = nullptr) const {
+                 T* const* qy = nullptr, const T* qcoef = nullptr,
+                 const Horner<T>* h = nullptr) const {
     const T nu2 = 2 * nu;
     const Dims dq{b, b, b};
     PassArgs<T> j[kMaxPassJobs];
@@ -275,12 +296,15 @@ struct Ops {
       const int64_t o = c * nvc;
       j[c] = job(tS + o, Mc, 1, tR + o, &Tc, nu2, comp(c), second_other(c), y + o, nullptr, 0, g,
                  own_axis(c));
+      horner(j[c], h, o);
     }
     band_pass_multi<T>(j, 3, s);
   }
 
-  // y_k = coef_k M_q x_k for nvec <= 2 independent vectors (M_q = M-check^(x)3)
-  void mq(int nvec, const T* const* x, T* const* y, const T* coef) const {
+  // y_k = coef_k M_q x_k for nvec <= 2 independent vectors (M_q = M-check^(x)3); h: Horner step
+  // applied to the (single) result
+  void mq(int nvec, const T* const* x, T* const* y, const T* coef,
+          const Horner<T>* h = nullptr) const {
     const Dims d{b, b, b};
     PassArgs<T> j[2];
     for (int k = 0; k < nvec; ++k)
@@ -289,8 +313,10 @@ struct Ops {
     for (int k = 0; k < nvec; ++k)
       j[k] = job(f1 + k * npres, Mc, 1, nullptr, nullptr, 0, d, 2, f2 + k * npres);
     band_pass_multi<T>(j, nvec, s);
-    for (int k = 0; k < nvec; ++k)
+    for (int k = 0; k < nvec; ++k) {
       j[k] = job(f2 + k * npres, Mc, coef[k], nullptr, nullptr, 0, d, 3, y[k]);
+      if (nvec == 1) horner(j[k], h, 0);
+    }
     band_pass_multi<T>(j, nvec, s);
   }
 
@@ -310,17 +336,18 @@ struct Ops {
     adiag_all(x, y, m2);
   }
 
-  void apply_A(const T* x, T* y) const {
+  // y = A x; with h, the Horner step of h is applied to A x instead (y is scratch then)
+  void apply_A(const T* x, T* y, const Horner<T>* h = nullptr) const {
     divergence<T>(x, x + nvc, x + 2 * nvc, a, b, delta, s, nb, bs);
     const T* in[1] = {delta};
     T* out[1] = {m2};
     const T coef[1] = {nu};
     if (Mc_w.val) {
-      adiag_all(x, y, m2, 1, in, out, coef);
+      adiag_all(x, y, m2, 1, in, out, coef, h);
       return;
     }
     mq(1, in, out, coef);
-    adiag_all(x, y, m2);
+    adiag_all(x, y, m2, 0, nullptr, nullptr, nullptr, h);
   }
 
   // y = M_V x: L2 Gram matrix of the velocity basis, per component (mass (x) mass (x) mass with
@@ -346,12 +373,13 @@ struct Ops {
     div_transpose<T>(m2, a, b, yu, yu + nvc, yu + 2 * nvc, 0, s, nb, bs);
   }
 
-  void apply_Bt(const T* u, T* yq) const {  // B^T u = M_q D_div u
+  // B^T u = M_q D_div u; with h, the Horner step of h is applied to it instead
+  void apply_Bt(const T* u, T* yq, const Horner<T>* h = nullptr) const {
     divergence<T>(u, u + nvc, u + 2 * nvc, a, b, delta, s, nb, bs);
     const T* in[1] = {delta};
     T* out[1] = {yq};
     const T coef[1] = {1};
-    mq(1, in, out, coef);
+    mq(1, in, out, coef, h);
   }
 
   ModeArgs<T> mjob(const T* X, T* Y, const T* U, int n, int trans, Dims in, int axis,
@@ -507,7 +535,6 @@ struct HyperPower {
   int64_t counts[4] = {0, 0, 0, 0};   // fd_V, minv_Q, A, (B + B^T)
 
   void V(const Ops<T>& o, const VLevels& L, int s, const T* x, T* y) {
-    const int64_t n = o.nvel;
     if (s == 0) {
       o.fd_V(x, y);
       ++counts[0];
@@ -517,10 +544,9 @@ struct HyperPower {
     // Horner steps from r = acc = x; the first reads x directly
     for (int j = 1; j < order; ++j) {
       V(o, L, s - 1, j == 1 ? x : r, t);
-      o.apply_A(t, u);
+      const Horner<T> h{j == 1 ? 1 : 2, r, acc, x};
+      o.apply_A(t, u, &h);   // the step r, acc <- (r - A~ t, acc + r) in the last pass
       ++counts[2];
-      if (j == 1) hp_first<T>(x, u, r, acc, n, o.s, o.nb, o.bs);
-      else hp_update<T>(r, u, acc, n, o.s, o.nb, o.bs);
     }
     V(o, L, s - 1, acc, y);
   }
@@ -531,7 +557,6 @@ struct HyperPower {
   }
 
   void Q(const Ops<T>& o, const VLevels& L, int m, const T* x, T* y) {
-    const int64_t n = o.npres;
     if (m == 0) {
       o.minv_Q(x, y);
       ++counts[1];
@@ -544,10 +569,9 @@ struct HyperPower {
       Q(o, L, m - 1, j == 1 ? x : r, t);
       o.apply_B(t, bv);          // A~_Q t = B^T P_{V,l}^-1 B t
       V(o, L, l, bv, hv);
-      o.apply_Bt(hv, u);
+      const Horner<T> h{j == 1 ? 1 : 2, r, acc, x};
+      o.apply_Bt(hv, u, &h);   // the step r, acc <- (r - A~_Q t, acc + r) in the last pass
       ++counts[3];
-      if (j == 1) hp_first<T>(x, u, r, acc, n, o.s, o.nb, o.bs);
-      else hp_update<T>(r, u, acc, n, o.s, o.nb, o.bs);
     }
     Q(o, L, m - 1, acc, y);
   }
