@@ -594,9 +594,17 @@ __global__ void __launch_bounds__(256) k_divergence(const T* __restrict__ u1, co
     const int64_t k = nb > 1 ? t / per : 0;
     const int64_t o = t - k * per;
     const int64_t kb = k * bs;
-    const int i1 = (int)(o % b);
-    const int i2 = (int)((o / b) % b);
-    const int i3 = (int)(o / ((int64_t)b * b));
+    int i1, i2, i3;
+    if (per < ((int64_t)1 << 31)) {   // 32-bit index arithmetic within an item
+      const int o32 = (int)o, q = o32 / b;
+      i1 = o32 - q * b;
+      i3 = q / b;
+      i2 = q - i3 * b;
+    } else {
+      i1 = (int)(o % b);
+      i2 = (int)((o / b) % b);
+      i3 = (int)(o / ((int64_t)b * b));
+    }
     T d = 0;
     // u1 extents (a, b, b)
     {
@@ -637,16 +645,20 @@ __global__ void __launch_bounds__(256) k_div_transpose(const T* __restrict__ g, 
     const int c = (int)(o / nc);
     const int64_t r = o - c * nc;
     T* y = (c == 0 ? y1 : (c == 1 ? y2 : y3)) + kb;
+    // extents of component c: (e1, e2, e3) with a in the own direction, b elsewhere
+    const int e1 = c == 0 ? a : b, e2 = c == 1 ? a : b;
     int i1, i2, i3;
-    int64_t gs;
-    if (c == 0) {
-      i1 = (int)(r % a); i2 = (int)((r / a) % b); i3 = (int)(r / ((int64_t)a * b)); gs = 1;
-    } else if (c == 1) {
-      i1 = (int)(r % b); i2 = (int)((r / b) % a); i3 = (int)(r / ((int64_t)a * b)); gs = b;
+    if (per < ((int64_t)1 << 31)) {   // 32-bit index arithmetic within an item
+      const int r32 = (int)r, q = r32 / e1;
+      i1 = r32 - q * e1;
+      i3 = q / e2;
+      i2 = q - i3 * e2;
     } else {
-      i1 = (int)(r % b); i2 = (int)((r / b) % b); i3 = (int)(r / ((int64_t)b * b));
-      gs = (int64_t)b * b;
+      i1 = (int)(r % e1);
+      i2 = (int)((r / e1) % e2);
+      i3 = (int)(r / ((int64_t)e1 * e2));
     }
+    const int64_t gs = c == 0 ? 1 : (c == 1 ? (int64_t)b : (int64_t)b * b);
     const int64_t gi = kb + i1 + (int64_t)b * (i2 + (int64_t)b * i3);
     const T v = g[gi] - g[gi + gs];
     y[r] = accumulate ? y[r] + v : v;
