@@ -53,6 +53,8 @@ enum { STOKES_SCHUR_INNER = 0, STOKES_SCHUR_NONE = 1 };
 enum { STOKES_PREC_FP64 = 0, STOKES_PREC_FP32 = 1, STOKES_PREC_TF32 = 2, STOKES_PREC_BF16 = 3 };
 enum { STOKES_SOLVER_MINRES = 0, STOKES_SOLVER_FGMRES = 1 };
 
+enum { STOKES_FORWARD_KRONECKER = 0, STOKES_FORWARD_QUADRATURE = 1 };
+
 typedef struct stokes_opts {
   double c_pen;       /* Nitsche penalty constant C_pen (Sec. 3.2); <= 0 selects 14 */
   int schur;          /* Q-block sequence: STOKES_SCHUR_INNER = Eq. 4.5 (with inner updates,
@@ -77,6 +79,13 @@ typedef struct stokes_opts {
   int autotune;       /* nonzero (default): time the candidate launch shapes of the FP64 kernels
                          at setup and keep the fastest (stokes_get_tuning); results do not depend
                          on the choice. 0: fixed defaults. */
+  int forward;        /* forward operator of stokes_apply_K and of the solvers:
+                         STOKES_FORWARD_KRONECKER (default; banded Kronecker products, Sec. 3.3)
+                         or STOKES_FORWARD_QUADRATURE (matrix-free formation by global sum
+                         factorisation on the Gauss grid of p + 2 points per element and
+                         direction, the forward operator of the paper's timings, Sec. 5.3; equal
+                         to the Kronecker operator up to rounding; nrhs = 1 only).
+                         stokes_apply_A always uses the Kronecker form. */
 } stokes_opts;
 
 typedef struct stokes_ctx* stokes_t;

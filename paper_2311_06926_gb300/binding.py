@@ -18,6 +18,7 @@ ERRORS = {-1: "ARG", -2: "CUDA", -3: "NONFINITE", -4: "NOT_SPD", -5: "MAXIT", -6
 SCHUR = {"inner": 0, "none": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 SOLVER = {"minres": 0, "fgmres": 1}
+FORWARD = {"kronecker": 0, "quadrature": 1}
 
 
 class StokesError(RuntimeError):
@@ -30,7 +31,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("c_pen", ctypes.c_double), ("schur", ctypes.c_int), ("precision", ctypes.c_int),
                 ("solver", ctypes.c_int), ("max_order", ctypes.c_int), ("max_steps", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("restart", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("nrhs", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("nrhs", ctypes.c_int), ("autotune", ctypes.c_int), ("forward", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -155,7 +156,7 @@ class Stokes:
 
     def __init__(self, n, p, nu=1.0, c_pen=14.0, schur="inner", precision="fp64",
                  solver=None, max_order=3, max_steps=4, maxit=2000, restart=60, device=None,
-                 nrhs=1, autotune=True):
+                 nrhs=1, autotune=True, forward="kronecker"):
         """nrhs > 1: the context holds nrhs right-hand sides; apply_K, apply_P,
         apply_hyperpower, solve and solve_multi then take nrhs stacked vectors of `size` entries
         each (`batch_size` in all), processed by the same launches (needs precision "tf32" or
@@ -175,6 +176,7 @@ class Stokes:
         o.max_order, o.max_steps, o.maxit, o.restart = max_order, max_steps, maxit, restart
         o.nrhs = nrhs
         o.autotune = 1 if autotune else 0
+        o.forward = FORWARD[forward]
         with torch.cuda.device(self.device):
             # the library runs on its own stream, ordered against the caller's current stream
             # at every call (inputs ready before, outputs visible after)

@@ -203,6 +203,52 @@ Univariate build_univariate(int n, int p, double c_pen) {
   return u;
 }
 
+QuadTables build_quad_tables(int n, int p, double c_pen) {
+  QuadTables qt;
+  const std::vector<double> tN = open_knots(n, p + 1), tM = open_knots(n, p);
+  const int nM = n + p, a = n + p - 1;
+  std::vector<double> mscale(nM);
+  for (int i = 0; i < nM; ++i) mscale[i] = (p + 1) / (tM[i + p + 1] - tM[i]);
+  std::vector<double> xs;
+  element_rule(n, p + 2, xs, qt.w);
+  qt.nq = (int)xs.size();
+  qt.BN = Dense(qt.nq, a);
+  qt.DN = Dense(qt.nq, a);
+  qt.BM = Dense(qt.nq, nM);
+  qt.DM = Dense(qt.nq, nM);
+  for (int q = 0; q < qt.nq; ++q) {
+    const std::vector<double> Nv = bspline_values(tN, p + 1, xs[q]), Nd = bspline_derivs(tN, p + 1, xs[q]);
+    const std::vector<double> Mv = bspline_values(tM, p, xs[q]), Md = bspline_derivs(tM, p, xs[q]);
+    for (int i = 0; i < a; ++i) {   // interior N functions 1 .. n+p-1
+      qt.BN(q, i) = Nv[i + 1];
+      qt.DN(q, i) = Nd[i + 1];
+    }
+    for (int i = 0; i < nM; ++i) {
+      qt.BM(q, i) = Mv[i] * mscale[i];
+      qt.DM(q, i) = Md[i] * mscale[i];
+    }
+  }
+  std::vector<double> M0 = bspline_values(tM, p, 0.0), M1 = bspline_values(tM, p, 1.0);
+  std::vector<double> dM0 = bspline_derivs(tM, p, 0.0), dM1 = bspline_derivs(tM, p, 1.0);
+  for (int i = 0; i < nM; ++i) {
+    M0[i] *= mscale[i];
+    M1[i] *= mscale[i];
+    dM0[i] *= mscale[i];
+    dM1[i] *= mscale[i];
+  }
+  const double alpha2 = 2.0 * c_pen * n;
+  qt.Tface = Dense(nM, nM);
+  for (int i = 0; i < nM; ++i)
+    for (int j = 0; j < nM; ++j) {
+      const double Nc = M1[i] * M1[j] + M0[i] * M0[j];
+      const double Bij = M1[i] * dM1[j] - M0[i] * dM0[j];
+      const double Bji = M1[j] * dM1[i] - M0[j] * dM0[i];
+      qt.Tface(i, j) = 0.5 * (alpha2 * Nc - Bij - Bji);
+    }
+  symmetrize(qt.Tface);
+  return qt;
+}
+
 bool generalized_eigh(const Dense& K, const Dense& M, std::vector<double>& lam, Dense& U) {
   const int n = K.rows;
   // Cholesky M = L L^T

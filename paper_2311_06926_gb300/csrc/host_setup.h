@@ -34,6 +34,21 @@ struct Univariate {
 
 Univariate build_univariate(int n, int p, double c_pen);
 
+// Tables of the quadrature-based forward operator (global sum factorisation, Sec. 5.3): on the
+// Gauss-Legendre rule with p + 2 points per element (nq = n (p + 2) points on [0, 1], exact for
+// the degree 2p + 2 integrands), the values and derivatives of the a interior N functions and of
+// the b M functions at every point (nq x a and nq x b), the weights, and the face part of T-check:
+// Tface = T-check - K-check / 2 = (2 alpha N-check - B-check - B-check^T) / 2 (Sec. 3.2), the
+// Nitsche terms in the direction normal to the two faces.
+struct QuadTables {
+  int nq = 0;
+  Dense BN, DN, BM, DM;
+  std::vector<double> w;
+  Dense Tface;
+};
+
+QuadTables build_quad_tables(int n, int p, double c_pen);
+
 // Symmetric-definite generalised eigenproblem K U = M U diag(lam), U^T M U = I, by Cholesky
 // reduction (App. A.3) and cyclic Jacobi rotations. Eigenvalues ascending. Returns false if M is
 // not positive definite.

@@ -131,6 +131,13 @@ template <typename T>
 void div_transpose(const T* g, int a, int b, T* y1, T* y2, T* y3, int accumulate,
                    cudaStream_t s, int nb = 1, int64_t bs = 0);
 
+// Quadrature-based forward operator (Sec. 5.3), pointwise step at the n^3 Gauss points (nq per
+// direction, x1 fastest): G holds the nine gradient tensors d_d u_c at G + (3c + d) nq^3, P the
+// pressure values. In place: G <- W (nu (d_d u_c + d_c u_d) + [c == d] q) (the weighted 2 nu
+// eps(u) of a(u, v) plus the pressure of b(v, q), to be contracted with d_d v_c) and
+// P <- W div u, with W = w[i1] w[i2] w[i3] the product Gauss weight.
+void quad_stress(double* G, double* P, const double* w, int nq, double nu, cudaStream_t s);
+
 // ---- dense mode products (k_dense.cu) ----------------------------------------------------
 // Y[l, i, r] = sum_j Op(i, j) X[l, j, r] along `axis` of X (extents `in`), Op(i, j) =
 // trans ? U[j * ld + i] : U[i * ld + j], output extents in.with(axis, m).

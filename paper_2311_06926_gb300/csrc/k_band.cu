@@ -1038,6 +1038,41 @@ void div_transpose(const T* g, int a, int b, T* y1, T* y2, T* y3, int accumulate
              ((double)b * b * b * nb + (accumulate ? 2.0 : 1.0) * total) * sizeof(T));
 }
 
+__global__ void __launch_bounds__(256) k_quad_stress(double* __restrict__ G, double* __restrict__ P,
+                                                     const double* __restrict__ w, int nq,
+                                                     double nu) {
+  pdl_begin();
+  const int64_t n3 = (int64_t)nq * nq * nq;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n3;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q12 = o / nq;
+    const int i1 = (int)(o - q12 * nq);
+    const int i3 = (int)(q12 / nq);
+    const int i2 = (int)(q12 - (int64_t)i3 * nq);
+    const double W = w[i1] * w[i2] * w[i3];
+    double g[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g[k] = G[k * n3 + o];
+    const double q = P[o];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        double t = W * (nu * (g[3 * c + d] + g[3 * d + c]));
+        if (c == d) t += W * q;
+        G[(3 * c + d) * n3 + o] = t;
+      }
+    P[o] = W * (g[0] + g[4] + g[8]);
+  }
+}
+
+void quad_stress(double* G, double* P, const double* w, int nq, double nu, cudaStream_t s) {
+  const int64_t n3 = (int64_t)nq * nq * nq;
+  launch_begin(kClassDiv, s);
+  launch_k(k_quad_stress, grid_for(n3, 256), 256, 0, s, G, P, w, nq, nu);
+  launch_end(kClassDiv, s, 40.0 * n3, 20.0 * n3 * sizeof(double));
+}
+
 template void band_pass<double>(const PassArgs<double>&, cudaStream_t);
 template void band_pass<float>(const PassArgs<float>&, cudaStream_t);
 template void band_pass_multi<double>(const PassArgs<double>*, int, cudaStream_t);

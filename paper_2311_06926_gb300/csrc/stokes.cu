@@ -513,6 +513,142 @@ struct Ops {
   }
 };
 
+// ---- quadrature-based forward operator (FP64) ---------------------------------------------------
+// K [u; q] by matrix-free formation with global sum factorisation on the Gauss-Legendre grid of
+// p + 2 points per element and direction (Sec. 5.3, the forward operator of Table 1's timings):
+//   - the nine gradients d_d u_c and the pressure at the nq^3 points, by banded passes with the
+//     value and derivative tables (N functions in a component's own direction, M elsewhere);
+//   - pointwise, the weighted 2 nu eps(u) + q I and W div u (quad_stress);
+//   - the transposed tables bring them back onto the test functions (a(u, v), b(v, q), b(u, .));
+//   - the Nitsche face terms of sigma(u, v) (Sec. 3.2), which involve only the component itself
+//     on each face (the other components' own-direction functions vanish there), as banded
+//     Kronecker passes with Tface = T-check - K-check / 2 in the face-normal directions.
+// Exact quadrature, so it equals the Kronecker operator to rounding (tests/test_gpu_quadrature).
+struct QuadOps {
+  int a = 0, b = 0, nq = 0;
+  double nu = 0;
+  int64_t nvc = 0, nvel = 0, n3 = 0;
+  int band_block = 256;
+  BandD<double> BN{}, DN{}, BM{}, DM{};       // nq x a, nq x a, nq x b, nq x b
+  BandD<double> BNt{}, DNt{}, BMt{}, DMt{};   // transposes
+  BandD<double> Tf{}, Mn{}, Mc{};             // b x b face part of T-check, a x a N mass, b x b
+  const double* w = nullptr;                  // nq Gauss weights
+  double* G = nullptr;                        // 9 x nq^3
+  double* P = nullptr;                        // nq^3
+  double *s1[2] = {nullptr, nullptr};         // x1 stage: nq * b * b
+  double *s2[3] = {nullptr, nullptr, nullptr};  // x2 stage: nq * nq * b
+  double *f1 = nullptr, *f2 = nullptr, *f3 = nullptr;   // face stage: component size
+  cudaStream_t s = nullptr;
+
+  Dims comp(int c) const {
+    if (c == 0) return Dims{a, b, b};
+    if (c == 1) return Dims{b, a, b};
+    return Dims{b, b, a};
+  }
+
+  PassArgs<double> pj(const double* X0, const BandD<double>& D0, double c0, const double* X1,
+                      const BandD<double>* D1, double c1, Dims in, int axis, double* Y,
+                      const double* Z = nullptr, double cz = 0) const {
+    PassArgs<double> p{};
+    p.X0 = X0;
+    p.D0 = D0;
+    p.c0 = c0;
+    p.X1 = X1;
+    p.D1 = D1 ? *D1 : D0;
+    p.c1 = c1;
+    p.nterms = X1 ? 2 : 1;
+    p.Z = Z;
+    p.cz = cz;
+    p.Y = Y;
+    p.in = in;
+    p.axis = axis;
+    p.nb = 1;
+    p.block = band_block;
+    return p;
+  }
+
+  // table of component c (3 = pressure) in direction k (1..3): value or derivative
+  const BandD<double>& tab(int c, int k, bool deriv, bool transposed) const {
+    const bool own = c == k - 1;
+    if (own) return deriv ? (transposed ? DNt : DN) : (transposed ? BNt : BN);
+    return deriv ? (transposed ? DMt : DM) : (transposed ? BMt : BM);
+  }
+
+  void apply_K(const double* x, double* y) const {
+    const double* q = x + nvel;
+    PassArgs<double> j[3];
+    // gradients d_d u_c at the points: x1 {value, derivative}, x2 {vv, vd, dv}, x3 {d1, d2, d3}
+    for (int c = 0; c < 3; ++c) {
+      const Dims e = comp(c);
+      const double* u = x + c * nvc;
+      const Dims d1{nq, e.n2, e.n3}, d2{nq, nq, e.n3};
+      j[0] = pj(u, tab(c, 1, false, false), 1, nullptr, nullptr, 0, e, 1, s1[0]);
+      j[1] = pj(u, tab(c, 1, true, false), 1, nullptr, nullptr, 0, e, 1, s1[1]);
+      band_pass_multi<double>(j, 2, s);
+      j[0] = pj(s1[0], tab(c, 2, false, false), 1, nullptr, nullptr, 0, d1, 2, s2[0]);   // v v
+      j[1] = pj(s1[0], tab(c, 2, true, false), 1, nullptr, nullptr, 0, d1, 2, s2[1]);    // v d
+      j[2] = pj(s1[1], tab(c, 2, false, false), 1, nullptr, nullptr, 0, d1, 2, s2[2]);   // d v
+      band_pass_multi<double>(j, 3, s);
+      double* g = G + (int64_t)3 * c * n3;
+      j[0] = pj(s2[2], tab(c, 3, false, false), 1, nullptr, nullptr, 0, d2, 3, g);            // d/dx1
+      j[1] = pj(s2[1], tab(c, 3, false, false), 1, nullptr, nullptr, 0, d2, 3, g + n3);       // d/dx2
+      j[2] = pj(s2[0], tab(c, 3, true, false), 1, nullptr, nullptr, 0, d2, 3, g + 2 * n3);    // d/dx3
+      band_pass_multi<double>(j, 3, s);
+    }
+    {  // pressure values at the points
+      const Dims e{b, b, b}, d1{nq, b, b}, d2{nq, nq, b};
+      j[0] = pj(q, BM, 1, nullptr, nullptr, 0, e, 1, s1[0]);
+      band_pass_multi<double>(j, 1, s);
+      j[0] = pj(s1[0], BM, 1, nullptr, nullptr, 0, d1, 2, s2[0]);
+      band_pass_multi<double>(j, 1, s);
+      j[0] = pj(s2[0], BM, 1, nullptr, nullptr, 0, d2, 3, P);
+      band_pass_multi<double>(j, 1, s);
+    }
+    quad_stress(G, P, w, nq, nu, s);
+    // Nitsche face terms into y_c: own direction N mass, then {Tface, M-check} in the first
+    // other direction, then y_c = 2 nu (M-check (Tface t) + Tface (M-check t)) in the second
+    for (int c = 0; c < 3; ++c) {
+      const Dims e = comp(c);
+      const int own = c + 1, o1 = c == 0 ? 2 : 1, o2 = c == 2 ? 2 : 3;
+      j[0] = pj(x + c * nvc, Mn, 1, nullptr, nullptr, 0, e, own, f1);
+      band_pass_multi<double>(j, 1, s);
+      j[0] = pj(f1, Tf, 1, nullptr, nullptr, 0, e, o1, f2);
+      j[1] = pj(f1, Mc, 1, nullptr, nullptr, 0, e, o1, f3);
+      band_pass_multi<double>(j, 2, s);
+      j[0] = pj(f2, Mc, 2 * nu, f3, &Tf, 2 * nu, e, o2, y + c * nvc);
+      band_pass_multi<double>(j, 1, s);
+    }
+    // back onto the test functions: y_c += D1^T B2^T B3^T T_c1 + B1^T D2^T B3^T T_c2
+    //                                       + B1^T B2^T D3^T T_c3
+    for (int c = 0; c < 3; ++c) {
+      const Dims e = comp(c);
+      const Dims q3{nq, nq, nq}, d2{nq, nq, e.n3}, d1{nq, e.n2, e.n3};
+      const double* t = G + (int64_t)3 * c * n3;
+      j[0] = pj(t, tab(c, 3, false, true), 1, nullptr, nullptr, 0, q3, 3, s2[0]);
+      j[1] = pj(t + n3, tab(c, 3, false, true), 1, nullptr, nullptr, 0, q3, 3, s2[1]);
+      j[2] = pj(t + 2 * n3, tab(c, 3, true, true), 1, nullptr, nullptr, 0, q3, 3, s2[2]);
+      band_pass_multi<double>(j, 3, s);
+      const BandD<double>& B2t = tab(c, 2, false, true);
+      j[0] = pj(s2[0], B2t, 1, nullptr, nullptr, 0, d2, 2, s1[0]);
+      j[1] = pj(s2[1], tab(c, 2, true, true), 1, s2[2], &B2t, 1, d2, 2, s1[1]);
+      band_pass_multi<double>(j, 2, s);
+      const BandD<double>& B1t = tab(c, 1, false, true);
+      double* yc = y + c * nvc;
+      j[0] = pj(s1[0], tab(c, 1, true, true), 1, s1[1], &B1t, 1, d1, 1, yc, yc, 1);
+      band_pass_multi<double>(j, 1, s);
+    }
+    {  // pressure rows: (B^T)^(x)3 W div u
+      const Dims q3{nq, nq, nq}, d2{nq, nq, b}, d1{nq, b, b};
+      j[0] = pj(P, BMt, 1, nullptr, nullptr, 0, q3, 3, s2[0]);
+      band_pass_multi<double>(j, 1, s);
+      j[0] = pj(s2[0], BMt, 1, nullptr, nullptr, 0, d2, 2, s1[0]);
+      band_pass_multi<double>(j, 1, s);
+      j[0] = pj(s1[0], BMt, 1, nullptr, nullptr, 0, d1, 1, y + nvel);
+      band_pass_multi<double>(j, 1, s);
+    }
+  }
+};
+
 // ---- hyper-power recursion in precision T ------------------------------------------------------
 template <typename T>
 struct HyperPower {
@@ -609,6 +745,7 @@ struct stokes_ctx {
   Ops<double> odq;                       // FP64 operators of the concurrent pressure branch
   cudaStream_t stream_q = nullptr;       // its stream (owned)
   Ops<float> of;
+  QuadOps* quad = nullptr;               // quadrature-based forward operator (opts.forward)
   HyperPower<double> hd;
   HyperPower<float> hf;
   float *xf = nullptr, *yf = nullptr;    // reduced-precision preconditioner in/out
@@ -641,6 +778,7 @@ struct stokes_ctx {
   bool no_capture = false;
   std::vector<RmpPlan> tc_plans;
   ~stokes_ctx() {
+    delete quad;
     for (auto& kv : minres_graphs) cudaGraphExecDestroy(kv.second);
     for (auto& kv : pk_graphs) cudaGraphExecDestroy(kv.second);
     if (hd.ev_fork) cudaEventDestroy(hd.ev_fork);
@@ -649,6 +787,13 @@ struct stokes_ctx {
 };
 
 namespace {
+
+// y = K x with the context's forward operator: banded Kronecker products (default) or the
+// quadrature-based formation (opts.forward)
+void apply_Kop(stokes_ctx* c, const double* x, double* y) {
+  if (c->quad) c->quad->apply_K(x, y);
+  else c->od.apply_K(x, y);
+}
 
 thread_local std::string g_setup_error;
 
@@ -911,7 +1056,7 @@ void normalize_pressure(stokes_ctx* c, double* x) {
 
 // true relative residual ||f - K x|| / ||f||
 double true_residual(stokes_ctx* c, const double* f, const double* x, double* tmp) {
-  c->od.apply_K(x, tmp);
+  apply_Kop(c, x, tmp);
   axpby<double>(1.0, f, -1.0, tmp, c->ntot, c->stream);
   dot<double>(tmp, tmp, c->ntot, c->partials, c->dsc + 1, c->stream);
   dot<double>(f, f, c->ntot, c->partials, c->dsc + 2, c->stream);
@@ -929,7 +1074,7 @@ void minres_iteration(stokes_ctx* c, double* vold, double* v, double* z, double*
   const int64_t n = c->ntot;
   cudaStream_t s = c->stream;
   minres_scale_z(z, c->st, n, s);
-  c->od.apply_K(z, Kz);
+  apply_Kop(c, z, Kz);
   dot<double>(Kz, z, n, c->partials, &c->st->delta, s);
   minres_lanczos(Kz, v, vold, c->st, n, s);            // v_new over v_old
   apply_prec(c, c->order, c->steps, vold, zn);
@@ -1068,7 +1213,7 @@ void pk_apply(stokes_ctx* c, const double* v, double* z, double* w) {
   if (!c->use_graphs || profiling_active(c) || !c->pk_in || w != c->kv[0] ||
       (c->no_capture && it == c->pk_graphs.end())) {
     apply_prec(c, c->order, c->steps, v, z);
-    c->od.apply_K(z, w);
+    apply_Kop(c, z, w);
     return;
   }
   cudaGraphExec_t exec = nullptr;
@@ -1076,7 +1221,7 @@ void pk_apply(stokes_ctx* c, const double* v, double* z, double* w) {
     int64_t k = 0;
     exec = capture_graph(s, [&] {
       apply_prec(c, c->order, c->steps, c->pk_in, c->pk_z);
-      c->od.apply_K(c->pk_z, w);
+      apply_Kop(c, c->pk_z, w);
     }, &k);
     c->pk_graphs[key] = exec;
     c->pk_graph_kernels[key] = k;
@@ -1195,7 +1340,7 @@ int run_fgmres(stokes_ctx* c, const double* f, double tol, double* x, int* iters
       return c->ratios.back() <= tol ? STOKES_OK : STOKES_ERR_MAXIT;
     }
     // restart: r = f - K x
-    c->od.apply_K(x, r);
+    apply_Kop(c, x, r);
     axpby<double>(1.0, f, -1.0, r, n, s);
   }
   *iters = it;
@@ -1368,7 +1513,7 @@ void run_fgmres_multi(stokes_ctx* c, const double* f, double tol, double* x, int
       if (stop[k]) done[k] = 1;
     if (all_done()) break;
     // restart: r = f - K x
-    c->od.apply_K(x, r);
+    apply_Kop(c, x, r);
     for (int k = 0; k < nb; ++k)
       if (!done[k]) axpby<double>(1.0, f + k * n, -1.0, r + k * n, n, s);
   }
@@ -1390,7 +1535,7 @@ int solve_multi_impl(stokes_ctx* c, const double* rhs, double tol, double* x, in
     axpy_dev(c->dsc + (size_t)k * ds, -1.0, c->zconst, q, c->npres, s);
   }
   double* tmp = c->kv[7];
-  c->od.apply_K(x, tmp);
+  apply_Kop(c, x, tmp);
   for (int k = 0; k < nb; ++k) {
     axpby<double>(1.0, rhs + k * n, -1.0, tmp + k * n, n, s);
     dot<double>(tmp + k * n, tmp + k * n, n, c->partials, c->dsc + (size_t)k * ds + 1, s);
@@ -1468,6 +1613,7 @@ constexpr int kBandBlocks[] = {128, 256, 512};
 void set_shapes(stokes_ctx* c, int mode_block, int band_block) {
   c->od.mode_block = c->odq.mode_block = mode_block;
   c->od.band_block = c->odq.band_block = band_block;
+  if (c->quad) c->quad->band_block = band_block;
   // captured graphs hold the previous launch shapes
   for (auto& kv : c->minres_graphs) cudaGraphExecDestroy(kv.second);
   c->minres_graphs.clear();
@@ -1475,6 +1621,51 @@ void set_shapes(stokes_ctx* c, int mode_block, int band_block) {
   for (auto& kv : c->pk_graphs) cudaGraphExecDestroy(kv.second);
   c->pk_graphs.clear();
   c->pk_graph_kernels.clear();
+}
+
+Dense transposed(const Dense& D) {
+  Dense T(D.cols, D.rows);
+  for (int i = 0; i < D.rows; ++i)
+    for (int j = 0; j < D.cols; ++j) T(j, i) = D(i, j);
+  return T;
+}
+
+void init_quad(stokes_ctx* c) {
+  const QuadTables qt = build_quad_tables(c->n, c->p, c->c_pen);
+  Arena& ar = c->arena;
+  cudaStream_t s = c->stream;
+  QuadOps* q = new QuadOps();
+  c->quad = q;
+  q->a = c->a;
+  q->b = c->b;
+  q->nq = qt.nq;
+  q->nu = c->nu;
+  q->nvc = c->nvc;
+  q->nvel = c->nvel;
+  q->n3 = (int64_t)qt.nq * qt.nq * qt.nq;
+  q->s = s;
+  q->band_block = c->od.band_block;
+  // tables in band form (exact zeros outside the supports)
+  q->BN = upload_band<double>(ar, to_band(qt.BN, 0.0), s);
+  q->DN = upload_band<double>(ar, to_band(qt.DN, 0.0), s);
+  q->BM = upload_band<double>(ar, to_band(qt.BM, 0.0), s);
+  q->DM = upload_band<double>(ar, to_band(qt.DM, 0.0), s);
+  q->BNt = upload_band<double>(ar, to_band(transposed(qt.BN), 0.0), s);
+  q->DNt = upload_band<double>(ar, to_band(transposed(qt.DN), 0.0), s);
+  q->BMt = upload_band<double>(ar, to_band(transposed(qt.BM), 0.0), s);
+  q->DMt = upload_band<double>(ar, to_band(transposed(qt.DM), 0.0), s);
+  q->Tf = upload_band<double>(ar, to_band(qt.Tface, 0.0), s);
+  q->Mn = c->od.M;
+  q->Mc = c->od.Mc;
+  q->w = upload<double>(ar, qt.w, s);
+  const int64_t nq = qt.nq, b = c->b;
+  q->G = ar.alloc<double>((size_t)9 * q->n3);
+  q->P = ar.alloc<double>((size_t)q->n3);
+  for (int k = 0; k < 2; ++k) q->s1[k] = ar.alloc<double>((size_t)(nq * b * b));
+  for (int k = 0; k < 3; ++k) q->s2[k] = ar.alloc<double>((size_t)(nq * nq * b));
+  q->f1 = ar.alloc<double>((size_t)c->nvc);
+  q->f2 = ar.alloc<double>((size_t)c->nvc);
+  q->f3 = ar.alloc<double>((size_t)c->nvc);
 }
 
 void autotune(stokes_ctx* c) {
@@ -1541,6 +1732,7 @@ void stokes_default_opts(stokes_opts* o) {
   o->stream = nullptr;
   o->nrhs = 1;
   o->autotune = 1;
+  o->forward = STOKES_FORWARD_KRONECKER;
 }
 
 int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stokes_opts* opts) {
@@ -1562,7 +1754,11 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
   if (o.solver == STOKES_SOLVER_MINRES && o.precision != STOKES_PREC_FP64)
     return fail(nullptr, STOKES_ERR_ARG,
                 "MINRES needs a fixed SPD preconditioner: use FP64 or the FGMRES solver");
+  if (o.forward != STOKES_FORWARD_KRONECKER && o.forward != STOKES_FORWARD_QUADRATURE)
+    return fail(nullptr, STOKES_ERR_ARG, "invalid forward operator");
   if (o.nrhs < 1) o.nrhs = 1;
+  if (o.nrhs > 1 && o.forward == STOKES_FORWARD_QUADRATURE)
+    return fail(nullptr, STOKES_ERR_ARG, "the quadrature forward operator takes nrhs = 1");
   if (o.nrhs > 1024) return fail(nullptr, STOKES_ERR_ARG, "nrhs out of range");
   if (o.nrhs > 1 && (o.solver != STOKES_SOLVER_FGMRES ||
                      (o.precision != STOKES_PREC_TF32 && o.precision != STOKES_PREC_BF16)))
@@ -1693,6 +1889,7 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
     c->xi = c->arena.alloc<double>(c->ntot);
     c->ratio_dev = c->arena.alloc<double>(o.maxit);
     if (const char* e = std::getenv("STOKES_NO_GRAPHS")) c->use_graphs = e[0] == '0';
+    if (o.forward == STOKES_FORWARD_QUADRATURE) init_quad(c);
     if (o.autotune) autotune(c);
     c->io_rhs = c->arena.alloc<double>(c->ntot);
     c->io_x = c->arena.alloc<double>(c->ntot);
@@ -1744,7 +1941,7 @@ int stokes_apply_A(stokes_t c, const double* x, double* y) {
 int stokes_apply_K(stokes_t c, const double* x, double* y) {
   if (!c || !x || !y) return c ? fail(c, STOKES_ERR_ARG, "null vector") : STOKES_ERR_ARG;
   try {
-    c->od.apply_K(x, y);
+    apply_Kop(c, x, y);
     check_launch("apply_K");
   } catch (const CudaError& e) {
     return cuda_fail(c, e);
