@@ -719,7 +719,8 @@ def main():
                        "unknowns": G.size, "precision": prec, "solves_per_step": len(sweep),
                        "tol": 1e-8, "l2": "flushed by a 256 MiB write before every step",
                        "parallelism": f"replicas x{ws}",
-                       "fp64_launch_shapes": dict(zip(("mode_block", "band_block"), G.tuning()))},
+                       "fp64_launch_shapes": dict(zip(("mode_block", "band_block", "fd_fused"),
+                                                     G.tuning()))},
             "per_preconditioner": per,
             "table1_form": table1,
             "sweep_concurrent": sweep_conc,

@@ -82,8 +82,8 @@ def load_library(path=None):
         "stokes_profile_begin": (ctypes.c_int, [vp]),
         "stokes_profile_end": (ctypes.c_int, [vp, ctypes.POINTER(KernelStat), ctypes.c_int]),
         "stokes_kernel_launches": (ctypes.c_int64, []),
-        "stokes_get_tuning": (ctypes.c_int, [vp, ip, ip]),
-        "stokes_set_tuning": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
+        "stokes_get_tuning": (ctypes.c_int, [vp, ip, ip, ip]),
+        "stokes_set_tuning": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "stokes_fd_apply_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
                                                    vp, vp, vp, vp, ctypes.c_double, vp, vp, vp]),
         "stokes_destroy": (None, [vp]),
@@ -218,14 +218,17 @@ class Stokes:
 
     # -- C ABI ----------------------------------------------------------------------------------
     def tuning(self):
-        """(mode_block, band_block): threads per block of the FP64 mode products and banded
-        passes (picked by the setup tuner unless autotune=False)."""
-        mb, bb = ctypes.c_int(), ctypes.c_int()
-        self._check(self.lib.stokes_get_tuning(self.h, ctypes.byref(mb), ctypes.byref(bb)))
-        return mb.value, bb.value
+        """(mode_block, band_block, fd_fused): threads per block of the FP64 mode products and
+        banded passes, and whether the FP64 fast diagonalisation runs as three fused launches
+        (picked by the setup tuner unless autotune=False)."""
+        mb, bb, ff = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.stokes_get_tuning(self.h, ctypes.byref(mb), ctypes.byref(bb),
+                                               ctypes.byref(ff)))
+        return mb.value, bb.value, ff.value
 
-    def set_tuning(self, mode_block, band_block):
-        self._check(self.lib.stokes_set_tuning(self.h, int(mode_block), int(band_block)))
+    def set_tuning(self, mode_block, band_block, fd_fused=0):
+        self._check(self.lib.stokes_set_tuning(self.h, int(mode_block), int(band_block),
+                                               int(fd_fused)))
 
     def set_preconditioner(self, order, steps):
         self._check(self.lib.stokes_set_preconditioner(self.h, order, steps))

@@ -34,6 +34,27 @@ inline void launch_k(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, c
   cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
 }
 
+// The same with a thread-block cluster of cluster_x blocks along x (grid.x a multiple of it).
+template <typename... P, typename... A>
+inline void launch_kc(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                      int cluster_x, A... args) {
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = cluster_x;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = cluster_x > 1 ? 2 : 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
+
 // Banded 1D matrix on the device: D(i, start[i] + w) = val[i * width + w].
 // Square matrices whose nonzeros all lie within |i - j| <= half also carry a centred copy:
 // D(i, i - half + k) = cval[i * cpitch + k] for k < 2 half + 1 (zero where i - half + k is out of
@@ -160,6 +181,43 @@ void mode_product(const ModeArgs<T>& a, cudaStream_t s);
 constexpr int kMaxModeJobs = 4;
 template <typename T>
 void mode_product_multi(const ModeArgs<T>* jobs, int njobs, cudaStream_t s);
+
+// Fused FP64 fast-diagonalisation passes (App. A.4), several tensors per launch. The operators
+// are square with parity-split eigenvector columns (eo even modes first, eo >= 1), as for
+// mode_product with eo_he > 0; each output is computed in the same operation order as by
+// mode_product, so the fused and the per-direction forms give identical bits.
+//
+// Plane pair: the two products along x1 and x2 of every x1-x2 plane, one block or one cluster of
+// blocks per plane (the plane and the intermediate stay in shared memory). fwd = 1: Y = (U2^T (x) U1^T) X per plane;
+// fwd = 0: Y = post (U2 (x) U1) X (the x2 product first, then x1).
+struct FdPlaneArgs {
+  const double* X; double* Y;
+  const double* U1; const double* U2;   // ld = in.n1 and in.n2
+  Dims in;
+  int eo1, eo2;
+  double post;
+};
+// Lines along x3: the forward product with U3^T, the eigenvalue scaling (invd, or
+// 1 / (scale (lam1 + lam2 + lam3)), or none), and the backward product with U3 (times post).
+struct FdLineArgs {
+  const double* X; double* Y;
+  const double* U3;                      // ld = in.n3
+  Dims in;
+  int eo3;
+  const double* invd;
+  const double *lam1, *lam2, *lam3;
+  double scale;
+  double post;
+};
+// Shared memory of one plane block (two plane buffers); 0 if the plane does not fit.
+int fd_plane_smem(Dims in);
+// Both return false without launching if a job does not qualify (plane too large for shared
+// memory, no parity split); the caller then uses mode_product_multi.
+// cluster: 1, 2 or 4 blocks per plane (a thread-block cluster sharing the plane's intermediate
+// through distributed shared memory).
+bool fd_plane_multi(const FdPlaneArgs* jobs, int njobs, int fwd, int block, int cluster,
+                    cudaStream_t s);
+bool fd_line3_multi(const FdLineArgs* jobs, int njobs, int block, cudaStream_t s);
 
 // In-place banded Cholesky solves along one direction of a (b, b, b) tensor: x <- post (L L^T)^-1 x
 // with L lower triangular of bandwidth p stored as rows lb[i * (p + 1) + (k - i + p)] for

@@ -11,6 +11,9 @@
 // FP32 (CUDA-core fallback of the reduced-precision preconditioner): 64 x 64 tiles, 256 threads,
 // 4 x 4 outputs per thread. FP64 uses the row-streaming kernel further below.
 #include <algorithm>
+#include <atomic>
+
+#include <cooperative_groups.h>
 
 #include "internal.h"
 #include "profile.h"
@@ -373,6 +376,249 @@ __global__ void __launch_bounds__(512) k_mode_tile(const __grid_constant__ RowBa
   }
 }
 
+
+// ---- FP64: fused fast-diagonalisation passes ---------------------------------------------------
+// At small meshes a single mode-product pass is one partial wave whose load, compute and store
+// phases run one after the other, so its fixed latency is comparable to its FP64 work. The fused
+// kernels keep the intermediate of two (or three) consecutive passes in shared memory: the x1 and
+// x2 products of one x1-x2 plane (one block per plane), and the forward x3 product, the
+// eigenvalue scaling and the backward x3 product of a group of x3 lines. Every output is
+// computed with the operations and the order of k_mode_tile (even/odd fold, half-length dots
+// from k = 0 upward, mirrored pairs a_e +- a_o), so the results are bit-identical.
+struct PlaneJob {
+  const double* X; double* Y;
+  const double* U1; const double* U2;
+  int n1, n2;
+  int eo1, eo2;
+  double post;
+};
+
+struct PlaneBatch {
+  PlaneJob job[kMaxModeJobs];
+  int first[kMaxModeJobs + 1];   // first block (plane) of each job
+  int njobs;
+  int fwd;
+};
+
+// One cluster of cs blocks per plane (cs = 1, 2, 4). Forward: block r loads and folds the x1 rows
+// of its slice, computes their x1 products and stores them into the plane buffer of every block
+// of the cluster; after the cluster barrier each block folds the whole intermediate along x2 and
+// computes its slice of the x2 outputs. Backward: block r takes a slice of the x1 columns for the
+// x2 products (stored to every block), then a slice of the rows for the x1 products.
+__global__ void __launch_bounds__(512) k_fd_plane(const __grid_constant__ PlaneBatch pb) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int cs = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  pdl_begin();
+  extern __shared__ double shd[];
+  const int pidx = (int)blockIdx.x / cs;
+  int jb = 0;
+  while (jb + 1 < pb.njobs && pidx >= pb.first[jb + 1]) ++jb;
+  const PlaneJob& J = pb.job[jb];
+  const int plane = pidx - pb.first[jb];
+  const int n1 = J.n1, n2 = J.n2, np = n1 * n2;
+  double* B0 = shd;        // [n2][n1], x1 fastest
+  double* B1 = shd + np;
+  double* peer0[4];
+  double* peer1[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    peer0[t] = t >= cs ? nullptr : (t == rank ? B0 : cl.map_shared_rank(B0, t));
+    peer1[t] = t >= cs ? nullptr : (t == rank ? B1 : cl.map_shared_rank(B1, t));
+  }
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const double* X = J.X + (int64_t)plane * np;
+  double* Y = J.Y + (int64_t)plane * np;
+  const int he1 = J.eo1, h1 = n1 - he1, he2 = J.eo2, h2 = n2 - he2;
+  const int r0 = n2 * rank / cs, r1 = n2 * (rank + 1) / cs;   // this block's x1 rows
+  if (cs > 1) cl.sync();   // every block of the cluster runs before any store into it
+  if (pb.fwd) {
+    const int nr = r1 - r0;
+    for (int idx = tid; idx < nr * n1; idx += nth) B0[r0 * n1 + idx] = X[r0 * n1 + idx];
+    __syncthreads();
+    // fold the x1 rows: (x_k + x_{n1-1-k} | x_k - x_{n1-1-k}), middle entry kept
+    for (int idx = tid; idx < he1 * nr; idx += nth) {
+      const int j2 = r0 + idx / he1, k = idx - (idx / he1) * he1;
+      const double* row = B0 + j2 * n1;
+      double* f = B1 + j2 * n1;
+      if (k < h1) {
+        const double a = row[k], b = row[n1 - 1 - k];
+        f[k] = a + b;
+        f[he1 + k] = a - b;
+      } else {
+        f[k] = row[k];
+      }
+    }
+    __syncthreads();
+    // x1 products of the rows: T[j2][i1] = sum_k U1[k][i1] f_{j2}[k], into every block's B0
+    for (int q = tid; q < nr * n1; q += nth) {
+      const int j2 = r0 + q / n1, i1 = q - (q / n1) * n1;
+      const int len = i1 < he1 ? he1 : h1;
+      const double* xr = B1 + j2 * n1 + (i1 < he1 ? 0 : he1);
+      const double* op = J.U1 + i1;
+      double acc = 0.0;
+      for (int k = 0; k < len; ++k) acc = fma(__ldg(op + k * n1), xr[k], acc);
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (t < cs) peer0[t][j2 * n1 + i1] = acc;
+    }
+    if (cs > 1) cl.sync(); else __syncthreads();
+    // fold every x2 column of the intermediate
+    for (int idx = tid; idx < he2 * n1; idx += nth) {
+      const int k = idx / n1, i1 = idx - k * n1;
+      if (k < h2) {
+        const double a = B0[k * n1 + i1], b = B0[(n2 - 1 - k) * n1 + i1];
+        B1[k * n1 + i1] = a + b;
+        B1[(he2 + k) * n1 + i1] = a - b;
+      } else {
+        B1[k * n1 + i1] = B0[k * n1 + i1];
+      }
+    }
+    __syncthreads();
+    // this block's x2 outputs i2 in [r0, r1), stored coalesced (i1 fastest)
+    for (int q = tid; q < nr * n1; q += nth) {
+      const int i2 = r0 + q / n1, i1 = q - (q / n1) * n1;
+      const int len = i2 < he2 ? he2 : h2;
+      const double* xc = B1 + (i2 < he2 ? 0 : he2) * n1 + i1;
+      const double* op = J.U2 + i2;
+      double acc = 0.0;
+      for (int k = 0; k < len; ++k) acc = fma(__ldg(op + k * n2), xc[k * n1], acc);
+      Y[i2 * n1 + i1] = acc * J.post;
+    }
+  } else {
+    const int c0 = n1 * rank / cs, c1 = n1 * (rank + 1) / cs, nc = c1 - c0;   // x1 columns
+    for (int idx = tid; idx < n2 * nc; idx += nth) {
+      const int j2 = idx / nc, i1 = c0 + (idx - (idx / nc) * nc);
+      B0[j2 * n1 + i1] = X[j2 * n1 + i1];
+    }
+    __syncthreads();
+    // backward x2: column i1, mirrored output pair (k, n2-1-k) from a_e (even modes) and a_o,
+    // into every block's B1
+    for (int q = tid; q < he2 * nc; q += nth) {
+      const int k = q / nc, i1 = c0 + (q - (q / nc) * nc);
+      const double* xc = B0 + i1;
+      const double* row = J.U2 + k * n2;
+      double ae = 0.0, ao = 0.0;
+      for (int j = 0; j < he2; ++j) ae = fma(__ldg(row + j), xc[j * n1], ae);
+      if (k < h2) {
+        for (int j = 0; j < h2; ++j) ao = fma(__ldg(row + he2 + j), xc[(he2 + j) * n1], ao);
+        const double vp = ae + ao, vm = ae - ao;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t < cs) {
+            peer1[t][k * n1 + i1] = vp;
+            peer1[t][(n2 - 1 - k) * n1 + i1] = vm;
+          }
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (t < cs) peer1[t][k * n1 + i1] = ae;
+      }
+    }
+    if (cs > 1) cl.sync(); else __syncthreads();
+    // backward x1 of this block's rows k2 in [r0, r1): mirrored pair (k, n1-1-k)
+    const int nr = r1 - r0;
+    for (int q = tid; q < nr * he1; q += nth) {
+      const int k2 = r0 + q / he1, k = q - (q / he1) * he1;
+      const double* xr = B1 + k2 * n1;
+      const double* row = J.U1 + k * n1;
+      double ae = 0.0, ao = 0.0;
+      for (int j = 0; j < he1; ++j) ae = fma(__ldg(row + j), xr[j], ae);
+      double* y = Y + k2 * n1;
+      if (k < h1) {
+        for (int j = 0; j < h1; ++j) ao = fma(__ldg(row + he1 + j), xr[he1 + j], ao);
+        y[k] = (ae + ao) * J.post;
+        y[n1 - 1 - k] = (ae - ao) * J.post;
+      } else {
+        y[k] = ae * J.post;
+      }
+    }
+  }
+}
+
+struct LineJob {
+  const double* X; double* Y; const double* U;
+  int64_t L;             // lines: n1 * n2 (stride of x3)
+  int K, eo, lb;         // extent along x3, even modes, lines per block
+  int n1;                // to split a line index into (i1, i2)
+  const double* invd;
+  const double *lam1, *lam2, *lam3;
+  double scale;
+  double post;
+};
+
+struct LineBatch {
+  LineJob job[kMaxModeJobs];
+  int64_t first[kMaxModeJobs + 1];
+  int njobs;
+};
+
+__global__ void __launch_bounds__(512) k_fd_line3(const __grid_constant__ LineBatch lbt) {
+  pdl_begin();
+  extern __shared__ double shd[];
+  int jb = 0;
+  while (jb + 1 < lbt.njobs && (int64_t)blockIdx.x >= lbt.first[jb + 1]) ++jb;
+  const LineJob& J = lbt.job[jb];
+  const int K = J.K, nlb = J.lb, P = nlb + 1;
+  const int64_t line0 = ((int64_t)blockIdx.x - lbt.first[jb]) * nlb;
+  const int nl = (int)(J.L - line0 < nlb ? J.L - line0 : nlb);
+  double* xs = shd;             // [K][P] input lines
+  double* xf = shd + K * P;     // [K][P] folded
+  double* ms = xf + K * P;      // [K][P] scaled mode coefficients
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int idx = tid; idx < K * nlb; idx += nth) {
+    const int l = idx % nlb, j = idx / nlb;
+    xs[j * P + l] = l < nl ? J.X[line0 + l + J.L * j] : 0.0;
+  }
+  __syncthreads();
+  const int he = J.eo, h = K - he;
+  for (int idx = tid; idx < he * nlb; idx += nth) {
+    const int l = idx % nlb, k = idx / nlb;
+    if (k < h) {
+      const double a = xs[k * P + l], b = xs[(K - 1 - k) * P + l];
+      xf[k * P + l] = a + b;
+      xf[(he + k) * P + l] = a - b;
+    } else {
+      xf[k * P + l] = xs[k * P + l];
+    }
+  }
+  __syncthreads();
+  for (int q = tid; q < nlb * K; q += nth) {
+    const int l = q / K, i = q - l * K;
+    if (l >= nl) continue;
+    const int len = i < he ? he : h;
+    const double* xcol = xf + (i < he ? 0 : he * P) + l;
+    const double* op = J.U + i;
+    double acc = 0.0;
+    for (int k = 0; k < len; ++k) acc = fma(__ldg(op + (int64_t)k * K), xcol[k * P], acc);
+    double v = acc;
+    if (J.invd) {
+      v *= J.invd[line0 + l + J.L * i];
+    } else if (J.lam1) {
+      const int64_t line = line0 + l;
+      const int i1 = (int)(line % J.n1), i2 = (int)(line / J.n1);
+      v /= J.scale * (J.lam1[i1] + J.lam2[i2] + J.lam3[i]);
+    }
+    ms[i * P + l] = v;
+  }
+  __syncthreads();
+  for (int q = tid; q < nlb * he; q += nth) {
+    const int l = q / he, k = q - l * he;
+    if (l >= nl) continue;
+    const double* xcol = ms + l;
+    const double* row = J.U + (int64_t)k * K;
+    double ae = 0.0, ao = 0.0;
+    for (int j = 0; j < he; ++j) ae = fma(__ldg(row + j), xcol[j * P], ae);
+    double* y = J.Y + line0 + l;
+    if (k < h) {
+      for (int j = 0; j < h; ++j) ao = fma(__ldg(row + he + j), xcol[(he + j) * P], ao);
+      y[J.L * k] = (ae + ao) * J.post;
+      y[J.L * (K - 1 - k)] = (ae - ao) * J.post;
+    } else {
+      y[J.L * k] = ae * J.post;
+    }
+  }
+}
 }  // namespace
 
 template <>
@@ -437,6 +683,100 @@ void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStr
   launch_begin(kClassMode, s);
   launch_k(k_mode_tile, blocks, threads, smem, s, rb);
   launch_end(kClassMode, s, flops, bytes);
+}
+
+
+int fd_plane_smem(Dims in) {
+  const int64_t bytes = 2 * (int64_t)in.n1 * in.n2 * (int64_t)sizeof(double);
+  return bytes <= 200 * 1024 ? (int)bytes : 0;
+}
+
+namespace {
+double eo_flops(int K, int he) {
+  const double e = he, o = K - he;
+  return 2.0 * (e * e + o * o);
+}
+std::atomic<int> g_plane_attr{0};
+}  // namespace
+
+bool fd_plane_multi(const FdPlaneArgs* jobs, int njobs, int fwd, int block, int cluster,
+                    cudaStream_t s) {
+  PlaneBatch pb{};
+  pb.njobs = njobs;
+  pb.fwd = fwd;
+  int blocks = 0, smem = 0;
+  double flops = 0, bytes = 0;
+  for (int j = 0; j < njobs; ++j) {
+    const FdPlaneArgs& a = jobs[j];
+    PlaneJob& J = pb.job[j];
+    J.X = a.X;
+    J.Y = a.Y;
+    J.U1 = a.U1;
+    J.U2 = a.U2;
+    J.n1 = a.in.n1;
+    J.n2 = a.in.n2;
+    J.eo1 = a.eo1;
+    J.eo2 = a.eo2;
+    J.post = a.post;
+    pb.first[j] = blocks;
+    blocks += a.in.n3;
+    const int sm = fd_plane_smem(a.in);
+    if (sm == 0 || a.eo1 < 1 || a.eo2 < 1) return false;
+    smem = std::max(smem, sm);
+    flops += (double)a.in.n3 * (a.in.n2 * eo_flops(a.in.n1, a.eo1) + a.in.n1 * eo_flops(a.in.n2, a.eo2));
+    bytes += 2.0 * (double)a.in.size() * sizeof(double);
+  }
+  pb.first[njobs] = blocks;
+  if (cluster != 1 && cluster != 2 && cluster != 4) return false;
+  const int threads = block > 0 ? std::min(block, 512) : 512;
+  if (smem > 48 * 1024 && smem > g_plane_attr.load()) {
+    cudaFuncSetAttribute(k_fd_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    g_plane_attr.store(smem);
+  }
+  launch_begin(kClassMode, s);
+  launch_kc(k_fd_plane, blocks * cluster, threads, smem, s, cluster, pb);
+  launch_end(kClassMode, s, flops, bytes);
+  return true;
+}
+
+bool fd_line3_multi(const FdLineArgs* jobs, int njobs, int block, cudaStream_t s) {
+  LineBatch lbt{};
+  lbt.njobs = njobs;
+  const int target = block > 0 ? std::min(block, 512) : 512;
+  int64_t blocks = 0;
+  int smem = 0, threads = 32;
+  double flops = 0, bytes = 0;
+  for (int j = 0; j < njobs; ++j) {
+    const FdLineArgs& a = jobs[j];
+    LineJob& J = lbt.job[j];
+    J.X = a.X;
+    J.Y = a.Y;
+    J.U = a.U3;
+    J.L = (int64_t)a.in.n1 * a.in.n2;
+    J.K = a.in.n3;
+    J.eo = a.eo3;
+    J.lb = J.K >= target ? 1 : target / J.K;
+    J.n1 = a.in.n1;
+    J.invd = a.invd;
+    J.lam1 = a.invd ? nullptr : a.lam1;
+    J.lam2 = a.lam2;
+    J.lam3 = a.lam3;
+    J.scale = a.scale;
+    J.post = a.post;
+    if (a.eo3 < 1) return false;
+    lbt.first[j] = blocks;
+    blocks += (J.L + J.lb - 1) / J.lb;
+    smem = std::max(smem, 3 * J.K * (J.lb + 1) * (int)sizeof(double));
+    threads = std::max(threads, std::min(target, ((J.lb * J.K + 31) / 32) * 32));
+    flops += 2.0 * (double)J.L * eo_flops(J.K, J.eo);
+    bytes += 2.0 * (double)a.in.size() * sizeof(double);
+  }
+  lbt.first[njobs] = blocks;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_fd_line3, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  launch_begin(kClassMode, s);
+  launch_k(k_fd_line3, (int)blocks, threads, smem, s, lbt);
+  launch_end(kClassMode, s, flops, bytes);
+  return true;
 }
 
 template <typename T>

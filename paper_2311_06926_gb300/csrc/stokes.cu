@@ -27,6 +27,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -192,6 +193,8 @@ struct Ops {
   const T *U_N = nullptr, *lam_N = nullptr, *U_T = nullptr, *lam_T = nullptr;
   const T* invd = nullptr;   // FP64: 1 / (2 nu (l1 + l2 + l3)) per velocity entry
   int eo_N = 0, eo_T = 0;    // FP64: even-mode counts of the parity-split eigenvectors
+  int fd_fused = 0;          // FP64: fast diagonalisation by the fused plane / x3-line kernels,
+                             // with this many blocks per plane (0: six single-direction passes)
   const double* chol_lb = nullptr;     // FP64 pressure block: banded Cholesky factor of M-check
   const double* chol_inv = nullptr;
   int chol_p = 0;
@@ -420,6 +423,12 @@ struct Ops {
     }
   }
 
+  // fused FP64 fast diagonalisation: selected, and every plane fits in shared memory
+  bool fused_fd_ok() const {
+    return fd_fused && eo_N >= 1 && eo_T >= 1 && fd_plane_smem(Dims{a, b, b}) > 0 &&
+           fd_plane_smem(Dims{b, a, b}) > 0 && fd_plane_smem(Dims{b, b, b}) > 0;
+  }
+
   void fd_V(const T* x, T* y) const {
     if (tc) {
       // the three components share each of the six tensor-core launches
@@ -453,6 +462,29 @@ struct Ops {
         L[c][k] = own ? lam_N : lam_T;
         n[c][k] = own ? a : b;
       }
+    if constexpr (std::is_same<T, double>::value) {
+      if (fused_fd_ok()) {
+        // three launches: (x1, x2) per plane, (x3, scaling, x3) per line group, (x2, x1) per
+        // plane; the same bits as the six single-direction launches below
+        FdPlaneArgs pa[3];
+        FdLineArgs la[3];
+        for (int c = 0; c < 3; ++c) {
+          const int64_t o = c * nvc;
+          const int e[3] = {c == 0 ? eo_N : eo_T, c == 1 ? eo_N : eo_T, c == 2 ? eo_N : eo_T};
+          pa[c] = FdPlaneArgs{x + o, f1 + o, U[c][0], U[c][1], comp(c), e[0], e[1], 1.0};
+          la[c] = FdLineArgs{f1 + o, f2 + o, U[c][2], comp(c), e[2], invd ? invd + o : nullptr,
+                             L[c][0], L[c][1], L[c][2], 2 * nu, 1.0};
+        }
+        if (fd_plane_multi(pa, 3, 1, mode_block, fd_fused, s) && fd_line3_multi(la, 3, mode_block, s)) {
+          for (int c = 0; c < 3; ++c) {
+            pa[c].X = f2 + c * nvc;
+            pa[c].Y = y + c * nvc;
+          }
+          if (fd_plane_multi(pa, 3, 0, mode_block, fd_fused, s)) return;
+        }
+        throw CudaError{cudaErrorInvalidValue, "fused fast diagonalisation rejected its jobs"};
+      }
+    }
     ModeArgs<T> j[3];
     const T* src;
     T* dst;
@@ -504,6 +536,17 @@ struct Ops {
       return;
     }
     const Dims d{b, b, b};
+    if constexpr (std::is_same<T, double>::value) {
+      if (fused_fd_ok()) {
+        FdPlaneArgs pa{x, f1, U_T, U_T, d, eo_T, eo_T, 1.0};
+        FdLineArgs la{f1, f2, U_T, d, eo_T, nullptr, nullptr, nullptr, nullptr, 1.0, 1.0};
+        if (fd_plane_multi(&pa, 1, 1, mode_block, fd_fused, s) && fd_line3_multi(&la, 1, mode_block, s)) {
+          pa = FdPlaneArgs{f2, y, U_T, U_T, d, eo_T, eo_T, 2 * nu};
+          if (fd_plane_multi(&pa, 1, 0, mode_block, fd_fused, s)) return;
+        }
+        throw CudaError{cudaErrorInvalidValue, "fused fast diagonalisation rejected its jobs"};
+      }
+    }
     mode(x, f1, U_T, b, 1, d, 1, 1, eo_T);
     mode(f1, f2, U_T, b, 1, d, 2, 1, eo_T);
     mode(f2, f1, U_T, b, 1, d, 3, 1, eo_T);
@@ -1609,10 +1652,12 @@ struct OneItem {
 // only, never a result bit.
 constexpr int kModeBlocks[] = {128, 256, 512};
 constexpr int kBandBlocks[] = {128, 256, 512};
+constexpr int kFdFused[] = {0, 1, 2, 4};
 
-void set_shapes(stokes_ctx* c, int mode_block, int band_block) {
+void set_shapes(stokes_ctx* c, int mode_block, int band_block, int fd_fused) {
   c->od.mode_block = c->odq.mode_block = mode_block;
   c->od.band_block = c->odq.band_block = band_block;
+  c->od.fd_fused = c->odq.fd_fused = fd_fused;
   if (c->quad) c->quad->band_block = band_block;
   // captured graphs hold the previous launch shapes
   for (auto& kv : c->minres_graphs) cudaGraphExecDestroy(kv.second);
@@ -1686,16 +1731,23 @@ void autotune(stokes_ctx* c) {
     ck(cudaEventElapsedTime(&ms, e0, e1), "event");
     return ms;
   };
-  int best_mode = c->od.mode_block, best_band = c->od.band_block;
+  int best_mode = c->od.mode_block, best_band = c->od.band_block, best_fused = c->od.fd_fused;
   if (!reduced(c)) {
+    // FP64 fast diagonalisation: threads per block, six single-direction launches or three
+    // fused ones (identical bits)
     float best = 1e30f;
-    for (int mb : kModeBlocks) {
-      c->od.mode_block = mb;
-      const float t = time3([&] { c->od.fd_V(x, y); });
-      if (t < best) { best = t; best_mode = mb; }
+    for (int fused : kFdFused) {
+      c->od.fd_fused = fused;
+      if (fused && !c->od.fused_fd_ok()) continue;
+      for (int mb : kModeBlocks) {
+        c->od.mode_block = mb;
+        const float t = time3([&] { c->od.fd_V(x, y); });
+        if (t < best) { best = t; best_mode = mb; best_fused = fused; }
+      }
     }
   }
   c->od.mode_block = best_mode;
+  c->od.fd_fused = best_fused;
   {
     OneItem one(c->od);
     float best = 1e30f;
@@ -1708,7 +1760,7 @@ void autotune(stokes_ctx* c) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   check_launch("autotune");
-  set_shapes(c, best_mode, best_band);
+  set_shapes(c, best_mode, best_band, best_fused);
 }
 
 
@@ -2216,20 +2268,31 @@ int stokes_profile_end(stokes_t c, stokes_kernel_stat* out, int capacity) {
 
 int64_t stokes_kernel_launches(void) { return launch_count(); }
 
-int stokes_get_tuning(stokes_t c, int* mode_block, int* band_block) {
+int stokes_get_tuning(stokes_t c, int* mode_block, int* band_block, int* fd_fused) {
   if (!c) return STOKES_ERR_ARG;
   if (mode_block) *mode_block = c->od.mode_block;
   if (band_block) *band_block = c->od.band_block;
+  if (fd_fused) *fd_fused = c->od.fd_fused;
   return STOKES_OK;
 }
 
-int stokes_set_tuning(stokes_t c, int mode_block, int band_block) {
+int stokes_set_tuning(stokes_t c, int mode_block, int band_block, int fd_fused) {
   if (!c) return STOKES_ERR_ARG;
   bool ok_m = false, ok_b = false;
   for (int v : kModeBlocks) ok_m = ok_m || v == mode_block;
   for (int v : kBandBlocks) ok_b = ok_b || v == band_block;
   if (!ok_m || !ok_b) return fail(c, STOKES_ERR_ARG, "launch shape not among the candidates");
-  set_shapes(c, mode_block, band_block);
+  bool ok_f = false;
+  for (int v : kFdFused) ok_f = ok_f || v == fd_fused;
+  if (!ok_f) return fail(c, STOKES_ERR_ARG, "fd_fused must be 0, 1, 2 or 4");
+  if (fd_fused) {
+    const int keep = c->od.fd_fused;
+    c->od.fd_fused = fd_fused;
+    const bool ok = c->od.fused_fd_ok();
+    c->od.fd_fused = keep;
+    if (!ok) return fail(c, STOKES_ERR_ARG, "fused fast diagonalisation does not fit this mesh");
+  }
+  set_shapes(c, mode_block, band_block, fd_fused);
   return STOKES_OK;
 }
 

@@ -249,22 +249,49 @@ def test_launch_shapes_do_not_change_results(n, p):
     generic-width kernel."""
     S, base, Kop, F = oracle(n, p)
     G = _ctx(n, p, 1.0, autotune=False)
-    assert G.tuning() == (512, 256)
+    assert G.tuning() == (512, 256, 0)
     x = dev(synthetic.random_vector(S.size, 700 + n))
     ref_K, ref_H = G.apply_K(x), G.apply_hyperpower(2, 1, x)
+    ref_P = G.apply_P(x)
     G.set_preconditioner(2, 1)
     ref_x, ref_it, _, _ = G.solve(dev(S.rhs_lid(1.0)), 1e-8)
-    for mb in (128, 256, 512):
-        for bb in (128, 256, 512):
-            G.set_tuning(mb, bb)
-            assert G.tuning() == (mb, bb)
-            assert torch.equal(G.apply_K(x), ref_K)
-            assert torch.equal(G.apply_hyperpower(2, 1, x), ref_H)
-    xs, it, _, _ = G.solve(dev(S.rhs_lid(1.0)), 1e-8)
-    assert it == ref_it and torch.equal(xs, ref_x)
+    for ff in (0, 1, 2, 4):
+        for mb in (128, 256, 512):
+            for bb in (128, 256, 512):
+                G.set_tuning(mb, bb, ff)
+                assert G.tuning() == (mb, bb, ff)
+                assert torch.equal(G.apply_K(x), ref_K)
+                assert torch.equal(G.apply_P(x), ref_P)
+                assert torch.equal(G.apply_hyperpower(2, 1, x), ref_H)
+        xs, it, _, _ = G.solve(dev(S.rhs_lid(1.0)), 1e-8)
+        assert it == ref_it and torch.equal(xs, ref_x)
     with pytest.raises(Exception):
         G.set_tuning(300, 256)
+    with pytest.raises(Exception):
+        G.set_tuning(512, 256, 3)
     G.close()
     Ga = _ctx(n, p, 1.0)
     assert Ga.tuning()[0] in (128, 256, 512) and Ga.tuning()[1] in (128, 256, 512)
+    assert Ga.tuning()[2] in (0, 1, 2, 4)
     Ga.close()
+
+
+def test_fused_fast_diagonalisation_profile():
+    """The fused form launches three kernels per fast diagonalisation instead of six, and does
+    the same algorithmic work."""
+    G = _ctx(20, 3, 1.0, autotune=False)
+    x = torch.randn(G.size, dtype=torch.float64, device="cuda")
+    counts = {}
+    for ff in (0, 1, 2, 4):
+        G.set_tuning(512, 256, ff)
+        G.profile_begin()
+        y = G.apply_P(x)
+        counts[ff] = G.profile_end()["mode_product"]
+        if ff == 0:
+            ref = y
+        assert torch.equal(y, ref)
+    assert counts[0]["launches"] == 12
+    for ff in (1, 2, 4):
+        assert counts[ff]["launches"] == 6
+        assert counts[0]["flops"] == pytest.approx(counts[ff]["flops"], rel=1e-12)
+    G.close()
