@@ -35,21 +35,31 @@ FP64_PEAK_TFLOPS = 1.25
 TF32_NOMINAL_TFLOPS = 1100.0
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the
-# captured launches) of a dominant kernel class on a workload, from one ncu capture, with the
-# SHA-256 of the kernel's source file when it was taken. roofline.traffic reports it only while
-# that source is unchanged, and null otherwise.
+# captured launches) of a dominant kernel class on a workload and launch form, from one ncu
+# capture, with the SHA-256 of the kernel's source file when it was taken. roofline.traffic
+# reports it only while that source is unchanged, and null otherwise.
 TRAFFIC = {
-    ("mode_product", "fp64", "cavity32"): {
+    ("mode_product", "fp64", "cavity32", "per-direction"): {
         "bytes_per_launch": 1035634,
         "source": "k_dense.cu",
         "sha256": "d05c14c82b258149fb7e1b53760b0abff0cde9339623d5309a23fb8b03d0c98f",
         "profile": "profiles/k_mode_tile_fp64_cavity32.md"},
+    ("mode_product", "fp64", "cavity32", "fused, 4 block(s) per plane"): {
+        "bytes_per_launch": 1028521,
+        "source": "k_dense.cu",
+        "sha256": "94da514429a5fad0a6c6bbcbb7e11a28ae0745942ba63e28524ec4879f093a15",
+        "profile": "profiles/k_fd_plane_fp64_cavity32.md"},
 }
 
 
-def traffic_for(kernel_class, precision, workload):
+def fd_form(fd_fused):
+    """Launch form of the FP64 fast diagonalisation chosen by the library's setup tuner."""
+    return f"fused, {fd_fused} block(s) per plane" if fd_fused else "per-direction"
+
+
+def traffic_for(kernel_class, precision, workload, form="per-direction"):
     import hashlib
-    t = TRAFFIC.get((kernel_class, precision, workload))
+    t = TRAFFIC.get((kernel_class, precision, workload, form))
     if not t:
         return None, None
     src = os.path.join(ROOT, "paper_2311_06926_gb300", "csrc", t["source"])
@@ -469,6 +479,10 @@ def main():
                     help="kernel probe for ncu: only apply the order-2, 1-step hyper-power "
                          "preconditioner K times on the workload's mesh in --precision (no "
                          "Krylov bases, small device footprint); prints per-kernel-class times")
+    ap.add_argument("--tuning", default="auto",
+                    help="FP64 launch shapes mode_block,band_block,fd_fused (default: the "
+                         "library's setup tuner); for profiling runs, whose kernel replay "
+                         "distorts the tuner's timings")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.precision:
@@ -502,6 +516,8 @@ def main():
     max_steps = max(s for _, s in sweep)
     max_order = max(q for q, _ in sweep)
     G = Stokes(n, p, precision=prec, max_order=max_order, max_steps=max_steps)
+    if args.tuning != "auto":
+        G.set_tuning(*[int(v) for v in args.tuning.split(",")])
     stream = torch.cuda.current_stream()
     f = G.rhs_cavity(1.0)
     x = G.empty()
@@ -623,9 +639,12 @@ def main():
         torch.cuda.synchronize()
         ms_p = a.elapsed_time(b)
         achieved = one["flops"] * reps / (ms_p / 1e3) / 1e12
+        fused = G.tuning()[2]
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "k_mode_tile (mode_product class)",
+                "kernel": ("k_fd_plane + k_fd_line3 (mode_product class, fused fast "
+                           "diagonalisation)" if fused else "k_mode_tile (mode_product class)"),
+                "form": fd_form(fused),
                 "measurement": f"{reps} back-to-back P_0 applications ({one['launches']} mode-product "
                                f"launches each) between two CUDA events on the library stream",
                 "avg_launch_us": 1e3 * ms_p / (reps * max(one["launches"], 1)),
@@ -649,7 +668,7 @@ def main():
                 "launches_per_step": dom["launches"],
                 "avg_launch_us": 1e3 * dom["ms"] / max(dom["launches"], 1),
                 "peak_note": "of measured" if "hbm_gbs" in peaks else "of fallback"}
-    traffic, traffic_src = traffic_for(dom_name, prec, args.workload)
+    traffic, traffic_src = traffic_for(dom_name, prec, args.workload, fd_form(G.tuning()[2]))
     roof["traffic"] = traffic
     if traffic is not None:
         roof["traffic_source"] = traffic_src

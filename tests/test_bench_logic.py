@@ -8,7 +8,7 @@ import bench
 
 
 def test_traffic_reported_only_for_the_measured_source(monkeypatch):
-    key = ("mode_product", "fp64", "cavity32")
+    key = ("mode_product", "fp64", "cavity32", "per-direction")
     entry = dict(bench.TRAFFIC[key])
     src = os.path.join(bench.ROOT, "paper_2311_06926_gb300", "csrc", entry["source"])
     digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
@@ -19,6 +19,7 @@ def test_traffic_reported_only_for_the_measured_source(monkeypatch):
     monkeypatch.setitem(bench.TRAFFIC, key, dict(entry, sha256="0" * 64))
     assert bench.traffic_for(*key) == (None, None)
     assert bench.traffic_for("band_pass", "fp64", "cavity32") == (None, None)
+    assert bench.traffic_for(*key[:3], bench.fd_form(4)) == (None, None)
 
 
 def test_one_thread_oracle_sample():
