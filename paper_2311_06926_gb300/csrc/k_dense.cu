@@ -400,11 +400,19 @@ struct PlaneBatch {
   int fwd;
 };
 
-// One cluster of cs blocks per plane (cs = 1, 2, 4). Forward: block r loads and folds the x1 rows
-// of its slice, computes their x1 products and stores them into the plane buffer of every block
-// of the cluster; after the cluster barrier each block folds the whole intermediate along x2 and
-// computes its slice of the x2 outputs. Backward: block r takes a slice of the x1 columns for the
-// x2 products (stored to every block), then a slice of the rows for the x1 products.
+// Store v at the same shared-memory offset as p in block `rank` of this cluster.
+__device__ __forceinline__ void st_peer(const double* p, int rank, double v) {
+  const uint32_t local = (uint32_t)__cvta_generic_to_shared(p);
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(remote), "d"(v) : "memory");
+}
+
+// One cluster of cs blocks per plane (cs = 1, 2, 4). Forward: block r loads and folds the x1
+// rows of its slice, computes their x1 products and stores them into the plane buffer of every
+// block of the cluster; after the cluster barrier each block folds the whole intermediate along x2
+// and computes its slice of the x2 outputs. Backward: block r takes a slice of the x1 columns for
+// the x2 products (stored to every block), then a slice of the rows for the x1 products.
 __global__ void __launch_bounds__(512) k_fd_plane(const __grid_constant__ PlaneBatch pb) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
@@ -419,13 +427,6 @@ __global__ void __launch_bounds__(512) k_fd_plane(const __grid_constant__ PlaneB
   const int n1 = J.n1, n2 = J.n2, np = n1 * n2;
   double* B0 = shd;        // [n2][n1], x1 fastest
   double* B1 = shd + np;
-  double* peer0[4];
-  double* peer1[4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    peer0[t] = t >= cs ? nullptr : (t == rank ? B0 : cl.map_shared_rank(B0, t));
-    peer1[t] = t >= cs ? nullptr : (t == rank ? B1 : cl.map_shared_rank(B1, t));
-  }
   const int tid = threadIdx.x, nth = blockDim.x;
   const double* X = J.X + (int64_t)plane * np;
   double* Y = J.Y + (int64_t)plane * np;
@@ -458,9 +459,9 @@ __global__ void __launch_bounds__(512) k_fd_plane(const __grid_constant__ PlaneB
       const double* op = J.U1 + i1;
       double acc = 0.0;
       for (int k = 0; k < len; ++k) acc = fma(__ldg(op + k * n1), xr[k], acc);
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-        if (t < cs) peer0[t][j2 * n1 + i1] = acc;
+      B0[j2 * n1 + i1] = acc;
+      for (int t = 1, r = rank + 1; t < cs; ++t, ++r)
+        st_peer(B0 + j2 * n1 + i1, r < cs ? r : r - cs, acc);
     }
     if (cs > 1) cl.sync(); else __syncthreads();
     // fold every x2 column of the intermediate
@@ -503,16 +504,17 @@ __global__ void __launch_bounds__(512) k_fd_plane(const __grid_constant__ PlaneB
       if (k < h2) {
         for (int j = 0; j < h2; ++j) ao = fma(__ldg(row + he2 + j), xc[(he2 + j) * n1], ao);
         const double vp = ae + ao, vm = ae - ao;
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          if (t < cs) {
-            peer1[t][k * n1 + i1] = vp;
-            peer1[t][(n2 - 1 - k) * n1 + i1] = vm;
-          }
+        B1[k * n1 + i1] = vp;
+        B1[(n2 - 1 - k) * n1 + i1] = vm;
+        for (int t = 1, r = rank + 1; t < cs; ++t, ++r) {
+          const int rr = r < cs ? r : r - cs;
+          st_peer(B1 + k * n1 + i1, rr, vp);
+          st_peer(B1 + (n2 - 1 - k) * n1 + i1, rr, vm);
+        }
       } else {
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          if (t < cs) peer1[t][k * n1 + i1] = ae;
+        B1[k * n1 + i1] = ae;
+        for (int t = 1, r = rank + 1; t < cs; ++t, ++r)
+          st_peer(B1 + k * n1 + i1, r < cs ? r : r - cs, ae);
       }
     }
     if (cs > 1) cl.sync(); else __syncthreads();
@@ -723,7 +725,8 @@ bool fd_plane_multi(const FdPlaneArgs* jobs, int njobs, int fwd, int block, int 
     const int sm = fd_plane_smem(a.in);
     if (sm == 0 || a.eo1 < 1 || a.eo2 < 1) return false;
     smem = std::max(smem, sm);
-    flops += (double)a.in.n3 * (a.in.n2 * eo_flops(a.in.n1, a.eo1) + a.in.n1 * eo_flops(a.in.n2, a.eo2));
+    flops += (double)a.in.n3 *
+             (a.in.n2 * eo_flops(a.in.n1, a.eo1) + a.in.n1 * eo_flops(a.in.n2, a.eo2));
     bytes += 2.0 * (double)a.in.size() * sizeof(double);
   }
   pb.first[njobs] = blocks;
@@ -772,7 +775,8 @@ bool fd_line3_multi(const FdLineArgs* jobs, int njobs, int block, cudaStream_t s
     bytes += 2.0 * (double)a.in.size() * sizeof(double);
   }
   lbt.first[njobs] = blocks;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_fd_line3, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_fd_line3, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   launch_begin(kClassMode, s);
   launch_k(k_fd_line3, (int)blocks, threads, smem, s, lbt);
   launch_end(kClassMode, s, flops, bytes);
