@@ -216,20 +216,27 @@ int stokes_profile_end(stokes_t ctx, stokes_kernel_stat* out, int capacity);
  * of a captured CUDA graph are counted each time the graph is replayed, not when it is captured. */
 int64_t stokes_kernel_launches(void);
 
-/* Launch shapes of the FP64 kernels: mode_block, the threads per block of the fast-diagonalisation
- * mode products (128, 256 or 512); band_block, those of the banded passes (128, 256 or 512);
- * fd_fused, how the fast diagonalisation (App. A.4) is launched: 0 = six single-direction mode
- * products; 1, 2 or 4 = three fused launches (the x1 and x2 products of each x1-x2 plane in one
- * cluster of fd_fused blocks sharing the plane through distributed shared memory, the forward x3
- * product, eigenvalue scaling and backward x3 product of each line group in one block, then the
- * x2 and x1 products per plane); fused forms need every plane to fit in shared memory
- * (2 x n1 x n2 doubles <= 200 KiB, meshes up to about 110 elements per direction). Chosen at
- * setup by timing when stokes_opts.autotune is set, otherwise 512, 256 and 0. Every output is
- * computed by one thread in a fixed order whatever the choice, so results do not depend on it.
- * stokes_set_tuning rejects other values, and fd_fused = 1 on a mesh whose planes do not fit,
- * with STOKES_ERR_ARG. Null output pointers of stokes_get_tuning are skipped. */
-int stokes_get_tuning(stokes_t ctx, int* mode_block, int* band_block, int* fd_fused);
-int stokes_set_tuning(stokes_t ctx, int mode_block, int band_block, int fd_fused);
+/* Launch shapes of the FP64 kernels, chosen at setup by timing when stokes_opts.autotune is set,
+ * otherwise {512, 256, 0}:
+ *   mode_block: threads per block of the fast-diagonalisation mode products (128, 256 or 512);
+ *   band_block: threads per block of the banded passes (128, 256 or 512);
+ *   fd_fused:   how the fast diagonalisation (App. A.4) is launched: 0 = six single-direction
+ *               mode products; 1, 2 or 4 = three fused launches (the x1 and x2 products of each
+ *               x1-x2 plane in one cluster of fd_fused blocks sharing the plane through
+ *               distributed shared memory, the forward x3 product, eigenvalue scaling and
+ *               backward x3 product of each line group in one block, then the x2 and x1
+ *               products per plane); fused forms need every plane to fit in shared memory
+ *               (2 x n1 x n2 doubles <= 200 KiB, meshes up to about 110 elements per direction).
+ * Every output is computed by one thread in a fixed order whatever the choice, so results do not
+ * depend on it. stokes_set_tuning rejects other values, and a fused form on a mesh whose planes
+ * do not fit, with STOKES_ERR_ARG (the context keeps its shapes). */
+typedef struct stokes_tuning {
+  int mode_block;
+  int band_block;
+  int fd_fused;
+} stokes_tuning;
+int stokes_get_tuning(stokes_t ctx, stokes_tuning* out);
+int stokes_set_tuning(stokes_t ctx, const stokes_tuning* tuning);
 
 /* ---- allocation-free variant (no counterpart in the paper) --------------------------------
  * For callers that cannot allocate device memory (their allocator is owned by a framework or

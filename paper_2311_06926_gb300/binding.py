@@ -27,6 +27,11 @@ class StokesError(RuntimeError):
         self.code = code
 
 
+class _Tuning(ctypes.Structure):
+    _fields_ = [("mode_block", ctypes.c_int), ("band_block", ctypes.c_int),
+                ("fd_fused", ctypes.c_int)]
+
+
 class _Opts(ctypes.Structure):
     _fields_ = [("c_pen", ctypes.c_double), ("schur", ctypes.c_int), ("precision", ctypes.c_int),
                 ("solver", ctypes.c_int), ("max_order", ctypes.c_int), ("max_steps", ctypes.c_int),
@@ -82,8 +87,8 @@ def load_library(path=None):
         "stokes_profile_begin": (ctypes.c_int, [vp]),
         "stokes_profile_end": (ctypes.c_int, [vp, ctypes.POINTER(KernelStat), ctypes.c_int]),
         "stokes_kernel_launches": (ctypes.c_int64, []),
-        "stokes_get_tuning": (ctypes.c_int, [vp, ip, ip, ip]),
-        "stokes_set_tuning": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "stokes_get_tuning": (ctypes.c_int, [vp, ctypes.POINTER(_Tuning)]),
+        "stokes_set_tuning": (ctypes.c_int, [vp, ctypes.POINTER(_Tuning)]),
         "stokes_fd_apply_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
                                                    vp, vp, vp, vp, ctypes.c_double, vp, vp, vp]),
         "stokes_destroy": (None, [vp]),
@@ -218,17 +223,15 @@ class Stokes:
 
     # -- C ABI ----------------------------------------------------------------------------------
     def tuning(self):
-        """(mode_block, band_block, fd_fused): threads per block of the FP64 mode products and
-        banded passes, and whether the FP64 fast diagonalisation runs as three fused launches
-        (picked by the setup tuner unless autotune=False)."""
-        mb, bb, ff = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        self._check(self.lib.stokes_get_tuning(self.h, ctypes.byref(mb), ctypes.byref(bb),
-                                               ctypes.byref(ff)))
-        return mb.value, bb.value, ff.value
+        """(mode_block, band_block, fd_fused): FP64 launch shapes (stokes_tuning), picked by the
+        setup tuner unless autotune=False."""
+        t = _Tuning()
+        self._check(self.lib.stokes_get_tuning(self.h, ctypes.byref(t)))
+        return t.mode_block, t.band_block, t.fd_fused
 
     def set_tuning(self, mode_block, band_block, fd_fused=0):
-        self._check(self.lib.stokes_set_tuning(self.h, int(mode_block), int(band_block),
-                                               int(fd_fused)))
+        t = _Tuning(int(mode_block), int(band_block), int(fd_fused))
+        self._check(self.lib.stokes_set_tuning(self.h, ctypes.byref(t)))
 
     def set_preconditioner(self, order, steps):
         self._check(self.lib.stokes_set_preconditioner(self.h, order, steps))

@@ -1654,10 +1654,11 @@ constexpr int kModeBlocks[] = {128, 256, 512};
 constexpr int kBandBlocks[] = {128, 256, 512};
 constexpr int kFdFused[] = {0, 1, 2, 4};
 
-void set_shapes(stokes_ctx* c, int mode_block, int band_block, int fd_fused) {
-  c->od.mode_block = c->odq.mode_block = mode_block;
-  c->od.band_block = c->odq.band_block = band_block;
-  c->od.fd_fused = c->odq.fd_fused = fd_fused;
+void set_shapes(stokes_ctx* c, const stokes_tuning& t) {
+  c->od.mode_block = c->odq.mode_block = t.mode_block;
+  c->od.band_block = c->odq.band_block = t.band_block;
+  c->od.fd_fused = c->odq.fd_fused = t.fd_fused;
+  const int band_block = t.band_block;
   if (c->quad) c->quad->band_block = band_block;
   // captured graphs hold the previous launch shapes
   for (auto& kv : c->minres_graphs) cudaGraphExecDestroy(kv.second);
@@ -1760,7 +1761,7 @@ void autotune(stokes_ctx* c) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   check_launch("autotune");
-  set_shapes(c, best_mode, best_band, best_fused);
+  set_shapes(c, stokes_tuning{best_mode, best_band, best_fused});
 }
 
 
@@ -2268,31 +2269,30 @@ int stokes_profile_end(stokes_t c, stokes_kernel_stat* out, int capacity) {
 
 int64_t stokes_kernel_launches(void) { return launch_count(); }
 
-int stokes_get_tuning(stokes_t c, int* mode_block, int* band_block, int* fd_fused) {
-  if (!c) return STOKES_ERR_ARG;
-  if (mode_block) *mode_block = c->od.mode_block;
-  if (band_block) *band_block = c->od.band_block;
-  if (fd_fused) *fd_fused = c->od.fd_fused;
+int stokes_get_tuning(stokes_t c, stokes_tuning* out) {
+  if (!c || !out) return c ? fail(c, STOKES_ERR_ARG, "null tuning") : STOKES_ERR_ARG;
+  out->mode_block = c->od.mode_block;
+  out->band_block = c->od.band_block;
+  out->fd_fused = c->od.fd_fused;
   return STOKES_OK;
 }
 
-int stokes_set_tuning(stokes_t c, int mode_block, int band_block, int fd_fused) {
-  if (!c) return STOKES_ERR_ARG;
-  bool ok_m = false, ok_b = false;
-  for (int v : kModeBlocks) ok_m = ok_m || v == mode_block;
-  for (int v : kBandBlocks) ok_b = ok_b || v == band_block;
+int stokes_set_tuning(stokes_t c, const stokes_tuning* t) {
+  if (!c || !t) return c ? fail(c, STOKES_ERR_ARG, "null tuning") : STOKES_ERR_ARG;
+  bool ok_m = false, ok_b = false, ok_f = false;
+  for (int v : kModeBlocks) ok_m = ok_m || v == t->mode_block;
+  for (int v : kBandBlocks) ok_b = ok_b || v == t->band_block;
+  for (int v : kFdFused) ok_f = ok_f || v == t->fd_fused;
   if (!ok_m || !ok_b) return fail(c, STOKES_ERR_ARG, "launch shape not among the candidates");
-  bool ok_f = false;
-  for (int v : kFdFused) ok_f = ok_f || v == fd_fused;
   if (!ok_f) return fail(c, STOKES_ERR_ARG, "fd_fused must be 0, 1, 2 or 4");
-  if (fd_fused) {
+  if (t->fd_fused) {
     const int keep = c->od.fd_fused;
-    c->od.fd_fused = fd_fused;
+    c->od.fd_fused = t->fd_fused;
     const bool ok = c->od.fused_fd_ok();
     c->od.fd_fused = keep;
     if (!ok) return fail(c, STOKES_ERR_ARG, "fused fast diagonalisation does not fit this mesh");
   }
-  set_shapes(c, mode_block, band_block, fd_fused);
+  set_shapes(c, *t);
   return STOKES_OK;
 }
 
