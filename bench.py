@@ -45,9 +45,9 @@ TRAFFIC = {
         "sha256": "d05c14c82b258149fb7e1b53760b0abff0cde9339623d5309a23fb8b03d0c98f",
         "profile": "profiles/k_mode_tile_fp64_cavity32.md"},
     ("mode_product", "fp64", "cavity32", "fused, 4 block(s) per plane"): {
-        "bytes_per_launch": 1028521,
+        "bytes_per_launch": 1029907,
         "source": "k_dense.cu",
-        "sha256": "94da514429a5fad0a6c6bbcbb7e11a28ae0745942ba63e28524ec4879f093a15",
+        "sha256": "4bdce6c0c26605a867f9b8a90deed2a5cd68c39768b2aacd0e50c239ec9214dc",
         "profile": "profiles/k_fd_plane_fp64_cavity32.md"},
 }
 
@@ -200,18 +200,22 @@ def cpu_threads():
         return os.cpu_count()
 
 
-def oracle_sample(n, p, q, s, repeats):
-    """Time `repeats` oracle MINRES solves (the oracle as it stands)."""
+def oracle_sample(n, p, q, s, repeats, solution=False):
+    """Time `repeats` oracle MINRES solves (the oracle as it stands). With solution=True also
+    return the last solution, pressure normalised to zero mean."""
     from oracle.krylov import minres
     from oracle.precond import HyperPowerPreconditioner
     S, F, base = oracle_solver(n, p)
     f = S.rhs_lid(1.0)
     P = HyperPowerPreconditioner(base, q, s)
     t0 = time.perf_counter()
-    its = None
+    res = None
     for _ in range(repeats):
-        its = minres(F.apply_K, P, f, 1e-8).iterations
-    return time.perf_counter() - t0, its
+        res = minres(F.apply_K, P, f, 1e-8)
+    dt = time.perf_counter() - t0
+    if solution:
+        return dt, res.iterations, S.normalize_pressure(res.x)
+    return dt, res.iterations
 
 
 def oracle_sample_one_thread(n, p, q, s, repeats):
@@ -331,6 +335,28 @@ def table1_quadrature(Stokes, Gk, n, p, steps=(0, 1, 2, 3, 4), reps=20):
             "T_p_over_T_f": [round(t / tf_q, 3) for t in tp],
             "operator": "MINRES with the quadrature-based forward operator (Gauss, p + 2 points "
                         "per element and direction), FP64"}
+
+
+def class_rooflines(prof, step_ms, prec, peaks):
+    """Per kernel class of one profiled step: launches, time, share, and the achieved rate of its
+    algorithmic work against the bound of that class (FP64 pipe for FP64 band passes and mode
+    products, HBM for the rest). Times include the per-launch events of the profiled pass."""
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out = {}
+    for k, v in prof.items():
+        e = {"launches": v["launches"], "ms": round(v["ms"], 4),
+             "share": round(v["ms"] / step_ms, 4) if step_ms > 0 else 0.0}
+        if v["launches"] and v["ms"] > 0:
+            sec = v["ms"] / 1e3
+            if prec == "fp64" and k in ("band_pass", "mode_product"):
+                tf = v["flops"] / sec / 1e12
+                e.update(bound="fp64", achieved_tflops=round(tf, 4),
+                         frac=round(tf / FP64_PEAK_TFLOPS, 4))
+            else:
+                gbs = v["bytes"] / sec / 1e9
+                e.update(bound="hbm", achieved_gbs=round(gbs, 1), frac=round(gbs / hbm, 4))
+        out[k] = e
+    return out
 
 
 def run_probe(args, wl):
@@ -515,7 +541,11 @@ def main():
     prec = wl["precision"]
     max_steps = max(s for _, s in sweep)
     max_order = max(q for q, _ in sweep)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter()
     G = Stokes(n, p, precision=prec, max_order=max_order, max_steps=max_steps)
+    torch.cuda.synchronize()
+    setup_ms = 1e3 * (time.perf_counter() - t_setup)
     if args.tuning != "auto":
         G.set_tuning(*[int(v) for v in args.tuning.split(",")])
     stream = torch.cuda.current_stream()
@@ -712,9 +742,17 @@ def main():
         mixed = mixed_vs_fp64(Stokes, load_peaks() or {})
 
     cpu = None
+    vs_oracle = None
     if rank == 0 and not args.no_cpu_baseline:
         q, s = (2, 1) if (2, 1) in sweep else sweep[0]
-        dt, its = oracle_sample(n, p, q, s, 1)
+        dt, its, x_or = oracle_sample(n, p, q, s, 1, solution=True)
+        # the same solve on the GPU against the oracle's solution (both pressures zero-mean)
+        G.set_preconditioner(q, s)
+        xg, it_g, _, _ = G.solve(f, 1e-8, out=x)
+        xg = xg.cpu().numpy()
+        import numpy as np
+        vs_oracle = {"solve": f"order {q}, {s} step(s)", "iterations": [int(it_g), int(its)],
+                     "rel_err": float(np.linalg.norm(xg - x_or) / np.linalg.norm(x_or))}
         reps = max(1, min(20, int(15.0 / max(dt, 1e-3))))
         if reps > 1:
             dt, its = oracle_sample(n, p, q, s, reps)
@@ -744,9 +782,9 @@ def main():
             "table1_form": table1,
             "sweep_concurrent": sweep_conc,
             "roofline": roof,
-            "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
-                                   "share": round(v["ms"] / step_ms_profiled, 4)}
-                               for k, v in prof.items()},
+            "kernel_classes": class_rooflines(prof, step_ms_profiled, prec, peaks),
+            "setup_ms": round(setup_ms, 1),
+            "vs_oracle": vs_oracle,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "solves/s",
                     "h2d_bytes_per_step": bytes_per_solve * len(sweep),

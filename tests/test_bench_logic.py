@@ -27,3 +27,17 @@ def test_one_thread_oracle_sample():
     assert out is not None
     seconds, iterations = out
     assert seconds > 0 and iterations > 0
+
+
+def test_class_rooflines():
+    prof = {"mode_product": dict(launches=10, ms=2.0, flops=1.0e9, bytes=4.0e6),
+            "vector": dict(launches=4, ms=1.0, flops=0.0, bytes=6.678e9),
+            "line_solve": dict(launches=0, ms=0.0, flops=0.0, bytes=0.0)}
+    out = bench.class_rooflines(prof, 4.0, "fp64", {"hbm_gbs": 6678.0})
+    assert out["mode_product"]["bound"] == "fp64"
+    assert abs(out["mode_product"]["achieved_tflops"] - 0.5) < 1e-9
+    assert abs(out["mode_product"]["frac"] - 0.5 / bench.FP64_PEAK_TFLOPS) < 1e-4
+    assert out["vector"]["bound"] == "hbm" and abs(out["vector"]["frac"] - 1.0) < 1e-6
+    assert out["mode_product"]["share"] == 0.5 and "frac" not in out["line_solve"]
+    # reduced precision: every class against HBM
+    assert bench.class_rooflines(prof, 4.0, "tf32", {})["mode_product"]["bound"] == "hbm"
