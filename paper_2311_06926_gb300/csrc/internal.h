@@ -227,8 +227,10 @@ void chol_solve_axis(double* x, int b, int p, int axis, const double* lb, const 
 
 // ---- vector kernels (k_vec.cu) -----------------------------------------------------------
 // Deterministic dot product: fixed grid, fixed-order tree reduction. Result written to *out
-// (device). `partials` holds kDotBlocks values.
+// (device). `partials` holds kDotBlocks values and, in the word after them, a completion counter
+// that must be zero before the first call (each call leaves it zero); kDotScratch doubles.
 constexpr int kDotBlocks = 512;
+constexpr int kDotScratch = kDotBlocks + 2;
 // grid of the multi-vector dot products (fixed, so their reductions are deterministic)
 constexpr int kMultiDotBlocks = 152 * 4;   // one resident wave (4 blocks per SM)
 template <typename T>

@@ -44,6 +44,39 @@ __global__ void __launch_bounds__(kThreads) k_dot_partial(const T* __restrict__ 
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
+// The two stages in one launch: every block writes its partial sum, and the last block to finish
+// (a completion counter in the word after the kDotBlocks partials) sums the partials in the order
+// of k_dot_final and resets the counter. The result has the bits of the two-kernel form.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_dot_single(const T* __restrict__ x,
+                                                         const T* __restrict__ y, int64_t n,
+                                                         T* partials, T* __restrict__ out) {
+  pdl_begin();
+  __shared__ T sh[kThreads];
+  __shared__ int last;
+  T s = 0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads)
+    s += x[i] * y[i];
+  const T tot = block_sum(s, sh);
+  unsigned int* ctr = reinterpret_cast<unsigned int*>(partials + kDotBlocks);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = tot;
+    __threadfence();
+    last = atomicAdd(ctr, 1u) == gridDim.x - 1 ? 1 : 0;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  T s2 = 0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += kThreads) s2 += __ldcg(partials + i);
+  const T t2 = block_sum(s2, sh);
+  if (threadIdx.x == 0) {
+    *out = t2;
+    *ctr = 0u;
+  }
+}
+
 // Stage 2: one block sums the partials in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_dot_final(const T* __restrict__ partials, int np,
@@ -351,18 +384,15 @@ __global__ void k_minres_update(const double* __restrict__ z, double* __restrict
 template <typename T>
 void dot(const T* x, const T* y, int64_t n, T* partials, T* out, cudaStream_t s) {
   launch_begin(kClassVector, s);
-  launch_k(k_dot_partial<T>, kDotBlocks, kThreads, 0, s, x, y, n, partials);
-  launch_end(kClassVector, s, 0.0, 0.0);
-  launch_begin(kClassVector, s);
-  launch_k(k_dot_final<T>, 1, kThreads, 0, s, partials, kDotBlocks, out);
-  launch_end(kClassVector, s, 0.0, 0.0);
+  launch_k(k_dot_single<T>, kDotBlocks, kThreads, 0, s, x, y, n, partials, out);
+  launch_end(kClassVector, s, 2.0 * (double)n, 2.0 * (double)n * sizeof(T));
 }
 
 template <typename T>
 void axpby(T a, const T* x, T b, T* y, int64_t n, cudaStream_t s) {
   launch_begin(kClassVector, s);
   launch_k(k_axpby<T>, grid_for(n), kThreads, 0, s, a, x, b, y, n);
-  launch_end(kClassVector, s, 0.0, 0.0);
+  launch_end(kClassVector, s, 3.0 * (double)n, 3.0 * (double)n * sizeof(T));
 }
 
 template <typename T>
@@ -370,7 +400,7 @@ void hp_update(T* r, const T* u, T* acc, int64_t n, cudaStream_t s, int nb, int6
   if (nb < 1) nb = 1;
   launch_begin(kClassVector, s);
   launch_k(k_hp_update<T>, grid_for(n * nb), kThreads, 0, s, r, u, acc, n, nb, nb > 1 ? bs : n);
-  launch_end(kClassVector, s, 0.0, 0.0);
+  launch_end(kClassVector, s, 2.0 * (double)n * nb, 5.0 * (double)n * nb * sizeof(T));
 }
 
 template <typename T>
@@ -378,7 +408,7 @@ void hp_first(const T* x, const T* u, T* r, T* acc, int64_t n, cudaStream_t s, i
   if (nb < 1) nb = 1;
   launch_begin(kClassVector, s);
   launch_k(k_hp_first<T>, grid_for(n * nb), kThreads, 0, s, x, u, r, acc, n, nb, nb > 1 ? bs : n);
-  launch_end(kClassVector, s, 0.0, 0.0);
+  launch_end(kClassVector, s, 2.0 * (double)n * nb, 4.0 * (double)n * nb * sizeof(T));
 }
 
 void copy_async(void* dst, const void* src, size_t bytes, cudaStream_t s) {
@@ -399,24 +429,24 @@ void fill_zero(void* dst, size_t bytes, cudaStream_t s) { cudaMemsetAsync(dst, 0
 void to_float(const double* x, float* y, int64_t n, cudaStream_t s) {
   launch_begin(kClassVector, s);
   launch_k(k_to_float, grid_for(n), kThreads, 0, s, x, y, n);
-  launch_end(kClassVector, s, 0.0, 0.0);
+  launch_end(kClassVector, s, 0.0, 12.0 * (double)n);
 }
 void to_double(const float* x, double* y, int64_t n, cudaStream_t s) {
   launch_begin(kClassVector, s);
   launch_k(k_to_double, grid_for(n), kThreads, 0, s, x, y, n);
-  launch_end(kClassVector, s, 0.0, 0.0);
+  launch_end(kClassVector, s, 0.0, 12.0 * (double)n);
 }
 
 void axpy_dev(const double* alpha, double sign, const double* x, double* y, int64_t n,
               cudaStream_t s) {
   launch_begin(kClassVector, s);
   launch_k(k_axpy_dev, grid_for(n), kThreads, 0, s, alpha, sign, x, y, n);
-  launch_end(kClassVector, s, 0.0, 0.0);
+  launch_end(kClassVector, s, 2.0 * (double)n, 24.0 * (double)n);
 }
 void scale_inv_dev(const double* alpha, const double* x, double* y, int64_t n, cudaStream_t s) {
   launch_begin(kClassVector, s);
   launch_k(k_scale_inv_dev, grid_for(n), kThreads, 0, s, alpha, x, y, n);
-  launch_end(kClassVector, s, 0.0, 0.0);
+  launch_end(kClassVector, s, (double)n, 16.0 * (double)n);
 }
 void multi_dot(const double* V, int64_t ldv, int nvec, const double* w, int64_t n,
                double* partials, double* out, cudaStream_t s) {
@@ -452,13 +482,13 @@ void minres_init(MinresState* st, cudaStream_t s) { launch_begin(kClassVector, s
 void minres_scale_z(double* z, MinresState* st, int64_t n, cudaStream_t s) {
   launch_begin(kClassVector, s);
   launch_k(k_minres_scale_z, grid_for(n), kThreads, 0, s, z, st, n);
-  launch_end(kClassVector, s, 0.0, 0.0);
+  launch_end(kClassVector, s, (double)n, 16.0 * (double)n);
 }
 void minres_lanczos(const double* Kz, const double* v, double* vold, MinresState* st, int64_t n,
                     cudaStream_t s) {
   launch_begin(kClassVector, s);
   launch_k(k_minres_lanczos, grid_for(n), kThreads, 0, s, Kz, v, vold, st, n);
-  launch_end(kClassVector, s, 0.0, 0.0);
+  launch_end(kClassVector, s, 4.0 * (double)n, 32.0 * (double)n);
 }
 void minres_scalars(MinresState* st, cudaStream_t s) {
   launch_begin(kClassVector, s);
@@ -469,7 +499,7 @@ void minres_update(const double* z, double* wold, const double* w, double* x, Mi
                    int64_t n, cudaStream_t s) {
   launch_begin(kClassVector, s);
   launch_k(k_minres_update, grid_for(n), kThreads, 0, s, z, wold, w, x, st, n);
-  launch_end(kClassVector, s, 0.0, 0.0);
+  launch_end(kClassVector, s, 6.0 * (double)n, 48.0 * (double)n);
 }
 
 template void dot<double>(const double*, const double*, int64_t, double*, double*, cudaStream_t);

@@ -1321,9 +1321,9 @@ int run_fgmres(stokes_ctx* c, const double* f, double tol, double* x, int* iters
       double* Zj = c->Z + (int64_t)j * n;
       pk_apply(c, Vj, Zj, w);
       // CGS2: h = V^T w; w -= V h; h2 = V^T w; w -= V h2; h += h2
-      multi_dot(c->V, n, j + 1, w, n, c->partials, hdev, s);
+      multi_dot(c->V, n, j + 1, w, n, c->partials + kDotScratch, hdev, s);
       multi_axpy(c->V, n, j + 1, hdev, -1.0, w, n, s);
-      multi_dot(c->V, n, j + 1, w, n, c->partials, h2dev, s);
+      multi_dot(c->V, n, j + 1, w, n, c->partials + kDotScratch, h2dev, s);
       multi_axpy(c->V, n, j + 1, h2dev, -1.0, w, n, s);
       dot<double>(w, w, n, c->partials, c->dsc + 6, s);
       check_launch("fgmres arnoldi");
@@ -1478,9 +1478,9 @@ void run_fgmres_multi(stokes_ctx* c, const double* f, double tol, double* x, int
         double* h2dev = dsc(k) + 8 + (m + 2);
         double* wk = w + k * n;
         const double* Vk = c->V + k * n;
-        multi_dot(Vk, N, j + 1, wk, n, c->partials, hdev, s);
+        multi_dot(Vk, N, j + 1, wk, n, c->partials + kDotScratch, hdev, s);
         multi_axpy(Vk, N, j + 1, hdev, -1.0, wk, n, s);
-        multi_dot(Vk, N, j + 1, wk, n, c->partials, h2dev, s);
+        multi_dot(Vk, N, j + 1, wk, n, c->partials + kDotScratch, h2dev, s);
         multi_axpy(Vk, N, j + 1, h2dev, -1.0, wk, n, s);
         dot<double>(wk, wk, n, c->partials, dsc(k) + 6, s);
       }
@@ -1926,7 +1926,10 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
           z[(size_t)i + (size_t)b * (j + (size_t)b * k)] = u.const_M[i] * u.const_M[j] * u.const_M[k];
     c->zconst = upload<double>(c->arena, z, c->stream);
     c->ones = upload<double>(c->arena, one, c->stream);
-    c->partials = c->arena.alloc<double>((size_t)std::max(kDotBlocks, kMultiDotBlocks) * (o.restart + 2));
+    // dot scratch (partials and completion counter), then the Gram-Schmidt partials
+    c->partials = c->arena.alloc<double>((size_t)kDotScratch +
+                                         (size_t)kMultiDotBlocks * (o.restart + 2));
+    fill_zero(c->partials, kDotScratch * sizeof(double), c->stream);
     c->dsc = c->arena.alloc<double>((size_t)c->nb * (16 + 2 * (o.restart + 2)));
     c->st = c->arena.alloc<MinresState>(1);
     ck(cudaMallocHost(&c->st_host, sizeof(MinresState)), "pinned");

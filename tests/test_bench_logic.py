@@ -19,7 +19,7 @@ def test_traffic_reported_only_for_the_measured_source(monkeypatch):
     monkeypatch.setitem(bench.TRAFFIC, key, dict(entry, sha256="0" * 64))
     assert bench.traffic_for(*key) == (None, None)
     assert bench.traffic_for("band_pass", "fp64", "cavity32") == (None, None)
-    assert bench.traffic_for(*key[:3], bench.fd_form(4)) == (None, None)
+    assert bench.traffic_for(*key[:3], bench.fd_form(2)) == (None, None)   # no capture of that form
 
 
 def test_one_thread_oracle_sample():
