@@ -1899,7 +1899,11 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
     const Ops<double>* odq = nullptr;
     if (!reduced(c)) {
       // FP64 preconditioner: the pressure recursion gets its own operator set and stream
-      ck(cudaStreamCreateWithFlags(&c->stream_q, cudaStreamNonBlocking), "stream");
+      // the pressure branch is the longer chain at two or more steps: its blocks go first when
+      // both branches have work ready
+      int prio_lo = 0, prio_hi = 0;
+      ck(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi), "priority range");
+      ck(cudaStreamCreateWithPriority(&c->stream_q, cudaStreamNonBlocking, prio_hi), "stream");
       c->odq = c->od;
       c->odq.s = c->stream_q;
       alloc_workspace<double>(c, c->odq);
