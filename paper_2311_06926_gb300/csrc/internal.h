@@ -1,7 +1,10 @@
 // Internal interfaces shared by the CUDA translation units of the library.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <cstdint>
+#include <mutex>
 
 namespace shp {
 
@@ -32,6 +35,19 @@ inline void launch_k(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, c
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` when that is above the 48 KiB default
+// and above every value set so far for it (`cache`). Several host threads may launch at once
+// (concurrent contexts), so the check and the attribute call are serialised.
+template <typename K>
+inline void raise_smem_limit(K kernel, std::atomic<int>& cache, int bytes) {
+  if (bytes <= 48 * 1024 || bytes <= cache.load()) return;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (bytes <= cache.load()) return;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cache.store(bytes);
 }
 
 // The same with a thread-block cluster of cluster_x blocks along x (grid.x a multiple of it).

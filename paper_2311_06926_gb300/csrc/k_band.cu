@@ -737,11 +737,8 @@ void chol_solve_axis(double* x, int b, int p, int axis, const double* lb, const 
                      double post, cudaStream_t s) {
   const int64_t lines = (int64_t)b * b;
   const int smem = b * (kCholLines + 1) * (int)sizeof(double);
-  static int attr = 0;
-  if (smem > 48 * 1024 && smem > attr) {
-    cudaFuncSetAttribute(k_chol_line, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr = smem;
-  }
+  static std::atomic<int> attr{0};
+  raise_smem_limit(k_chol_line, attr, smem);
   launch_begin(kClassLine, s);
   launch_k(k_chol_line, (unsigned)((lines + kCholLines - 1) / kCholLines), kCholLines, smem, s, 
       x, b, p, axis, lb, inv_diag, post);
@@ -847,14 +844,9 @@ void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {
     switch (Wc) {
 #define SHP_SLIDE_W(w)                                                                          \
   case w: {                                                                                     \
-    static int attr = 0;                                                                        \
-    if (smem_c > 48 * 1024 && smem_c > attr) {                                                  \
-      cudaFuncSetAttribute(k_band_slide<w, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                           smem_c);                                                             \
-      cudaFuncSetAttribute(k_band_slide<w, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                           smem_c);                                                             \
-      attr = smem_c;                                                                            \
-    }                                                                                           \
+    static std::atomic<int> attr0{0}, attr1{0};                                                 \
+    raise_smem_limit(k_band_slide<w, false>, attr0, smem_c);                                    \
+    raise_smem_limit(k_band_slide<w, true>, attr1, smem_c);                                     \
     if (has_g) launch_k(k_band_slide<w, true>, blocks, 256, smem_c, s, pb);                      \
     else launch_k(k_band_slide<w, false>, blocks, 256, smem_c, s, pb);                          \
     break;                                                                                      \
@@ -905,22 +897,16 @@ void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {
   switch (W) {
 #define SHP_TILE_W(w)                                                                         \
   case w: {                                                                                   \
-    static int attr = 0;                                                                      \
-    if (smem > 48 * 1024 && smem > attr) {                                                    \
-      cudaFuncSetAttribute(k_band_tile<w>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
-      attr = smem;                                                                            \
-    }                                                                                         \
+    static std::atomic<int> attr{0};                                                          \
+    raise_smem_limit(k_band_tile<w>, attr, smem);                                             \
     launch_k(k_band_tile<w>, blocks, 256, smem, s, pb);                                             \
     break;                                                                                    \
   }
     SHP_TILE_W(3) SHP_TILE_W(5) SHP_TILE_W(7) SHP_TILE_W(9) SHP_TILE_W(11) SHP_TILE_W(13)
     SHP_TILE_W(15) SHP_TILE_W(17) SHP_TILE_W(19) SHP_TILE_W(21)
     default: {
-      static int attr = 0;
-      if (smem > 48 * 1024 && smem > attr) {
-        cudaFuncSetAttribute(k_band_tile<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = smem;
-      }
+      static std::atomic<int> attr{0};
+      raise_smem_limit(k_band_tile<0>, attr, smem);
       launch_k(k_band_tile<0>, blocks, 256, smem, s, pb);
     }
 #undef SHP_TILE_W
@@ -983,12 +969,8 @@ void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s) {
   switch (W) {
 #define SHP_PASS_W(w)                                                                     \
   case w: {                                                                               \
-    static int attr = 0;                                                                  \
-    if (smem > 48 * 1024 && smem > attr) {                                                \
-      cudaFuncSetAttribute(k_band_pass<T, w>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                           smem);                                                         \
-      attr = smem;                                                                        \
-    }                                                                                     \
+    static std::atomic<int> attr{0};                                                      \
+    raise_smem_limit(k_band_pass<T, w>, attr, smem);                                      \
     launch_k(k_band_pass<T, w>, blocks, bt, smem, s, pb);                                       \
     break;                                                                                \
   }

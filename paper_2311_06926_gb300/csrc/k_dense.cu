@@ -159,21 +159,15 @@ GemmArgs<T> make_gemm(const ModeArgs<T>& m) {
   return g;
 }
 
-// ---- FP64: row-streaming mode products ---------------------------------------------------------
+// ---- FP64 mode products ------------------------------------------------------------------------
 // GB300 executes about two FP64 FMA per clock per SM, so an FP64 mode product is bound by the
-// FP64 pipe on every mesh size. Each thread owns one output line position and kRowsPerThread
-// consecutive output indices i (independent accumulators hide the FMA latency), streams the
-// contracted line of X through the read-only cache and reads Op(i, j) from it as well (a warp
-// shares its i range, so those loads broadcast). Extents are used exactly: no padded tiles.
-constexpr int kRowsPerThread = 8;   // upper bound of the outputs per thread
-
+// FP64 pipe on every mesh size. Extents are used exactly: no padded tiles.
 struct RowJob {
   const double* X; double* Y; const double* U;
   int64_t op_i, op_j;      // Op(i, j) = U[i * op_i + j * op_j]
   int64_t L;               // product of the extents before the contracted direction
-  int K, m, groups;        // contracted extent, output extent, ceil(m / MI)
+  int K, m, groups;        // contracted extent, output extent, lines per block
   int64_t R;               // product of the extents after it
-  int64_t threads;         // L * groups * R
   const double* invd;      // optional multiplier per output entry
   const double *lam1, *lam2, *lam3;   // otherwise optional eigenvalue-sum divisor
   double scale;
@@ -187,68 +181,7 @@ struct RowBatch {
   RowJob job[kMaxModeJobs];
   int64_t first[kMaxModeJobs + 1];   // first block of each job
   int njobs;
-  int isplit;                        // blocks sharing one line tile (each takes a range of i)
 };
-
-template <int MI>
-__global__ void __launch_bounds__(128) k_mode_rows(const __grid_constant__ RowBatch rb) {
-  pdl_begin();
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= rb.first[rb.njobs]) return;
-  int jb = 0;
-  while (jb + 1 < rb.njobs && t >= rb.first[jb + 1]) ++jb;
-  const RowJob& J = rb.job[jb];
-  int64_t u = t - rb.first[jb];
-  // l fastest, then the i group, then r: a warp shares (group, r) when L >= 32 (coalesced X,
-  // broadcast Op); for L = 1 consecutive threads take consecutive groups of one r.
-  const int64_t l = u % J.L;
-  u /= J.L;
-  const int g = (int)(u % J.groups);
-  const int64_t r = u / J.groups;
-  const int i0 = g * MI;
-  const double* x = J.X + l + J.L * (int64_t)J.K * r;
-  double acc[MI];
-#pragma unroll
-  for (int k = 0; k < MI; ++k) acc[k] = 0.0;
-  const double* op = J.U + i0 * J.op_i;
-  if (i0 + MI <= J.m) {
-    for (int j = 0; j < J.K; ++j) {
-      const double xv = __ldg(x + J.L * j);
-      const double* o = op + j * J.op_j;
-#pragma unroll
-      for (int k = 0; k < MI; ++k) acc[k] = fma(__ldg(o + k * J.op_i), xv, acc[k]);
-    }
-  } else {
-    const int cnt = J.m - i0;
-    for (int j = 0; j < J.K; ++j) {
-      const double xv = __ldg(x + J.L * j);
-      const double* o = op + j * J.op_j;
-#pragma unroll
-      for (int k = 0; k < MI; ++k)
-        if (k < cnt) acc[k] = fma(__ldg(o + k * J.op_i), xv, acc[k]);
-    }
-  }
-  double* y = J.Y + l + J.L * (int64_t)J.m * r;
-#pragma unroll
-  for (int k = 0; k < MI; ++k) {
-    const int i = i0 + k;
-    if (i < J.m) {
-      const int64_t off = J.L * (int64_t)i;
-      double v = acc[k];
-      const int64_t o = l + off + J.L * (int64_t)J.m * r;
-      if (J.invd) {
-        v *= J.invd[o];
-      } else if (J.lam1) {
-        const int i1 = (int)(o % J.out.n1);
-        const int64_t t2 = o / J.out.n1;
-        v /= J.scale * (J.lam1[i1] + J.lam2[(int)(t2 % J.out.n2)] + J.lam3[(int)(t2 / J.out.n2)]);
-      } else {
-        v *= J.post;
-      }
-      y[off] = v;
-    }
-  }
-}
 
 // Shared-memory staged FP64 variant. GB300's FP64 pipe reaches its rate only with many resident
 // warps, so every thread computes exactly one output (line, i): a block owns lb neighbouring lines
@@ -650,7 +583,6 @@ void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStr
     // threads per line: one per output, or one per mirrored output pair (even/odd backward)
     const int tpl = (J.eo && !J.fwd) ? J.eo : m.m;
     J.groups = tpl >= target ? 1 : target / tpl;  // lines per block
-    J.threads = 0;
     J.invd = m.invd;
     J.lam1 = m.invd ? nullptr : m.lam1;
     J.lam2 = m.lam2;
@@ -676,12 +608,8 @@ void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStr
   }
   first_block[njobs] = blocks;
   for (int j = 0; j <= njobs; ++j) rb.first[j] = first_block[j];
-  rb.isplit = 1;
-  static int attr = 0;
-  if (smem > 48 * 1024 && smem > attr) {
-    cudaFuncSetAttribute(k_mode_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr = smem;
-  }
+  static std::atomic<int> attr{0};
+  raise_smem_limit(k_mode_tile, attr, smem);
   launch_begin(kClassMode, s);
   launch_k(k_mode_tile, blocks, threads, smem, s, rb);
   launch_end(kClassMode, s, flops, bytes);
@@ -732,10 +660,7 @@ bool fd_plane_multi(const FdPlaneArgs* jobs, int njobs, int fwd, int block, int 
   pb.first[njobs] = blocks;
   if (cluster != 1 && cluster != 2 && cluster != 4) return false;
   const int threads = block > 0 ? std::min(block, 512) : 512;
-  if (smem > 48 * 1024 && smem > g_plane_attr.load()) {
-    cudaFuncSetAttribute(k_fd_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    g_plane_attr.store(smem);
-  }
+  raise_smem_limit(k_fd_plane, g_plane_attr, smem);
   launch_begin(kClassMode, s);
   launch_kc(k_fd_plane, blocks * cluster, threads, smem, s, cluster, pb);
   launch_end(kClassMode, s, flops, bytes);
@@ -775,8 +700,8 @@ bool fd_line3_multi(const FdLineArgs* jobs, int njobs, int block, cudaStream_t s
     bytes += 2.0 * (double)a.in.size() * sizeof(double);
   }
   lbt.first[njobs] = blocks;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_fd_line3, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  static std::atomic<int> attr{0};
+  raise_smem_limit(k_fd_line3, attr, smem);
   launch_begin(kClassMode, s);
   launch_k(k_fd_line3, (int)blocks, threads, smem, s, lbt);
   launch_end(kClassMode, s, flops, bytes);

@@ -479,11 +479,8 @@ void launch_rmp_t(const RmpPlan* const* plans, int njobs, int* err, int sms, cud
   b.total_tiles = tiles;
   const int grid = tiles < sms ? tiles : sms;
   if (smem < 116 * 1024) smem = 116 * 1024;   // one CTA, one 512-column TMEM allocation per SM
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_rmp<KIND, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    attr_set = true;
-  }
+  static std::atomic<int> attr{0};
+  raise_smem_limit(k_rmp<KIND, TO>, attr, 220 * 1024);
   launch_begin(kClassMma, s);
   launch_k(k_rmp<KIND, TO>, grid, kThreads, smem, s, b, err);
   launch_end(kClassMma, s, flops, bytes);
