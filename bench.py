@@ -45,9 +45,9 @@ TRAFFIC = {
         "sha256": "d05c14c82b258149fb7e1b53760b0abff0cde9339623d5309a23fb8b03d0c98f",
         "profile": "profiles/k_mode_tile_fp64_cavity32.md"},
     ("mode_product", "fp64", "cavity32", "fused, 4 block(s) per plane"): {
-        "bytes_per_launch": 1029907,
+        "bytes_per_launch": 1029976,
         "source": "k_dense.cu",
-        "sha256": "4bdce6c0c26605a867f9b8a90deed2a5cd68c39768b2aacd0e50c239ec9214dc",
+        "sha256": "d9a3689312a3e5696df3815780d87a617cf85647bdf288b2d115eee5be5668d5",
         "profile": "profiles/k_fd_plane_fp64_cavity32.md"},
 }
 
