@@ -235,6 +235,12 @@ bool fd_plane_multi(const FdPlaneArgs* jobs, int njobs, int fwd, int block, int 
                     cudaStream_t s);
 bool fd_line3_multi(const FdLineArgs* jobs, int njobs, int block, cudaStream_t s);
 
+// delta = D_div u (and e = nu delta + q when q is set) and their band pass along x1 in one launch:
+// y0 = D .x1 delta, y1 = D .x1 e on the (b, b, b) pressure grid (FP64 contexts, one item).
+template <typename T>
+void div_band_x1(const T* u1, const T* u2, const T* u3, int a, int b, const T* q, T nu,
+                 const BandD<T>& D, T* y0, T* y1, cudaStream_t s);
+
 // In-place banded Cholesky solves along one direction of a (b, b, b) tensor: x <- post (L L^T)^-1 x
 // with L lower triangular of bandwidth p stored as rows lb[i * (p + 1) + (k - i + p)] for
 // k in [i - p, i], and inv_diag[i] = 1 / L[i][i] (pressure mass inverse, FP64 path).

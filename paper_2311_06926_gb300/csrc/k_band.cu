@@ -625,7 +625,71 @@ __global__ void __launch_bounds__(256) k_divergence(const T* __restrict__ u1, co
       if (i3 >= 1) d -= u3[off + (int64_t)b * b * (i3 - 1)];
     }
     delta[kb + o] = d;
-    if (e) e[kb + o] = nu * d + q[kb + o];
+    if (e) e[kb + o] = fma(nu, d, q[kb + o]);
+  }
+}
+
+// The divergence and the first pressure-mass pass in one launch (FP64 A and K applies): a block
+// owns lpb whole x1 lines of the pressure grid, forms delta (and e = nu delta + q when q is set)
+// on them in shared memory with the operations of k_divergence, and applies the band D along x1
+// with the two partial sums of the flat x1 pass: y0 = D .x1 delta, y1 = D .x1 e.
+template <typename T>
+__global__ void __launch_bounds__(512) k_div_band_x1(const T* __restrict__ u1,
+                                                     const T* __restrict__ u2,
+                                                     const T* __restrict__ u3, int a, int b,
+                                                     const T* __restrict__ q, T nu,
+                                                     const __grid_constant__ BandD<T> D, int lpb,
+                                                     T* __restrict__ y0, T* __restrict__ y1) {
+  pdl_begin();
+  extern __shared__ __align__(16) unsigned char div_smem[];
+  T* sd = reinterpret_cast<T*>(div_smem);   // [lpb][b]: delta
+  T* se = sd + lpb * b;                     // [lpb][b]: e
+  const int lines = b * b;
+  const int t = threadIdx.x;
+  const int l = t / b, i1 = t - l * b;
+  const int line = blockIdx.x * lpb + l;
+  const bool active = l < lpb && line < lines;
+  if (active) {
+    const int i2 = line % b, i3 = line / b;
+    T d = 0;
+    {
+      const int64_t row = (int64_t)a * (i2 + (int64_t)b * i3);
+      if (i1 < a) d += u1[row + i1];
+      if (i1 >= 1) d -= u1[row + i1 - 1];
+    }
+    {
+      const int64_t off = i1 + (int64_t)b * a * i3;
+      if (i2 < a) d += u2[off + (int64_t)b * i2];
+      if (i2 >= 1) d -= u2[off + (int64_t)b * (i2 - 1)];
+    }
+    {
+      const int64_t off = i1 + (int64_t)b * i2;
+      if (i3 < a) d += u3[off + (int64_t)b * b * i3];
+      if (i3 >= 1) d -= u3[off + (int64_t)b * b * (i3 - 1)];
+    }
+    sd[l * b + i1] = d;
+    if (q) se[l * b + i1] = fma(nu, d, q[(int64_t)line * b + i1]);
+  }
+  __syncthreads();
+  if (!active) return;
+  const int W = D.width;
+  const T* cv = D.val + (int64_t)i1 * W;
+  const int s0i = __ldg(D.start + i1);
+  const T* xd = sd + l * b + s0i;
+  T s0 = 0, s1 = 0;
+  for (int w = 0; w < W; ++w) {
+    if (w % 2 == 0) s0 = fma(__ldg(cv + w), xd[w], s0);
+    else s1 = fma(__ldg(cv + w), xd[w], s1);
+  }
+  y0[(int64_t)line * b + i1] = T(1) * (s0 + s1);
+  if (q) {
+    const T* xe = se + l * b + s0i;
+    T e0 = 0, e1 = 0;
+    for (int w = 0; w < W; ++w) {
+      if (w % 2 == 0) e0 = fma(__ldg(cv + w), xe[w], e0);
+      else e1 = fma(__ldg(cv + w), xe[w], e1);
+    }
+    y1[(int64_t)line * b + i1] = T(1) * (e0 + e1);
   }
 }
 
@@ -998,6 +1062,22 @@ void divergence(const T* u1, const T* u2, const T* u3, int a, int b, T* delta, c
 }
 
 template <typename T>
+void div_band_x1(const T* u1, const T* u2, const T* u3, int a, int b, const T* q, T nu,
+                 const BandD<T>& D, T* y0, T* y1, cudaStream_t s) {
+  const int lpb = b >= 512 ? 1 : 512 / b;       // whole lines per block
+  const int threads = ((lpb * b + 31) / 32) * 32;
+  const int blocks = (b * b + lpb - 1) / lpb;
+  const int smem = (q ? 2 : 1) * lpb * b * (int)sizeof(T);
+  static std::atomic<int> attr{0};
+  raise_smem_limit(k_div_band_x1<T>, attr, smem);
+  const double np = (double)b * b * b;
+  launch_begin(kClassDiv, s);
+  launch_k(k_div_band_x1<T>, blocks, threads, smem, s, u1, u2, u3, a, b, q, nu, D, lpb, y0, y1);
+  launch_end(kClassDiv, s, (q ? 8.0 : 6.0) * np + (q ? 4.0 : 2.0) * D.width * np,
+             (3.0 * a * b * b + (q ? 3.0 : 1.0) * np) * sizeof(T));
+}
+
+template <typename T>
 void divergence_plus(const T* u1, const T* u2, const T* u3, int a, int b, T* delta, const T* q,
                      T nu, T* e, cudaStream_t s, int nb, int64_t bs) {
   if (nb < 1) nb = 1;
@@ -1055,6 +1135,9 @@ void quad_stress(double* G, double* P, const double* w, int nq, double nu, cudaS
   launch_end(kClassDiv, s, 40.0 * n3, 20.0 * n3 * sizeof(double));
 }
 
+template void div_band_x1<double>(const double*, const double*, const double*, int, int,
+                                  const double*, double, const BandD<double>&, double*, double*,
+                                  cudaStream_t);
 template void band_pass<double>(const PassArgs<double>&, cudaStream_t);
 template void band_pass<float>(const PassArgs<float>&, cudaStream_t);
 template void band_pass_multi<double>(const PassArgs<double>*, int, cudaStream_t);

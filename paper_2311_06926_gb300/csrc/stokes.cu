@@ -268,9 +268,12 @@ struct Ops {
   // the same launches: their passes along x1 and x2 ride with the first two velocity passes (the
   // x1 pass with Mc_w, M-check padded with zeros to the width of K and M, so that every job of a
   // launch has one band width), their pass along x3 runs alone, then the last velocity pass.
+  // x1_done: the inputs qx already carry the pass along x1 (div_band_x1); their passes along x2
+  // (with Mc_w) and x3 then ride with the first and second velocity passes, and no pressure-mass
+  // launch of its own remains.
   void adiag_all(const T* u, T* y, const T* g, int nq = 0, const T* const* qx = nullptr,
                  T* const* qy = nullptr, const T* qcoef = nullptr,
-                 const Horner<T>* h = nullptr) const {
+                 const Horner<T>* h = nullptr, bool x1_done = false) const {
     const T nu2 = 2 * nu;
     const Dims dq{b, b, b};
     PassArgs<T> j[kMaxPassJobs];
@@ -280,7 +283,8 @@ struct Ops {
       j[2 * c + 1] = job(u + o, M, 1, nullptr, nullptr, 0, comp(c), own_axis(c), tM + o);
     }
     for (int k = 0; k < nq; ++k)
-      j[6 + k] = job(qx[k], Mc_w, 1, nullptr, nullptr, 0, dq, 1, f1 + k * npres);
+      j[6 + k] = x1_done ? job(qx[k], Mc_w, 1, nullptr, nullptr, 0, dq, 2, f2 + k * npres)
+                         : job(qx[k], Mc_w, 1, nullptr, nullptr, 0, dq, 1, f1 + k * npres);
     band_pass_multi<T>(j, 6 + nq, s);
     for (int c = 0; c < 3; ++c) {
       const int64_t o = c * nvc;
@@ -288,9 +292,11 @@ struct Ops {
       j[2 * c + 1] = job(tM + o, Mc, 1, nullptr, nullptr, 0, comp(c), first_other(c), tR + o);
     }
     for (int k = 0; k < nq; ++k)
-      j[6 + k] = job(f1 + k * npres, Mc, 1, nullptr, nullptr, 0, dq, 2, f2 + k * npres);
+      j[6 + k] = x1_done
+                     ? job(f2 + k * npres, Mc, qcoef[k], nullptr, nullptr, 0, dq, 3, qy[k])
+                     : job(f1 + k * npres, Mc, 1, nullptr, nullptr, 0, dq, 2, f2 + k * npres);
     band_pass_multi<T>(j, 6 + nq, s);
-    if (nq > 0) {
+    if (nq > 0 && !x1_done) {
       for (int k = 0; k < nq; ++k)
         j[k] = job(f2 + k * npres, Mc, qcoef[k], nullptr, nullptr, 0, dq, 3, qy[k]);
       band_pass_multi<T>(j, nq, s);
@@ -306,13 +312,16 @@ struct Ops {
 
   // y_k = coef_k M_q x_k for nvec <= 2 independent vectors (M_q = M-check^(x)3); h: Horner step
   // applied to the (single) result
+  // x1_done: the pass along x1 has already been applied, its results are in f1 + k npres.
   void mq(int nvec, const T* const* x, T* const* y, const T* coef,
-          const Horner<T>* h = nullptr) const {
+          const Horner<T>* h = nullptr, bool x1_done = false) const {
     const Dims d{b, b, b};
     PassArgs<T> j[2];
-    for (int k = 0; k < nvec; ++k)
-      j[k] = job(x[k], Mc, 1, nullptr, nullptr, 0, d, 1, f1 + k * npres);
-    band_pass_multi<T>(j, nvec, s);
+    if (!x1_done) {
+      for (int k = 0; k < nvec; ++k)
+        j[k] = job(x[k], Mc, 1, nullptr, nullptr, 0, d, 1, f1 + k * npres);
+      band_pass_multi<T>(j, nvec, s);
+    }
     for (int k = 0; k < nvec; ++k)
       j[k] = job(f1 + k * npres, Mc, 1, nullptr, nullptr, 0, d, 2, f2 + k * npres);
     band_pass_multi<T>(j, nvec, s);
@@ -323,9 +332,25 @@ struct Ops {
     band_pass_multi<T>(j, nvec, s);
   }
 
+  // FP64, one item: the divergence and the pressure-mass pass along x1 fused (div_band_x1), so
+  // an A or K apply takes four launches
+  bool fused_div() const {
+    return std::is_same<T, double>::value && nb == 1 && Mc_w.val != nullptr && b <= 512;
+  }
+
   void apply_K(const T* x, T* y) const {
     const T* q = x + nvel;
     T* yq = y + nvel;
+    if constexpr (std::is_same<T, double>::value) {
+      if (fused_div()) {
+        div_band_x1<T>(x, x + nvc, x + 2 * nvc, a, b, q, nu, Mc_w, f1, f1 + npres, s);
+        const T* in2[2] = {f1, f1 + npres};
+        T* out2[2] = {yq, m2};
+        const T coef2[2] = {1, 1};
+        adiag_all(x, y, m2, 2, in2, out2, coef2, nullptr, true);
+        return;
+      }
+    }
     // delta = D_div u, e = nu delta + q; B^T u = M_q delta; g = M_q e
     divergence_plus<T>(x, x + nvc, x + 2 * nvc, a, b, delta, q, nu, m1, s, nb, bs);
     const T* in[2] = {delta, m1};
@@ -341,6 +366,16 @@ struct Ops {
 
   // y = A x; with h, the Horner step of h is applied to A x instead (y is scratch then)
   void apply_A(const T* x, T* y, const Horner<T>* h = nullptr) const {
+    if constexpr (std::is_same<T, double>::value) {
+      if (fused_div()) {
+        div_band_x1<T>(x, x + nvc, x + 2 * nvc, a, b, nullptr, nu, Mc_w, f1, nullptr, s);
+        const T* in1[1] = {f1};
+        T* out1[1] = {m2};
+        const T coef1[1] = {nu};
+        adiag_all(x, y, m2, 1, in1, out1, coef1, h, true);
+        return;
+      }
+    }
     divergence<T>(x, x + nvc, x + 2 * nvc, a, b, delta, s, nb, bs);
     const T* in[1] = {delta};
     T* out[1] = {m2};
@@ -378,10 +413,19 @@ struct Ops {
 
   // B^T u = M_q D_div u; with h, the Horner step of h is applied to it instead
   void apply_Bt(const T* u, T* yq, const Horner<T>* h = nullptr) const {
-    divergence<T>(u, u + nvc, u + 2 * nvc, a, b, delta, s, nb, bs);
-    const T* in[1] = {delta};
     T* out[1] = {yq};
     const T coef[1] = {1};
+    if constexpr (std::is_same<T, double>::value) {
+      if (nb == 1 && b <= 512) {
+        // the divergence and the pass along x1 in one launch (the same bits as two)
+        div_band_x1<T>(u, u + nvc, u + 2 * nvc, a, b, nullptr, nu, Mc, f1, nullptr, s);
+        const T* in1[1] = {f1};
+        mq(1, in1, out, coef, h, true);
+        return;
+      }
+    }
+    divergence<T>(u, u + nvc, u + 2 * nvc, a, b, delta, s, nb, bs);
+    const T* in[1] = {delta};
     mq(1, in, out, coef, h);
   }
 
