@@ -1064,7 +1064,8 @@ void divergence(const T* u1, const T* u2, const T* u3, int a, int b, T* delta, c
 template <typename T>
 void div_band_x1(const T* u1, const T* u2, const T* u3, int a, int b, const T* q, T nu,
                  const BandD<T>& D, T* y0, T* y1, cudaStream_t s) {
-  const int lpb = b >= 512 ? 1 : 512 / b;       // whole lines per block
+  // whole lines per block, about 256 threads, so that the b^2 lines spread over every SM
+  const int lpb = b >= 256 ? 1 : 256 / b;
   const int threads = ((lpb * b + 31) / 32) * 32;
   const int blocks = (b * b + lpb - 1) / lpb;
   const int smem = (q ? 2 : 1) * lpb * b * (int)sizeof(T);
