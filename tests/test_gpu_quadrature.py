@@ -18,7 +18,7 @@ def _ctx(n, p, nu=1.0, **kw):
 
 
 @pytest.mark.parametrize("n,p,nu", [(1, 1, 1.0), (2, 1, 0.7), (3, 2, 1.0), (4, 3, 2.5),
-                                    (6, 2, 1.0), (9, 3, 1.0), (5, 4, 0.4)])
+                                    (6, 2, 1.0), (9, 3, 1.0), (5, 4, 0.4), (32, 3, 1.0)])
 def test_quadrature_operator_equals_kronecker_and_oracle(n, p, nu):
     S, base, Kop, F = oracle(n, p, nu)
     Gk = _ctx(n, p, nu)
@@ -59,3 +59,20 @@ def test_quadrature_forward_options():
     from paper_2311_06926_gb300 import StokesError
     with pytest.raises(StokesError):
         _ctx(4, 2, precision="tf32", nrhs=2, forward="quadrature")
+
+
+def test_quadrature_forward_solve_at_32():
+    """The Table-1 workload's mesh (32^3, p = 3), order 2, 1 step: the quadrature-forward MINRES
+    solve takes the Kronecker solve's iterations and reaches its solution."""
+    n, p = 32, 3
+    Gk = _ctx(n, p)
+    Gq = _ctx(n, p, forward="quadrature")
+    f = Gk.rhs_cavity(1.0)
+    for G in (Gk, Gq):
+        G.set_preconditioner(2, 1)
+    xk, itk, rrk, _ = Gk.solve(f, 1e-8)
+    xq, itq, rrq, _ = Gq.solve(f.clone(), 1e-8)
+    assert abs(itq - itk) <= 1 and rrq < 1e-7
+    assert relerr(host(xq), host(xk)) < 1e-7
+    Gk.close()
+    Gq.close()
