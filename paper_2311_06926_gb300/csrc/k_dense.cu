@@ -634,11 +634,14 @@ bool fd_plane_multi(const FdPlaneArgs* jobs, int njobs, int fwd, int block, int 
   PlaneBatch pb{};
   pb.njobs = njobs;
   pb.fwd = fwd;
-  int blocks = 0, smem = 0;
+  int blocks = 0, smem = 0, work = 32;
   double flops = 0, bytes = 0;
   for (int j = 0; j < njobs; ++j) {
     const FdPlaneArgs& a = jobs[j];
     PlaneJob& J = pb.job[j];
+    // outputs (forward) or mirrored pairs (backward) of one block's slice in its larger pass
+    const int rows = (a.in.n2 + cluster - 1) / cluster, cols = (a.in.n1 + cluster - 1) / cluster;
+    work = std::max(work, fwd ? rows * a.in.n1 : std::max(a.eo2 * cols, rows * a.eo1));
     J.X = a.X;
     J.Y = a.Y;
     J.U1 = a.U1;
@@ -659,7 +662,11 @@ bool fd_plane_multi(const FdPlaneArgs* jobs, int njobs, int fwd, int block, int 
   }
   pb.first[njobs] = blocks;
   if (cluster != 1 && cluster != 2 && cluster != 4) return false;
-  const int threads = block > 0 ? std::min(block, 512) : 512;
+  // one thread per output of the block's slice (whole warps, at most 512), so every pass is a
+  // single round of dot products; with more blocks per plane than the tuned size, block caps it
+  const int cap = block > 0 ? std::min(block, 512) : 512;
+  const int fit = std::min(512, (work + 31) / 32 * 32);
+  const int threads = cluster > 1 ? fit : std::min(cap, fit);
   raise_smem_limit(k_fd_plane, g_plane_attr, smem);
   launch_begin(kClassMode, s);
   launch_kc(k_fd_plane, blocks * cluster, threads, smem, s, cluster, pb);
