@@ -45,9 +45,9 @@ TRAFFIC = {
         "sha256": "d05c14c82b258149fb7e1b53760b0abff0cde9339623d5309a23fb8b03d0c98f",
         "profile": "profiles/k_mode_tile_fp64_cavity32.md"},
     ("mode_product", "fp64", "cavity32", "fused, 4 block(s) per plane"): {
-        "bytes_per_launch": 1029976,
+        "bytes_per_launch": 1029889,
         "source": "k_dense.cu",
-        "sha256": "d9a3689312a3e5696df3815780d87a617cf85647bdf288b2d115eee5be5668d5",
+        "sha256": "61e438359185f0bf02457abbb4b35a9d25bc8bf38ee72e6c89be7a2bce8c995e",
         "profile": "profiles/k_fd_plane_fp64_cavity32.md"},
 }
 
