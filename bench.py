@@ -337,6 +337,48 @@ def table1_quadrature(Stokes, Gk, n, p, steps=(0, 1, 2, 3, 4), reps=20):
                         "per element and direction), FP64"}
 
 
+def other_mesh_baselines(Stokes):
+    """The oracle beside the GPU on two more cavity solves (order 2, 1 step, FP64 MINRES to 1e-8):
+    8^3 p=2, a full oracle solve; 64^3 p=3, a bounded sample of oracle MINRES iterations whose
+    per-iteration time is scaled to the GPU's iteration count."""
+    import torch
+    from oracle.krylov import minres
+    from oracle.precond import HyperPowerPreconditioner
+    out = []
+    for n, p, sample_its in [(8, 2, None), (64, 3, 10)]:
+        G = Stokes(n, p, max_order=2, max_steps=1)
+        G.set_preconditioner(2, 1)
+        f = G.rhs_cavity(1.0)
+        x = G.empty()
+        G.solve(f, 1e-8, out=x)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        _, it_g, rr_g, _ = G.solve(f, 1e-8, out=x)
+        b.record()
+        torch.cuda.synchronize()
+        gpu_ms = a.elapsed_time(b)
+        G.close()
+        S, F, base = oracle_solver(n, p)
+        P = HyperPowerPreconditioner(base, 2, 1)
+        fo = S.rhs_lid(1.0)
+        t0 = time.perf_counter()
+        res = minres(F.apply_K, P, fo, 1e-8, maxiter=sample_its or 1000)
+        dt = time.perf_counter() - t0
+        if sample_its:
+            ms = 1e3 * dt / res.iterations * it_g
+            sample = (f"{res.iterations} oracle MINRES iterations timed, {1e3 * dt / res.iterations:.0f} "
+                      f"ms each, scaled to the GPU's {it_g}")
+        else:
+            ms = 1e3 * dt
+            sample = f"one full oracle solve, {res.iterations} iterations"
+        out.append({"mesh": f"{n}^3 p={p}", "gpu_ms": round(gpu_ms, 3), "gpu_iterations": it_g,
+                    "oracle_ms": round(ms, 1), "oracle_iterations": res.iterations,
+                    "cores": cpu_threads(), "sample": sample,
+                    "gpu_speedup": round(ms / gpu_ms, 1)})
+    return out
+
+
 def class_rooflines(prof, step_ms, prec, peaks):
     """Per kernel class of one profiled step: launches, time, share, and the achieved rate of its
     algorithmic work against the bound of that class (FP64 pipe for FP64 band passes and mode
@@ -766,6 +808,7 @@ def main():
         cpu["one_thread"] = ({"value": reps1 / one[0], "unit": "solves/s", "cores": 1,
                               "sample": f"{reps1} solve(s) as above, BLAS/OpenMP with one thread"}
                              if one else None)
+        cpu["other_meshes"] = other_mesh_baselines(Stokes)
 
     if rank == 0:
         line = {
