@@ -379,6 +379,68 @@ def other_mesh_baselines(Stokes):
     return out
 
 
+def adjoint_timing(Stokes, n=64, p=3):
+    """Differentiation on the 64^3, p = 3 cavity (order 2, 1 step, tolerance 1e-8): J = 1/2 |u -
+    u_t|^2_M and its gradient with respect to 16 lid-profile coefficients, 3 x 8 body-force
+    coefficients and nu through the autograd function whose backward is the adjoint solve; one
+    forward + backward pass timed with CUDA events after an untimed one."""
+    import numpy as np
+    import torch
+    from paper_2311_06926_gb300 import synthetic
+    from paper_2311_06926_gb300.adjoint import cavity_solve, mass_misfit
+    G = Stokes(n, p, max_order=2, max_steps=1)
+    G.set_preconditioner(2, 1)
+    theta = np.random.default_rng(3).uniform(0.5, 1.5, 16)
+    coef, waves = synthetic.forcing_modes(3, n_modes=8)
+    ut = torch.from_numpy(synthetic.random_vector(G.n_vel, 1000) * 0.01).cuda()
+
+    def once():
+        th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+        cf = torch.tensor(coef, dtype=torch.float64, requires_grad=True)
+        nu_t = torch.tensor(G.nu, dtype=torch.float64, requires_grad=True)
+        x = cavity_solve(G, th, cf, nu_t, waves, 1e-8)
+        J = mass_misfit(G, x, ut)
+        J.backward()
+        return th.grad.numel() + cf.grad.numel() + 1
+
+    once()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    entries = once()
+    b.record()
+    torch.cuda.synchronize()
+    G.close()
+    return {"workload": f"{n}^3 p={p} cavity, lid profile + body force, order 2, 1 step, tol 1e-8",
+            "ms_per_gradient": round(a.elapsed_time(b), 2), "gradient_entries": entries,
+            "what": "forward solve, adjoint solve and the gradient's inner products"}
+
+
+def schur_variants(Stokes, n=32, p=3):
+    """The pressure-block sequence with inner updates (Eq. 4.5, the sweep's) and without (Eq. 4.6):
+    MINRES iterations and solve time of the cavity at order 2, steps 1-3."""
+    import torch
+    out = {}
+    for schur in ("inner", "none"):
+        G = Stokes(n, p, schur=schur, max_order=2, max_steps=3)
+        f = G.rhs_cavity(1.0)
+        x = G.empty()
+        rows = []
+        for steps in (1, 2, 3):
+            G.set_preconditioner(2, steps)
+            G.solve(f, 1e-8, out=x)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            _, it, rr, _ = G.solve(f, 1e-8, out=x)
+            b.record()
+            torch.cuda.synchronize()
+            rows.append({"steps": steps, "iterations": it, "ms": round(a.elapsed_time(b), 2)})
+        out["eq_4_5_inner_updates" if schur == "inner" else "eq_4_6_no_inner_updates"] = rows
+        G.close()
+    return out
+
+
 def class_rooflines(prof, step_ms, prec, peaks):
     """Per kernel class of one profiled step: launches, time, share, and the achieved rate of its
     algorithmic work against the bound of that class (FP64 pipe for FP64 band passes and mode
@@ -782,6 +844,10 @@ def main():
     mixed = None
     if not args.no_mixed:
         mixed = mixed_vs_fp64(Stokes, load_peaks() or {})
+    adjoint = schur = None
+    if args.workload == "cavity32" and ws == 1:
+        adjoint = adjoint_timing(Stokes)
+        schur = schur_variants(Stokes)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -836,6 +902,8 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clocks,
             "mixed_vs_fp64": mixed,
+            "adjoint": adjoint,
+            "schur_variants": schur,
         }
         print(json.dumps(line), flush=True)
     G.close()

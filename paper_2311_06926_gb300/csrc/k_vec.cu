@@ -77,6 +77,21 @@ __global__ void __launch_bounds__(kThreads) k_dot_single(const T* __restrict__ x
   }
 }
 
+// dst[i1 + e1 (i2 + e2 i3)] += cf l2[i2] l3[i3] l1[i1]: one rank-one term of a separable load.
+__global__ void k_outer3_acc(const double* __restrict__ l1, const double* __restrict__ l2,
+                             const double* __restrict__ l3, double cf, double* __restrict__ dst,
+                             int e1, int e2, int e3) {
+  pdl_begin();
+  const int64_t total = (int64_t)e1 * e2 * e3;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = t / e1;
+    const int i1 = (int)(t - q * e1), i2 = (int)(q % e2), i3 = (int)(q / e2);
+    const double s23 = __dmul_rn(__dmul_rn(cf, l2[i2]), l3[i3]);
+    dst[t] = __dadd_rn(dst[t], __dmul_rn(s23, l1[i1]));
+  }
+}
+
 // Stage 2: one block sums the partials in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_dot_final(const T* __restrict__ partials, int np,
@@ -474,6 +489,14 @@ void multi_axpy(const double* V, int64_t ldv, int nvec, const double* h, double 
   launch_begin(kClassVector, s);
   launch_k(k_multi_axpy, grid_for(n), kThreads, 0, s, V, ldv, nvec, h, sign, w, n);
   launch_end(kClassVector, s, 2.0 * nvec * (double)n, 8.0 * (double)n * (nvec + 2));
+}
+
+void outer3_acc(const double* l1, const double* l2, const double* l3, double cf, double* dst,
+                int e1, int e2, int e3, cudaStream_t s) {
+  const int64_t total = (int64_t)e1 * e2 * e3;
+  launch_begin(kClassVector, s);
+  launch_k(k_outer3_acc, grid_for(total), kThreads, 0, s, l1, l2, l3, cf, dst, e1, e2, e3);
+  launch_end(kClassVector, s, 4.0 * (double)total, 16.0 * (double)total);
 }
 
 void minres_init(MinresState* st, cudaStream_t s) { launch_begin(kClassVector, s);

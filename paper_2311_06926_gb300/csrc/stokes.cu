@@ -837,6 +837,7 @@ struct stokes_ctx {
   HyperPower<float> hf;
   float *xf = nullptr, *yf = nullptr;    // reduced-precision preconditioner in/out
   double *zconst = nullptr, *ones = nullptr, *partials = nullptr, *dsc = nullptr;
+  double* load1d = nullptr;              // three 1D factors of a separable load, 3 (b + 1)
   MinresState* st = nullptr;
   MinresState* st_host = nullptr;
   double* pinned = nullptr;              // small pinned host scratch
@@ -1978,6 +1979,7 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
     c->partials = c->arena.alloc<double>((size_t)kDotScratch +
                                          (size_t)kMultiDotBlocks * (o.restart + 2));
     fill_zero(c->partials, kDotScratch * sizeof(double), c->stream);
+    c->load1d = c->arena.alloc<double>(3 * (size_t)(c->b + 1));
     c->dsc = c->arena.alloc<double>((size_t)c->nb * (16 + 2 * (o.restart + 2)));
     c->st = c->arena.alloc<MinresState>(1);
     ck(cudaMallocHost(&c->st_host, sizeof(MinresState)), "pinned");
@@ -2103,29 +2105,33 @@ int stokes_rhs_body(stokes_t c, int n_modes, const double* coef, const int* wave
   for (int i = 0; i < 9 * n_modes; ++i)
     if (waves[i] < 1 || waves[i] > 64) return fail(c, STOKES_ERR_ARG, "wave numbers in [1, 64]");
   const Univariate& u = c->uv;
-  std::vector<double> host((size_t)c->nvel, 0.0);
-  for (int comp = 0; comp < 3; ++comp) {
-    const int e1 = comp == 0 ? c->a : c->b, e2 = comp == 1 ? c->a : c->b;
-    const int e3 = comp == 2 ? c->a : c->b;
-    double* dst = host.data() + (size_t)comp * c->nvc;
-    for (int m = 0; m < n_modes; ++m) {
-      const double cf = coef[comp * n_modes + m];
-      const int* k = waves + (size_t)(comp * n_modes + m) * 3;
-      std::vector<double> l1 = comp == 0 ? sine_load_N(u, k[0]) : sine_load_M(u, k[0]);
-      std::vector<double> l2 = comp == 1 ? sine_load_N(u, k[1]) : sine_load_M(u, k[1]);
-      std::vector<double> l3 = comp == 2 ? sine_load_N(u, k[2]) : sine_load_M(u, k[2]);
-      for (int i3 = 0; i3 < e3; ++i3)
-        for (int i2 = 0; i2 < e2; ++i2) {
-          const double s23 = cf * l2[i2] * l3[i3];
-          double* row = dst + (size_t)e1 * (i2 + (size_t)e2 * i3);
-          for (int i1 = 0; i1 < e1; ++i1) row[i1] += s23 * l1[i1];
-        }
-    }
-  }
   try {
+    // each mode's load is separable: its three 1D sine loads are formed on the host and their
+    // outer product is accumulated on the device (modes with a zero coefficient are skipped)
     double* tmp = c->kv[7];
-    ck(cudaMemcpyAsync(tmp, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice,
-                       c->stream), "rhs upload");
+    fill_zero(tmp, c->nvel * sizeof(double), c->stream);
+    const int ld = c->b + 1;
+    std::vector<double> l(3 * (size_t)ld);
+    for (int comp = 0; comp < 3; ++comp) {
+      const int e1 = comp == 0 ? c->a : c->b, e2 = comp == 1 ? c->a : c->b;
+      const int e3 = comp == 2 ? c->a : c->b;
+      for (int m = 0; m < n_modes; ++m) {
+        const double cf = coef[comp * n_modes + m];
+        if (cf == 0.0) continue;
+        const int* k = waves + (size_t)(comp * n_modes + m) * 3;
+        const std::vector<double> l1 = comp == 0 ? sine_load_N(u, k[0]) : sine_load_M(u, k[0]);
+        const std::vector<double> l2 = comp == 1 ? sine_load_N(u, k[1]) : sine_load_M(u, k[1]);
+        const std::vector<double> l3 = comp == 2 ? sine_load_N(u, k[2]) : sine_load_M(u, k[2]);
+        std::copy(l1.begin(), l1.end(), l.begin());
+        std::copy(l2.begin(), l2.end(), l.begin() + ld);
+        std::copy(l3.begin(), l3.end(), l.begin() + 2 * ld);
+        // pageable source: the call returns once the host buffer has been read
+        ck(cudaMemcpyAsync(c->load1d, l.data(), l.size() * sizeof(double), cudaMemcpyHostToDevice,
+                           c->stream), "load upload");
+        outer3_acc(c->load1d, c->load1d + ld, c->load1d + 2 * ld, cf, tmp + comp * c->nvc, e1, e2,
+                   e3, c->stream);
+      }
+    }
     if (accumulate) {
       axpby<double>(1.0, tmp, 1.0, f, c->nvel, c->stream);
     } else {
@@ -2152,17 +2158,20 @@ int stokes_rhs_lid_profile(stokes_t c, int ncoef, const double* theta, int accum
   for (int i = 0; i < c->a; ++i)
     for (int k = 0; k < ncoef; ++k) P[i] += G(i, k) * theta[k];
   const double alpha = c->c_pen / u.h;
-  std::vector<double> f1((size_t)c->nvc);
-  for (int i3 = 0; i3 < c->b; ++i3)
-    for (int i2 = 0; i2 < c->b; ++i2) {
-      const double g2 = c->nu * (2.0 * alpha * u.M_at_1[i2] - u.dM_at_1[i2]);
-      for (int i1 = 0; i1 < c->a; ++i1)
-        f1[(size_t)i1 + (size_t)c->a * (i2 + (size_t)c->b * i3)] = g2 * P[i1];
-    }
   try {
+    // rank one: f1 = P (x) g2 (x) 1, its outer product formed on the device
+    const int ld = c->b + 1;
+    std::vector<double> l(3 * (size_t)ld, 0.0);
+    for (int i1 = 0; i1 < c->a; ++i1) l[i1] = P[i1];
+    for (int i2 = 0; i2 < c->b; ++i2)
+      l[ld + i2] = c->nu * (2.0 * alpha * u.M_at_1[i2] - u.dM_at_1[i2]);
+    for (int i3 = 0; i3 < c->b; ++i3) l[2 * ld + i3] = 1.0;
     double* tmp = c->kv[7];
-    ck(cudaMemcpyAsync(tmp, f1.data(), f1.size() * sizeof(double), cudaMemcpyHostToDevice,
-                       c->stream), "rhs upload");
+    fill_zero(tmp, c->nvc * sizeof(double), c->stream);
+    ck(cudaMemcpyAsync(c->load1d, l.data(), l.size() * sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream), "load upload");
+    outer3_acc(c->load1d, c->load1d + ld, c->load1d + 2 * ld, 1.0, tmp, c->a, c->b, c->b,
+               c->stream);
     if (accumulate) {
       axpby<double>(1.0, tmp, 1.0, f, c->nvc, c->stream);
     } else {
