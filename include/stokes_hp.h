@@ -155,6 +155,18 @@ int stokes_apply_mass(stokes_t ctx, const double* x, double* y);
  * fixed-order reduction of the solver. Synchronizes the context's stream. */
 int stokes_dot(stokes_t ctx, const double* x, const double* y, int64_t n, double* result);
 
+/* Inner products of x with the unit loads of the two load families, without forming them (each
+ * is separable: the device contracts x with the outer product of its three 1D factors); they are
+ * the gradient of lambda^T f with respect to the load coefficients (adjoint, Sec. 3.1 loads).
+ * stokes_body_load_dots: out[c n_modes + m] = x_c . (load of mode (c, m) of stokes_rhs_body with
+ * coefficient 1), waves as there; out: host, 3 n_modes.
+ * stokes_lid_profile_dots: out[k] = x . (stokes_rhs_lid_profile with theta = e_k), k < ncoef;
+ * out: host, ncoef.
+ * x: device, n_vel + n_pres (the velocity part is read). Deterministic. One item. */
+int stokes_body_load_dots(stokes_t ctx, int n_modes, const int* waves, const double* x,
+                          double* out);
+int stokes_lid_profile_dots(stokes_t ctx, int ncoef, const double* x, double* out);
+
 /* Solve K x = rhs with the selected preconditioner and solver to relative tolerance tol
  * (MINRES: ||r||_{P^-1} / ||rhs||_{P^-1}; FGMRES: ||r||_2 / ||rhs||_2), starting from x = 0,
  * then shift the pressure to zero mean. iterations and final_rel_res (the true

@@ -44,18 +44,11 @@ class CavitySolve(torch.autograd.Function):
             raise NotImplementedError("objectives must not depend on the pressure")
         lam, it, rr, _ = G.solve(g, ctx.tol)
         (th_shape, cf_shape) = ctx.shapes
-        grad_theta = np.zeros(th_shape)
-        for k in range(grad_theta.size):
-            e = np.zeros(grad_theta.size)
-            e[k] = 1.0
-            grad_theta[k] = G.dot(lam, G.rhs_lid_profile(e))
+        # lambda against the unit loads, contracted on the device without forming the loads
+        grad_theta = G.lid_profile_dots(int(np.prod(th_shape)), lam).reshape(th_shape)
         grad_coef = np.zeros(cf_shape)
         if grad_coef.size:
-            for c in range(cf_shape[0]):
-                for m in range(cf_shape[1]):
-                    unit = np.zeros(cf_shape)
-                    unit[c, m] = 1.0
-                    grad_coef[c, m] = G.dot(lam, G.rhs_body(unit, ctx.waves))
+            grad_coef = G.body_load_dots(ctx.waves, lam).reshape(cf_shape)
         Ax = G.apply_A(x[:G.n_vel].contiguous())
         grad_nu = (G.dot(lam, f_lid) - G.dot(lam[:G.n_vel].contiguous(), Ax)) / G.nu
         d_th, d_cf, d_nu = ctx.devices

@@ -77,6 +77,8 @@ def load_library(path=None):
         "stokes_rhs_lid_profile": (ctypes.c_int, [vp, ctypes.c_int, dp, ctypes.c_int, vp]),
         "stokes_apply_mass": (ctypes.c_int, [vp, vp, vp]),
         "stokes_dot": (ctypes.c_int, [vp, vp, vp, ctypes.c_int64, dp]),
+        "stokes_body_load_dots": (ctypes.c_int, [vp, ctypes.c_int, ip, vp, dp]),
+        "stokes_lid_profile_dots": (ctypes.c_int, [vp, ctypes.c_int, vp, dp]),
         "stokes_solve": (ctypes.c_int, [vp, vp, ctypes.c_double, vp, ip, dp]),
         "stokes_solve_host": (ctypes.c_int, [vp, vp, ctypes.c_double, vp, ip, dp]),
         "stokes_solve_multi": (ctypes.c_int, [vp, vp, ctypes.c_double, vp, ip, dp, ip]),
@@ -277,6 +279,28 @@ class Stokes:
             waves.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(accumulate),
             _ptr(self._vec(f, self.size))))
         return f
+
+    def body_load_dots(self, waves, x):
+        """(3, n_modes) host array: x . (load of sine mode (c, m) with unit coefficient), the
+        waves of rhs_body; the loads are not formed."""
+        import numpy as np
+        waves = np.ascontiguousarray(waves, dtype=np.int32)
+        m = waves.shape[1]
+        out = np.zeros((3, m))
+        self._check(self._call(self.lib.stokes_body_load_dots, self.h, m,
+                               waves.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                               _ptr(self._vec(x, self.size)),
+                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def lid_profile_dots(self, ncoef, x):
+        """(ncoef,) host array: x . rhs_lid_profile(e_k); the loads are not formed."""
+        import numpy as np
+        out = np.zeros(int(ncoef))
+        self._check(self._call(self.lib.stokes_lid_profile_dots, self.h, int(ncoef),
+                               _ptr(self._vec(x, self.size)),
+                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
 
     def rhs_lid_profile(self, theta, accumulate=False, out=None):
         import numpy as np

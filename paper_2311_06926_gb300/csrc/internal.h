@@ -285,6 +285,10 @@ void multi_axpy(const double* V, int64_t ldv, int nvec, const double* h, double 
 // y = x * (1 / *alpha)
 void scale_inv_dev(const double* alpha, const double* x, double* y, int64_t n, cudaStream_t s);
 void fill_zero(void* dst, size_t bytes, cudaStream_t s);
+// out[m] = <x, l1_m (x) l2_m (x) l3_m> for m < nm (extents e1, e2, e3, x1 fastest; device factors
+// packed as f[m][3][ld]); deterministic; partials: nm * kMultiDotBlocks.
+void sep_dots(const double* x, const double* f, int ld, int nm, int e1, int e2, int e3,
+              double* partials, double* out, cudaStream_t s);
 // dst (extents e1, e2, e3, x1 fastest) += cf l2 (x) l3 (x) l1 elementwise, in that order of
 // operations (device vectors l1, l2, l3 of lengths e1, e2, e3).
 void outer3_acc(const double* l1, const double* l2, const double* l3, double cf, double* dst,

@@ -191,6 +191,47 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Inner products of x with separable tensors T_m = l1_m (x) l2_m (x) l3_m (extents e1, e2, e3,
+// x1 fastest), m = k0 .. k0 + NG - 1, whose factors are packed as f[m][3][ld]: the tensors are
+// formed on the fly; per-block partial sums in a fixed order, as in k_multi_dot_partial.
+template <int NG>
+__global__ void __launch_bounds__(kThreads, 4) k_sep_dot_partial(const double* __restrict__ x,
+                                                              const double* __restrict__ f,
+                                                              int ld, int k0, int e1, int e2,
+                                                              int e3,
+                                                              double* __restrict__ partials) {
+  pdl_begin();
+  __shared__ double sh[NG][kThreads / 32];
+  double acc[NG];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) acc[g] = 0.0;
+  const double* f0 = f + (int64_t)k0 * 3 * ld;
+  const int64_t n = (int64_t)e1 * e2 * e3;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads) {
+    const int64_t q = i / e1;
+    const int i1 = (int)(i - q * e1), i2 = (int)(q % e2), i3 = (int)(q / e2);
+    const double xv = x[i];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      const double* fg = f0 + (int64_t)g * 3 * ld;
+      acc[g] = fma(xv, __ldg(fg + i1) * __ldg(fg + ld + i2) * __ldg(fg + 2 * ld + i3), acc[g]);
+    }
+  }
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    const double t = warp_sum(acc[g]);
+    if (lane == 0) sh[g][warp] = t;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < NG) {
+    double t = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) t += sh[threadIdx.x][k];
+    partials[(int64_t)(k0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+  }
+}
+
 template <int NG>
 __global__ void __launch_bounds__(kThreads, 4) k_multi_dot_partial(const double* __restrict__ V,
                                                                 int64_t ldv, int k0,
@@ -484,6 +525,30 @@ void multi_dot(const double* V, int64_t ldv, int nvec, const double* w, int64_t 
   launch_k(k_multi_dot_final, nvec, kThreads, 0, s, partials, kMultiDotBlocks, out);
   launch_end(kClassVector, s, 0.0, 0.0);
 }
+void sep_dots(const double* x, const double* f, int ld, int nm, int e1, int e2, int e3,
+              double* partials, double* out, cudaStream_t s) {
+  const double n = (double)e1 * e2 * e3;
+  for (int k0 = 0; k0 < nm; k0 += kDotGroup) {
+    const int ng = nm - k0 < kDotGroup ? nm - k0 : kDotGroup;
+    launch_begin(kClassVector, s);
+    switch (ng) {
+#define SHP_SDOT(g)                                                                         \
+  case g:                                                                                   \
+    launch_k(k_sep_dot_partial<g>, kMultiDotBlocks, kThreads, 0, s, x, f, ld, k0, e1, e2, e3, \
+             partials);                                                                     \
+    break;
+      SHP_SDOT(1) SHP_SDOT(2) SHP_SDOT(3) SHP_SDOT(4) SHP_SDOT(5) SHP_SDOT(6) SHP_SDOT(7)
+      SHP_SDOT(8)
+#undef SHP_SDOT
+      default: break;
+    }
+    launch_end(kClassVector, s, 4.0 * n * ng, 8.0 * n);
+  }
+  launch_begin(kClassVector, s);
+  launch_k(k_multi_dot_final, nm, kThreads, 0, s, partials, kMultiDotBlocks, out);
+  launch_end(kClassVector, s, 0.0, 0.0);
+}
+
 void multi_axpy(const double* V, int64_t ldv, int nvec, const double* h, double sign, double* w,
                 int64_t n, cudaStream_t s) {
   launch_begin(kClassVector, s);

@@ -2186,6 +2186,88 @@ int stokes_rhs_lid_profile(stokes_t c, int ncoef, const double* theta, int accum
   return STOKES_OK;
 }
 
+// factors of separable loads packed [m][3][ld]; chunks of terms go through the scratch vector
+// kv[7] (factors, then results) and the Gram-Schmidt partials, as many as both hold
+namespace {
+int sep_dots_chunked(stokes_t c, const std::vector<double>& fac, int ld, int nm, const double* x,
+                     int e1, int e2, int e3, double* out) {
+  const int64_t fit = c->ntot / (3 * (int64_t)ld + 1);
+  const int chunk = (int)std::min<int64_t>(fit, std::min(32, c->opts.restart + 2));
+  if (chunk < 1) return fail(c, STOKES_ERR_ARG, "mesh too small for the load scratch");
+  double* fdev = c->kv[7];
+  for (int m0 = 0; m0 < nm; m0 += chunk) {
+    const int k = std::min(chunk, nm - m0);
+    double* rdev = fdev + (int64_t)k * 3 * ld;
+    ck(cudaMemcpyAsync(fdev, fac.data() + (size_t)m0 * 3 * ld, (size_t)k * 3 * ld * sizeof(double),
+                       cudaMemcpyHostToDevice, c->stream), "load factors");
+    sep_dots(x, fdev, ld, k, e1, e2, e3, c->partials + kDotScratch, rdev, c->stream);
+    ck(cudaMemcpyAsync(out + m0, rdev, k * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+       "dots");
+    ck(cudaStreamSynchronize(c->stream), "dots");
+  }
+  return STOKES_OK;
+}
+}  // namespace
+
+int stokes_body_load_dots(stokes_t c, int n_modes, const int* waves, const double* x,
+                          double* out) {
+  if (!c || !x || !out || n_modes < 1 || !waves)
+    return c ? fail(c, STOKES_ERR_ARG, "invalid body-load arguments") : STOKES_ERR_ARG;
+  for (int i = 0; i < 9 * n_modes; ++i)
+    if (waves[i] < 1 || waves[i] > 64) return fail(c, STOKES_ERR_ARG, "wave numbers in [1, 64]");
+  const Univariate& u = c->uv;
+  const int ld = c->b + 1;
+  try {
+    for (int comp = 0; comp < 3; ++comp) {
+      const int e1 = comp == 0 ? c->a : c->b, e2 = comp == 1 ? c->a : c->b;
+      const int e3 = comp == 2 ? c->a : c->b;
+      std::vector<double> fac((size_t)n_modes * 3 * ld, 0.0);
+      for (int m = 0; m < n_modes; ++m) {
+        const int* k = waves + (size_t)(comp * n_modes + m) * 3;
+        const std::vector<double> l1 = comp == 0 ? sine_load_N(u, k[0]) : sine_load_M(u, k[0]);
+        const std::vector<double> l2 = comp == 1 ? sine_load_N(u, k[1]) : sine_load_M(u, k[1]);
+        const std::vector<double> l3 = comp == 2 ? sine_load_N(u, k[2]) : sine_load_M(u, k[2]);
+        double* f = fac.data() + (size_t)m * 3 * ld;
+        std::copy(l1.begin(), l1.end(), f);
+        std::copy(l2.begin(), l2.end(), f + ld);
+        std::copy(l3.begin(), l3.end(), f + 2 * ld);
+      }
+      const int rc = sep_dots_chunked(c, fac, ld, n_modes, x + comp * c->nvc, e1, e2, e3,
+                                      out + comp * n_modes);
+      if (rc != STOKES_OK) return rc;
+    }
+    check_launch("body_load_dots");
+  } catch (const CudaError& e) {
+    return cuda_fail(c, e);
+  }
+  return STOKES_OK;
+}
+
+int stokes_lid_profile_dots(stokes_t c, int ncoef, const double* x, double* out) {
+  if (!c || !x || !out || ncoef < 4 || ncoef > 4096)
+    return c ? fail(c, STOKES_ERR_ARG, "invalid lid-profile arguments") : STOKES_ERR_ARG;
+  const Univariate& u = c->uv;
+  const Dense G = lid_profile_matrix(u, ncoef);
+  const double alpha = c->c_pen / u.h;
+  const int ld = c->b + 1;
+  std::vector<double> fac((size_t)ncoef * 3 * ld, 0.0);
+  for (int k = 0; k < ncoef; ++k) {
+    double* f = fac.data() + (size_t)k * 3 * ld;
+    for (int i1 = 0; i1 < c->a; ++i1) f[i1] = G(i1, k);
+    for (int i2 = 0; i2 < c->b; ++i2)
+      f[ld + i2] = c->nu * (2.0 * alpha * u.M_at_1[i2] - u.dM_at_1[i2]);
+    for (int i3 = 0; i3 < c->b; ++i3) f[2 * ld + i3] = 1.0;
+  }
+  try {
+    const int rc = sep_dots_chunked(c, fac, ld, ncoef, x, c->a, c->b, c->b, out);
+    if (rc != STOKES_OK) return rc;
+    check_launch("lid_profile_dots");
+  } catch (const CudaError& e) {
+    return cuda_fail(c, e);
+  }
+  return STOKES_OK;
+}
+
 int stokes_apply_mass(stokes_t c, const double* x, double* y) {
   if (!c || !x || !y) return c ? fail(c, STOKES_ERR_ARG, "null vector") : STOKES_ERR_ARG;
   try {

@@ -127,3 +127,25 @@ def test_central_differences_16cubed():
 def test_central_differences_64cubed_p3():
     """The differentiation workload size: 64^3 elements, p = 3."""
     _fd_check(64, 3, 1.0, rel_small=2e-3)
+
+
+@pytest.mark.parametrize("n,p", [(3, 1), (6, 2), (11, 3)])
+def test_load_dots_equal_dots_with_formed_loads(n, p):
+    """stokes_body_load_dots / stokes_lid_profile_dots (the loads' factors contracted on the
+    device) against the inner products with the formed unit loads."""
+    G = _ctx(n, p, 1.0)
+    x = dev(synthetic.random_vector(G.size, 77 + n))
+    coef, waves = synthetic.forcing_modes(n, n_modes=8)
+    got = G.body_load_dots(waves, x)
+    for c in range(3):
+        for m in range(coef.shape[1]):
+            unit = np.zeros_like(coef)
+            unit[c, m] = 1.0
+            ref = G.dot(x, G.rhs_body(unit, waves))
+            assert got[c, m] == pytest.approx(ref, rel=1e-11, abs=1e-12)
+    lid = G.lid_profile_dots(16, x)
+    for k in range(16):
+        e = np.zeros(16)
+        e[k] = 1.0
+        assert lid[k] == pytest.approx(G.dot(x, G.rhs_lid_profile(e)), rel=1e-11, abs=1e-12)
+    G.close()
