@@ -148,4 +148,11 @@ def test_load_dots_equal_dots_with_formed_loads(n, p):
         e = np.zeros(16)
         e[k] = 1.0
         assert lid[k] == pytest.approx(G.dot(x, G.rhs_lid_profile(e)), rel=1e-11, abs=1e-12)
+    from paper_2311_06926_gb300 import StokesError
+    bad = np.array(waves)
+    bad[0, 0, 0] = 0
+    with pytest.raises(StokesError):
+        G.body_load_dots(bad, x)
+    with pytest.raises(StokesError):
+        G.lid_profile_dots(3, x)
     G.close()
