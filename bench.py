@@ -716,7 +716,8 @@ def main():
                     "steps": ks,
                     "iterations": [per[f"q{q}s{k}"]["iterations"] for k in ks],
                     "normalized_time": [round(per[f"q{q}s{k}"]["ms"] / t0, 3) for k in ks]}
-        table1["order2_quadrature_forward"] = table1_quadrature(Stokes, G, n, p)
+        if ws == 1:
+            table1["order2_quadrature_forward"] = table1_quadrature(Stokes, G, n, p)
         table1["paper_order2"] = {"steps": [0, 1, 2, 3, 4], "iterations": [56, 30, 20, 14, 9],
                                   "normalized_time": [1.0, 0.54, 0.38, 0.30, 0.25],
                                   "source": "Table 1, 32^3, degree 4 (one CPU thread, "
@@ -842,7 +843,7 @@ def main():
             Gc.close()
 
     mixed = None
-    if not args.no_mixed:
+    if not args.no_mixed and ws == 1:
         mixed = mixed_vs_fp64(Stokes, load_peaks() or {})
     adjoint = schur = None
     if args.workload == "cavity32" and ws == 1:
