@@ -1,17 +1,22 @@
 #!/usr/bin/env python
 """Benchmark: Stokes cavity solves per second to 1e-8 relative residual on GB300.
 
-Workload (default, ``--workload cavity32``): the 3D lid-driven cavity on 32^3 elements,
-pressure degree p = 3 (velocity degree 4 in its own direction), nu = 1, lid (1, 0, 0) on x2 = 1,
-solved for each preconditioner of the sweep hyper-power order {2, 3} x steps {0, 1, 2, 3}
-(Schur sequence with inner updates). One step = the 8 solves of the sweep; value = solves/s.
-``--workload cavity128`` runs a 128^3, p = 3 cavity with order 2, steps 2 in the plain FP64 form
-and the mixed-precision form.
+Workload (default, ``--workload cavity128``): the 3D lid-driven cavity (Sec. 5, Fig. 2) on 128^3
+elements, pressure degree p = 3 (velocity degree 4 in its own direction, the paper's degree 4;
+8.94 M unknowns), nu = 1, lid (1, 0, 0) on x2 = 1, order-2 hyper-power preconditioner with 2
+steps (Schur sequence with inner updates, Eq. 4.5). One step = one solve of the mixed form:
+tensor-core (TF32 operands, FP32 accumulation) fast diagonalisation and FP32 inner hyper-power
+steps inside FP64 flexible GMRES, to a true relative residual ||f - K x||_2 / ||f||_2 <= 1e-8;
+value = solves/s. Beside it: the plain FP64 form (MINRES, Table 1's criterion) and the mixed form
+at the FP64 solve's true residual (equal accuracy) and in BF16, each with its error against the
+oracle's solution (tests/golden/cavity128_p3_q2s2.json, written by a script that calls only the
+oracle). ``--workload cavity32`` times the 32^3 FP64 sweep of order {2, 3} x steps {0..3}; it also
+appears in the default line as ``sweep32``, with the 64-problem batch as ``batch64``.
 
 Timing: W warm-up steps, then K steps between a barrier + device synchronize on both sides,
-CUDA events on the library's stream, L2 flushed (a 256 MiB write) before every step, the max over
+CUDA events on the launching stream, L2 flushed (a 256 MiB write) before every step, the max over
 ranks. Ranks (torchrun) run independent replicas (weak scaling, no collective on the data path).
-``e2e``: the same sweep through stokes_solve_host (pinned host rhs and x, copies in the call).
+``e2e``: the same solve through stokes_solve_host (pinned host rhs and x, copies in the call).
 ``roofline``: the dominant kernel class, from a separate profiled pass (CUDA events around each
 launch). ``cpu_baseline``: the FP64 oracle on the host cores on a bounded sample.
 ``--impl reference``: the oracle as the reference arm (rank 0 only).
@@ -73,6 +78,12 @@ def traffic_for(kernel_class, precision, workload, form="per-direction"):
     return t["bytes_per_launch"], t["profile"]
 
 WORKLOADS = {
+    "cavity128": dict(n=128, p=3, sweep=[(2, 2)], precision="tf32",
+                      desc="3D lid-driven cavity, 128^3 elements, p=3 (velocity degree 4 in its "
+                           "own direction), nu=1, order-2 hyper-power preconditioner with 2 steps "
+                           "(Schur with inner updates); mixed form: TF32 tensor-core fast "
+                           "diagonalisation and FP32 inner steps inside FP64 flexible GMRES to a "
+                           "true relative residual of 1e-8, one RHS per solve"),
     "cavity32": dict(n=32, p=3, sweep=[(q, s) for q in (2, 3) for s in (0, 1, 2, 3)],
                      precision="fp64",
                      desc="3D lid-driven cavity, 32^3 elements, p=3 (velocity degree 4 in its own "
@@ -81,9 +92,6 @@ WORKLOADS = {
     "cavity8": dict(n=8, p=2, sweep=[(2, 1)], precision="fp64",
                     desc="3D lid-driven cavity, 8^3 elements, p=2, nu=1, FP64 MINRES to 1e-8, "
                          "order 2, 1 step"),
-    "cavity128": dict(n=128, p=3, sweep=[(2, 2)], precision="fp64",
-                      desc="3D lid-driven cavity, 128^3 elements, p=3, nu=1, FP64 MINRES to 1e-8, "
-                           "order 2, 2 steps"),
     "batch64": dict(n=0, p=0, sweep=[(2, 1)], precision="tf32",
                     desc="64 right-hand sides, RHS i on n = (16,24,32,48)[i mod 4], p = (2,3,4)"
                          "[(i div 4) mod 3]: body force of 8 seeded sine modes per component plus a "
@@ -94,6 +102,42 @@ WORKLOADS = {
     "cavity96": dict(n=96, p=3, sweep=[(2, 2)], precision="fp64",
                      desc="3D lid-driven cavity, 96^3 elements, p=3, nu=1, order 2, 2 steps"),
 }
+
+GOLDEN_128 = os.path.join(ROOT, "tests", "golden", "cavity128_p3_q2s2.json")
+L2_NOTE = ("working set of several GB, larger than the 129 MB L2; the GPU arm also writes 256 MiB "
+           "before every step")
+
+
+def workload_config(args, wl):
+    """The config object of the JSON line: the same for both arms of a workload."""
+    cfg = {"workload": wl["desc"], "n_elems": wl["n"], "degree_p": wl["p"],
+           "preconditioners": [f"order {q}, {s} step(s)" for q, s in wl["sweep"]],
+           "tol": 1e-8, "l2": L2_NOTE, "parallelism": f"replicas x{args.gpus}"}
+    return cfg
+
+
+def load_golden(path=GOLDEN_128):
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def oracle_error(x, g):
+    """Error of a solution x (host float64, pressure zero-mean) against the oracle's stored
+    solution: ``rel_2norm_est`` = sqrt(N / n sum_samples (x_i - x_o,i)^2) / ||x_o|| (an unbiased
+    estimate of ||x - x_o||^2 / ||x_o||^2 from the n seeded sampled entries), ``max_sampled`` =
+    max |x_i - x_o,i| / max |x_o| over the samples, ``functionals`` = max_k |<x - x_o, w_k>| /
+    (||x_o|| ||w_k||) over the seeded vectors (every entry of x contributes)."""
+    import numpy as np
+    from paper_2311_06926_gb300 import synthetic
+    idx = np.asarray(g["sample_index"])
+    d = x[idx] - np.asarray(g["sample_value"])
+    est = float(np.sqrt(g["size"] / len(idx) * np.sum(d * d)) / g["norm2"])
+    fun = 0.0
+    for k, val in enumerate(g["functionals"]):
+        w = synthetic.random_vector(g["size"], g["functional_seed"] + k)
+        fun = max(fun, abs(float(np.dot(x, w)) - val) / (g["norm2"] * float(np.linalg.norm(w))))
+    return {"rel_2norm_est": est, "max_sampled": float(np.abs(d).max() / g["max_abs"]),
+            "functionals": fun}
 
 
 def aggregate(ms_local, units_local, dist=None):
@@ -235,51 +279,41 @@ def oracle_sample_one_thread(n, p, q, s, repeats):
         return None
 
 
-def mixed_vs_fp64(Stokes, peaks, n=128, p=3, q=2, s=2):
-    """128^3 cavity, order 2, 2 steps: plain FP64 MINRES vs the mixed form (TF32 / BF16
-    tensor-core fast diagonalisation and FP32 inner steps inside FP64 flexible GMRES), each to the
-    1e-8 tolerance; times by CUDA events after one untimed solve; error against the FP64 solution."""
-    import torch
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    res = {"workload": f"3D lid-driven cavity, {n}^3 elements, p={p}, nu=1, order {q}, {s} steps, "
-                       f"tol 1e-8", "forms": {}}
-    ref = None
-    for prec in ["fp64", "tf32", "bf16"]:
-        G = Stokes(n, p, precision=prec, max_order=q, max_steps=s)
-        G.set_preconditioner(q, s)
-        f = G.rhs_cavity(1.0)
-        x, it, rr, _ = G.solve(f, 1e-8)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        x, it, rr, _ = G.solve(f, 1e-8, out=x)
-        b.record()
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b)
-        G.profile_begin()
-        G.solve(f, 1e-8)
-        prof = G.profile_end()
-        if ref is None:
-            ref = x.clone()
-        err = float((x - ref).norm() / ref.norm())
-        entry = {"ms": ms, "iterations": it, "true_rel_res": rr,
-                 "solver": "minres" if prec == "fp64" else "fgmres",
-                 "rel_err_vs_fp64_solution": err,
-                 "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()}}
-        for name, key in [("mma_mode_product", "tensor_core_fd"), ("band_pass", "band_pass")]:
-            st = prof.get(name)
-            if st and st["launches"] and prec != "fp64":
-                gbs = st["bytes"] / (st["ms"] / 1e3) / 1e9
-                entry[f"roofline_{key}"] = {
-                    "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                    "frac": gbs / hbm, "avg_launch_us": 1e3 * st["ms"] / st["launches"],
-                    "tflops": st["flops"] / (st["ms"] / 1e3) / 1e12}
-        res["forms"][prec] = entry
-        G.close()
-        del G
-        torch.cuda.empty_cache()
-    f64 = res["forms"]["fp64"]["ms"]
-    res["speedup_vs_fp64"] = {k: f64 / v["ms"] for k, v in res["forms"].items() if k != "fp64"}
-    return res
+def oracle_iteration_sample(n, p, q, s, reps, warmup=0, seed=77):
+    """Seconds for `reps` applications of the oracle's order-q, s-step preconditioner P_s^-1
+    followed by its K apply (the operator work of one MINRES iteration; the few vector updates of
+    an iteration are not included), after `warmup` untimed ones, on a seeded vector."""
+    import numpy as np
+    from oracle.precond import HyperPowerPreconditioner
+    from paper_2311_06926_gb300 import synthetic
+    S, F, base = oracle_solver(n, p)
+    P = HyperPowerPreconditioner(base, q, s)
+    v = synthetic.random_vector(S.size, seed)
+
+    def it(v):
+        w = F.apply_K(P(v))
+        return w / np.linalg.norm(w)
+
+    for _ in range(warmup):
+        v = it(v)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        v = it(v)
+    return time.perf_counter() - t0
+
+
+def run_child(extra_args, timeout=900):
+    """Run this script with other arguments in a child process and return its JSON line (or an
+    error note). Used for the context measurements on other workloads, each in a fresh process."""
+    try:
+        out = subprocess.run([sys.executable, os.path.abspath(__file__)] + extra_args,
+                             capture_output=True, text=True, timeout=timeout)
+    except subprocess.TimeoutExpired:
+        return {"error": f"timed out after {timeout} s"}
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    if out.returncode != 0 or not lines:
+        return {"error": f"exit {out.returncode}: {(out.stderr or out.stdout)[-300:]}"}
+    return json.loads(lines[-1])
 
 
 def table1_quadrature(Stokes, Gk, n, p, steps=(0, 1, 2, 3, 4), reps=20):
@@ -572,25 +606,259 @@ def run_reference(args, wl):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    q, s = (2, 1) if (2, 1) in wl["sweep"] else wl["sweep"][0]
-    for _ in range(args.warmup):
-        oracle_sample(wl["n"], wl["p"], q, s, 1)
-    dt, its = oracle_sample(wl["n"], wl["p"], q, s, args.steps)
-    value = args.steps / dt
-    sample = (f"oracle (NumPy/SciPy FP64, matrix-free Kronecker mode products) MINRES solve of "
-              f"the {wl['n']}^3 p={wl['p']} cavity with order {q}, {s} step(s) "
-              f"({its} iterations), one solve per step")
+    cfg = workload_config(args, wl)
+    if args.workload == "cavity128":
+        q, s = wl["sweep"][0]
+        its = load_golden()["iterations"]
+        dt = oracle_iteration_sample(wl["n"], wl["p"], q, s, args.steps, warmup=args.warmup)
+        value = 1.0 / (dt / args.steps * its)
+        ms_step = 1e3 * dt / args.steps
+        sample = (f"oracle (NumPy/SciPy FP64, matrix-free Kronecker mode products) on the "
+                  f"{wl['n']}^3 p={wl['p']} cavity: each step is one application of its order-{q}, "
+                  f"{s}-step preconditioner and one K apply (the operator work of one MINRES "
+                  f"iteration, {ms_step:.0f} ms); value = 1 / (time per step x {its} iterations, "
+                  f"the oracle's MINRES count for this solve to 1e-8)")
+    else:
+        q, s = (2, 1) if (2, 1) in wl["sweep"] else wl["sweep"][0]
+        for _ in range(args.warmup):
+            oracle_sample(wl["n"], wl["p"], q, s, 1)
+        dt, its = oracle_sample(wl["n"], wl["p"], q, s, args.steps)
+        value = args.steps / dt
+        ms_step = 1e3 * dt / args.steps
+        sample = (f"oracle (NumPy/SciPy FP64, matrix-free Kronecker mode products) MINRES solve "
+                  f"of the {wl['n']}^3 p={wl['p']} cavity with order {q}, {s} step(s) "
+                  f"({its} iterations), one solve per step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["desc"], "n_elems": wl["n"], "degree_p": wl["p"],
-                       "reference_sample": f"order {q}, steps {s}"},
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def tc_peak_tflops(peaks, kind):
+    """Dense tensor-core peak for a kind: the measured BF16 burst figure, times the nominal
+    TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s) for TF32."""
+    bf16 = peaks.get("bf16_tflops")
+    if not bf16:
+        return None
+    return bf16 if kind == "bf16" else bf16 * 1.1 / 2.25
+
+
+def run_cavity128(args, wl):
+    """Headline: the mixed form on the 128^3 cavity (see the module docstring)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2311_06926_gb300 import Stokes
+    from paper_2311_06926_gb300.binding import kernel_launches
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev_index = torch.cuda.current_device()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    n, p = wl["n"], wl["p"]
+    q, s = wl["sweep"][0]
+    prec = wl["precision"]
+    tol = 1e-8
+    g = load_golden()
+    peaks = load_peaks() or {}
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter()
+    G = Stokes(n, p, precision=prec, max_order=q, max_steps=s)
+    G.set_preconditioner(q, s)
+    torch.cuda.synchronize()
+    setup_ms = 1e3 * (time.perf_counter() - t_setup)
+    cur = torch.cuda.current_stream()
+    f = G.rhs_cavity(1.0)
+    x = G.empty()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    last = {}
+
+    def step():
+        flush.fill_(1.0)
+        _, it, rr, _ = G.solve(f, tol, out=x)
+        last["it"], last["rr"] = it, rr
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    sampler = ClockSampler(dev_index)
+    sampler.start()
+    launches0 = kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(cur)
+    for _ in range(args.steps):
+        step()
+    e1.record(cur)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    launches = kernel_launches() - launches0
+    ms = e0.elapsed_time(e1)
+    value, ms_max = aggregate(ms, args.steps, dist if ws > 1 else None)
+    x_head = x.cpu().numpy()
+    head = {"ms": ms / args.steps, "iterations": last["it"], "true_rel_res": last["rr"],
+            "solver": "fgmres", "error_vs_oracle": oracle_error(x_head, g)}
+
+    # end to end through the host-buffer C-ABI call (pinned host memory, copies in the call)
+    rhs_h = f.cpu().pin_memory()
+    x_h = torch.empty_like(rhs_h).pin_memory()
+
+    def step_e2e():
+        flush.fill_(1.0)
+        G.solve_host(rhs_h, x_h, tol)
+
+    step_e2e()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_value, _ = aggregate(1e3 * (time.perf_counter() - t0), args.steps,
+                             dist if ws > 1 else None)
+
+    # profiled pass: per-kernel-class event timing over one solve
+    G.profile_begin()
+    step()
+    prof = G.profile_end()
+    step_ms_profiled = sum(v["ms"] for v in prof.values())
+    dom_name = max(prof, key=lambda k: prof[k]["ms"])
+    dom = prof[dom_name]
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "kernel": dom_name,
+            "launches_per_step": dom["launches"],
+            "avg_launch_us": 1e3 * dom["ms"] / max(dom["launches"], 1),
+            "share_of_solve": dom["ms"] / step_ms_profiled,
+            "measurement": "CUDA events around every launch of one profiled solve (algorithmic "
+                           "bytes: each input read once, each output written once)",
+            "peak_note": "of measured" if "hbm_gbs" in peaks else "of fallback"}
+    traffic, traffic_src = traffic_for(dom_name, prec, args.workload)
+    roof["traffic"] = traffic
+    if traffic is not None:
+        roof["traffic_source"] = traffic_src
+    tc = prof.get("mma_mode_product")
+    tc_roof = None
+    if tc and tc["launches"]:
+        tflops = tc["flops"] / (tc["ms"] / 1e3) / 1e12
+        gbs = tc["bytes"] / (tc["ms"] / 1e3) / 1e9
+        pk = tc_peak_tflops(peaks, prec)
+        tc_roof = {"kernel": "k_rmp (tcgen05 mode products)", "launches": tc["launches"],
+                   "ms": tc["ms"], "avg_launch_us": 1e3 * tc["ms"] / tc["launches"],
+                   "achieved_gbs": gbs, "hbm_frac": gbs / hbm, "achieved_tflops": tflops,
+                   "tensor_peak_tflops": pk, "tensor_frac": (tflops / pk) if pk else None,
+                   "peak_note": "measured BF16 burst x nominal TF32/BF16 ratio"
+                                if prec == "tf32" else "measured BF16 burst"}
+
+    forms = None
+    if ws == 1:
+        def timed_solve(Gx, tol_x, reps=3):
+            xx = Gx.empty()
+            Gx.solve(f if Gx is G else fx[Gx], tol_x, out=xx)
+            times, it_x, rr_x = [], 0, 0.0
+            for _ in range(reps):
+                flush.fill_(1.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record(cur)
+                _, it_x, rr_x, _ = Gx.solve(f if Gx is G else fx[Gx], tol_x, out=xx)
+                b.record(cur)
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+            return {"ms": statistics.median(times), "iterations": it_x, "true_rel_res": rr_x,
+                    "tol": tol_x, "error_vs_oracle": oracle_error(xx.cpu().numpy(), g)}
+
+        fx = {}
+        forms = {prec: head}
+        G64 = Stokes(n, p, precision="fp64", max_order=q, max_steps=s)
+        G64.set_preconditioner(q, s)
+        fx[G64] = G64.rhs_cavity(1.0)
+        forms["fp64"] = dict(timed_solve(G64, tol), solver="minres",
+                             stopping="||r||_{P^-1} / ||f||_{P^-1} <= 1e-8 (Table 1)")
+        G64.close()
+        del G64
+        rr64 = forms["fp64"]["true_rel_res"]
+        forms[f"{prec}_at_fp64_residual"] = dict(timed_solve(G, rr64), solver="fgmres",
+                                                 stopping="true residual <= the FP64 solve's")
+        other = "bf16" if prec == "tf32" else "tf32"
+        Go = Stokes(n, p, precision=other, max_order=q, max_steps=s)
+        Go.set_preconditioner(q, s)
+        fx[Go] = Go.rhs_cavity(1.0)
+        forms[other] = dict(timed_solve(Go, tol), solver="fgmres")
+        forms[f"{other}_at_fp64_residual"] = dict(timed_solve(Go, rr64), solver="fgmres",
+                                                  stopping="true residual <= the FP64 solve's")
+        Go.close()
+        del Go
+        torch.cuda.empty_cache()
+        f64ms = forms["fp64"]["ms"]
+        forms["speedup_vs_fp64"] = {
+            k: f64ms / v["ms"] for k, v in forms.items() if isinstance(v, dict) and k != "fp64"}
+        forms["oracle_reference"] = {
+            "iterations": g["iterations"], "true_rel_res": g["true_rel_res"],
+            "source": "tests/golden/cavity128_p3_q2s2.json (oracle MINRES, order 2, 2 steps)",
+            "error_measure": "rel_2norm_est: sqrt(N/n sum over 1024 seeded sampled entries of "
+                             "(x - x_oracle)^2) / ||x_oracle||; max_sampled and functionals as "
+                             "in tests/test_gpu_fullsize.py"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        reps = 2
+        dt = oracle_iteration_sample(n, p, q, s, reps, warmup=1)
+        cpu = {"value": 1.0 / (dt / reps * g["iterations"]), "unit": "solves/s",
+               "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"{reps} oracle MINRES iterations' operator work on the {n}^3 p={p} "
+                         f"cavity (each one application of the order-{q}, {s}-step "
+                         f"preconditioner and one K apply, {1e3 * dt / reps:.0f} ms) after one "
+                         f"untimed, scaled to the oracle's {g['iterations']} iterations"}
+
+    extras = {}
+    if ws == 1 and not args.no_extras:
+        extras["sweep32"] = run_child(["--workload", "cavity32", "--steps", "3", "--warmup", "3",
+                                       "--no-cpu-baseline"])
+        extras["batch64"] = run_child(["--workload", "batch64", "--steps", "2", "--warmup", "3"])
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": f"{prec}+f64", "data": "synthetic",
+            "config": workload_config(args, wl),
+            "unknowns": G.size,
+            "headline": head,
+            "forms": forms,
+            "roofline": roof,
+            "tensor_core_fd": tc_roof,
+            "kernel_classes": class_rooflines(prof, step_ms_profiled, prec, peaks),
+            "setup_ms": round(setup_ms, 1),
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "solves/s",
+                    "h2d_bytes_per_step": G.size * 8, "d2h_bytes_per_step": G.size * 8},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    G.close()
+    if ws > 1:
+        dist.destroy_process_group()
     return 0
 
 
@@ -600,11 +868,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cavity32", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="cavity128", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true",
-                    help="skip the 128^3 mixed-precision vs FP64 comparison")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the 32^3 sweep and 64-problem batch lines")
     ap.add_argument("--probe", action="store_true",
                     help="kernel probe for ncu: only apply the order-2, 1-step hyper-power "
                          "preconditioner K times on the workload's mesh in --precision (no "
@@ -617,15 +885,21 @@ def main():
     wl = dict(WORKLOADS[args.workload])
     if args.precision:
         wl["precision"] = args.precision
-    if args.warmup < 3:
-        args.warmup = 3
     if args.impl == "reference":
         return run_reference(args, wl)
     if args.probe:
         return run_probe(args, wl)
     if args.workload == "batch64":
         return run_batch(args, wl)
+    if args.workload == "cavity128":
+        return run_cavity128(args, wl)
+    return run_sweep(args, wl)
 
+
+def run_sweep(args, wl):
+    """The 32^3 FP64 sweep (``--workload cavity32``): one step = the 8 solves of order {2, 3} x
+    steps {0..3}, with the context measurements of the other paper rows (Table 1's form with the
+    quadrature forward operator, Schur variants, adjoint gradient)."""
     import torch
     import torch.distributed as dist
     from paper_2311_06926_gb300 import Stokes
@@ -842,9 +1116,6 @@ def main():
         for Gc in cs:
             Gc.close()
 
-    mixed = None
-    if not args.no_mixed and ws == 1:
-        mixed = mixed_vs_fp64(Stokes, load_peaks() or {})
     adjoint = schur = None
     if args.workload == "cavity32" and ws == 1:
         adjoint = adjoint_timing(Stokes)
@@ -884,12 +1155,10 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == "fp64" else f"{prec}+f64",
             "data": "synthetic",
-            "config": {"workload": wl["desc"], "n_elems": n, "degree_p": p,
-                       "unknowns": G.size, "precision": prec, "solves_per_step": len(sweep),
-                       "tol": 1e-8, "l2": "flushed by a 256 MiB write before every step",
-                       "parallelism": f"replicas x{ws}",
-                       "fp64_launch_shapes": dict(zip(("mode_block", "band_block", "fd_fused"),
-                                                     G.tuning()))},
+            "config": workload_config(args, wl),
+            "unknowns": G.size, "solves_per_step": len(sweep),
+            "fp64_launch_shapes": dict(zip(("mode_block", "band_block", "fd_fused"),
+                                           G.tuning())),
             "per_preconditioner": per,
             "table1_form": table1,
             "sweep_concurrent": sweep_conc,
@@ -902,7 +1171,6 @@ def main():
                     "d2h_bytes_per_step": bytes_per_solve * len(sweep)},
             "gpu_launches": int(launches),
             "clocks": clocks,
-            "mixed_vs_fp64": mixed,
             "adjoint": adjoint,
             "schur_variants": schur,
         }

@@ -250,6 +250,18 @@ typedef struct stokes_tuning {
 int stokes_get_tuning(stokes_t ctx, stokes_tuning* out);
 int stokes_set_tuning(stokes_t ctx, const stokes_tuning* tuning);
 
+/* Test hook (no counterpart in the paper): the number of polls each pipeline wait of the
+ * tensor-core mode products (mbarrier waits on TMA copies, MMA completion and the epilogue) makes
+ * before it gives up; 0 restores the default (2^22 polls, at least 128 ns apart after the first
+ * 64: about half a second). A wait that gives up raises the context's error flag, the kernel
+ * stops issuing work, waits (with the default limit) for the copies and tensor-core operations it
+ * has in flight, frees its tensor memory and returns; the call then fails with STOKES_ERR_CUDA
+ * ("tensor-core pipeline wait timed out") and the context should be destroyed. A tiny limit makes
+ * the waits run out on purpose, so that this path can be tested without a fault or a hang. Applies
+ * to launches made after the call (CUDA graphs the solvers captured earlier keep their limit);
+ * contexts without tensor-core mode products ignore it. */
+int stokes_set_wait_limit(stokes_t ctx, int64_t polls);
+
 /* ---- allocation-free variant (no counterpart in the paper) --------------------------------
  * For callers that cannot allocate device memory (their allocator is owned by a framework or
  * memory pool, or allocation is forbidden after start-up): the fast-diagonalisation apply of one
@@ -260,7 +272,12 @@ int stokes_set_tuning(stokes_t ctx, const stokes_tuning* tuning);
  * aliased. stream: a cudaStream_t (NULL = legacy default stream). Returns after enqueueing.
  * Its two intermediate tensors live in a static device array of 2 x 2^19 float64 (8 MiB), held
  * by every GPU that loads the library until the process exits; n1 n2 n3 > 2^19 is rejected with
- * STOKES_ERR_ARG. The first call on a device (made with that device current) looks up the
+ * STOKES_ERR_ARG. Each of the six mode products stages its contracted lines in shared memory, so
+ * an extent must also fit the device's opt-in shared memory per block: with 227 KiB, n1 <= 7264
+ * and n2, n3 <= 14528 (7264 when every extent before it is 1); a call beyond that is rejected
+ * with STOKES_ERR_ARG before anything is launched. A launch that fails stops the sequence and
+ * returns STOKES_ERR_CUDA (y is then incomplete); errors left pending by unrelated earlier work
+ * are neither reported nor cleared. The first call on a device (made with that device current) looks up the
  * array's device address; make it before any stream capture. All calls share the array: calls
  * that overlap on the GPU race, so serialise them. No part of the array needs to start at zero. */
 int stokes_fd_apply_noalloc(int n1, int n2, int n3, const double* U1, const double* U2,

@@ -71,6 +71,7 @@ def load_library(path=None):
         "stokes_apply_A": (ctypes.c_int, [vp, vp, vp]),
         "stokes_apply_K": (ctypes.c_int, [vp, vp, vp]),
         "stokes_apply_P": (ctypes.c_int, [vp, vp, vp]),
+        "stokes_set_wait_limit": (ctypes.c_int, [vp, ctypes.c_int64]),
         "stokes_apply_hyperpower": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp]),
         "stokes_rhs_cavity": (ctypes.c_int, [vp, ctypes.c_double, vp]),
         "stokes_rhs_body": (ctypes.c_int, [vp, ctypes.c_int, dp, ip, ctypes.c_int, vp]),
@@ -234,6 +235,10 @@ class Stokes:
     def set_tuning(self, mode_block, band_block, fd_fused=0):
         t = _Tuning(int(mode_block), int(band_block), int(fd_fused))
         self._check(self.lib.stokes_set_tuning(self.h, ctypes.byref(t)))
+
+    def set_wait_limit(self, polls):
+        """Test hook: polls per pipeline wait of the tensor-core kernel (0 = default)."""
+        self._check(self.lib.stokes_set_wait_limit(self.h, int(polls)))
 
     def set_preconditioner(self, order, steps):
         self._check(self.lib.stokes_set_preconditioner(self.h, order, steps))

@@ -21,9 +21,10 @@ __device__ __forceinline__ void pdl_begin() {
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
 }
 
+// Returns the launch's own status (configuration errors), not errors left pending by earlier work.
 template <typename... P, typename... A>
-inline void launch_k(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                     A... args) {
+inline cudaError_t launch_k(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t s, A... args) {
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -34,20 +35,24 @@ inline void launch_k(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, c
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
 }
 
 // Raises a kernel's dynamic shared-memory limit to `bytes` when that is above the 48 KiB default
 // and above every value set so far for it (`cache`). Several host threads may launch at once
-// (concurrent contexts), so the check and the attribute call are serialised.
+// (concurrent contexts), so the check and the attribute call are serialised. The cache records
+// only a size the attribute call accepted; a refused size (above the device's opt-in maximum)
+// leaves it unchanged and returns the error, and the launch that needed it must not be made.
 template <typename K>
-inline void raise_smem_limit(K kernel, std::atomic<int>& cache, int bytes) {
-  if (bytes <= 48 * 1024 || bytes <= cache.load()) return;
+inline cudaError_t raise_smem_limit(K kernel, std::atomic<int>& cache, int bytes) {
+  if (bytes <= 48 * 1024 || bytes <= cache.load()) return cudaSuccess;
   static std::mutex mu;
   std::lock_guard<std::mutex> lock(mu);
-  if (bytes <= cache.load()) return;
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cache.store(bytes);
+  if (bytes <= cache.load()) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) cache.store(bytes);
+  return e;
 }
 
 // The same with a thread-block cluster of cluster_x blocks along x (grid.x a multiple of it).
@@ -191,12 +196,16 @@ struct ModeArgs {
   int eo_he;       // FP64 path: U's columns are [he even; n - he odd] eigenvectors (0: generic)
   int block;       // FP64 path: target threads per block (<= 0: 512); chosen by the setup tuner
 };
+// Both return the status of their launch (cudaSuccess, or the error of the shared-memory limit
+// or of the launch itself; nothing is launched when the limit cannot be raised).
 template <typename T>
-void mode_product(const ModeArgs<T>& a, cudaStream_t s);
+cudaError_t mode_product(const ModeArgs<T>& a, cudaStream_t s);
 // Several independent mode products (up to kMaxModeJobs) in one launch.
 constexpr int kMaxModeJobs = 4;
 template <typename T>
-void mode_product_multi(const ModeArgs<T>* jobs, int njobs, cudaStream_t s);
+cudaError_t mode_product_multi(const ModeArgs<T>* jobs, int njobs, cudaStream_t s);
+// Dynamic shared memory (bytes) of the FP64 mode-product kernel for this one job.
+int64_t mode_product_smem(const ModeArgs<double>& m);
 
 // Fused FP64 fast-diagonalisation passes (App. A.4), several tensors per launch. The operators
 // are square with parity-split eigenvector columns (eo even modes first, eo >= 1), as for

@@ -556,8 +556,34 @@ __global__ void __launch_bounds__(512) k_fd_line3(const __grid_constant__ LineBa
 }
 }  // namespace
 
+// Lines per block of k_mode_tile for one job, and the dynamic shared memory that job needs:
+// inputs [K][groups + 1]; outputs staged when the lines are contiguous (L == 1); folded inputs
+// (even/odd forward).
+namespace {
+int mode_tile_target(const ModeArgs<double>& m) {
+  return m.block > 0 ? std::min(m.block, 512) : 512;
+}
+int mode_tile_groups(const ModeArgs<double>& m, int target) {
+  // threads per line: one per output, or one per mirrored output pair (even/odd backward)
+  const int tpl = (m.eo_he && !m.trans) ? m.eo_he : m.m;
+  return tpl >= target ? 1 : target / tpl;
+}
+int64_t mode_tile_smem(const ModeArgs<double>& m, int target) {
+  const int K = m.in.get(m.axis);
+  const int groups = mode_tile_groups(m, target);
+  // contiguous lines (stride 1 between the lines' first elements: axis 1, or axis 2 with n1 = 1)
+  const int64_t L = m.axis == 1 ? 1 : (m.axis == 2 ? m.in.n1 : (int64_t)m.in.n1 * m.in.n2);
+  return (int64_t)(K + (L == 1 ? m.m : 0) + ((m.eo_he && m.trans) ? K : 0)) * (groups + 1) *
+         (int64_t)sizeof(double);
+}
+}  // namespace
+
+int64_t mode_product_smem(const ModeArgs<double>& m) {
+  return mode_tile_smem(m, mode_tile_target(m));
+}
+
 template <>
-void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStream_t s) {
+cudaError_t mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStream_t s) {
   RowBatch rb{};
   rb.njobs = njobs;
   int blocks = 0, smem = 0, threads = 32;
@@ -582,7 +608,7 @@ void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStr
     J.fwd = m.trans ? 1 : 0;
     // threads per line: one per output, or one per mirrored output pair (even/odd backward)
     const int tpl = (J.eo && !J.fwd) ? J.eo : m.m;
-    J.groups = tpl >= target ? 1 : target / tpl;  // lines per block
+    J.groups = mode_tile_groups(m, target);  // lines per block
     J.invd = m.invd;
     J.lam1 = m.invd ? nullptr : m.lam1;
     J.lam2 = m.lam2;
@@ -593,11 +619,9 @@ void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStr
     first_block[j] = blocks;
     blocks += (int)((J.L * J.R + J.groups - 1) / J.groups);
     threads = std::max(threads, std::min(target, ((J.groups * tpl + 31) / 32) * 32));
-    // inputs [K][P]; outputs staged when the lines are contiguous (L == 1); folded inputs
-    // (even/odd forward)
-    const int sm = (J.K + (J.L == 1 ? J.m : 0) + ((J.eo && J.fwd) ? J.K : 0)) * (J.groups + 1) *
-                   (int)sizeof(double);
-    smem = sm > smem ? sm : smem;
+    const int64_t sm = mode_tile_smem(m, target);
+    if (sm > 1024 * 1024) return cudaErrorInvalidValue;
+    smem = sm > smem ? (int)sm : smem;
     if (J.eo) {   // even/odd split: two half-size products per line
       const double he = J.eo, ho = J.K - J.eo;
       flops += 2.0 * J.L * J.R * (he * he + ho * ho);
@@ -609,10 +633,12 @@ void mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, cudaStr
   first_block[njobs] = blocks;
   for (int j = 0; j <= njobs; ++j) rb.first[j] = first_block[j];
   static std::atomic<int> attr{0};
-  raise_smem_limit(k_mode_tile, attr, smem);
+  const cudaError_t e = raise_smem_limit(k_mode_tile, attr, smem);
+  if (e != cudaSuccess) return e;
   launch_begin(kClassMode, s);
-  launch_k(k_mode_tile, blocks, threads, smem, s, rb);
+  const cudaError_t l = launch_k(k_mode_tile, blocks, threads, smem, s, rb);
   launch_end(kClassMode, s, flops, bytes);
+  return l;
 }
 
 
@@ -716,7 +742,7 @@ bool fd_line3_multi(const FdLineArgs* jobs, int njobs, int block, cudaStream_t s
 }
 
 template <typename T>
-void mode_product_multi(const ModeArgs<T>* jobs, int njobs, cudaStream_t s) {
+cudaError_t mode_product_multi(const ModeArgs<T>* jobs, int njobs, cudaStream_t s) {
   GemmBatch<T> gb{};
   gb.njobs = njobs;
   int blocks = 0;
@@ -732,17 +758,18 @@ void mode_product_multi(const ModeArgs<T>* jobs, int njobs, cudaStream_t s) {
   }
   gb.first_block[njobs] = blocks;
   launch_begin(kClassMode, s);
-  launch_k(k_gemm<T>, blocks, Tile<T>::NTH, 0, s, gb);
+  const cudaError_t l = launch_k(k_gemm<T>, blocks, Tile<T>::NTH, 0, s, gb);
   launch_end(kClassMode, s, flops, bytes);
+  return l;
 }
 
 template <typename T>
-void mode_product(const ModeArgs<T>& m, cudaStream_t s) {
-  mode_product_multi<T>(&m, 1, s);
+cudaError_t mode_product(const ModeArgs<T>& m, cudaStream_t s) {
+  return mode_product_multi<T>(&m, 1, s);
 }
 
-template void mode_product<double>(const ModeArgs<double>&, cudaStream_t);
-template void mode_product<float>(const ModeArgs<float>&, cudaStream_t);
-template void mode_product_multi<float>(const ModeArgs<float>*, int, cudaStream_t);
+template cudaError_t mode_product<double>(const ModeArgs<double>&, cudaStream_t);
+template cudaError_t mode_product<float>(const ModeArgs<float>&, cudaStream_t);
+template cudaError_t mode_product_multi<float>(const ModeArgs<float>*, int, cudaStream_t);
 
 }  // namespace shp

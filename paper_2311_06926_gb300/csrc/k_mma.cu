@@ -71,8 +71,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // flag and the global error flag) if it does not complete within the limit or if another role
 // has already aborted.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          int* err) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+                                          int* err, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
     if (i > 64) __nanosleep(128);
@@ -167,6 +167,7 @@ struct RmpBatch {
   RmpJob job[kMaxRmpJobs];
   int njobs;
   int total_tiles;
+  uint32_t spin_limit;   // polls of each pipeline wait before it gives up (drain waits: kSpinLimit)
 };
 
 __device__ __forceinline__ int job_of(const RmpBatch& b, int t) {
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const RmpJob& J = batch.job[j];
         if (j != cur) {
           // operator of job j; when replacing one, wait until its last MMAs have completed
-          if (nb > 0 && !mbar_wait(&b_free_bar, (nb - 1) & 1, abort_p, err)) break;
+          if (nb > 0 && !mbar_wait(&b_free_bar, (nb - 1) & 1, abort_p, err, batch.spin_limit)) break;
           mbar_expect_tx(&b_bar, (uint32_t)(J.nchunks * J.args.npad * kChunkBytes));
           for (int c = 0; c < J.nchunks; ++c)
             tma_load_2d(b_tile + c * J.args.npad * kChunkBytes, &J.map_op, c * chunk_elems, 0,
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int c = 0; c < J.nchunks; ++c, ++it) {
           const int s = it % kStages;
           const uint32_t ph = (it / kStages) & 1;
-          if (it >= kStages && !mbar_wait(&empty_bar[s], ph ^ 1, abort_p, err)) {
+          if (it >= kStages && !mbar_wait(&empty_bar[s], ph ^ 1, abort_p, err, batch.spin_limit)) {
             ok = false;
             break;
           }
@@ -275,17 +276,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int j = job_of(batch, t);
         const RmpJob& J = batch.job[j];
         if (j != cur) {
-          if (!mbar_wait(&b_bar, nbw & 1, abort_p, err)) break;
+          if (!mbar_wait(&b_bar, nbw & 1, abort_p, err, batch.spin_limit)) break;
           ++nbw;
           cur = j;
         }
         const int acc = local & 1;
         const uint32_t d_tmem = tmem + acc * 256;
-        if (local >= 2 && !mbar_wait(&tempty_bar[acc], ((local / 2) - 1) & 1, abort_p, err)) break;
+        if (local >= 2 && !mbar_wait(&tempty_bar[acc], ((local / 2) - 1) & 1, abort_p, err, batch.spin_limit)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         for (int c = 0; c < J.nchunks; ++c, ++it) {
           const int s = it % kStages;
-          if (!mbar_wait(&full_bar[s], (it / kStages) & 1, abort_p, err)) {
+          if (!mbar_wait(&full_bar[s], (it / kStages) & 1, abort_p, err, batch.spin_limit)) {
             ok = false;
             break;
           }
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const RmpArgs& args = J.args;
       const int acc = local & 1;
       int ok = 1;
-      if (lane == 0) ok = mbar_wait(&tfull_bar[acc], (local / 2) & 1, abort_p, err) ? 1 : 0;
+      if (lane == 0) ok = mbar_wait(&tfull_bar[acc], (local / 2) & 1, abort_p, err, batch.spin_limit) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -454,7 +455,8 @@ uint32_t rmp_idesc(int kind, int npad) {
 }
 
 template <int KIND, typename TO>
-void launch_rmp_t(const RmpPlan* const* plans, int njobs, int* err, int sms, cudaStream_t s) {
+void launch_rmp_t(const RmpPlan* const* plans, int njobs, int* err, int sms, cudaStream_t s,
+                  uint32_t spin_limit) {
   RmpBatch b{};
   b.njobs = njobs;
   int tiles = 0, smem = 0;
@@ -477,6 +479,7 @@ void launch_rmp_t(const RmpPlan* const* plans, int njobs, int* err, int sms, cud
     bytes += (double)rows * (p.args.K * elem + p.args.m * (double)sizeof(TO));
   }
   b.total_tiles = tiles;
+  b.spin_limit = spin_limit > 0 ? spin_limit : kSpinLimit;
   const int grid = tiles < sms ? tiles : sms;
   if (smem < 116 * 1024) smem = 116 * 1024;   // one CTA, one 512-column TMEM allocation per SM
   static std::atomic<int> attr{0};
@@ -486,11 +489,13 @@ void launch_rmp_t(const RmpPlan* const* plans, int njobs, int* err, int sms, cud
   launch_end(kClassMma, s, flops, bytes);
 }
 
-void launch_rmp_multi(const RmpPlan* const* plans, int njobs, int* err, int sms, cudaStream_t s) {
+void launch_rmp_multi(const RmpPlan* const* plans, int njobs, int* err, int sms, cudaStream_t s,
+                      uint32_t spin_limit) {
   const RmpPlan& p = *plans[0];
-  if (p.kind == kMmaTF32) launch_rmp_t<kMmaTF32, float>(plans, njobs, err, sms, s);
-  else if (p.out_bf16) launch_rmp_t<kMmaBF16, __nv_bfloat16>(plans, njobs, err, sms, s);
-  else launch_rmp_t<kMmaBF16, float>(plans, njobs, err, sms, s);
+  if (p.kind == kMmaTF32) launch_rmp_t<kMmaTF32, float>(plans, njobs, err, sms, s, spin_limit);
+  else if (p.out_bf16)
+    launch_rmp_t<kMmaBF16, __nv_bfloat16>(plans, njobs, err, sms, s, spin_limit);
+  else launch_rmp_t<kMmaBF16, float>(plans, njobs, err, sms, s, spin_limit);
 }
 
 void pad_rows(const float* x, int e1, int64_t R, int ld, void* y, bool to_bf16, cudaStream_t s,
@@ -509,9 +514,9 @@ void pad_rows(const float* x, int e1, int64_t R, int ld, void* y, bool to_bf16, 
   launch_end(kClassVector, s, 0.0, (double)total * (to_bf16 ? 6.0 : 8.0));
 }
 
-void launch_rmp(const RmpPlan& p, int* err, int sms, cudaStream_t s) {
+void launch_rmp(const RmpPlan& p, int* err, int sms, cudaStream_t s, uint32_t spin_limit) {
   const RmpPlan* one = &p;
-  launch_rmp_multi(&one, 1, err, sms, s);
+  launch_rmp_multi(&one, 1, err, sms, s, spin_limit);
 }
 
 }  // namespace shp

@@ -43,8 +43,12 @@ int rmp_smem_bytes(int kind, int K, int npad);
 bool rmp_supported(int kind, int K, int m);
 bool make_map(void* map, const void* base, int kind, int cols, int64_t rows, int ld, int box_rows);
 uint32_t rmp_idesc(int kind, int npad);
-void launch_rmp(const RmpPlan& p, int* err, int sms, cudaStream_t s);
-void launch_rmp_multi(const RmpPlan* const* plans, int njobs, int* err, int sms, cudaStream_t s);
+// spin_limit: polls of each pipeline wait before it gives up and raises *err (0: the default,
+// 2^22 polls of at least 128 ns each after the first 64); the kernel's final waits for its own
+// copies and tensor-core operations in flight always use the default.
+void launch_rmp(const RmpPlan& p, int* err, int sms, cudaStream_t s, uint32_t spin_limit = 0);
+void launch_rmp_multi(const RmpPlan* const* plans, int njobs, int* err, int sms, cudaStream_t s,
+                      uint32_t spin_limit = 0);
 
 // Copy a canonical float tensor (rows of e1 entries, R rows) into rows of pitch ld, converting
 // to bfloat16 if to_bf16. nb items: item k's tensor starts xbs elements after item k - 1's in x,

@@ -57,6 +57,13 @@ extern "C" int stokes_fd_apply_noalloc(int n1, int n2, int n3, const double* U1,
       !(scale > 0.0))
     return STOKES_ERR_ARG;
   if ((int64_t)n1 * n2 * n3 > kNoallocTensor) return STOKES_ERR_ARG;
+  // every one of the six mode products must fit the device's shared memory per block (staged
+  // lines of the contracted extent); checked before anything is launched
+  int dev = -1, smem_max = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+          cudaSuccess)
+    return STOKES_ERR_CUDA;
   double* scratch = nullptr;
   if (scratch_address(&scratch) != cudaSuccess) return STOKES_ERR_CUDA;
   double* f1 = scratch;
@@ -65,7 +72,7 @@ extern "C" int stokes_fd_apply_noalloc(int n1, int n2, int n3, const double* U1,
   const Dims d{n1, n2, n3};
   const double* U[3] = {U1, U2, U3};
   const int n[3] = {n1, n2, n3};
-  auto mode = [&](const double* X, double* Y, int k, int trans, bool last_forward) {
+  auto job = [&](const double* X, double* Y, int k, int trans, bool last_forward) {
     ModeArgs<double> m{};
     m.X = X;
     m.Y = Y;
@@ -82,13 +89,15 @@ extern "C" int stokes_fd_apply_noalloc(int n1, int n2, int n3, const double* U1,
       m.scale = scale;
     }
     m.post = 1.0;
-    mode_product<double>(m, s);
+    return m;
   };
-  mode(x, f1, 0, 1, false);
-  mode(f1, f2, 1, 1, false);
-  mode(f2, f1, 2, 1, true);
-  mode(f1, f2, 2, 0, false);
-  mode(f2, f1, 1, 0, false);
-  mode(f1, y, 0, 0, false);
-  return cudaGetLastError() == cudaSuccess ? STOKES_OK : STOKES_ERR_CUDA;
+  const ModeArgs<double> seq[6] = {job(x, f1, 0, 1, false),  job(f1, f2, 1, 1, false),
+                                   job(f2, f1, 2, 1, true),  job(f1, f2, 2, 0, false),
+                                   job(f2, f1, 1, 0, false), job(f1, y, 0, 0, false)};
+  for (const ModeArgs<double>& m : seq)
+    if (mode_product_smem(m) > smem_max) return STOKES_ERR_ARG;
+  // each launch's own status; the first failure stops the sequence
+  for (const ModeArgs<double>& m : seq)
+    if (mode_product<double>(m, s) != cudaSuccess) return STOKES_ERR_CUDA;
+  return STOKES_OK;
 }

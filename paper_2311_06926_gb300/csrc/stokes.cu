@@ -213,6 +213,7 @@ struct Ops {
   bool tc_bf16 = false;
   int sms = 152;
   int* tc_err = nullptr;
+  uint32_t tc_spin = 0;         // polls per pipeline wait of the tensor-core kernel (0: default)
   void* tc_p0[4] = {nullptr, nullptr, nullptr, nullptr};
   int tc_ld0[4] = {0, 0, 0, 0};
   RmpPlan* tc_plan = nullptr;   // [4][6], host memory
@@ -463,7 +464,7 @@ struct Ops {
         p.args.Y = y;
         p.args.ybs = bs;
       }
-      launch_rmp(p, tc_err, sms, s);
+      launch_rmp(p, tc_err, sms, s, tc_spin);
     }
   }
 
@@ -492,7 +493,7 @@ struct Ops {
           }
           pp[c] = &p[c];
         }
-        launch_rmp_multi(pp, 3, tc_err, sms, s);
+        launch_rmp_multi(pp, 3, tc_err, sms, s, tc_spin);
       }
       return;
     }
@@ -2435,6 +2436,14 @@ int stokes_set_tuning(stokes_t c, const stokes_tuning* t) {
     if (!ok) return fail(c, STOKES_ERR_ARG, "fused fast diagonalisation does not fit this mesh");
   }
   set_shapes(c, *t);
+  return STOKES_OK;
+}
+
+int stokes_set_wait_limit(stokes_t c, int64_t polls) {
+  if (!c) return STOKES_ERR_ARG;
+  if (polls < 0 || polls > (int64_t)UINT32_MAX)
+    return fail(c, STOKES_ERR_ARG, "wait limit outside [0, 2^32)");
+  c->of.tc_spin = (uint32_t)polls;
   return STOKES_OK;
 }
 

@@ -295,3 +295,27 @@ def test_fused_fast_diagonalisation_profile():
         assert counts[ff]["launches"] == 6
         assert counts[0]["flops"] == pytest.approx(counts[ff]["flops"], rel=1e-12)
     G.close()
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_tensor_core_wait_runs_out(prec):
+    """The tensor-core mode products bound every pipeline wait. With the test hook's limit of one
+    poll the first wait gives up before its copy lands: the kernel raises the context's error
+    flag, finishes its copies and tensor-core work in flight, frees its tensor memory and returns,
+    and the call fails with STOKES_ERR_CUDA instead of hanging. The device stays usable: a new
+    context gives the result of one made before."""
+    from paper_2311_06926_gb300 import Stokes, StokesError
+    x = torch.from_numpy(synthetic.random_vector(Stokes(16, 3, precision=prec).size, 31)).cuda()
+    G = Stokes(16, 3, precision=prec)
+    ref = G.apply_P(x).clone()
+    G.close()
+    G = Stokes(16, 3, precision=prec)
+    G.set_wait_limit(1)
+    with pytest.raises(StokesError) as exc:
+        G.apply_P(x)
+    assert exc.value.code == -2 and "timed out" in str(exc.value)
+    G.close()
+    G = Stokes(16, 3, precision=prec)
+    G.set_wait_limit(0)
+    assert torch.equal(G.apply_P(x), ref)
+    G.close()
