@@ -121,23 +121,36 @@ def load_golden(path=GOLDEN_128):
         return json.load(fh)
 
 
-def oracle_error(x, g):
-    """Error of a solution x (host float64, pressure zero-mean) against the oracle's stored
-    solution: ``rel_2norm_est`` = sqrt(N / n sum_samples (x_i - x_o,i)^2) / ||x_o|| (an unbiased
-    estimate of ||x - x_o||^2 / ||x_o||^2 from the n seeded sampled entries), ``max_sampled`` =
-    max |x_i - x_o,i| / max |x_o| over the samples, ``functionals`` = max_k |<x - x_o, w_k>| /
-    (||x_o|| ||w_k||) over the seeded vectors (every entry of x contributes)."""
+_FUNCTIONAL_VECTORS = {}
+
+
+def oracle_error(x, g, prefix="exact_"):
+    """Error of a solution x (host float64, pressure zero-mean) against a stored oracle solution
+    (prefix "exact_": the oracle's MINRES solve to 1e-11, the reference for accuracy; "": its
+    solve to 1e-8 with the same preconditioner): ``rel_2norm_est`` = sqrt(N / n sum_samples
+    (x_i - x_o,i)^2) / ||x_o|| (an unbiased estimate of ||x - x_o||^2 / ||x_o||^2 from the n
+    seeded sampled entries), ``max_sampled`` = max |x_i - x_o,i| / max |x_o| over the samples,
+    ``functionals`` = max_k |<x - x_o, w_k>| / (||x_o|| ||w_k||) over the seeded vectors (every
+    entry of x contributes), ``max`` the largest of the last two and the block-norm errors."""
     import numpy as np
     from paper_2311_06926_gb300 import synthetic
     idx = np.asarray(g["sample_index"])
-    d = x[idx] - np.asarray(g["sample_value"])
-    est = float(np.sqrt(g["size"] / len(idx) * np.sum(d * d)) / g["norm2"])
+    d = x[idx] - np.asarray(g[prefix + "sample_value"])
+    est = float(np.sqrt(g["size"] / len(idx) * np.sum(d * d)) / g[prefix + "norm2"])
     fun = 0.0
-    for k, val in enumerate(g["functionals"]):
-        w = synthetic.random_vector(g["size"], g["functional_seed"] + k)
-        fun = max(fun, abs(float(np.dot(x, w)) - val) / (g["norm2"] * float(np.linalg.norm(w))))
-    return {"rel_2norm_est": est, "max_sampled": float(np.abs(d).max() / g["max_abs"]),
-            "functionals": fun}
+    for k, val in enumerate(g[prefix + "functionals"]):
+        key = (g["size"], g["functional_seed"] + k)
+        if key not in _FUNCTIONAL_VECTORS:
+            w = synthetic.random_vector(*key)
+            _FUNCTIONAL_VECTORS[key] = (w, float(np.linalg.norm(w)))
+        w, wn = _FUNCTIONAL_VECTORS[key]
+        fun = max(fun, abs(float(np.dot(x, w)) - val) / (g[prefix + "norm2"] * wn))
+    blocks = np.cumsum([0, g["n_vel"] // 3, g["n_vel"] // 3, g["n_vel"] // 3, g["n_pres"]])
+    nrm = max(abs(float(np.linalg.norm(x[blocks[k]:blocks[k + 1]])) -
+                  g[prefix + "block_norm2"][k]) / g[prefix + "norm2"] for k in range(4))
+    samp = float(np.abs(d).max() / g[prefix + "max_abs"])
+    return {"rel_2norm_est": est, "max_sampled": samp, "functionals": fun,
+            "max": max(samp, fun, nrm)}
 
 
 def aggregate(ms_local, units_local, dist=None):
@@ -712,7 +725,7 @@ def run_cavity128(args, wl):
     value, ms_max = aggregate(ms, args.steps, dist if ws > 1 else None)
     x_head = x.cpu().numpy()
     head = {"ms": ms / args.steps, "iterations": last["it"], "true_rel_res": last["rr"],
-            "solver": "fgmres", "error_vs_oracle": oracle_error(x_head, g)}
+            "tol": tol, "solver": "fgmres"}
 
     # end to end through the host-buffer C-ABI call (pinned host memory, copies in the call)
     rhs_h = f.cpu().pin_memory()
@@ -769,53 +782,82 @@ def run_cavity128(args, wl):
 
     forms = None
     if ws == 1:
-        def timed_solve(Gx, tol_x, reps=3):
+        def timed_solve(Gx, fx, tol_x, reps=3):
             xx = Gx.empty()
-            Gx.solve(f if Gx is G else fx[Gx], tol_x, out=xx)
+            Gx.solve(fx, tol_x, out=xx)
             times, it_x, rr_x = [], 0, 0.0
             for _ in range(reps):
                 flush.fill_(1.0)
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 torch.cuda.synchronize()
                 a.record(cur)
-                _, it_x, rr_x, _ = Gx.solve(f if Gx is G else fx[Gx], tol_x, out=xx)
+                _, it_x, rr_x, _ = Gx.solve(fx, tol_x, out=xx)
                 b.record(cur)
                 torch.cuda.synchronize()
                 times.append(a.elapsed_time(b))
+            xh = xx.cpu().numpy()
             return {"ms": statistics.median(times), "iterations": it_x, "true_rel_res": rr_x,
-                    "tol": tol_x, "error_vs_oracle": oracle_error(xx.cpu().numpy(), g)}
+                    "tol": tol_x, "error_vs_exact": oracle_error(xh, g)}, xh
 
-        fx = {}
-        forms = {prec: head}
-        G64 = Stokes(n, p, precision="fp64", max_order=q, max_steps=s)
-        G64.set_preconditioner(q, s)
-        fx[G64] = G64.rhs_cavity(1.0)
-        forms["fp64"] = dict(timed_solve(G64, tol), solver="minres",
-                             stopping="||r||_{P^-1} / ||f||_{P^-1} <= 1e-8 (Table 1)")
+        def equal_accuracy(Gx, fx, target):
+            """The mixed form stopped at the first tolerance of a decreasing ladder whose
+            solution is at least as accurate (largest error measure against the oracle's tight
+            solution) as the target."""
+            for t in (1e-8, 3e-9, 1e-9, 3e-10, 1e-10, 3e-11, 1e-11, 3e-12):
+                r, _ = timed_solve(Gx, fx, t)
+                if r["error_vs_exact"]["max"] <= target:
+                    return dict(r, matched=True)
+            return dict(r, matched=False)
+
+        forms = {"error_measure":
+                 "against the oracle's MINRES solve to 1e-11 (tests/golden/cavity128_p3_q2s2.json): "
+                 "rel_2norm_est = sqrt(N/n sum over 1024 seeded sampled entries of (x - x_o)^2) / "
+                 "||x_o||; max = the largest of the sampled-entry, block-norm and seeded-inner-"
+                 "product errors (as in tests/test_gpu_fullsize.py)",
+                 "oracle": {"iterations": g["iterations"], "true_rel_res": g["true_rel_res"],
+                            "error_vs_exact": g["error_vs_exact"],
+                            "note": "the oracle's own MINRES solve (order 2, 2 steps) to 1e-8"}}
+        head["error_vs_exact"] = oracle_error(x_head, g)
+        forms[prec] = head
+        # the plain FP64 form (MINRES to 1e-8, Table 1's criterion) with each preconditioner of a
+        # short sweep; the fastest is the FP64 form's best
+        G64 = Stokes(n, p, precision="fp64", max_order=3, max_steps=2)
+        f64 = G64.rhs_cavity(1.0)
+        sweep64 = []
+        for qq, ss in ((2, 0), (2, 1), (3, 1), (2, 2)):
+            G64.set_preconditioner(qq, ss)
+            r, xh = timed_solve(G64, f64, tol, reps=2)
+            r.update(order=qq, steps=ss, solver="minres")
+            if (qq, ss) == (q, s):
+                r["error_vs_oracle_same_solve"] = oracle_error(xh, g, "")
+            sweep64.append(r)
         G64.close()
         del G64
-        rr64 = forms["fp64"]["true_rel_res"]
-        forms[f"{prec}_at_fp64_residual"] = dict(timed_solve(G, rr64), solver="fgmres",
-                                                 stopping="true residual <= the FP64 solve's")
+        torch.cuda.empty_cache()
+        best64 = min(sweep64, key=lambda r: r["ms"])
+        forms["fp64_sweep"] = sweep64
+        forms["fp64"] = next(r for r in sweep64 if (r["order"], r["steps"]) == (q, s))
+        forms["fp64_best"] = best64
+        target = best64["error_vs_exact"]["max"]
+        forms[f"{prec}_equal_accuracy"] = dict(equal_accuracy(G, f, target), target_error=target)
         other = "bf16" if prec == "tf32" else "tf32"
         Go = Stokes(n, p, precision=other, max_order=q, max_steps=s)
         Go.set_preconditioner(q, s)
-        fx[Go] = Go.rhs_cavity(1.0)
-        forms[other] = dict(timed_solve(Go, tol), solver="fgmres")
-        forms[f"{other}_at_fp64_residual"] = dict(timed_solve(Go, rr64), solver="fgmres",
-                                                  stopping="true residual <= the FP64 solve's")
+        fo = Go.rhs_cavity(1.0)
+        forms[other] = timed_solve(Go, fo, tol)[0]
+        forms[f"{other}_equal_accuracy"] = dict(equal_accuracy(Go, fo, target),
+                                                target_error=target)
         Go.close()
         del Go
         torch.cuda.empty_cache()
-        f64ms = forms["fp64"]["ms"]
-        forms["speedup_vs_fp64"] = {
-            k: f64ms / v["ms"] for k, v in forms.items() if isinstance(v, dict) and k != "fp64"}
-        forms["oracle_reference"] = {
-            "iterations": g["iterations"], "true_rel_res": g["true_rel_res"],
-            "source": "tests/golden/cavity128_p3_q2s2.json (oracle MINRES, order 2, 2 steps)",
-            "error_measure": "rel_2norm_est: sqrt(N/n sum over 1024 seeded sampled entries of "
-                             "(x - x_oracle)^2) / ||x_oracle||; max_sampled and functionals as "
-                             "in tests/test_gpu_fullsize.py"}
+        f64ms, b64ms = forms["fp64"]["ms"], best64["ms"]
+        forms["speedup"] = {
+            "vs_fp64_same_preconditioner": {k: f64ms / forms[k]["ms"] for k in (prec, other)},
+            "vs_fp64_best": {k: b64ms / forms[k]["ms"]
+                             for k in (prec, other, f"{prec}_equal_accuracy",
+                                       f"{other}_equal_accuracy")},
+            "note": "equal_accuracy: the mixed form stopped where its error against the oracle's "
+                    "tight solution is no larger than the fastest FP64 solve's"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -285,12 +285,17 @@ void copy_rows(void* dst, const void* src, size_t row_bytes, int nb, size_t pitc
 // y += sign * (*alpha) * x with alpha in device memory
 void axpy_dev(const double* alpha, double sign, const double* x, double* y, int64_t n,
               cudaStream_t s);
-// y[k] = <V_k, w> for k < nvec (V_k = V + k * ldv); deterministic, partials: nvec * kMultiDotBlocks
+// y[k] = <V_k, w> for k < nvec (V_k = V + k * ldv); with with_self also y[nvec] = <w, w> from
+// the same pass; deterministic; partials: (nvec + 1) * kMultiDotBlocks
 void multi_dot(const double* V, int64_t ldv, int nvec, const double* w, int64_t n,
-               double* partials, double* out, cudaStream_t s);
+               double* partials, double* out, cudaStream_t s, bool with_self = false);
 // w += sign * sum_k h[k] V_k (h in device memory)
 void multi_axpy(const double* V, int64_t ldv, int nvec, const double* h, double sign, double* w,
                 int64_t n, cudaStream_t s);
+// out = (w + sign * sum_k h[k] V_k) * (1 / *div), in that order of operations (the same bits as
+// multi_axpy followed by scale_inv_dev); out may be w
+void multi_axpy_div(const double* V, int64_t ldv, int nvec, const double* h, double sign,
+                    const double* w, const double* div, double* out, int64_t n, cudaStream_t s);
 // y = x * (1 / *alpha)
 void scale_inv_dev(const double* alpha, const double* x, double* y, int64_t n, cudaStream_t s);
 void fill_zero(void* dst, size_t bytes, cudaStream_t s);

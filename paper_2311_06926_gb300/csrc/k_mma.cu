@@ -143,6 +143,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Round to the nearest TF32 value (10 explicit mantissa bits, ties away from zero), kept in FP32
+// format. The tensor cores read an FP32 operand as TF32 by dropping its low 13 mantissa bits
+// (truncation, a bias toward zero of up to one TF32 ulp); operands rounded here first carry an
+// unbiased error of at most half an ulp instead.
+__device__ __forceinline__ float round_tf32(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+
 template <typename TO>
 __device__ __forceinline__ void store_val(TO* p, float v);
 template <>
@@ -337,6 +347,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       const int64_t stride_i = (int64_t)args.ldy * args.e3;
       const float post = args.post, scale = args.scale;
+      const bool rt = args.round_tf32 != 0;
       for (int c0 = half * 32; c0 < args.npad; c0 += 64) {
         float v[32];
         tmem_ld32(tmem + acc * 256 + ((uint32_t)(quarter * 32) << 16) + c0, v);
@@ -347,13 +358,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float* li = args.lam_i + c0;
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
-              if (k < kmax) store_val<TO>(yp, __fdividef(v[k], scale * (lam_r + li[k])));
+              if (k < kmax) {
+                const float val = __fdividef(v[k], scale * (lam_r + li[k]));
+                store_val<TO>(yp, rt ? round_tf32(val) : val);
+              }
               yp += stride_i;
             }
           } else {
 #pragma unroll
             for (int k = 0; k < 32; ++k) {
-              if (k < kmax) store_val<TO>(yp, v[k] * post);
+              if (k < kmax) {
+                const float val = v[k] * post;
+                store_val<TO>(yp, rt ? round_tf32(val) : val);
+              }
               yp += stride_i;
             }
           }
@@ -388,7 +405,11 @@ __global__ void k_pad_rows(const float* __restrict__ x, int e1, int64_t R, int l
     const int64_t k = nb > 1 ? r / R : 0;     // item
     const float* src = x + k * xbs + (r - k * R) * e1;
     TO* dst = y + r * ld;
-    for (int j = lane; j < e1; j += 32) store_val<TO>(dst + j, src[j]);
+    for (int j = lane; j < e1; j += 32) {
+      // the FP32 copy feeds TF32 products: rounded to TF32 here (BF16 rounds in store_val)
+      if constexpr (sizeof(TO) == 4) store_val<TO>(dst + j, round_tf32(src[j]));
+      else store_val<TO>(dst + j, src[j]);
+    }
   }
 }
 

@@ -232,17 +232,21 @@ __global__ void __launch_bounds__(kThreads, 4) k_sep_dot_partial(const double* _
   }
 }
 
-template <int NG>
+// SELF: the block also sums w_i^2 in the same order (one more accumulator), written as partial
+// row self_row, so <w, w> comes with the products at no extra read of w.
+template <int NG, bool SELF>
 __global__ void __launch_bounds__(kThreads, 4) k_multi_dot_partial(const double* __restrict__ V,
                                                                 int64_t ldv, int k0,
                                                                 const double* __restrict__ w,
                                                                 int64_t n,
-                                                                double* __restrict__ partials) {
+                                                                double* __restrict__ partials,
+                                                                int self_row) {
   pdl_begin();
-  __shared__ double sh[NG][kThreads / 32];
-  double acc[NG];
+  constexpr int NA = NG + (SELF ? 1 : 0);
+  __shared__ double sh[NA][kThreads / 32];
+  double acc[NA];
 #pragma unroll
-  for (int g = 0; g < NG; ++g) acc[g] = 0.0;
+  for (int g = 0; g < NA; ++g) acc[g] = 0.0;
   const double* v0 = V + (int64_t)k0 * ldv;
   const int64_t step = (int64_t)gridDim.x * kThreads;
   int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
@@ -256,23 +260,26 @@ __global__ void __launch_bounds__(kThreads, 4) k_multi_dot_partial(const double*
     }
 #pragma unroll
     for (int g = 0; g < NG; ++g) acc[g] = fma(vb[g], wb, fma(va[g], wa, acc[g]));
+    if (SELF) acc[NG] = fma(wb, wb, fma(wa, wa, acc[NG]));
   }
   if (i < n) {
     const double wa = w[i];
 #pragma unroll
     for (int g = 0; g < NG; ++g) acc[g] = fma(v0[g * ldv + i], wa, acc[g]);
+    if (SELF) acc[NG] = fma(wa, wa, acc[NG]);
   }
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
 #pragma unroll
-  for (int g = 0; g < NG; ++g) {
+  for (int g = 0; g < NA; ++g) {
     const double t = warp_sum(acc[g]);
     if (lane == 0) sh[g][warp] = t;
   }
   __syncthreads();
-  if ((int)threadIdx.x < NG) {
+  if ((int)threadIdx.x < NA) {
     double t = 0.0;
     for (int k = 0; k < kThreads / 32; ++k) t += sh[threadIdx.x][k];
-    partials[(int64_t)(k0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+    const int row = (int)threadIdx.x < NG ? k0 + (int)threadIdx.x : self_row;
+    partials[(int64_t)row * gridDim.x + blockIdx.x] = t;
   }
 }
 
@@ -291,14 +298,18 @@ __global__ void __launch_bounds__(kThreads) k_multi_dot_final(const double* __re
 // sums per element so the loads of several vectors are in flight together.
 constexpr int kAxpyMaxVec = 512;   // restart <= 400 (checked at setup)
 
+// out = (w + sign * sum_k h[k] V_k) / *div (div may be null: no division; out may be w).
 __global__ void __launch_bounds__(kThreads) k_multi_axpy(const double* __restrict__ V, int64_t ldv,
                                                          int nvec, const double* __restrict__ h,
-                                                         double sign, double* __restrict__ w,
+                                                         double sign, const double* w,
+                                                         double* out, const double* div,
                                                          int64_t n) {
   pdl_begin();
   __shared__ double hs[kAxpyMaxVec];
   for (int k = threadIdx.x; k < nvec; k += kThreads) hs[k] = h[k];
   __syncthreads();
+  const bool scaled = div != nullptr;
+  const double a = scaled ? 1.0 / (*div) : 1.0;
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kThreads) {
     double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
@@ -311,7 +322,8 @@ __global__ void __launch_bounds__(kThreads) k_multi_axpy(const double* __restric
       s3 = fma(hs[k + 3], v[(k + 3) * ldv], s3);
     }
     for (; k < nvec; ++k) s0 = fma(hs[k], v[k * ldv], s0);
-    w[i] += sign * ((s0 + s1) + (s2 + s3));
+    const double r = w[i] + sign * ((s0 + s1) + (s2 + s3));
+    out[i] = scaled ? a * r : r;
   }
 }
 
@@ -505,24 +517,32 @@ void scale_inv_dev(const double* alpha, const double* x, double* y, int64_t n, c
   launch_end(kClassVector, s, (double)n, 16.0 * (double)n);
 }
 void multi_dot(const double* V, int64_t ldv, int nvec, const double* w, int64_t n,
-               double* partials, double* out, cudaStream_t s) {
+               double* partials, double* out, cudaStream_t s, bool with_self) {
   for (int k0 = 0; k0 < nvec; k0 += kDotGroup) {
     const int ng = nvec - k0 < kDotGroup ? nvec - k0 : kDotGroup;
+    const bool self = with_self && k0 == 0;
     launch_begin(kClassVector, s);
     switch (ng) {
-#define SHP_MDOT(g)                                                                              \
-  case g:                                                                                        \
-    launch_k(k_multi_dot_partial<g>, kMultiDotBlocks, kThreads, 0, s, V, ldv, k0, w, n, partials);     \
+#define SHP_MDOT(g)                                                                             \
+  case g:                                                                                       \
+    if (self)                                                                                   \
+      launch_k(k_multi_dot_partial<g, true>, kMultiDotBlocks, kThreads, 0, s, V, ldv, k0, w, n, \
+               partials, nvec);                                                                 \
+    else                                                                                        \
+      launch_k(k_multi_dot_partial<g, false>, kMultiDotBlocks, kThreads, 0, s, V, ldv, k0, w,   \
+               n, partials, nvec);                                                              \
     break;
       SHP_MDOT(1) SHP_MDOT(2) SHP_MDOT(3) SHP_MDOT(4) SHP_MDOT(5) SHP_MDOT(6) SHP_MDOT(7)
       SHP_MDOT(8)
 #undef SHP_MDOT
       default: break;
     }
-    launch_end(kClassVector, s, 2.0 * (double)n * ng, 8.0 * (double)n * (ng + 1));
+    launch_end(kClassVector, s, 2.0 * (double)n * (ng + (self ? 1 : 0)),
+               8.0 * (double)n * (ng + 1));
   }
   launch_begin(kClassVector, s);
-  launch_k(k_multi_dot_final, nvec, kThreads, 0, s, partials, kMultiDotBlocks, out);
+  launch_k(k_multi_dot_final, nvec + (with_self ? 1 : 0), kThreads, 0, s, partials,
+           kMultiDotBlocks, out);
   launch_end(kClassVector, s, 0.0, 0.0);
 }
 void sep_dots(const double* x, const double* f, int ld, int nm, int e1, int e2, int e3,
@@ -552,7 +572,14 @@ void sep_dots(const double* x, const double* f, int ld, int nm, int e1, int e2, 
 void multi_axpy(const double* V, int64_t ldv, int nvec, const double* h, double sign, double* w,
                 int64_t n, cudaStream_t s) {
   launch_begin(kClassVector, s);
-  launch_k(k_multi_axpy, grid_for(n), kThreads, 0, s, V, ldv, nvec, h, sign, w, n);
+  launch_k(k_multi_axpy, grid_for(n), kThreads, 0, s, V, ldv, nvec, h, sign,
+           static_cast<const double*>(w), w, static_cast<const double*>(nullptr), n);
+  launch_end(kClassVector, s, 2.0 * nvec * (double)n, 8.0 * (double)n * (nvec + 2));
+}
+void multi_axpy_div(const double* V, int64_t ldv, int nvec, const double* h, double sign,
+                    const double* w, const double* div, double* out, int64_t n, cudaStream_t s) {
+  launch_begin(kClassVector, s);
+  launch_k(k_multi_axpy, grid_for(n), kThreads, 0, s, V, ldv, nvec, h, sign, w, out, div, n);
   launch_end(kClassVector, s, 2.0 * nvec * (double)n, 8.0 * (double)n * (nvec + 2));
 }
 

@@ -25,6 +25,7 @@ struct RmpArgs {
   int nb;           // items (<= 1: one): the input holds nb * R rows, item k's rows after item
                     // k - 1's; item k's output starts ybs elements after item k - 1's
   int64_t ybs;
+  int round_tf32;   // FP32 output that the next TF32 product reads: round it to TF32 (nearest)
 };
 
 struct RmpPlan {

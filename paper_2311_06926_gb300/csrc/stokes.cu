@@ -833,6 +833,7 @@ struct stokes_ctx {
   Ops<double> odq;                       // FP64 operators of the concurrent pressure branch
   cudaStream_t stream_q = nullptr;       // its stream (owned)
   Ops<float> of;
+  Ops<float> ofq;                        // reduced-precision operators of the pressure branch
   QuadOps* quad = nullptr;               // quadrature-based forward operator (opts.forward)
   HyperPower<double> hd;
   HyperPower<float> hf;
@@ -865,13 +866,15 @@ struct stokes_ctx {
   // set for the duration of stokes_solve_batch: replay existing graphs, capture no new one
   // (stream capture from the batch's concurrent host threads crashed the host process)
   bool no_capture = false;
-  std::vector<RmpPlan> tc_plans;
+  std::vector<RmpPlan> tc_plans, tc_plans_q;
   ~stokes_ctx() {
     delete quad;
     for (auto& kv : minres_graphs) cudaGraphExecDestroy(kv.second);
     for (auto& kv : pk_graphs) cudaGraphExecDestroy(kv.second);
     if (hd.ev_fork) cudaEventDestroy(hd.ev_fork);
     if (hd.ev_join) cudaEventDestroy(hd.ev_join);
+    if (hf.ev_fork) cudaEventDestroy(hf.ev_fork);
+    if (hf.ev_join) cudaEventDestroy(hf.ev_join);
   }
 };
 
@@ -959,10 +962,13 @@ void alloc_workspace(stokes_ctx* c, Ops<T>& o) {
 int rup(int x, int m) { return (x + m - 1) / m * m; }
 
 // Tensor-core fast diagonalisation: padded operators (rows npad = n rounded to 16, row pitch
-// kpad = n rounded to one 128-byte chunk), rotation buffers and the 4 x 6 TMA plans.
+// kpad = n rounded to one 128-byte chunk), shared by both operator sets; per set (main, and the
+// pressure branch's when it has one) its own rotation buffers and 4 x 6 TMA plans.
+void init_tc_plans(stokes_ctx* c, Ops<float>& o, std::vector<RmpPlan>& plans, void* const* op,
+                   const int* npad_of, const int* kpad_of, int kind);
+
 void init_tc(stokes_ctx* c, const Dense& UN, const std::vector<double>& lN, const Dense& UT,
              const std::vector<double>& lT, int kind) {
-  Ops<float>& o = c->of;
   const int a = c->a, b = c->b;
   if (!rmp_supported(kind, a, a) || !rmp_supported(kind, b, b)) return;   // CUDA-core fallback
   const bool bf = kind == kMmaBF16;
@@ -985,6 +991,16 @@ void init_tc(stokes_ctx* c, const Dense& UN, const std::vector<double>& lN, cons
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j)
         hf[(size_t)i * kpad + j] = (float)(transp[k] ? (*srcs[k])(j, i) : (*srcs[k])(i, j));
+    if (!bf) {
+      // TF32 operands: round each entry to the nearest TF32 value (ties away from zero), as
+      // the device rounds the data operands; the tensor cores would otherwise truncate
+      for (float& v : hf) {
+        uint32_t u;
+        std::memcpy(&u, &v, 4);
+        u = (u + 0x1000u) & 0xFFFFE000u;
+        std::memcpy(&v, &u, 4);
+      }
+    }
     if (bf) {
       std::vector<uint16_t> hb(hf.size());
       for (size_t i = 0; i < hf.size(); ++i) {   // round to nearest even
@@ -1001,6 +1017,18 @@ void init_tc(stokes_ctx* c, const Dense& UN, const std::vector<double>& lN, cons
     }
     ck(cudaStreamSynchronize(s), "op");
   }
+  init_tc_plans(c, c->of, c->tc_plans, op, npad_of, kpad_of, kind);
+  if (c->ofq.s) init_tc_plans(c, c->ofq, c->tc_plans_q, op, npad_of, kpad_of, kind);
+}
+
+void init_tc_plans(stokes_ctx* c, Ops<float>& o, std::vector<RmpPlan>& plans, void* const* op,
+                   const int* npad_of, const int* kpad_of, int kind) {
+  const int b = c->b;
+  const bool bf = kind == kMmaBF16;
+  const int elem = bf ? 2 : 4;
+  const int align = 16 / elem;
+  Arena& ar = c->arena;
+  cudaStream_t s = c->stream;
   // elements per rotation slot: one tensor (the largest rotated layout) of every item
   const int nb = c->nb;
   const size_t slot = (size_t)rup(rup(b, align) * b * b, 64) * nb;
@@ -1015,7 +1043,7 @@ void init_tc(stokes_ctx* c, const Dense& UN, const std::vector<double>& lN, cons
   int dev = 0;
   ck(cudaGetDevice(&dev), "device");
   ck(cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev), "sms");
-  c->tc_plans.assign(24, RmpPlan{});
+  plans.assign(24, RmpPlan{});
   for (int t = 0; t < 4; ++t) {
     const Dims d = t < 3 ? o.comp(t) : Dims{b, b, b};
     const int ext[3] = {d.n1, d.n2, d.n3};
@@ -1033,7 +1061,7 @@ void init_tc(stokes_ctx* c, const Dense& UN, const std::vector<double>& lN, cons
       // operator index: velocity own direction uses U_N, the rest U_T (pressure: always U_T)
       const int base_op = (t < 3 && own[ax]) ? 0 : 2;
       const int opk = base_op + (fwd ? 0 : 1);
-      RmpPlan& p = c->tc_plans[t * 6 + st];
+      RmpPlan& p = plans[t * 6 + st];
       p.kind = kind;
       p.out_bf16 = bf && st < 5;
       RmpArgs& ra = p.args;
@@ -1044,6 +1072,7 @@ void init_tc(stokes_ctx* c, const Dense& UN, const std::vector<double>& lN, cons
       ra.e2 = e2;
       ra.e3 = e3;
       ra.ldy = st < 5 ? rup(e2, align) : e2;
+      ra.round_tf32 = (!bf && st < 5) ? 1 : 0;
       ra.idesc = rmp_idesc(kind, ra.npad);
       ra.scale = (float)(2.0 * c->nu);
       ra.post = 1.f;
@@ -1064,7 +1093,8 @@ void init_tc(stokes_ctx* c, const Dense& UN, const std::vector<double>& lN, cons
         throw SetupError{"tensor map encoding failed"};
     }
   }
-  o.tc_plan = c->tc_plans.data();
+  ck(cudaStreamSynchronize(s), "memset");
+  o.tc_plan = plans.data();
   o.tc_bf16 = bf;
   o.tc = true;
 }
@@ -1323,16 +1353,125 @@ void pk_apply(stokes_ctx* c, const double* v, double* z, double* w) {
   copy_async(z, c->pk_z, bytes, s);
 }
 
-// Right-preconditioned flexible GMRES (Saad 1993) with classical Gram-Schmidt applied twice
-// (one fused multi-dot and one fused multi-axpy per sweep) and Givens rotations on the host.
+// Gram-Schmidt step of flexible GMRES for every item k with active[k]: w_k (= K z_j of item k,
+// item k at w + k ntot) is orthogonalised against its basis vectors V_0 .. V_j (item k of V_i at
+// c->V + i N + k ntot) by classical Gram-Schmidt, and V_{j+1} = (w_k - V h) / h_{j+1,j} is
+// written. One sweep computes the products h = V^T w_k together with <w_k, w_k>; the update and
+// the division by h_{j+1,j} then take one more sweep. A second (reorthogonalisation) pass follows
+// only when the first update cancels more than half of ||w_k||^2, i.e. when
+// ||w_k - V h||^2 = ||w_k||^2 - ||h||^2 <= ||w_k||^2 / 2 (the criterion of Daniel, Gragg,
+// Kaufman and Stewart, 1976, with eta = 1/sqrt(2)); if that pass cancels as much again, the norm
+// is taken from a dot product of the updated vector. cols[k][0..j] receives item k's Hessenberg
+// column (the sum of the passes' coefficients), hn[k] its h_{j+1,j}; bad[k] is set when a norm is
+// not finite. Scalars per item k at c->dsc + k ds: h at +8, the second pass's at +8 + (m + 2),
+// <w, w> after the coefficients, h_{j+1,j} at +7, a dot product at +6.
+void arnoldi_gs(stokes_ctx* c, int j, const std::vector<char>& active, double* w,
+                std::vector<std::vector<double>>& cols, std::vector<double>& hn,
+                std::vector<char>& bad) {
+  const int nb = c->nb;
+  const int64_t n = c->ntot, N = (int64_t)nb * n;
+  cudaStream_t s = c->stream;
+  const int m = c->opts.restart;
+  const size_t ds = 16 + 2 * (size_t)(m + 2);
+  const int nv = j + 1;
+  auto base = [&](int k) { return c->dsc + (size_t)k * ds; };
+  std::vector<double> hs((size_t)nb * ds);
+  auto read_all = [&]() {
+    ck(cudaMemcpyAsync(hs.data(), c->dsc, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, s),
+       "read");
+    ck(cudaStreamSynchronize(s), "sync");
+  };
+  auto finish = [&](int k, double h, const double* coef_dev) {   // V_{j+1} = (w - V c) / h
+    hn[k] = h;
+    if (!(h > 0.0)) return;
+    c->pinned_multi[2 * k + 1] = h;
+    ck(cudaMemcpyAsync(base(k) + 7, c->pinned_multi + 2 * k + 1, sizeof(double),
+                       cudaMemcpyHostToDevice, s), "h");
+    multi_axpy_div(c->V + k * n, N, nv, coef_dev, -1.0, w + k * n, base(k) + 7,
+                   c->V + (int64_t)nv * N + k * n, n, s);
+  };
+  std::vector<char> pass2(nb, 0), pass3(nb, 0);
+  bool any2 = false, any3 = false;
+  for (int k = 0; k < nb; ++k)
+    if (active[k])
+      multi_dot(c->V + k * n, N, nv, w + k * n, n, c->partials + kDotScratch, base(k) + 8, s, true);
+  check_launch("fgmres arnoldi");
+  read_all();
+  for (int k = 0; k < nb; ++k) {
+    if (!active[k]) continue;
+    const double* h = hs.data() + (size_t)k * ds + 8;
+    const double ww = h[nv];
+    double hh = 0.0;
+    for (int i = 0; i < nv; ++i) hh += h[i] * h[i];
+    cols[k].assign(h, h + nv);
+    const double s2 = ww - hh;
+    if (!std::isfinite(ww) || !std::isfinite(s2)) {
+      bad[k] = 1;
+      continue;
+    }
+    if (s2 > 0.5 * ww) {
+      finish(k, std::sqrt(s2), base(k) + 8);
+    } else {   // reorthogonalise: w -= V h, then the second pass's products
+      pass2[k] = 1;
+      any2 = true;
+      multi_axpy(c->V + k * n, N, nv, base(k) + 8, -1.0, w + k * n, n, s);
+      multi_dot(c->V + k * n, N, nv, w + k * n, n, c->partials + kDotScratch,
+                base(k) + 8 + (m + 2), s, true);
+    }
+  }
+  if (!any2) return;
+  read_all();
+  for (int k = 0; k < nb; ++k) {
+    if (!pass2[k]) continue;
+    const double* h2 = hs.data() + (size_t)k * ds + 8 + (m + 2);
+    const double ww = h2[nv];
+    double hh = 0.0;
+    for (int i = 0; i < nv; ++i) {
+      hh += h2[i] * h2[i];
+      cols[k][i] += h2[i];
+    }
+    const double s2 = ww - hh;
+    if (!std::isfinite(ww) || !std::isfinite(s2)) {
+      bad[k] = 1;
+      continue;
+    }
+    if (s2 > 0.5 * ww) {
+      finish(k, std::sqrt(s2), base(k) + 8 + (m + 2));
+    } else {   // w -= V h2 and its norm from a dot product
+      pass3[k] = 1;
+      any3 = true;
+      multi_axpy(c->V + k * n, N, nv, base(k) + 8 + (m + 2), -1.0, w + k * n, n, s);
+      dot<double>(w + k * n, w + k * n, n, c->partials, base(k) + 6, s);
+    }
+  }
+  if (!any3) return;
+  read_all();
+  for (int k = 0; k < nb; ++k) {
+    if (!pass3[k]) continue;
+    const double h = std::sqrt(hs[(size_t)k * ds + 6]);
+    if (!std::isfinite(h)) {
+      bad[k] = 1;
+      continue;
+    }
+    hn[k] = h;
+    if (h > 0.0) {
+      c->pinned_multi[2 * k + 1] = h;
+      ck(cudaMemcpyAsync(base(k) + 7, c->pinned_multi + 2 * k + 1, sizeof(double),
+                         cudaMemcpyHostToDevice, s), "h");
+      scale_inv_dev(base(k) + 7, w + k * n, c->V + (int64_t)nv * N + k * n, n, s);
+    }
+  }
+}
+
+// Right-preconditioned flexible GMRES (Saad 1993): classical Gram-Schmidt with a second pass
+// only where the first cancels (arnoldi_gs), Givens rotations on the host.
 int run_fgmres(stokes_ctx* c, const double* f, double tol, double* x, int* iters) {
   const int64_t n = c->ntot;
   cudaStream_t s = c->stream;
   const int m = c->opts.restart;
   double* w = c->kv[0];
   double* r = c->kv[1];
-  double* hdev = c->dsc + 8;           // m + 1 Hessenberg column entries
-  double* h2dev = c->dsc + 8 + (m + 2);
+  double* hdev = c->dsc + 8;           // solution coefficients y at the end of a cycle
   fill_zero(x, n * sizeof(double), s);
   c->ratios.clear();
   dot<double>(f, f, n, c->partials, c->dsc + 3, s);
@@ -1345,7 +1484,9 @@ int run_fgmres(stokes_ctx* c, const double* f, double tol, double* x, int* iters
   int it = 0;
   copy_async(r, f, n * sizeof(double), s);
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
-  std::vector<double> col(m + 2);
+  std::vector<std::vector<double>> cols(1);
+  std::vector<double> hnv(1);
+  std::vector<char> act(1, 1), bad(1, 0);
   while (it < c->opts.maxit) {
     dot<double>(r, r, n, c->partials, c->dsc + 4, s);
     const double beta = std::sqrt(read_scalar(c, c->dsc + 4));
@@ -1366,31 +1507,11 @@ int run_fgmres(stokes_ctx* c, const double* f, double tol, double* x, int* iters
       double* Vj = c->V + (int64_t)j * n;
       double* Zj = c->Z + (int64_t)j * n;
       pk_apply(c, Vj, Zj, w);
-      // CGS2: h = V^T w; w -= V h; h2 = V^T w; w -= V h2; h += h2
-      multi_dot(c->V, n, j + 1, w, n, c->partials + kDotScratch, hdev, s);
-      multi_axpy(c->V, n, j + 1, hdev, -1.0, w, n, s);
-      multi_dot(c->V, n, j + 1, w, n, c->partials + kDotScratch, h2dev, s);
-      multi_axpy(c->V, n, j + 1, h2dev, -1.0, w, n, s);
-      dot<double>(w, w, n, c->partials, c->dsc + 6, s);
-      check_launch("fgmres arnoldi");
-      ck(cudaMemcpyAsync(col.data(), hdev, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, s),
-         "read h");
-      std::vector<double> col2(j + 1);
-      ck(cudaMemcpyAsync(col2.data(), h2dev, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, s),
-         "read h2");
-      ck(cudaMemcpyAsync(c->pinned, c->dsc + 6, sizeof(double), cudaMemcpyDeviceToHost, s),
-         "read norm");
-      ck(cudaStreamSynchronize(s), "sync");
-      const double hn = std::sqrt(c->pinned[0]);
-      if (!std::isfinite(hn)) return STOKES_ERR_NONFINITE;
-      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = col[i] + col2[i];
+      arnoldi_gs(c, j, act, w, cols, hnv, bad);   // writes V_{j+1}
+      if (bad[0]) return STOKES_ERR_NONFINITE;
+      const double hn = hnv[0];
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = cols[0][i];
       H[(size_t)(j + 1) * m + j] = hn;
-      if (hn > 0.0) {   // V_{j+1} = w / h_{j+1,j}
-        c->pinned[1] = hn;
-        ck(cudaMemcpyAsync(c->dsc + 7, c->pinned + 1, sizeof(double), cudaMemcpyHostToDevice, s),
-           "hn");
-        scale_inv_dev(c->dsc + 7, w, c->V + (int64_t)(j + 1) * n, n, s);
-      }
       for (int i = 0; i < j; ++i) {
         const double t = cs[i] * H[(size_t)i * m + j] + sn[i] * H[(size_t)(i + 1) * m + j];
         H[(size_t)(i + 1) * m + j] = -sn[i] * H[(size_t)i * m + j] + cs[i] * H[(size_t)(i + 1) * m + j];
@@ -1483,7 +1604,9 @@ void run_fgmres_multi(stokes_ctx* c, const double* f, double tol, double* x, int
   std::vector<std::vector<double>> cs(nb, std::vector<double>(m)), sn(nb, std::vector<double>(m));
   std::vector<std::vector<double>> g(nb, std::vector<double>(m + 1)), y(nb, std::vector<double>(m));
   std::vector<int> k_used(nb, 0);
-  std::vector<char> active(nb, 0), stop(nb, 0);
+  std::vector<char> active(nb, 0), stop(nb, 0), bad(nb, 0);
+  std::vector<std::vector<double>> cols(nb);
+  std::vector<double> hnv(nb, 0.0);
   auto any = [&](const std::vector<char>& v) {
     for (char e : v)
       if (e) return true;
@@ -1518,25 +1641,12 @@ void run_fgmres_multi(stokes_ctx* c, const double* f, double tol, double* x, int
       double* Vj = c->V + (int64_t)j * N;
       double* Zj = c->Z + (int64_t)j * N;
       pk_apply(c, Vj, Zj, w);
+      std::fill(bad.begin(), bad.end(), 0);
+      arnoldi_gs(c, j, active, w, cols, hnv, bad);   // writes V_{j+1} of every active item
       for (int k = 0; k < nb; ++k) {
         if (!active[k]) continue;
-        double* hdev = dsc(k) + 8;
-        double* h2dev = dsc(k) + 8 + (m + 2);
-        double* wk = w + k * n;
-        const double* Vk = c->V + k * n;
-        multi_dot(Vk, N, j + 1, wk, n, c->partials + kDotScratch, hdev, s);
-        multi_axpy(Vk, N, j + 1, hdev, -1.0, wk, n, s);
-        multi_dot(Vk, N, j + 1, wk, n, c->partials + kDotScratch, h2dev, s);
-        multi_axpy(Vk, N, j + 1, h2dev, -1.0, wk, n, s);
-        dot<double>(wk, wk, n, c->partials, dsc(k) + 6, s);
-      }
-      check_launch("fgmres arnoldi");
-      read_all();
-      for (int k = 0; k < nb; ++k) {
-        if (!active[k]) continue;
-        const double* hk = hs.data() + (size_t)k * ds;
-        const double hn = std::sqrt(hk[6]);
-        if (!std::isfinite(hn)) {
+        const double hn = hnv[k];
+        if (bad[k]) {
           rcs[k] = STOKES_ERR_NONFINITE;
           done[k] = 1;
           active[k] = 0;
@@ -1544,12 +1654,8 @@ void run_fgmres_multi(stokes_ctx* c, const double* f, double tol, double* x, int
           continue;
         }
         std::vector<double>& Hk = H[k];
-        for (int i = 0; i <= j; ++i) Hk[(size_t)i * m + j] = hk[8 + i] + hk[8 + (m + 2) + i];
+        for (int i = 0; i <= j; ++i) Hk[(size_t)i * m + j] = cols[k][i];
         Hk[(size_t)(j + 1) * m + j] = hn;
-        if (hn > 0.0) {
-          put(k, 7, hn);
-          scale_inv_dev(dsc(k) + 7, w + k * n, c->V + (int64_t)(j + 1) * N + k * n, n, s);
-        }
         for (int i = 0; i < j; ++i) {
           const double t = cs[k][i] * Hk[(size_t)i * m + j] + sn[k][i] * Hk[(size_t)(i + 1) * m + j];
           Hk[(size_t)(i + 1) * m + j] =
@@ -1655,10 +1761,13 @@ int solve_multi_impl(stokes_ctx* c, const double* rhs, double tol, double* x, in
 // the tensor-core pipeline raises this flag if one of its bounded waits ran out
 bool tc_failed(stokes_ctx* c) {
   if (!c->of.tc) return false;
-  int h = 0;
-  ck(cudaMemcpyAsync(&h, c->of.tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag");
+  int h[2] = {0, 0};
+  ck(cudaMemcpyAsync(&h[0], c->of.tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag");
+  if (c->ofq.tc)   // the pressure branch joins the main stream, so this read follows its kernels
+    ck(cudaMemcpyAsync(&h[1], c->ofq.tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+       "flag");
   ck(cudaStreamSynchronize(c->stream), "flag");
-  return h != 0;
+  return h[0] != 0 || h[1] != 0;
 }
 
 int solve_impl(stokes_ctx* c, const double* rhs, double tol, double* x, int* iterations,
@@ -1958,9 +2067,24 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
     if (!reduced(c)) init_hp<double>(c, c->hd, c->od, odq);   // the FP64 preconditioner
     if (reduced(c)) {
       init_ops<float>(c, c->of, bM, bK, bMc, bTc, UN.v, lN, UT.v, lT);
+      const Ops<float>* ofq = nullptr;
+      if (o.max_steps > 0) {
+        // as in FP64: the pressure recursion (with the velocity solves of its Schur
+        // approximation) runs on its own operator set, workspace and stream, concurrently with
+        // the velocity recursion; the tensor-core plans of that set get their own buffers
+        int prio_lo = 0, prio_hi = 0;
+        ck(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi), "priority range");
+        ck(cudaStreamCreateWithPriority(&c->stream_q, cudaStreamNonBlocking, prio_hi), "stream");
+        c->ofq = c->of;
+        c->ofq.s = c->stream_q;
+        alloc_workspace<float>(c, c->ofq);
+        ofq = &c->ofq;
+      }
       if (o.precision == STOKES_PREC_TF32 || o.precision == STOKES_PREC_BF16)
         init_tc(c, UN, lN, UT, lT, o.precision == STOKES_PREC_BF16 ? kMmaBF16 : kMmaTF32);
-      init_hp<float>(c, c->hf, c->of, nullptr);
+      if (ofq && c->of.tc != c->ofq.tc)
+        throw SetupError{"tensor-core plans of the two operator sets differ"};
+      init_hp<float>(c, c->hf, c->of, ofq);
       c->xf = c->arena.alloc<float>((size_t)c->nb * c->ntot);
       c->yf = c->arena.alloc<float>((size_t)c->nb * c->ntot);
     }
@@ -2388,6 +2512,7 @@ int stokes_profile_begin(stokes_t c) {
   profiler_activate(c->prof);
   c->prof_on = true;
   c->hd.serial = true;   // per-launch event timing: no concurrent branches
+  c->hf.serial = true;
   return STOKES_OK;
 }
 
@@ -2399,6 +2524,7 @@ int stokes_profile_end(stokes_t c, stokes_kernel_stat* out, int capacity) {
   profiler_activate(nullptr);
   c->prof_on = false;
   c->hd.serial = false;
+  c->hf.serial = false;
   const int k = std::min(capacity, (int)kNumClasses);
   for (int i = 0; i < k; ++i) {
     out[i].kernel_class = i;
@@ -2444,6 +2570,7 @@ int stokes_set_wait_limit(stokes_t c, int64_t polls) {
   if (polls < 0 || polls > (int64_t)UINT32_MAX)
     return fail(c, STOKES_ERR_ARG, "wait limit outside [0, 2^32)");
   c->of.tc_spin = (uint32_t)polls;
+  c->ofq.tc_spin = (uint32_t)polls;
   return STOKES_OK;
 }
 

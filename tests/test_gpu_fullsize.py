@@ -108,19 +108,21 @@ def test_reduced_precision_batched_48(prec):
         assert e1 < reduced_tol(prec, 1), (k, e1)
 
 
-def _against_golden(x, g):
-    """Relative errors of the GPU solution x (host, pressure zero-mean) against the stored oracle
-    solution: max over the sampled entries (relative to the largest magnitude), the block norms
-    and the inner products with the seeded vectors (relative to ||x_o|| ||w_k||)."""
+def _against_golden(x, g, prefix=""):
+    """Relative errors of the GPU solution x (host, pressure zero-mean) against a stored oracle
+    solution (prefix "": its MINRES solve to 1e-8; "exact_": its MINRES solve to 1e-11, the
+    reference for accuracy): max over the sampled entries (relative to the largest magnitude), the
+    block norms and the inner products with the seeded vectors (relative to ||x_o|| ||w_k||)."""
     idx = np.asarray(g["sample_index"])
-    e_samp = np.abs(x[idx] - np.asarray(g["sample_value"])).max() / g["max_abs"]
+    e_samp = np.abs(x[idx] - np.asarray(g[prefix + "sample_value"])).max() / g[prefix + "max_abs"]
     blocks = np.cumsum([0, g["n_vel"] // 3, g["n_vel"] // 3, g["n_vel"] // 3, g["n_pres"]])
-    e_norm = max(abs(np.linalg.norm(x[blocks[k]:blocks[k + 1]]) - g["block_norm2"][k]) /
-                 g["norm2"] for k in range(4))
+    e_norm = max(abs(np.linalg.norm(x[blocks[k]:blocks[k + 1]]) - g[prefix + "block_norm2"][k]) /
+                 g[prefix + "norm2"] for k in range(4))
     e_fun = 0.0
-    for k, val in enumerate(g["functionals"]):
+    for k, val in enumerate(g[prefix + "functionals"]):
         w = synthetic.random_vector(g["size"], g["functional_seed"] + k)
-        e_fun = max(e_fun, abs(float(np.dot(x, w)) - val) / (g["norm2"] * np.linalg.norm(w)))
+        e_fun = max(e_fun, abs(float(np.dot(x, w)) - val) /
+                    (g[prefix + "norm2"] * np.linalg.norm(w)))
     return e_samp, e_norm, e_fun
 
 
@@ -139,9 +141,12 @@ def test_fp64_minres_full_size_against_oracle(golden):
     assert rc == 0 and it == g["iterations"], (it, g["iterations"])
     assert np.allclose(ratios, g["ratios"], rtol=1e-6, atol=1e-14)
     e = _against_golden(xh, g)
+    ex = _against_golden(xh, g, "exact_")
     print(f"[measured] fp64 128^3 solve vs oracle: samples {e[0]:.2e} norms {e[1]:.2e} "
-          f"functionals {e[2]:.2e}; true residual {rr:.3e} (oracle {g['true_rel_res']:.3e})")
+          f"functionals {e[2]:.2e}; true residual {rr:.3e} (oracle {g['true_rel_res']:.3e}); "
+          f"vs the tight solution {max(ex):.2e} (oracle's {g['error_vs_exact']:.2e})")
     assert max(e) < 1e-10, e
+    assert abs(max(ex) - g["error_vs_exact"]) <= 1e-3 * g["error_vs_exact"]
     assert abs(rr - g["true_rel_res"]) <= 1e-3 * g["true_rel_res"]
 
 
@@ -149,7 +154,12 @@ def test_fp64_minres_full_size_against_oracle(golden):
 def test_mixed_solve_full_size_against_oracle(orc, golden, prec):
     """The mixed form at 128^3 (tensor-core preconditioner inside FP64 flexible GMRES), order 2,
     2 steps, to a true relative residual of 1e-8: its residual recomputed with the oracle's
-    operator, and its error against the oracle's solution."""
+    operator, and its error against the oracle's tight (1e-11) solution. A residual r leaves the
+    error K^-1 r; how much error per unit of 2-norm residual flexible GMRES leaves on this
+    problem is measured by the oracle's own flexible GMRES (golden fgmres_error_per_residual,
+    about 90, seven times MINRES's, since it minimises the 2-norm rather than the P^-1-norm of the
+    residual). The bound is 8 times that rate: the reduced-precision preconditioner perturbs the
+    Krylov space and so the directions of the final residual (measured: about 4 times)."""
     from paper_2311_06926_gb300 import Stokes
     S, base, Kop = orc
     g = golden
@@ -161,11 +171,11 @@ def test_mixed_solve_full_size_against_oracle(orc, golden, prec):
     xh = host(x)
     fh = S.rhs_lid(1.0)
     rr_oracle = np.linalg.norm(fh - Kop(xh)) / np.linalg.norm(fh)
-    e = _against_golden(xh, g)
+    e = _against_golden(xh, g, "exact_")
     print(f"[measured] {prec} 128^3 FGMRES: {it} iterations, residual {rr:.3e} (oracle operator "
-          f"{rr_oracle:.3e}); vs oracle solution: samples {e[0]:.2e} norms {e[1]:.2e} "
-          f"functionals {e[2]:.2e}")
+          f"{rr_oracle:.3e}); vs the oracle's tight solution: samples {e[0]:.2e} norms "
+          f"{e[1]:.2e} functionals {e[2]:.2e} ({max(e) / rr_oracle:.0f} per unit residual)")
     assert rc == 0 and 0 < it < 100
     assert abs(rr_oracle - rr) <= 1e-3 * rr
     assert rr_oracle <= 1.001e-8
-    assert max(e) < g["error_per_residual"] * 4 * max(rr_oracle, g["true_rel_res"]), e
+    assert max(e) < 8 * g["fgmres_error_per_residual"] * rr_oracle, e
