@@ -289,6 +289,10 @@ void axpy_dev(const double* alpha, double sign, const double* x, double* y, int6
 // the same pass; deterministic; partials: (nvec + 1) * kMultiDotBlocks
 void multi_dot(const double* V, int64_t ldv, int nvec, const double* w, int64_t n,
                double* partials, double* out, cudaStream_t s, bool with_self = false);
+// out[k] = <V_k, w>, out[nvec + k] = <V_k, z> for k < nvec and out[2 nvec] = <w, w>, from one
+// sweep over the vectors; deterministic; partials: (2 nvec + 1) * kMultiDotBlocks
+void multi_dot2(const double* V, int64_t ldv, int nvec, const double* w, const double* z,
+                int64_t n, double* partials, double* out, cudaStream_t s);
 // w += sign * sum_k h[k] V_k (h in device memory)
 void multi_axpy(const double* V, int64_t ldv, int nvec, const double* h, double sign, double* w,
                 int64_t n, cudaStream_t s);

@@ -40,6 +40,9 @@ struct PassBatch {
 template <typename T>
 constexpr int seg_len() { return sizeof(T) == 4 ? 32 : 1; }
 
+// One FMA chain per band row: the FP64 passes are bound by the FP64 pipe, where every add or
+// multiply besides the FMAs costs as much as an FMA (the pipe has the warps to hide the chain's
+// latency).
 template <int W, typename T>
 __device__ __forceinline__ T band_dot(const BandD<T>& D, int i, const T* __restrict__ X,
                                       int64_t base, int64_t stride) {
@@ -47,15 +50,9 @@ __device__ __forceinline__ T band_dot(const BandD<T>& D, int i, const T* __restr
   const T* x = X + base + (int64_t)s0 * stride;
   T sum = 0;
   if (W > 0) {
-    // two interleaved partial sums halve the dependent FMA chain
     const T* v = D.val + (int64_t)i * W;
-    T s1 = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-      if (w % 2 == 0) sum = fma(__ldg(v + w), __ldg(x + (int64_t)w * stride), sum);
-      else s1 = fma(__ldg(v + w), __ldg(x + (int64_t)w * stride), s1);
-    }
-    sum += s1;
+    for (int w = 0; w < W; ++w) sum = fma(__ldg(v + w), __ldg(x + (int64_t)w * stride), sum);
   } else {
     const T* v = D.val + (int64_t)i * D.width;
     for (int w = 0; w < D.width; ++w) sum = fma(__ldg(v + w), __ldg(x + (int64_t)w * stride), sum);
@@ -81,22 +78,16 @@ __device__ __forceinline__ void band_pass_flat_x1(const PassArgs<T>& a, int64_t 
   const T* cs = csh + i;
   const int64_t base_in = kb + (int64_t)a.in.n1 * line;
   const T* x0 = a.X0 + base_in + __ldg(a.D0.start + i);
-  T s0 = 0, s1 = 0;
+  T acc = 0;
 #pragma unroll
-  for (int w = 0; w < W; ++w) {
-    if (w % 2 == 0) s0 = fma(cs[w * m], __ldg(x0 + w), s0);
-    else s1 = fma(cs[w * m], __ldg(x0 + w), s1);
-  }
-  T acc = a.c0 * (s0 + s1);
+  for (int w = 0; w < W; ++w) acc = fma(cs[w * m], __ldg(x0 + w), acc);
+  if (a.c0 != T(1)) acc *= a.c0;   // (a product with 1 is exact: skipped)
   if (a.nterms > 1) {
     const T* x1 = a.X1 + base_in + __ldg(a.D1.start + i);
-    T u0 = 0, u1 = 0;
+    T u = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-      if (w % 2 == 0) u0 = fma(cs[(W + w) * m], __ldg(x1 + w), u0);
-      else u1 = fma(cs[(W + w) * m], __ldg(x1 + w), u1);
-    }
-    acc += a.c1 * (u0 + u1);
+    for (int w = 0; w < W; ++w) u = fma(cs[(W + w) * m], __ldg(x1 + w), u);
+    acc = fma(a.c1, u, acc);
   }
   const int64_t o = kb + (int64_t)m * line + i;
   if (a.Z) acc += a.cz * a.Z[o];
@@ -196,8 +187,9 @@ __global__ void __launch_bounds__(512) k_band_pass(const __grid_constant__ PassB
   }
   const int i_end = min(m, (seg + 1) * seg_n);
   for (int i = seg * seg_n; i < i_end; ++i) {
-    T acc = a.c0 * band_dot<W>(a.D0, i, a.X0, base_in, stride_in);
-    if (a.nterms > 1) acc += a.c1 * band_dot<W>(a.D1, i, a.X1, base_in, stride_in);
+    T acc = band_dot<W>(a.D0, i, a.X0, base_in, stride_in);
+    if (a.c0 != T(1)) acc *= a.c0;   // (a product with 1 is exact: skipped)
+    if (a.nterms > 1) acc = fma(a.c1, band_dot<W>(a.D1, i, a.X1, base_in, stride_in), acc);
     const int64_t o = base_out + (int64_t)i * stride_out;
     if (a.Z) acc += a.cz * a.Z[o];
     if (a.g) {
@@ -632,7 +624,7 @@ __global__ void __launch_bounds__(256) k_divergence(const T* __restrict__ u1, co
 // The divergence and the first pressure-mass pass in one launch (FP64 A and K applies): a block
 // owns lpb whole x1 lines of the pressure grid, forms delta (and e = nu delta + q when q is set)
 // on them in shared memory with the operations of k_divergence, and applies the band D along x1
-// with the two partial sums of the flat x1 pass: y0 = D .x1 delta, y1 = D .x1 e.
+// with the single FMA chain of the flat x1 pass: y0 = D .x1 delta, y1 = D .x1 e.
 template <typename T>
 __global__ void __launch_bounds__(512) k_div_band_x1(const T* __restrict__ u1,
                                                      const T* __restrict__ u2,
@@ -676,20 +668,14 @@ __global__ void __launch_bounds__(512) k_div_band_x1(const T* __restrict__ u1,
   const T* cv = D.val + (int64_t)i1 * W;
   const int s0i = __ldg(D.start + i1);
   const T* xd = sd + l * b + s0i;
-  T s0 = 0, s1 = 0;
-  for (int w = 0; w < W; ++w) {
-    if (w % 2 == 0) s0 = fma(__ldg(cv + w), xd[w], s0);
-    else s1 = fma(__ldg(cv + w), xd[w], s1);
-  }
-  y0[(int64_t)line * b + i1] = T(1) * (s0 + s1);
+  T s0 = 0;
+  for (int w = 0; w < W; ++w) s0 = fma(__ldg(cv + w), xd[w], s0);
+  y0[(int64_t)line * b + i1] = s0;
   if (q) {
     const T* xe = se + l * b + s0i;
-    T e0 = 0, e1 = 0;
-    for (int w = 0; w < W; ++w) {
-      if (w % 2 == 0) e0 = fma(__ldg(cv + w), xe[w], e0);
-      else e1 = fma(__ldg(cv + w), xe[w], e1);
-    }
-    y1[(int64_t)line * b + i1] = T(1) * (e0 + e1);
+    T e0 = 0;
+    for (int w = 0; w < W; ++w) e0 = fma(__ldg(cv + w), xe[w], e0);
+    y1[(int64_t)line * b + i1] = e0;
   }
 }
 

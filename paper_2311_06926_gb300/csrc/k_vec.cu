@@ -283,6 +283,66 @@ __global__ void __launch_bounds__(kThreads, 4) k_multi_dot_partial(const double*
   }
 }
 
+// Products of NG basis vectors with two vectors in one sweep: <V_k, w> (partial row k) and
+// <V_k, z> (row nvec + k), and with SELF also <w, w> (row 2 nvec); per-block sums in the fixed
+// order of k_multi_dot_partial.
+template <int NG, bool SELF>
+__global__ void __launch_bounds__(kThreads, 4) k_multi_dot2_partial(const double* __restrict__ V,
+                                                                 int64_t ldv, int k0, int nvec,
+                                                                 const double* __restrict__ w,
+                                                                 const double* __restrict__ z,
+                                                                 int64_t n,
+                                                                 double* __restrict__ partials) {
+  pdl_begin();
+  constexpr int NA = 2 * NG + (SELF ? 1 : 0);
+  __shared__ double sh[NA][kThreads / 32];
+  double acc[NA];
+#pragma unroll
+  for (int g = 0; g < NA; ++g) acc[g] = 0.0;
+  const double* v0 = V + (int64_t)k0 * ldv;
+  const int64_t step = (int64_t)gridDim.x * kThreads;
+  int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  for (; i + step < n; i += 2 * step) {
+    const double wa = w[i], wb = w[i + step], za = z[i], zb = z[i + step];
+    double va[NG], vb[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      va[g] = v0[g * ldv + i];
+      vb[g] = v0[g * ldv + i + step];
+    }
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      acc[g] = fma(vb[g], wb, fma(va[g], wa, acc[g]));
+      acc[NG + g] = fma(vb[g], zb, fma(va[g], za, acc[NG + g]));
+    }
+    if (SELF) acc[2 * NG] = fma(wb, wb, fma(wa, wa, acc[2 * NG]));
+  }
+  if (i < n) {
+    const double wa = w[i], za = z[i];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      const double va = v0[g * ldv + i];
+      acc[g] = fma(va, wa, acc[g]);
+      acc[NG + g] = fma(va, za, acc[NG + g]);
+    }
+    if (SELF) acc[2 * NG] = fma(wa, wa, acc[2 * NG]);
+  }
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+#pragma unroll
+  for (int g = 0; g < NA; ++g) {
+    const double t = warp_sum(acc[g]);
+    if (lane == 0) sh[g][warp] = t;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < NA) {
+    double t = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) t += sh[threadIdx.x][k];
+    const int g = threadIdx.x;
+    const int row = g < NG ? k0 + g : (g < 2 * NG ? nvec + k0 + (g - NG) : 2 * nvec);
+    partials[(int64_t)row * gridDim.x + blockIdx.x] = t;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) k_multi_dot_final(const double* __restrict__ partials,
                                                               int np, double* __restrict__ out) {
   pdl_begin();
@@ -545,6 +605,35 @@ void multi_dot(const double* V, int64_t ldv, int nvec, const double* w, int64_t 
            kMultiDotBlocks, out);
   launch_end(kClassVector, s, 0.0, 0.0);
 }
+void multi_dot2(const double* V, int64_t ldv, int nvec, const double* w, const double* z,
+                int64_t n, double* partials, double* out, cudaStream_t s) {
+  for (int k0 = 0; k0 < nvec; k0 += kDotGroup) {
+    const int ng = nvec - k0 < kDotGroup ? nvec - k0 : kDotGroup;
+    const bool self = k0 == 0;
+    launch_begin(kClassVector, s);
+    switch (ng) {
+#define SHP_MDOT2(g)                                                                            \
+  case g:                                                                                       \
+    if (self)                                                                                   \
+      launch_k(k_multi_dot2_partial<g, true>, kMultiDotBlocks, kThreads, 0, s, V, ldv, k0,      \
+               nvec, w, z, n, partials);                                                        \
+    else                                                                                        \
+      launch_k(k_multi_dot2_partial<g, false>, kMultiDotBlocks, kThreads, 0, s, V, ldv, k0,     \
+               nvec, w, z, n, partials);                                                        \
+    break;
+      SHP_MDOT2(1) SHP_MDOT2(2) SHP_MDOT2(3) SHP_MDOT2(4) SHP_MDOT2(5) SHP_MDOT2(6)
+      SHP_MDOT2(7) SHP_MDOT2(8)
+#undef SHP_MDOT2
+      default: break;
+    }
+    launch_end(kClassVector, s, 4.0 * (double)n * ng + (self ? 2.0 * n : 0.0),
+               8.0 * (double)n * (ng + 2));
+  }
+  launch_begin(kClassVector, s);
+  launch_k(k_multi_dot_final, 2 * nvec + 1, kThreads, 0, s, partials, kMultiDotBlocks, out);
+  launch_end(kClassVector, s, 0.0, 0.0);
+}
+
 void sep_dots(const double* x, const double* f, int ld, int nm, int e1, int e2, int e3,
               double* partials, double* out, cudaStream_t s) {
   const double n = (double)e1 * e2 * e3;

@@ -844,6 +844,7 @@ struct stokes_ctx {
   MinresState* st_host = nullptr;
   double* pinned = nullptr;              // small pinned host scratch
   double* pinned_multi = nullptr;        // 2 scalars per item (nrhs > 1)
+  double* pinned_h = nullptr;            // Gram-Schmidt coefficients, restart + 2 per item
   // Krylov vectors
   double *kv[8] = {nullptr};
   double *V = nullptr, *Z = nullptr;     // FGMRES bases ((restart + 1) x ntot, restart x ntot)
@@ -1355,23 +1356,31 @@ void pk_apply(stokes_ctx* c, const double* v, double* z, double* w) {
 
 // Gram-Schmidt step of flexible GMRES for every item k with active[k]: w_k (= K z_j of item k,
 // item k at w + k ntot) is orthogonalised against its basis vectors V_0 .. V_j (item k of V_i at
-// c->V + i N + k ntot) by classical Gram-Schmidt, and V_{j+1} = (w_k - V h) / h_{j+1,j} is
-// written. One sweep computes the products h = V^T w_k together with <w_k, w_k>; the update and
-// the division by h_{j+1,j} then take one more sweep. A second (reorthogonalisation) pass follows
-// only when the first update cancels more than half of ||w_k||^2, i.e. when
-// ||w_k - V h||^2 = ||w_k||^2 - ||h||^2 <= ||w_k||^2 / 2 (the criterion of Daniel, Gragg,
-// Kaufman and Stewart, 1976, with eta = 1/sqrt(2)); if that pass cancels as much again, the norm
-// is taken from a dot product of the updated vector. cols[k][0..j] receives item k's Hessenberg
-// column (the sum of the passes' coefficients), hn[k] its h_{j+1,j}; bad[k] is set when a norm is
-// not finite. Scalars per item k at c->dsc + k ds: h at +8, the second pass's at +8 + (m + 2),
-// <w, w> after the coefficients, h_{j+1,j} at +7, a dot product at +6.
+// c->V + i N + k ntot) by classical Gram-Schmidt applied twice, in one sweep over the basis:
+//   c = V^T w and d = V^T v_j (the new column of the Gram matrix G = V^T V, which is the identity
+//   up to the rounding of the basis) and <w, w> come from one fused reduction;
+//   the two passes' coefficients are h = c + (c - G c): the second pass's products
+//   V^T (w - V c) equal c - G c exactly in real arithmetic, so the reduction that forms them is
+//   replaced by the Gram matrix the earlier sweeps built (one column per step);
+//   ||w - V h||^2 = <w, w> - 2 h.c + h^T G h, and V_{j+1} = (w - V h) / ||w - V h|| is written by
+//   one fused update-and-divide sweep.
+// This is the one-reduction form of reorthogonalised classical Gram-Schmidt (the Gram-matrix
+// correction of the low-synchronisation Gram-Schmidt methods, Swirydowicz, Langou, Ananthan, Yang
+// and Thomas, 2020): two sweeps over the basis per step instead of four, one host read.
+// When the update cancels all but 1e-6 of <w, w> (a near breakdown, where the expanded norm
+// loses its accuracy), the vector is updated first and its norm taken by a dot product.
+// gram[k] ((m + 1)^2, row-major) holds item k's Gram matrix for the current cycle; cols[k][0..j]
+// receives item k's Hessenberg column h, hn[k] h_{j+1,j}; bad[k] is set when a value is not
+// finite. Scalars per item k at c->dsc + k ds: c, d, <w, w> from +8, h_{j+1,j} at +7, a dot at +6;
+// h is staged through c->pinned_h to +8 + (m + 2).
 void arnoldi_gs(stokes_ctx* c, int j, const std::vector<char>& active, double* w,
-                std::vector<std::vector<double>>& cols, std::vector<double>& hn,
-                std::vector<char>& bad) {
+                std::vector<std::vector<double>>& gram, std::vector<std::vector<double>>& cols,
+                std::vector<double>& hn, std::vector<char>& bad) {
   const int nb = c->nb;
   const int64_t n = c->ntot, N = (int64_t)nb * n;
   cudaStream_t s = c->stream;
   const int m = c->opts.restart;
+  const int mg = m + 1;
   const size_t ds = 16 + 2 * (size_t)(m + 2);
   const int nv = j + 1;
   auto base = [&](int k) { return c->dsc + (size_t)k * ds; };
@@ -1381,73 +1390,65 @@ void arnoldi_gs(stokes_ctx* c, int j, const std::vector<char>& active, double* w
        "read");
     ck(cudaStreamSynchronize(s), "sync");
   };
-  auto finish = [&](int k, double h, const double* coef_dev) {   // V_{j+1} = (w - V c) / h
-    hn[k] = h;
-    if (!(h > 0.0)) return;
-    c->pinned_multi[2 * k + 1] = h;
-    ck(cudaMemcpyAsync(base(k) + 7, c->pinned_multi + 2 * k + 1, sizeof(double),
-                       cudaMemcpyHostToDevice, s), "h");
-    multi_axpy_div(c->V + k * n, N, nv, coef_dev, -1.0, w + k * n, base(k) + 7,
-                   c->V + (int64_t)nv * N + k * n, n, s);
-  };
-  std::vector<char> pass2(nb, 0), pass3(nb, 0);
-  bool any2 = false, any3 = false;
   for (int k = 0; k < nb; ++k)
     if (active[k])
-      multi_dot(c->V + k * n, N, nv, w + k * n, n, c->partials + kDotScratch, base(k) + 8, s, true);
+      multi_dot2(c->V + k * n, N, nv, w + k * n, c->V + (int64_t)j * N + k * n, n,
+                 c->partials + kDotScratch, base(k) + 8, s);
   check_launch("fgmres arnoldi");
   read_all();
+  std::vector<char> explicit_norm(nb, 0);
+  bool any_explicit = false;
   for (int k = 0; k < nb; ++k) {
     if (!active[k]) continue;
-    const double* h = hs.data() + (size_t)k * ds + 8;
-    const double ww = h[nv];
-    double hh = 0.0;
-    for (int i = 0; i < nv; ++i) hh += h[i] * h[i];
-    cols[k].assign(h, h + nv);
-    const double s2 = ww - hh;
-    if (!std::isfinite(ww) || !std::isfinite(s2)) {
-      bad[k] = 1;
-      continue;
-    }
-    if (s2 > 0.5 * ww) {
-      finish(k, std::sqrt(s2), base(k) + 8);
-    } else {   // reorthogonalise: w -= V h, then the second pass's products
-      pass2[k] = 1;
-      any2 = true;
-      multi_axpy(c->V + k * n, N, nv, base(k) + 8, -1.0, w + k * n, n, s);
-      multi_dot(c->V + k * n, N, nv, w + k * n, n, c->partials + kDotScratch,
-                base(k) + 8 + (m + 2), s, true);
-    }
-  }
-  if (!any2) return;
-  read_all();
-  for (int k = 0; k < nb; ++k) {
-    if (!pass2[k]) continue;
-    const double* h2 = hs.data() + (size_t)k * ds + 8 + (m + 2);
-    const double ww = h2[nv];
-    double hh = 0.0;
+    const double* cv = hs.data() + (size_t)k * ds + 8;
+    const double* dv = cv + nv;
+    const double ww = dv[nv];
+    std::vector<double>& G = gram[k];
+    for (int i = 0; i <= j; ++i) G[(size_t)i * mg + j] = G[(size_t)j * mg + i] = dv[i];
+    std::vector<double>& h = cols[k];
+    h.assign(nv, 0.0);
     for (int i = 0; i < nv; ++i) {
-      hh += h2[i] * h2[i];
-      cols[k][i] += h2[i];
+      double gc = 0.0;
+      for (int l = 0; l < nv; ++l) gc += G[(size_t)i * mg + l] * cv[l];
+      h[i] = cv[i] + (cv[i] - gc);
     }
-    const double s2 = ww - hh;
-    if (!std::isfinite(ww) || !std::isfinite(s2)) {
+    double hc = 0.0, hgh = 0.0;
+    for (int i = 0; i < nv; ++i) {
+      hc += h[i] * cv[i];
+      double gh = 0.0;
+      for (int l = 0; l < nv; ++l) gh += G[(size_t)i * mg + l] * h[l];
+      hgh += h[i] * gh;
+    }
+    const double s2 = ww - 2.0 * hc + hgh;
+    bool finite = std::isfinite(ww) && std::isfinite(s2);
+    for (int i = 0; i < nv && finite; ++i) finite = std::isfinite(h[i]);
+    if (!finite) {
       bad[k] = 1;
       continue;
     }
-    if (s2 > 0.5 * ww) {
-      finish(k, std::sqrt(s2), base(k) + 8 + (m + 2));
-    } else {   // w -= V h2 and its norm from a dot product
-      pass3[k] = 1;
-      any3 = true;
-      multi_axpy(c->V + k * n, N, nv, base(k) + 8 + (m + 2), -1.0, w + k * n, n, s);
+    double* hp = c->pinned_h + (size_t)k * (m + 2);
+    for (int i = 0; i < nv; ++i) hp[i] = h[i];
+    double* hdev = base(k) + 8 + (m + 2);
+    ck(cudaMemcpyAsync(hdev, hp, nv * sizeof(double), cudaMemcpyHostToDevice, s), "h");
+    if (s2 > 1e-6 * ww) {
+      const double hv = std::sqrt(s2);
+      hn[k] = hv;
+      hp[m + 1] = hv;
+      ck(cudaMemcpyAsync(base(k) + 7, hp + m + 1, sizeof(double), cudaMemcpyHostToDevice, s),
+         "h");
+      multi_axpy_div(c->V + k * n, N, nv, hdev, -1.0, w + k * n, base(k) + 7,
+                     c->V + (int64_t)nv * N + k * n, n, s);
+    } else {   // w -= V h, then its norm from a dot product
+      explicit_norm[k] = 1;
+      any_explicit = true;
+      multi_axpy(c->V + k * n, N, nv, hdev, -1.0, w + k * n, n, s);
       dot<double>(w + k * n, w + k * n, n, c->partials, base(k) + 6, s);
     }
   }
-  if (!any3) return;
+  if (!any_explicit) return;
   read_all();
   for (int k = 0; k < nb; ++k) {
-    if (!pass3[k]) continue;
+    if (!explicit_norm[k]) continue;
     const double h = std::sqrt(hs[(size_t)k * ds + 6]);
     if (!std::isfinite(h)) {
       bad[k] = 1;
@@ -1455,9 +1456,10 @@ void arnoldi_gs(stokes_ctx* c, int j, const std::vector<char>& active, double* w
     }
     hn[k] = h;
     if (h > 0.0) {
-      c->pinned_multi[2 * k + 1] = h;
-      ck(cudaMemcpyAsync(base(k) + 7, c->pinned_multi + 2 * k + 1, sizeof(double),
-                         cudaMemcpyHostToDevice, s), "h");
+      double* hp = c->pinned_h + (size_t)k * (m + 2);
+      hp[m + 1] = h;
+      ck(cudaMemcpyAsync(base(k) + 7, hp + m + 1, sizeof(double), cudaMemcpyHostToDevice, s),
+         "h");
       scale_inv_dev(base(k) + 7, w + k * n, c->V + (int64_t)nv * N + k * n, n, s);
     }
   }
@@ -1484,7 +1486,7 @@ int run_fgmres(stokes_ctx* c, const double* f, double tol, double* x, int* iters
   int it = 0;
   copy_async(r, f, n * sizeof(double), s);
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
-  std::vector<std::vector<double>> cols(1);
+  std::vector<std::vector<double>> cols(1), gram(1, std::vector<double>((size_t)(m + 1) * (m + 1)));
   std::vector<double> hnv(1);
   std::vector<char> act(1, 1), bad(1, 0);
   while (it < c->opts.maxit) {
@@ -1507,7 +1509,7 @@ int run_fgmres(stokes_ctx* c, const double* f, double tol, double* x, int* iters
       double* Vj = c->V + (int64_t)j * n;
       double* Zj = c->Z + (int64_t)j * n;
       pk_apply(c, Vj, Zj, w);
-      arnoldi_gs(c, j, act, w, cols, hnv, bad);   // writes V_{j+1}
+      arnoldi_gs(c, j, act, w, gram, cols, hnv, bad);   // writes V_{j+1}
       if (bad[0]) return STOKES_ERR_NONFINITE;
       const double hn = hnv[0];
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = cols[0][i];
@@ -1606,6 +1608,7 @@ void run_fgmres_multi(stokes_ctx* c, const double* f, double tol, double* x, int
   std::vector<int> k_used(nb, 0);
   std::vector<char> active(nb, 0), stop(nb, 0), bad(nb, 0);
   std::vector<std::vector<double>> cols(nb);
+  std::vector<std::vector<double>> gram(nb, std::vector<double>((size_t)(m + 1) * (m + 1)));
   std::vector<double> hnv(nb, 0.0);
   auto any = [&](const std::vector<char>& v) {
     for (char e : v)
@@ -1642,7 +1645,7 @@ void run_fgmres_multi(stokes_ctx* c, const double* f, double tol, double* x, int
       double* Zj = c->Z + (int64_t)j * N;
       pk_apply(c, Vj, Zj, w);
       std::fill(bad.begin(), bad.end(), 0);
-      arnoldi_gs(c, j, active, w, cols, hnv, bad);   // writes V_{j+1} of every active item
+      arnoldi_gs(c, j, active, w, gram, cols, hnv, bad);   // writes V_{j+1} of every active item
       for (int k = 0; k < nb; ++k) {
         if (!active[k]) continue;
         const double hn = hnv[k];
@@ -2102,7 +2105,7 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
     c->ones = upload<double>(c->arena, one, c->stream);
     // dot scratch (partials and completion counter), then the Gram-Schmidt partials
     c->partials = c->arena.alloc<double>((size_t)kDotScratch +
-                                         (size_t)kMultiDotBlocks * (o.restart + 2));
+                                         (size_t)kMultiDotBlocks * (2 * o.restart + 4));
     fill_zero(c->partials, kDotScratch * sizeof(double), c->stream);
     c->load1d = c->arena.alloc<double>(3 * (size_t)(c->b + 1));
     c->dsc = c->arena.alloc<double>((size_t)c->nb * (16 + 2 * (o.restart + 2)));
@@ -2110,6 +2113,7 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
     ck(cudaMallocHost(&c->st_host, sizeof(MinresState)), "pinned");
     ck(cudaMallocHost(&c->pinned, 64 * sizeof(double)), "pinned");
     ck(cudaMallocHost(&c->pinned_multi, 2 * (size_t)c->nb * sizeof(double)), "pinned");
+    ck(cudaMallocHost(&c->pinned_h, (size_t)c->nb * (o.restart + 2) * sizeof(double)), "pinned");
     for (int i = 0; i < 8; ++i) c->kv[i] = c->arena.alloc<double>((size_t)c->nb * c->ntot);
     if (o.solver == STOKES_SOLVER_FGMRES) {
       c->V = c->arena.alloc<double>((size_t)(o.restart + 1) * c->nb * c->ntot);
@@ -2581,6 +2585,7 @@ void stokes_destroy(stokes_t c) {
   if (c->st_host) cudaFreeHost(c->st_host);
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->pinned_multi) cudaFreeHost(c->pinned_multi);
+  if (c->pinned_h) cudaFreeHost(c->pinned_h);
   if (c->stream_q) cudaStreamSynchronize(c->stream_q);
   cudaStream_t s = c->own_stream ? c->stream : nullptr;
   cudaStream_t sq = c->stream_q;
