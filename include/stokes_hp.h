@@ -207,9 +207,9 @@ int stokes_solve_batch(stokes_t* ctxs, int count, const double* const* rhs, doub
 int stokes_last_ratios(stokes_t ctx, double* ratios, int capacity);
 
 /* ---- instrumentation (no counterpart in the paper) ------------------------------------------
- * Kernel classes: 0 banded Kronecker passes, 1 dense mode products on CUDA cores, 2 discrete
- * divergence / transpose, 3 Krylov vector kernels, 4 tensor-core mode products, 5 banded
- * Cholesky line solves.
+ * Kernel classes: 0 banded Kronecker passes in FP32, 1 dense mode products on CUDA cores,
+ * 2 discrete divergence / transpose, 3 Krylov vector kernels, 4 tensor-core mode products,
+ * 5 banded Cholesky line solves, 6 banded Kronecker passes in FP64.
  * stokes_profile_begin brackets every later launch of this thread with CUDA events on the
  * launching stream; stokes_profile_end synchronizes, writes per-class totals (launches, summed
  * event intervals in ms, algorithmic flops and bytes: each input read once, each output written

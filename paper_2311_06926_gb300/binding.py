@@ -45,7 +45,7 @@ class KernelStat(ctypes.Structure):
 
 
 KERNEL_CLASSES = ["band_pass", "mode_product", "divergence", "vector", "mma_mode_product",
-                  "line_solve"]
+                  "line_solve", "band_pass_fp64"]
 
 _lib = None
 

@@ -1015,7 +1015,9 @@ void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s) {
   }
   pb.first_block[njobs] = blocks;
   pb.seg = seg_len<T>();
-  launch_begin(kClassBand, s);
+  // FP64 passes (bound by the FP64 pipe) are accounted apart from the FP32 ones
+  const int cls = sizeof(T) == 8 ? kClassBand64 : kClassBand;
+  launch_begin(cls, s);
   switch (W) {
 #define SHP_PASS_W(w)                                                                     \
   case w: {                                                                               \
@@ -1028,7 +1030,7 @@ void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s) {
 #undef SHP_PASS_W
     default: launch_k(k_band_pass<T, 0>, blocks, bt, 0, s, pb);
   }
-  launch_end(kClassBand, s, flops, bytes);
+  launch_end(cls, s, flops, bytes);
 }
 
 template <typename T>

@@ -356,13 +356,30 @@ __global__ void __launch_bounds__(kThreads, 1)
           TO* yp = yrow + stride_i * c0;
           if (args.lam_i) {
             const float* li = args.lam_i + c0;
+            if (kmax == 32) {
 #pragma unroll
-            for (int k = 0; k < 32; ++k) {
-              if (k < kmax) {
+              for (int k = 0; k < 32; ++k) {
                 const float val = __fdividef(v[k], scale * (lam_r + li[k]));
-                store_val<TO>(yp, rt ? round_tf32(val) : val);
+                store_val<TO>(yp + stride_i * k, rt ? round_tf32(val) : val);
               }
-              yp += stride_i;
+            } else {
+#pragma unroll
+              for (int k = 0; k < 32; ++k) {
+                if (k < kmax) {
+                  const float val = __fdividef(v[k], scale * (lam_r + li[k]));
+                  store_val<TO>(yp, rt ? round_tf32(val) : val);
+                }
+                yp += stride_i;
+              }
+            }
+          } else if (kmax == 32) {
+            // full chunk: no per-element predicate (it cost twice the time of the stores)
+            if (rt) {
+#pragma unroll
+              for (int k = 0; k < 32; ++k) store_val<TO>(yp + stride_i * k, round_tf32(v[k] * post));
+            } else {
+#pragma unroll
+              for (int k = 0; k < 32; ++k) store_val<TO>(yp + stride_i * k, v[k] * post);
             }
           } else {
 #pragma unroll

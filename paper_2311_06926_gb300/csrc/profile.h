@@ -15,7 +15,8 @@ enum KernelClass {
   kClassVector = 3,    // Krylov vector kernels, dot products, conversions
   kClassMma = 4,       // tensor-core mode products
   kClassLine = 5,      // banded Cholesky line solves (FP64 pressure block)
-  kNumClasses = 6
+  kClassBand64 = 6,    // FP64 banded Kronecker passes (class 0 then holds the FP32 ones)
+  kNumClasses = 7
 };
 
 void launch_begin(int cls, cudaStream_t s);
