@@ -536,6 +536,43 @@ def run_probe(args, wl):
     return 0
 
 
+def run_solve(args, wl):
+    """Solve probe for ncu launch lists: the workload's first (order, steps) solve in its
+    precision, --warmup untimed solves, then --steps solves between cudaProfilerStart and
+    cudaProfilerStop (so ``ncu --profile-from-start off`` captures exactly those launches);
+    prints the CUDA-event time per solve."""
+    import torch
+    from paper_2311_06926_gb300 import Stokes
+    from paper_2311_06926_gb300.binding import kernel_launches
+    q, s = wl["sweep"][0]
+    G = Stokes(wl["n"], wl["p"], precision=wl["precision"], max_order=q, max_steps=s)
+    G.set_preconditioner(q, s)
+    f = G.rhs_cavity(1.0)
+    x = G.empty()
+    last = {}
+    for _ in range(args.warmup):
+        _, last["it"], last["rr"], _ = G.solve(f, 1e-8, out=x)
+    torch.cuda.synchronize()
+    cur = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = kernel_launches()
+    torch.cuda.profiler.start()
+    e0.record(cur)
+    for _ in range(args.steps):
+        _, last["it"], last["rr"], _ = G.solve(f, 1e-8, out=x)
+    e1.record(cur)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"solve_probe": wl["desc"], "precision": wl["precision"], "order": q,
+                      "steps": s, "solves": args.steps, "iterations": last["it"],
+                      "true_rel_res": last["rr"],
+                      "ms_per_solve": round(e0.elapsed_time(e1) / args.steps, 3),
+                      "gpu_launches_per_solve": (kernel_launches() - n0) / args.steps}),
+          flush=True)
+    G.close()
+    return 0
+
+
 def run_batch(args, wl):
     """The batched heterogeneous workload: one step = the 64 solves.
 
@@ -934,6 +971,9 @@ def main():
                     help="kernel probe for ncu: only apply the order-2, 1-step hyper-power "
                          "preconditioner K times on the workload's mesh in --precision (no "
                          "Krylov bases, small device footprint); prints per-kernel-class times")
+    ap.add_argument("--solve", action="store_true",
+                    help="solve probe for ncu: only the workload's first solve, --steps times "
+                         "between cudaProfilerStart/Stop; prints the time per solve")
     ap.add_argument("--tuning", default="auto",
                     help="FP64 launch shapes mode_block,band_block,fd_fused (default: the "
                          "library's setup tuner); for profiling runs, whose kernel replay "
@@ -946,6 +986,8 @@ def main():
         return run_reference(args, wl)
     if args.probe:
         return run_probe(args, wl)
+    if args.solve:
+        return run_solve(args, wl)
     if args.workload == "batch64":
         return run_batch(args, wl)
     if args.workload == "cavity128":

@@ -29,9 +29,10 @@ def test_quadrature_operator_equals_kronecker_and_oracle(n, p, nu):
     yq = host(Gq.apply_K(dev(x)))
     prof = Gq.profile_end()
     # the quadrature path ran: one pointwise stress launch (the only non-band kernel) and the
-    # forward and transposed evaluation trees as banded passes
+    # forward and transposed evaluation trees as FP64 banded passes
     assert prof["divergence"]["launches"] == 1
-    assert prof["band_pass"]["launches"] >= 30 and prof["mode_product"]["launches"] == 0
+    assert prof["band_pass_fp64"]["launches"] >= 30 and prof["band_pass"]["launches"] == 0
+    assert prof["mode_product"]["launches"] == 0
     assert relerr(yq, yk) < 1e-12
     assert relerr(yq, Kop(x)) < 1e-12
     Gk.close()
