@@ -90,8 +90,10 @@ WORKLOADS = {
                       desc="3D lid-driven cavity, 128^3 elements, p=3 (velocity degree 4 in its "
                            "own direction), nu=1, order-2 hyper-power preconditioner with 2 steps "
                            "(Schur with inner updates); mixed form: TF32 tensor-core fast "
-                           "diagonalisation and FP32 inner steps inside FP64 flexible GMRES to a "
-                           "true relative residual of 1e-8, one RHS per solve"),
+                           "diagonalisation and FP32 inner steps inside flexible GMRES (FP64 "
+                           "vectors and inner products, Arnoldi products K z in pair-of-FP32 "
+                           "arithmetic) to a true relative residual of 1e-8 (FP64 operator), one "
+                           "RHS per solve"),
     "cavity32": dict(n=32, p=3, sweep=[(q, s) for q in (2, 3) for s in (0, 1, 2, 3)],
                      precision="fp64",
                      desc="3D lid-driven cavity, 32^3 elements, p=3 (velocity degree 4 in its own "
@@ -521,17 +523,25 @@ def class_rooflines(prof, step_ms, prec, peaks):
 def run_probe(args, wl):
     import torch
     from paper_2311_06926_gb300 import Stokes
-    G = Stokes(wl["n"], wl["p"], precision=wl["precision"], max_order=2, max_steps=1)
+    G = Stokes(wl["n"], wl["p"], precision=wl["precision"], max_order=2, max_steps=1, restart=2,
+               outer=args.outer)
     x = torch.randn(G.size, dtype=torch.float64, device="cuda")
+    if args.probe == "k":
+        xf = x.float()
+        op, what = (lambda: G.apply_K_f32(xf)), "K applications to an FP32 vector (outer " + \
+            args.outer + ")"
+    else:
+        op, what = (lambda: G.apply_hyperpower(2, 1, x)), "order-2, 1-step preconditioner " \
+            "applications"
     for _ in range(args.warmup):
-        G.apply_hyperpower(2, 1, x)
+        op()
     torch.cuda.synchronize()
     G.profile_begin()
     for _ in range(args.steps):
-        G.apply_hyperpower(2, 1, x)
+        op()
     prof = G.profile_end()
-    print(json.dumps({"probe": wl["desc"], "precision": wl["precision"], "applications": args.steps,
-                      "kernel_classes": prof}), flush=True)
+    print(json.dumps({"probe": wl["desc"], "precision": wl["precision"], "what": what,
+                      "applications": args.steps, "kernel_classes": prof}), flush=True)
     G.close()
     return 0
 
@@ -545,7 +555,8 @@ def run_solve(args, wl):
     from paper_2311_06926_gb300 import Stokes
     from paper_2311_06926_gb300.binding import kernel_launches
     q, s = wl["sweep"][0]
-    G = Stokes(wl["n"], wl["p"], precision=wl["precision"], max_order=q, max_steps=s)
+    G = Stokes(wl["n"], wl["p"], precision=wl["precision"], max_order=q, max_steps=s,
+               outer=args.outer)
     G.set_preconditioner(q, s)
     f = G.rhs_cavity(1.0)
     x = G.empty()
@@ -563,7 +574,8 @@ def run_solve(args, wl):
     e1.record(cur)
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
-    print(json.dumps({"solve_probe": wl["desc"], "precision": wl["precision"], "order": q,
+    print(json.dumps({"solve_probe": wl["desc"], "precision": wl["precision"], "outer": args.outer,
+                      "order": q,
                       "steps": s, "solves": args.steps, "iterations": last["it"],
                       "true_rel_res": last["rr"],
                       "ms_per_solve": round(e0.elapsed_time(e1) / args.steps, 3),
@@ -902,6 +914,14 @@ def run_cavity128(args, wl):
         Go.close()
         del Go
         torch.cuda.empty_cache()
+        # the headline form with FP64 Arnoldi products K z instead of pair-of-FP32 ones
+        Gd = Stokes(n, p, precision=prec, max_order=q, max_steps=s, outer="fp64")
+        Gd.set_preconditioner(q, s)
+        forms[f"{prec}_fp64_products"] = dict(timed_solve(Gd, Gd.rhs_cavity(1.0), tol)[0],
+                                               outer="fp64")
+        Gd.close()
+        del Gd
+        torch.cuda.empty_cache()
         f64ms, b64ms = forms["fp64"]["ms"], best64["ms"]
         forms["speedup"] = {
             "vs_fp64_same_preconditioner": {k: f64ms / forms[k]["ms"] for k in (prec, other)},
@@ -933,7 +953,7 @@ def run_cavity128(args, wl):
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": f"{prec}+f64", "data": "synthetic",
+            "dtype": f"{prec}+f32x2+f64", "data": "synthetic",
             "config": workload_config(args, wl),
             "unknowns": G.size,
             "headline": head,
@@ -967,13 +987,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload: skip the 32^3 sweep and 64-problem batch lines")
-    ap.add_argument("--probe", action="store_true",
+    ap.add_argument("--probe", nargs="?", const="p", default=None, choices=["p", "k"],
                     help="kernel probe for ncu: only apply the order-2, 1-step hyper-power "
-                         "preconditioner K times on the workload's mesh in --precision (no "
-                         "Krylov bases, small device footprint); prints per-kernel-class times")
+                         "preconditioner (p, the default) or the Arnoldi product K z of an FP32 z "
+                         "(k) --steps times on the workload's mesh in --precision (restart 2, "
+                         "small device footprint); prints per-kernel-class times")
     ap.add_argument("--solve", action="store_true",
                     help="solve probe for ncu: only the workload's first solve, --steps times "
                          "between cudaProfilerStart/Stop; prints the time per solve")
+    ap.add_argument("--outer", default="pair", choices=["pair", "fp64"],
+                    help="solve probe: arithmetic of the Arnoldi products K z (reduced-precision "
+                         "preconditioner)")
     ap.add_argument("--tuning", default="auto",
                     help="FP64 launch shapes mode_block,band_block,fd_fused (default: the "
                          "library's setup tuner); for profiling runs, whose kernel replay "

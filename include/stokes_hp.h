@@ -54,6 +54,7 @@ enum { STOKES_PREC_FP64 = 0, STOKES_PREC_FP32 = 1, STOKES_PREC_TF32 = 2, STOKES_
 enum { STOKES_SOLVER_MINRES = 0, STOKES_SOLVER_FGMRES = 1 };
 
 enum { STOKES_FORWARD_KRONECKER = 0, STOKES_FORWARD_QUADRATURE = 1 };
+enum { STOKES_OUTER_PAIR = 0, STOKES_OUTER_FP64 = 1 };
 
 typedef struct stokes_opts {
   double c_pen;       /* Nitsche penalty constant C_pen (Sec. 3.2); <= 0 selects 14 */
@@ -86,12 +87,23 @@ typedef struct stokes_opts {
                          direction, the forward operator of the paper's timings, Sec. 5.3; equal
                          to the Kronecker operator up to rounding; nrhs = 1 only).
                          stokes_apply_A always uses the Kronecker form. */
+  int outer;          /* arithmetic of the products w = K z of flexible GMRES when the
+                         preconditioner runs in reduced precision (z is then its FP32 output):
+                         STOKES_OUTER_PAIR (default; every value carried as an unevaluated sum
+                         of two FP32 numbers, about 48 significant bits, w rounded to FP64; on
+                         this GPU's reduced FP64 pipe several times faster than FP64) or
+                         STOKES_OUTER_FP64. Residuals of the iterate (restarts, the final true
+                         residual), stokes_apply_K and every FP64-preconditioned solve use the
+                         FP64 operator either way. Used with the Kronecker forward operator when
+                         n_elems + degree_p <= 256 and every band has half width <= 6; the FP64
+                         operator otherwise. */
 } stokes_opts;
 
 typedef struct stokes_ctx* stokes_t;
 
 /* Fill *o with the defaults: c_pen 14, Schur with inner updates, FP64, MINRES, max_order 3,
- * max_steps 4, maxit 2000, restart 60, stream NULL. */
+ * max_steps 4, maxit 2000, restart 60, stream NULL, nrhs 1, autotune on, Kronecker forward
+ * operator, pair-of-FP32 Arnoldi products. */
 void stokes_default_opts(stokes_opts* o);
 
 /* Build the univariate matrices (App. B.3, T-check of Sec. 3.3), the fast-diagonalisation
@@ -121,6 +133,13 @@ int stokes_apply_K(stokes_t ctx, const double* x, double* y);
  * diagonal blocks of A (Sec. 4, App. A.4) and the pressure mass block M-check^3 / (2 nu)
  * (Sec. 4). Runs in the context's preconditioner precision. x, y: n_vel + n_pres. */
 int stokes_apply_P(stokes_t ctx, const double* x, double* y);
+
+/* y = K x for an FP32 vector x (nrhs items), in the arithmetic of the context's Arnoldi products
+ * (stokes_opts.outer): pairs of FP32 numbers rounded to FP64, or the FP64 operator applied to x
+ * converted exactly to FP64. x: device FP32 (n_vel + n_pres entries per item, the layout of the
+ * FP64 vectors); y: device FP64. Needs a reduced-precision context (STOKES_ERR_ARG otherwise).
+ * Returns STOKES_OK or a negative code. */
+int stokes_apply_K_f32(stokes_t ctx, const float* x, double* y);
 
 /* y = P_s^-1 x for the order-q hyper-power sequence (Eqs. 2.1, 4.4 for the velocity block,
  * 4.5 or 4.6 for the pressure block) with q = order, s = steps; steps = 0 equals
@@ -209,7 +228,8 @@ int stokes_last_ratios(stokes_t ctx, double* ratios, int capacity);
 /* ---- instrumentation (no counterpart in the paper) ------------------------------------------
  * Kernel classes: 0 banded Kronecker passes in FP32, 1 dense mode products on CUDA cores,
  * 2 discrete divergence / transpose, 3 Krylov vector kernels, 4 tensor-core mode products,
- * 5 banded Cholesky line solves, 6 banded Kronecker passes in FP64.
+ * 5 banded Cholesky line solves, 6 banded Kronecker passes in FP64, 7 the saddle-point operator
+ * in pair-of-FP32 arithmetic (its banded passes and fused divergence).
  * stokes_profile_begin brackets every later launch of this thread with CUDA events on the
  * launching stream; stokes_profile_end synchronizes, writes per-class totals (launches, summed
  * event intervals in ms, algorithmic flops and bytes: each input read once, each output written

@@ -19,6 +19,7 @@ SCHUR = {"inner": 0, "none": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 SOLVER = {"minres": 0, "fgmres": 1}
 FORWARD = {"kronecker": 0, "quadrature": 1}
+OUTER = {"pair": 0, "fp64": 1}
 
 
 class StokesError(RuntimeError):
@@ -36,7 +37,8 @@ class _Opts(ctypes.Structure):
     _fields_ = [("c_pen", ctypes.c_double), ("schur", ctypes.c_int), ("precision", ctypes.c_int),
                 ("solver", ctypes.c_int), ("max_order", ctypes.c_int), ("max_steps", ctypes.c_int),
                 ("maxit", ctypes.c_int), ("restart", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("nrhs", ctypes.c_int), ("autotune", ctypes.c_int), ("forward", ctypes.c_int)]
+                ("nrhs", ctypes.c_int), ("autotune", ctypes.c_int), ("forward", ctypes.c_int),
+                ("outer", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -45,7 +47,7 @@ class KernelStat(ctypes.Structure):
 
 
 KERNEL_CLASSES = ["band_pass", "mode_product", "divergence", "vector", "mma_mode_product",
-                  "line_solve", "band_pass_fp64"]
+                  "line_solve", "band_pass_fp64", "pair_operator"]
 
 _lib = None
 
@@ -70,6 +72,7 @@ def load_library(path=None):
         "stokes_set_preconditioner": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
         "stokes_apply_A": (ctypes.c_int, [vp, vp, vp]),
         "stokes_apply_K": (ctypes.c_int, [vp, vp, vp]),
+        "stokes_apply_K_f32": (ctypes.c_int, [vp, vp, vp]),
         "stokes_apply_P": (ctypes.c_int, [vp, vp, vp]),
         "stokes_set_wait_limit": (ctypes.c_int, [vp, ctypes.c_int64]),
         "stokes_apply_hyperpower": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp]),
@@ -164,7 +167,7 @@ class Stokes:
 
     def __init__(self, n, p, nu=1.0, c_pen=14.0, schur="inner", precision="fp64",
                  solver=None, max_order=3, max_steps=4, maxit=2000, restart=60, device=None,
-                 nrhs=1, autotune=True, forward="kronecker"):
+                 nrhs=1, autotune=True, forward="kronecker", outer="pair"):
         """nrhs > 1: the context holds nrhs right-hand sides; apply_K, apply_P,
         apply_hyperpower, solve and solve_multi then take nrhs stacked vectors of `size` entries
         each (`batch_size` in all), processed by the same launches (needs precision "tf32" or
@@ -185,6 +188,7 @@ class Stokes:
         o.nrhs = nrhs
         o.autotune = 1 if autotune else 0
         o.forward = FORWARD[forward]
+        o.outer = OUTER[outer]
         with torch.cuda.device(self.device):
             # the library runs on its own stream, ordered against the caller's current stream
             # at every call (inputs ready before, outputs visible after)
@@ -253,6 +257,16 @@ class Stokes:
         y = out if out is not None else self.empty(self.batch_size)
         self._check(self._call(self.lib.stokes_apply_K, self.h, _ptr(self._vec(x, self.batch_size)),
                                             _ptr(self._vec(y, self.batch_size))))
+        return y
+
+    def apply_K_f32(self, x, out=None):
+        """K x for a float32 CUDA tensor x in the arithmetic of the Arnoldi products (`outer`)."""
+        if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous() and
+                x.numel() == self.batch_size):
+            raise ValueError(f"expected a contiguous float32 CUDA tensor of {self.batch_size} entries")
+        y = out if out is not None else self.empty(self.batch_size)
+        self._check(self._call(self.lib.stokes_apply_K_f32, self.h, _ptr(x),
+                               _ptr(self._vec(y, self.batch_size))))
         return y
 
     def apply_P(self, x, out=None):

@@ -13,7 +13,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libstokes_hp.so")
-SOURCES = ["host_setup.cpp", "profile.cpp", "k_band.cu", "k_dense.cu", "k_vec.cu", "stokes.cu", "noalloc.cu", "k_mma.cu"]
+SOURCES = ["host_setup.cpp", "profile.cpp", "k_band.cu", "k_dense.cu", "k_vec.cu", "stokes.cu",
+           "noalloc.cu", "k_mma.cu", "k_pair.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

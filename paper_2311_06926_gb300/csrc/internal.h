@@ -331,6 +331,38 @@ void minres_update(const double* z, double* w_old_inout, const double* w, double
                    MinresState* st, int64_t n, cudaStream_t s);
 void minres_init(MinresState* st, cudaStream_t s);
 
+// ---- the saddle-point operator in pair-of-FP32 arithmetic (k_pair.cu) ----------------------
+// A value is carried as the unevaluated sum hi + lo of two floats (float2 {hi, lo}), about 48
+// significant bits. Band matrices in the centred form of BandD: row i, entry k in [0, 2 H]
+// holds D(i, i - H + k) (zero outside the matrix), `pitch` (even) pairs per row, rows padded with
+// zeros to a multiple of 8; every term of one launch has the same half width H (1 <= H <= 6).
+struct PairBand {
+  const float2* c;
+  int rows, pitch;
+};
+// Y = sum_t D_t .axis X_t [+ D^T_gaxis g] (up to two terms). X_t: FP32 (in_f32; the value is
+// exact with lo = 0) or pairs; g: pairs on the b^3 grid gdims; Y: FP64 (out_f64) or pairs. Every
+// term has X's extents `in`; Y has in.with(axis, rows). nb items, item k of every tensor at k * bs
+// elements from its pointer.
+struct PairPass {
+  const void* X[2];
+  PairBand D[2];
+  int nterms, in_f32, out_f64;
+  const float2* g; int gaxis; Dims gdims;
+  void* Y;
+  Dims in; int axis;
+  int nb; int64_t bs;
+};
+constexpr int kMaxPairJobs = 8;
+// Several passes (up to kMaxPairJobs) of half width H in one launch.
+cudaError_t pair_pass_multi(const PairPass* jobs, int njobs, int H, cudaStream_t s);
+// delta = D_div u and e = nu delta + q on the (b, b, b) pressure grid from FP32 u1, u2, u3, q,
+// formed in pairs, and their band pass along x1: y0 = D .x1 delta, y1 = D .x1 e (pairs); nb
+// items at pitch bs. D: centred, half width H.
+cudaError_t pair_div_x1(const float* u1, const float* u2, const float* u3, const float* q, int a,
+                        int b, float2 nu, const PairBand& D, int H, float2* y0, float2* y1,
+                        int nb, int64_t bs, cudaStream_t s);
+
 // float <-> double conversions for the mixed-precision preconditioner
 void to_float(const double* x, float* y, int64_t n, cudaStream_t s);
 void to_double(const float* x, double* y, int64_t n, cudaStream_t s);

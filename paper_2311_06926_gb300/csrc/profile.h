@@ -16,7 +16,8 @@ enum KernelClass {
   kClassMma = 4,       // tensor-core mode products
   kClassLine = 5,      // banded Cholesky line solves (FP64 pressure block)
   kClassBand64 = 6,    // FP64 banded Kronecker passes (class 0 then holds the FP32 ones)
-  kNumClasses = 7
+  kClassPair = 7,      // banded passes and divergence in pair-of-FP32 arithmetic
+  kNumClasses = 8
 };
 
 void launch_begin(int cls, cudaStream_t s);

