@@ -3,15 +3,18 @@
 
 Workload (default, ``--workload cavity128``): the 3D lid-driven cavity (Sec. 5, Fig. 2) on 128^3
 elements, pressure degree p = 3 (velocity degree 4 in its own direction, the paper's degree 4;
-8.94 M unknowns), nu = 1, lid (1, 0, 0) on x2 = 1, order-2 hyper-power preconditioner with 2
-steps (Schur sequence with inner updates, Eq. 4.5). One step = one solve of the mixed form:
-tensor-core (TF32 operands, FP32 accumulation) fast diagonalisation and FP32 inner hyper-power
-steps inside FP64 flexible GMRES, to a true relative residual ||f - K x||_2 / ||f||_2 <= 1e-8;
-value = solves/s. Beside it: the plain FP64 form (MINRES, Table 1's criterion) and the mixed form
-at the FP64 solve's true residual (equal accuracy) and in BF16, each with its error against the
-oracle's solution (tests/golden/cavity128_p3_q2s2.json, written by a script that calls only the
-oracle). ``--workload cavity32`` times the 32^3 FP64 sweep of order {2, 3} x steps {0..3}; it also
-appears in the default line as ``sweep32``, with the 64-problem batch as ``batch64``.
+8.94 M unknowns), nu = 1, lid (1, 0, 0) on x2 = 1, order-3 hyper-power preconditioner with 1
+step (Schur sequence with inner updates, Eq. 4.5; the fastest of the mixed form's sweep, which
+the line reports). One step = one solve of the mixed form: tensor-core (TF32 operands, FP32
+accumulation) fast diagonalisation and FP32 inner hyper-power steps inside FP64 flexible GMRES
+(FP64 residual, Arnoldi products, orthogonalisation and inner products), to a true relative
+residual ||f - K x||_2 / ||f||_2 <= 1e-8; value = solves/s. Beside it: the plain FP64 form
+(MINRES, Table 1's criterion) with a short preconditioner sweep, the mixed form at the fastest
+FP64 solve's accuracy (equal accuracy), in BF16, and with its Arnoldi products in pair-of-FP32
+arithmetic, each with its error against the oracle's tight solution (tests/golden/
+cavity128_p3_q*.json, written by a script that calls only the oracle). ``--workload cavity32``
+times the 32^3 FP64 sweep of order {2, 3} x steps {0..3}; it also appears in the default line as
+``sweep32``, with the 64-problem batch as ``batch64``.
 
 Timing: W warm-up steps, then K steps between a barrier + device synchronize on both sides,
 CUDA events on the launching stream, L2 flushed (a 256 MiB write) before every step, the max over
@@ -86,14 +89,12 @@ def traffic_for(kernel_class, precision, workload, form="per-direction"):
     return t["bytes_per_launch"], t["profile"]
 
 WORKLOADS = {
-    "cavity128": dict(n=128, p=3, sweep=[(2, 2)], precision="tf32",
+    "cavity128": dict(n=128, p=3, sweep=[(3, 1)], precision="tf32",
                       desc="3D lid-driven cavity, 128^3 elements, p=3 (velocity degree 4 in its "
-                           "own direction), nu=1, order-2 hyper-power preconditioner with 2 steps "
+                           "own direction), nu=1, order-3 hyper-power preconditioner with 1 step "
                            "(Schur with inner updates); mixed form: TF32 tensor-core fast "
-                           "diagonalisation and FP32 inner steps inside flexible GMRES (FP64 "
-                           "vectors and inner products, Arnoldi products K z in pair-of-FP32 "
-                           "arithmetic) to a true relative residual of 1e-8 (FP64 operator), one "
-                           "RHS per solve"),
+                           "diagonalisation and FP32 inner steps inside FP64 flexible GMRES to a "
+                           "true relative residual of 1e-8, one RHS per solve"),
     "cavity32": dict(n=32, p=3, sweep=[(q, s) for q in (2, 3) for s in (0, 1, 2, 3)],
                      precision="fp64",
                      desc="3D lid-driven cavity, 32^3 elements, p=3 (velocity degree 4 in its own "
@@ -113,7 +114,17 @@ WORKLOADS = {
                      desc="3D lid-driven cavity, 96^3 elements, p=3, nu=1, order 2, 2 steps"),
 }
 
-GOLDEN_128 = os.path.join(ROOT, "tests", "golden", "cavity128_p3_q2s2.json")
+GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
+
+
+def golden_path(q, s):
+    """The oracle's stored 128^3 solve with the order-q, s-step preconditioner (written by
+    tests/golden/make_cavity128.py); every file also holds the oracle's tight (1e-11) solve,
+    the reference for accuracy."""
+    return os.path.join(GOLDEN_DIR, f"cavity128_p3_q{q}s{s}.json")
+
+
+GOLDEN_128 = golden_path(2, 2)
 L2_NOTE = ("working set of several GB, larger than the 129 MB L2; the GPU arm also writes 256 MiB "
            "before every step")
 
@@ -679,7 +690,7 @@ def run_reference(args, wl):
     cfg = workload_config(args, wl)
     if args.workload == "cavity128":
         q, s = wl["sweep"][0]
-        its = load_golden()["iterations"]
+        its = load_golden(golden_path(q, s))["iterations"]
         dt = oracle_iteration_sample(wl["n"], wl["p"], q, s, args.steps, warmup=args.warmup)
         value = 1.0 / (dt / args.steps * its)
         ms_step = 1e3 * dt / args.steps
@@ -741,11 +752,13 @@ def run_cavity128(args, wl):
     q, s = wl["sweep"][0]
     prec = wl["precision"]
     tol = 1e-8
-    g = load_golden()
+    g = load_golden()                   # the tight oracle solve (accuracy reference)
+    gq = load_golden(golden_path(q, s))  # the oracle's solve with the headline preconditioner
     peaks = load_peaks() or {}
     torch.cuda.synchronize()
     t_setup = time.perf_counter()
-    G = Stokes(n, p, precision=prec, max_order=q, max_steps=s)
+    # workspace for the short preconditioner sweep of the forms below as well
+    G = Stokes(n, p, precision=prec, max_order=max(q, 4), max_steps=max(s, 2))
     G.set_preconditioner(q, s)
     torch.cuda.synchronize()
     setup_ms = 1e3 * (time.perf_counter() - t_setup)
@@ -874,15 +887,25 @@ def run_cavity128(args, wl):
             return dict(r, matched=False)
 
         forms = {"error_measure":
-                 "against the oracle's MINRES solve to 1e-11 (tests/golden/cavity128_p3_q2s2.json): "
+                 "against the oracle's MINRES solve to 1e-11 (tests/golden/cavity128_p3_q2s2.json "
+                 "exact_*): "
                  "rel_2norm_est = sqrt(N/n sum over 1024 seeded sampled entries of (x - x_o)^2) / "
                  "||x_o||; max = the largest of the sampled-entry, block-norm and seeded-inner-"
                  "product errors (as in tests/test_gpu_fullsize.py)",
-                 "oracle": {"iterations": g["iterations"], "true_rel_res": g["true_rel_res"],
-                            "error_vs_exact": g["error_vs_exact"],
-                            "note": "the oracle's own MINRES solve (order 2, 2 steps) to 1e-8"}}
+                 "oracle": {"iterations": gq["iterations"], "true_rel_res": gq["true_rel_res"],
+                            "error_vs_exact": gq["error_vs_exact"],
+                            "note": f"the oracle's own MINRES solve (order {q}, {s} step(s)) to "
+                                    f"1e-8 ({os.path.relpath(golden_path(q, s), ROOT)})"}}
         head["error_vs_exact"] = oracle_error(x_head, g)
         forms[prec] = head
+        # the same mixed form with the other preconditioners of a short sweep (order, steps)
+        sweep_mixed = []
+        for qq, ss in ((2, 1), (3, 1), (4, 1), (2, 2)):
+            G.set_preconditioner(qq, ss)
+            r, _ = timed_solve(G, f, tol)
+            sweep_mixed.append(dict(r, order=qq, steps=ss))
+        G.set_preconditioner(q, s)
+        forms[f"{prec}_sweep"] = sweep_mixed
         # the plain FP64 form (MINRES to 1e-8, Table 1's criterion) with each preconditioner of a
         # short sweep; the fastest is the FP64 form's best
         G64 = Stokes(n, p, precision="fp64", max_order=3, max_steps=2)
@@ -893,7 +916,7 @@ def run_cavity128(args, wl):
             r, xh = timed_solve(G64, f64, tol, reps=2)
             r.update(order=qq, steps=ss, solver="minres")
             if (qq, ss) == (q, s):
-                r["error_vs_oracle_same_solve"] = oracle_error(xh, g, "")
+                r["error_vs_oracle_same_solve"] = oracle_error(xh, gq, "")
             sweep64.append(r)
         G64.close()
         del G64
@@ -914,20 +937,25 @@ def run_cavity128(args, wl):
         Go.close()
         del Go
         torch.cuda.empty_cache()
-        # the headline form with FP64 Arnoldi products K z instead of pair-of-FP32 ones
-        Gd = Stokes(n, p, precision=prec, max_order=q, max_steps=s, outer="fp64")
+        # the headline form with its Arnoldi products K z in pair-of-FP32 arithmetic (about 48
+        # significant bits) instead of FP64: time, and accuracy at 1e-8 and at equal accuracy
+        Gd = Stokes(n, p, precision=prec, max_order=q, max_steps=s, outer="pair")
         Gd.set_preconditioner(q, s)
-        forms[f"{prec}_fp64_products"] = dict(timed_solve(Gd, Gd.rhs_cavity(1.0), tol)[0],
-                                               outer="fp64")
+        fd = Gd.rhs_cavity(1.0)
+        forms[f"{prec}_pair_products"] = dict(timed_solve(Gd, fd, tol)[0], outer="pair")
+        forms[f"{prec}_pair_products_equal_accuracy"] = dict(equal_accuracy(Gd, fd, target),
+                                                              target_error=target, outer="pair")
         Gd.close()
         del Gd
         torch.cuda.empty_cache()
         f64ms, b64ms = forms["fp64"]["ms"], best64["ms"]
         forms["speedup"] = {
-            "vs_fp64_same_preconditioner": {k: f64ms / forms[k]["ms"] for k in (prec, other)},
+            "vs_fp64_same_preconditioner": {k: f64ms / forms[k]["ms"]
+                                            for k in (prec, other, f"{prec}_pair_products")},
             "vs_fp64_best": {k: b64ms / forms[k]["ms"]
                              for k in (prec, other, f"{prec}_equal_accuracy",
-                                       f"{other}_equal_accuracy")},
+                                       f"{other}_equal_accuracy", f"{prec}_pair_products",
+                                       f"{prec}_pair_products_equal_accuracy")},
             "note": "equal_accuracy: the mixed form stopped where its error against the oracle's "
                     "tight solution is no larger than the fastest FP64 solve's"}
 
@@ -935,12 +963,12 @@ def run_cavity128(args, wl):
     if rank == 0 and not args.no_cpu_baseline:
         reps = 2
         dt = oracle_iteration_sample(n, p, q, s, reps, warmup=1)
-        cpu = {"value": 1.0 / (dt / reps * g["iterations"]), "unit": "solves/s",
+        cpu = {"value": 1.0 / (dt / reps * gq["iterations"]), "unit": "solves/s",
                "cores": cpu_threads(), "kind": "oracle",
                "sample": f"{reps} oracle MINRES iterations' operator work on the {n}^3 p={p} "
                          f"cavity (each one application of the order-{q}, {s}-step "
                          f"preconditioner and one K apply, {1e3 * dt / reps:.0f} ms) after one "
-                         f"untimed, scaled to the oracle's {g['iterations']} iterations"}
+                         f"untimed, scaled to the oracle's {gq['iterations']} iterations"}
 
     extras = {}
     if ws == 1 and not args.no_extras:
@@ -953,7 +981,7 @@ def run_cavity128(args, wl):
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": f"{prec}+f32x2+f64", "data": "synthetic",
+            "dtype": f"{prec}+f64", "data": "synthetic",
             "config": workload_config(args, wl),
             "unknowns": G.size,
             "headline": head,
@@ -995,7 +1023,7 @@ def main():
     ap.add_argument("--solve", action="store_true",
                     help="solve probe for ncu: only the workload's first solve, --steps times "
                          "between cudaProfilerStart/Stop; prints the time per solve")
-    ap.add_argument("--outer", default="pair", choices=["pair", "fp64"],
+    ap.add_argument("--outer", default="fp64", choices=["fp64", "pair"],
                     help="solve probe: arithmetic of the Arnoldi products K z (reduced-precision "
                          "preconditioner)")
     ap.add_argument("--tuning", default="auto",

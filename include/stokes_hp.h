@@ -54,7 +54,7 @@ enum { STOKES_PREC_FP64 = 0, STOKES_PREC_FP32 = 1, STOKES_PREC_TF32 = 2, STOKES_
 enum { STOKES_SOLVER_MINRES = 0, STOKES_SOLVER_FGMRES = 1 };
 
 enum { STOKES_FORWARD_KRONECKER = 0, STOKES_FORWARD_QUADRATURE = 1 };
-enum { STOKES_OUTER_PAIR = 0, STOKES_OUTER_FP64 = 1 };
+enum { STOKES_OUTER_FP64 = 0, STOKES_OUTER_PAIR = 1 };
 
 typedef struct stokes_opts {
   double c_pen;       /* Nitsche penalty constant C_pen (Sec. 3.2); <= 0 selects 14 */
@@ -89,12 +89,12 @@ typedef struct stokes_opts {
                          stokes_apply_A always uses the Kronecker form. */
   int outer;          /* arithmetic of the products w = K z of flexible GMRES when the
                          preconditioner runs in reduced precision (z is then its FP32 output):
-                         STOKES_OUTER_PAIR (default; every value carried as an unevaluated sum
-                         of two FP32 numbers, about 48 significant bits, w rounded to FP64; on
-                         this GPU's reduced FP64 pipe several times faster than FP64) or
-                         STOKES_OUTER_FP64. Residuals of the iterate (restarts, the final true
-                         residual), stokes_apply_K and every FP64-preconditioned solve use the
-                         FP64 operator either way. Used with the Kronecker forward operator when
+                         STOKES_OUTER_FP64 (default) or STOKES_OUTER_PAIR (every value carried as
+                         an unevaluated sum of two FP32 numbers, about 48 significant bits, w
+                         rounded to FP64; on this GPU's reduced FP64 pipe about twice as fast).
+                         Residuals of the iterate (restarts, the final true residual),
+                         stokes_apply_K and every FP64-preconditioned solve use the FP64
+                         operator either way. Used with the Kronecker forward operator when
                          n_elems + degree_p <= 256 and every band has half width <= 6; the FP64
                          operator otherwise. */
 } stokes_opts;
@@ -103,7 +103,7 @@ typedef struct stokes_ctx* stokes_t;
 
 /* Fill *o with the defaults: c_pen 14, Schur with inner updates, FP64, MINRES, max_order 3,
  * max_steps 4, maxit 2000, restart 60, stream NULL, nrhs 1, autotune on, Kronecker forward
- * operator, pair-of-FP32 Arnoldi products. */
+ * operator, FP64 Arnoldi products. */
 void stokes_default_opts(stokes_opts* o);
 
 /* Build the univariate matrices (App. B.3, T-check of Sec. 3.3), the fast-diagonalisation

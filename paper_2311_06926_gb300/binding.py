@@ -19,7 +19,7 @@ SCHUR = {"inner": 0, "none": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
 SOLVER = {"minres": 0, "fgmres": 1}
 FORWARD = {"kronecker": 0, "quadrature": 1}
-OUTER = {"pair": 0, "fp64": 1}
+OUTER = {"fp64": 0, "pair": 1}
 
 
 class StokesError(RuntimeError):
@@ -167,7 +167,7 @@ class Stokes:
 
     def __init__(self, n, p, nu=1.0, c_pen=14.0, schur="inner", precision="fp64",
                  solver=None, max_order=3, max_steps=4, maxit=2000, restart=60, device=None,
-                 nrhs=1, autotune=True, forward="kronecker", outer="pair"):
+                 nrhs=1, autotune=True, forward="kronecker", outer="fp64"):
         """nrhs > 1: the context holds nrhs right-hand sides; apply_K, apply_P,
         apply_hyperpower, solve and solve_multi then take nrhs stacked vectors of `size` entries
         each (`batch_size` in all), processed by the same launches (needs precision "tf32" or

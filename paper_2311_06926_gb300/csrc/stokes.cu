@@ -2097,7 +2097,7 @@ void stokes_default_opts(stokes_opts* o) {
   o->nrhs = 1;
   o->autotune = 1;
   o->forward = STOKES_FORWARD_KRONECKER;
-  o->outer = STOKES_OUTER_PAIR;
+  o->outer = STOKES_OUTER_FP64;
 }
 
 int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stokes_opts* opts) {

@@ -41,6 +41,11 @@ def golden():
         return json.load(fh)
 
 
+def _golden(q, s):
+    with open(os.path.join(os.path.dirname(GOLDEN), f"cavity128_p3_q{q}s{s}.json")) as fh:
+        return json.load(fh)
+
+
 def _ref_hp(base, S, x, q, s):
     if s == 0:
         return np.concatenate([base.pv0_inv(x[:S.n_vel]), base.pq0_inv(x[S.n_vel:])])
@@ -126,13 +131,15 @@ def _against_golden(x, g, prefix=""):
     return e_samp, e_norm, e_fun
 
 
-def test_fp64_minres_full_size_against_oracle(golden):
-    """128^3 FP64 MINRES, order 2, 2 steps, to 1e-8 (Table 1's criterion): the oracle's iteration
-    count, its per-iteration ratios to 1e-6 and its solution to 1e-10."""
+@pytest.mark.parametrize("q,s", [(2, 2), (3, 1)])
+def test_fp64_minres_full_size_against_oracle(q, s):
+    """128^3 FP64 MINRES to 1e-8 (Table 1's criterion) with the order-2, 2-step and the order-3,
+    1-step preconditioners: the oracle's iteration count, its per-iteration ratios to 1e-6 and its
+    solution to 1e-10."""
     from paper_2311_06926_gb300 import Stokes
-    g = golden
-    G = Stokes(N, P, max_order=2, max_steps=2)
-    G.set_preconditioner(2, 2)
+    g = _golden(q, s)
+    G = Stokes(N, P, max_order=q, max_steps=s)
+    G.set_preconditioner(q, s)
     f = G.rhs_cavity(1.0)
     x, it, rr, rc = G.solve(f, g["tol"])
     ratios = G.last_ratios()
@@ -142,7 +149,7 @@ def test_fp64_minres_full_size_against_oracle(golden):
     assert np.allclose(ratios, g["ratios"], rtol=1e-6, atol=1e-14)
     e = _against_golden(xh, g)
     ex = _against_golden(xh, g, "exact_")
-    print(f"[measured] fp64 128^3 solve vs oracle: samples {e[0]:.2e} norms {e[1]:.2e} "
+    print(f"[measured] fp64 128^3 q={q} s={s} solve vs oracle: samples {e[0]:.2e} norms {e[1]:.2e} "
           f"functionals {e[2]:.2e}; true residual {rr:.3e} (oracle {g['true_rel_res']:.3e}); "
           f"vs the tight solution {max(ex):.2e} (oracle's {g['error_vs_exact']:.2e})")
     assert max(e) < 1e-10, e

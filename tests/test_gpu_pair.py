@@ -32,7 +32,8 @@ def _f32(x):
 def test_pair_operator_against_oracle(n, p, nu):
     from paper_2311_06926_gb300 import Stokes
     S, base, Kop, F = oracle(n, p, nu)
-    G = Stokes(n, p, nu=nu, precision="tf32", max_order=2, max_steps=1, autotune=False)
+    G = Stokes(n, p, nu=nu, precision="tf32", max_order=2, max_steps=1, autotune=False,
+               outer="pair")
     xf, x = _f32(synthetic.random_vector(S.size, 700 + n))
     G.profile_begin()
     y = host(G.apply_K_f32(xf))
@@ -52,8 +53,9 @@ def test_pair_operator_items():
     from paper_2311_06926_gb300 import Stokes
     n, p, nrhs = 9, 3, 3
     S, base, Kop, F = oracle(n, p)
-    G3 = Stokes(n, p, precision="tf32", nrhs=nrhs, max_order=2, max_steps=1, autotune=False)
-    G1 = Stokes(n, p, precision="tf32", max_order=2, max_steps=1, autotune=False)
+    G3 = Stokes(n, p, precision="tf32", nrhs=nrhs, max_order=2, max_steps=1, autotune=False,
+                outer="pair")
+    G1 = Stokes(n, p, precision="tf32", max_order=2, max_steps=1, autotune=False, outer="pair")
     xs = [_f32(synthetic.random_vector(S.size, 710 + k)) for k in range(nrhs)]
     import torch
     Y3 = host(G3.apply_K_f32(torch.cat([xf for xf, _ in xs])))
@@ -71,8 +73,8 @@ def test_pair_operator_equals_fp64_option():
     from paper_2311_06926_gb300 import Stokes
     n, p = 20, 3
     S, base, Kop, F = oracle(n, p)
-    Gp = Stokes(n, p, precision="tf32", max_order=2, max_steps=1, autotune=False)
-    Gd = Stokes(n, p, precision="tf32", max_order=2, max_steps=1, autotune=False, outer="fp64")
+    Gp = Stokes(n, p, precision="tf32", max_order=2, max_steps=1, autotune=False, outer="pair")
+    Gd = Stokes(n, p, precision="tf32", max_order=2, max_steps=1, autotune=False)
     xf, x = _f32(synthetic.random_vector(S.size, 720))
     yp, yd = host(Gp.apply_K_f32(xf)), host(Gd.apply_K_f32(xf))
     Gp.close()
