@@ -124,6 +124,10 @@ struct PassArgs {
   int nb;
   int64_t bs;
   int block;   // FP64 line kernel: threads per block (<= 0: 256); chosen by the setup tuner
+  int c0_one;  // c0 == 1 (set by the launcher: the FP64 kernels test this integer instead of
+               // comparing c0 per output, an instruction of the slow FP64 pipe)
+  int chain;   // two terms with c0 == c1 == 1 (set by the launcher): the FP64 kernels run one
+               // FMA chain over both band rows
   // Horner epilogue (one hyper-power step fused into the pass that produces u = A~ t): instead
   // of writing the result v to Y, hmode 1 sets r = hx - v, acc = hx + r (first step, from
   // r = acc = hx); hmode 2 sets r = r - v, acc = acc + r. hr, hacc, hx have Y's layout.

@@ -43,19 +43,18 @@ constexpr int seg_len() { return sizeof(T) == 4 ? 32 : 1; }
 // One FMA chain per band row: the FP64 passes are bound by the FP64 pipe, where every add or
 // multiply besides the FMAs costs as much as an FMA (the pipe has the warps to hide the chain's
 // latency).
-template <int W, typename T>
-__device__ __forceinline__ T band_dot(const BandD<T>& D, int i, const T* __restrict__ X,
-                                      int64_t base, int64_t stride) {
+template <int W, typename T, typename IT>
+__device__ __forceinline__ T band_dot(const BandD<T>& D, int i, const T* __restrict__ X, IT base,
+                                      IT stride, T sum = T(0)) {
   const int s0 = __ldg(D.start + i);
-  const T* x = X + base + (int64_t)s0 * stride;
-  T sum = 0;
+  const T* x = X + (base + (IT)s0 * stride);
   if (W > 0) {
     const T* v = D.val + (int64_t)i * W;
 #pragma unroll
-    for (int w = 0; w < W; ++w) sum = fma(__ldg(v + w), __ldg(x + (int64_t)w * stride), sum);
+    for (int w = 0; w < W; ++w) sum = fma(__ldg(v + w), __ldg(x + (IT)w * stride), sum);
   } else {
     const T* v = D.val + (int64_t)i * D.width;
-    for (int w = 0; w < D.width; ++w) sum = fma(__ldg(v + w), __ldg(x + (int64_t)w * stride), sum);
+    for (int w = 0; w < D.width; ++w) sum = fma(__ldg(v + w), __ldg(x + (IT)w * stride), sum);
   }
   return sum;
 }
@@ -64,45 +63,60 @@ __device__ __forceinline__ T band_dot(const BandD<T>& D, int i, const T* __restr
 // reads a contiguous stretch of the input and writes a contiguous stretch of the output; the band
 // coefficients of the job are staged in shared memory transposed ([term][w][row]) so that lanes
 // with consecutive rows read consecutive words.
-template <typename T, int W>
-__device__ __forceinline__ void band_pass_flat_x1(const PassArgs<T>& a, int64_t t, T* csh) {
+// IT: index type of the thread's (line, row) arithmetic: int when every job's outputs (all items)
+// and tensors fit below 2^31, so that no 64-bit division runs (on this part 64-bit integer
+// division issues FP64-pipe instructions, the pipe these FP64 passes are bound by); int64_t
+// otherwise. Item offsets k * bs are always 64-bit.
+template <typename T, int W, typename IT>
+__device__ __forceinline__ void band_pass_flat_x1(const PassArgs<T>& a, IT t, T* csh) {
   const int m = a.D0.rows;
   const Dims out = a.in.with(1, m);
   const int nb = a.nb > 1 ? a.nb : 1;
-  if (t >= out.size() * nb) return;
-  const int64_t lines = out.size() / m;
-  int64_t line = t / m;
+  const IT per = (IT)out.size();
+  if (t >= per * nb) return;
+  const IT lines = per / m;
+  IT line = t / m;
   const int i = (int)(t - line * m);
-  const int64_t kb = nb > 1 ? (line / lines) * a.bs : 0;   // item offset
-  if (nb > 1) line %= lines;
+  int64_t kb = 0;   // item offset
+  if (nb > 1) {
+    const IT k = line / lines;
+    kb = (int64_t)k * a.bs;
+    line -= k * lines;
+  }
   const T* cs = csh + i;
-  const int64_t base_in = kb + (int64_t)a.in.n1 * line;
+  const int64_t base_in = kb + (int64_t)((IT)a.in.n1 * line);
   const T* x0 = a.X0 + base_in + __ldg(a.D0.start + i);
   T acc = 0;
 #pragma unroll
   for (int w = 0; w < W; ++w) acc = fma(cs[w * m], __ldg(x0 + w), acc);
-  if (a.c0 != T(1)) acc *= a.c0;   // (a product with 1 is exact: skipped)
-  if (a.nterms > 1) {
+  if (a.chain) {
     const T* x1 = a.X1 + base_in + __ldg(a.D1.start + i);
-    T u = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) u = fma(cs[(W + w) * m], __ldg(x1 + w), u);
-    acc = fma(a.c1, u, acc);
+    for (int w = 0; w < W; ++w) acc = fma(cs[(W + w) * m], __ldg(x1 + w), acc);
+  } else {
+    if (!a.c0_one) acc *= a.c0;   // (a product with 1 is exact: skipped)
+    if (a.nterms > 1) {
+      const T* x1 = a.X1 + base_in + __ldg(a.D1.start + i);
+      T u = 0;
+#pragma unroll
+      for (int w = 0; w < W; ++w) u = fma(cs[(W + w) * m], __ldg(x1 + w), u);
+      acc = fma(a.c1, u, acc);
+    }
   }
-  const int64_t o = kb + (int64_t)m * line + i;
+  const int64_t o = kb + (int64_t)((IT)m * line + i);
   if (a.Z) acc += a.cz * a.Z[o];
   if (a.g) {
     // g has extents b^3; along x1 the output's own index is i, the line is (i2, i3)
     const Dims gd = a.gdims;
-    const int64_t i3 = line / out.n2, i2 = line - i3 * out.n2;
-    const int64_t gi = kb + i + (int64_t)gd.n1 * (i2 + (int64_t)gd.n2 * i3);
+    const IT i3 = line / out.n2, i2 = line - i3 * out.n2;
+    const int64_t gi = kb + (int64_t)(i + (IT)gd.n1 * (i2 + (IT)gd.n2 * i3));
     const int64_t gstep = a.gaxis == 1 ? 1 : (a.gaxis == 2 ? (int64_t)gd.n1 : (int64_t)gd.n1 * gd.n2);
     acc += a.g[gi] - a.g[gi + gstep];
   }
   pass_store(a, o, acc);
 }
 
-template <typename T, int W>
+template <typename T, int W, typename IT>
 __global__ void __launch_bounds__(512) k_band_pass(const __grid_constant__ PassBatch<T> pb) {
   pdl_begin();
   int jb = 0;
@@ -121,8 +135,8 @@ __global__ void __launch_bounds__(512) k_band_pass(const __grid_constant__ PassB
         csh[idx] = (tt == 0 ? a.D0 : a.D1).val[(int64_t)i * W + w];
       }
       __syncthreads();
-      band_pass_flat_x1<T, W>(a, (int64_t)(blockIdx.x - pb.first_block[jb]) * blockDim.x + threadIdx.x,
-                              csh);
+      band_pass_flat_x1<T, W, IT>(a, (IT)(blockIdx.x - pb.first_block[jb]) * (IT)blockDim.x +
+                                         (IT)threadIdx.x, csh);
       return;
     }
   }
@@ -130,71 +144,84 @@ __global__ void __launch_bounds__(512) k_band_pass(const __grid_constant__ PassB
   const int m = a.D0.rows;
   const int seg_n = pb.seg;
   const int nseg = (m + seg_n - 1) / seg_n;
-  const int64_t lines1 = out.size() / m;              // lines of one item
+  const IT lines1 = (IT)(out.size() / m);              // lines of one item
   const int nb = a.nb > 1 ? a.nb : 1;
-  const int64_t lines = lines1 * nb;
-  const int64_t t = (int64_t)(blockIdx.x - pb.first_block[jb]) * blockDim.x + threadIdx.x;
-  // t = line + lines_rounded * seg with lines rounded to a warp multiple (warps share seg)
-  const int64_t lines_r = (lines + 31) / 32 * 32;
-  int64_t line = t % lines_r;
-  const int seg = (int)(t / lines_r);
+  const IT lines = lines1 * nb;
+  const IT t = (IT)(blockIdx.x - pb.first_block[jb]) * (IT)blockDim.x + (IT)threadIdx.x;
+  // t = line + lines_r * seg with lines rounded to a warp multiple (warps share seg)
+  const IT lines_r = (lines + 31) / 32 * 32;
+  const IT sq = t / lines_r;
+  IT line = t - sq * lines_r;
+  const int seg = (int)sq;
   if (line >= lines || seg >= nseg) return;
-  const int64_t kb = nb > 1 ? (line / lines1) * a.bs : 0;   // item offset
-  if (nb > 1) line %= lines1;
+  int64_t kb = 0;   // item offset
+  if (nb > 1) {
+    const IT k = line / lines1;
+    kb = (int64_t)k * a.bs;
+    line -= k * lines1;
+  }
   // line -> (j_a, j_b): the two non-band indices, the first one fastest
-  int64_t base_in, stride_in, base_out, stride_out;
+  IT base_in, stride_in, base_out, stride_out;
   int k1, k2;   // indices along (x1, x2, x3) of the line position, filled per axis
   if (axis == 1) {
-    const int i2 = (int)(line % out.n2), i3 = (int)(line / out.n2);
-    base_in = (int64_t)a.in.n1 * (i2 + (int64_t)a.in.n2 * i3);
+    const IT q = line / out.n2;
+    const int i2 = (int)(line - q * out.n2), i3 = (int)q;
+    base_in = (IT)a.in.n1 * (i2 + (IT)a.in.n2 * i3);
     stride_in = 1;
-    base_out = (int64_t)out.n1 * (i2 + (int64_t)out.n2 * i3);
+    base_out = (IT)out.n1 * (i2 + (IT)out.n2 * i3);
     stride_out = 1;
     k1 = i2;
     k2 = i3;
   } else if (axis == 2) {
-    const int i1 = (int)(line % out.n1), i3 = (int)(line / out.n1);
-    base_in = i1 + (int64_t)a.in.n1 * a.in.n2 * i3;
+    const IT q = line / out.n1;
+    const int i1 = (int)(line - q * out.n1), i3 = (int)q;
+    base_in = i1 + (IT)a.in.n1 * a.in.n2 * i3;
     stride_in = a.in.n1;
-    base_out = i1 + (int64_t)out.n1 * out.n2 * i3;
+    base_out = i1 + (IT)out.n1 * out.n2 * i3;
     stride_out = out.n1;
     k1 = i1;
     k2 = i3;
   } else {
-    const int i1 = (int)(line % out.n1), i2 = (int)(line / out.n1);
-    base_in = i1 + (int64_t)a.in.n1 * i2;
-    stride_in = (int64_t)a.in.n1 * a.in.n2;
-    base_out = i1 + (int64_t)out.n1 * i2;
-    stride_out = (int64_t)out.n1 * out.n2;
+    const IT q = line / out.n1;
+    const int i1 = (int)(line - q * out.n1), i2 = (int)q;
+    base_in = i1 + (IT)a.in.n1 * i2;
+    stride_in = (IT)a.in.n1 * a.in.n2;
+    base_out = i1 + (IT)out.n1 * i2;
+    stride_out = (IT)out.n1 * out.n2;
     k1 = i1;
     k2 = i2;
   }
-  base_in += kb;
-  base_out += kb;
-  int64_t gbase = 0, gstride = 0, gstep = 0;
+  const T* X0 = a.X0 + kb;
+  const T* X1 = a.nterms > 1 ? a.X1 + kb : nullptr;
+  IT gbase = 0, gstride = 0, gstep = 0;
   if (a.g) {
     // g has extents b^3 (gdims); the output's own index along gaxis is the band index when
     // gaxis == axis, otherwise one of (k1, k2)
     const Dims gd = a.gdims;
-    const int64_t gs[3] = {1, (int64_t)gd.n1, (int64_t)gd.n1 * gd.n2};
-    int idx[3];
-    if (axis == 1) { idx[0] = 0; idx[1] = k1; idx[2] = k2; }
-    else if (axis == 2) { idx[0] = k1; idx[1] = 0; idx[2] = k2; }
-    else { idx[0] = k1; idx[1] = k2; idx[2] = 0; }
-    gbase = kb + idx[0] * gs[0] + idx[1] * gs[1] + idx[2] * gs[2];
-    gstride = gs[axis - 1];     // moving along the band direction
-    gstep = gs[a.gaxis - 1];    // the difference direction
+    const IT g2 = gd.n1, g3 = (IT)gd.n1 * gd.n2;
+    int j1, j2, j3;
+    if (axis == 1) { j1 = 0; j2 = k1; j3 = k2; }
+    else if (axis == 2) { j1 = k1; j2 = 0; j3 = k2; }
+    else { j1 = k1; j2 = k2; j3 = 0; }
+    gbase = j1 + g2 * j2 + g3 * j3;
+    gstride = axis == 1 ? 1 : (axis == 2 ? g2 : g3);     // moving along the band direction
+    gstep = a.gaxis == 1 ? 1 : (a.gaxis == 2 ? g2 : g3); // the difference direction
   }
+  const T* g = a.g ? a.g + kb : nullptr;
   const int i_end = min(m, (seg + 1) * seg_n);
   for (int i = seg * seg_n; i < i_end; ++i) {
-    T acc = band_dot<W>(a.D0, i, a.X0, base_in, stride_in);
-    if (a.c0 != T(1)) acc *= a.c0;   // (a product with 1 is exact: skipped)
-    if (a.nterms > 1) acc = fma(a.c1, band_dot<W>(a.D1, i, a.X1, base_in, stride_in), acc);
-    const int64_t o = base_out + (int64_t)i * stride_out;
+    T acc = band_dot<W>(a.D0, i, X0, base_in, stride_in);
+    if (a.chain) {
+      acc = band_dot<W>(a.D1, i, X1, base_in, stride_in, acc);
+    } else {
+      if (!a.c0_one) acc *= a.c0;   // (a product with 1 is exact: skipped)
+      if (a.nterms > 1) acc = fma(a.c1, band_dot<W>(a.D1, i, X1, base_in, stride_in), acc);
+    }
+    const int64_t o = kb + (int64_t)(base_out + (IT)i * stride_out);
     if (a.Z) acc += a.cz * a.Z[o];
-    if (a.g) {
-      const int64_t gi = gbase + (int64_t)i * gstride;
-      acc += a.g[gi] - a.g[gi + gstep];
+    if (g) {
+      const IT gi = gbase + (IT)i * gstride;
+      acc += g[gi] - g[gi + gstep];
     }
     pass_store(a, o, acc);
   }
@@ -728,17 +755,18 @@ __global__ void __launch_bounds__(kCholLines) k_chol_line(double* __restrict__ x
   pdl_begin();
   extern __shared__ double cs[];
   constexpr int P = kCholLines + 1;
-  const int64_t lines = (int64_t)b * b;
-  const int64_t line0 = (int64_t)blockIdx.x * kCholLines;
-  const int nl = (int)(lines - line0 < kCholLines ? lines - line0 : kCholLines);
+  const int lines = b * b;   // b <= 4096: fewer than 2^31 lines (32-bit division below)
+  const int line0 = blockIdx.x * kCholLines;
+  const int nl = lines - line0 < kCholLines ? lines - line0 : kCholLines;
   const int l = threadIdx.x;
   int64_t base = 0, stride = 0;
-  const int64_t line = line0 + l;
+  const int line = line0 + l;
   if (axis == 1) {
     base = (int64_t)b * line;
     stride = 1;
   } else if (axis == 2) {
-    base = (line % b) + (int64_t)b * b * (line / b);
+    const int q = line / b;
+    base = (line - q * b) + (int64_t)b * b * q;
     stride = b;
   } else {
     base = line;
@@ -996,6 +1024,8 @@ void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s) {
   for (int j = 0; j < njobs; ++j) {
     const PassArgs<T>& a = jobs[j];
     pb.job[j] = a;
+    pb.job[j].c0_one = a.c0 == T(1) ? 1 : 0;
+    pb.job[j].chain = (a.nterms > 1 && a.c0 == T(1) && a.c1 == T(1)) ? 1 : 0;
     pb.first_block[j] = blocks;
     const Dims out = a.in.with(a.axis, a.D0.rows);
     const int nbj = a.nb > 1 ? a.nb : 1;
@@ -1015,20 +1045,36 @@ void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s) {
   }
   pb.first_block[njobs] = blocks;
   pb.seg = seg_len<T>();
+  // 32-bit thread index arithmetic when every job's thread range (all items) and tensors fit
+  bool i32 = (int64_t)blocks * bt < ((int64_t)1 << 31);
+  for (int j = 0; j < njobs && i32; ++j) {
+    const PassArgs<T>& a = jobs[j];
+    const int64_t big = std::max({a.in.size(), a.in.with(a.axis, a.D0.rows).size(),
+                                  a.g ? a.gdims.size() : (int64_t)0});
+    const int nbj = a.nb > 1 ? a.nb : 1;
+    if (big * nbj + 64 >= ((int64_t)1 << 31)) i32 = false;
+  }
   // FP64 passes (bound by the FP64 pipe) are accounted apart from the FP32 ones
   const int cls = sizeof(T) == 8 ? kClassBand64 : kClassBand;
   launch_begin(cls, s);
   switch (W) {
 #define SHP_PASS_W(w)                                                                     \
   case w: {                                                                               \
-    static std::atomic<int> attr{0};                                                      \
-    raise_smem_limit(k_band_pass<T, w>, attr, smem);                                      \
-    launch_k(k_band_pass<T, w>, blocks, bt, smem, s, pb);                                       \
+    static std::atomic<int> attr32{0}, attr64{0};                                         \
+    if (i32) {                                                                            \
+      raise_smem_limit(k_band_pass<T, w, int>, attr32, smem);                             \
+      launch_k(k_band_pass<T, w, int>, blocks, bt, smem, s, pb);                          \
+    } else {                                                                              \
+      raise_smem_limit(k_band_pass<T, w, int64_t>, attr64, smem);                         \
+      launch_k(k_band_pass<T, w, int64_t>, blocks, bt, smem, s, pb);                      \
+    }                                                                                     \
     break;                                                                                \
   }
     SHP_PASS_W(3) SHP_PASS_W(5) SHP_PASS_W(7) SHP_PASS_W(9) SHP_PASS_W(11) SHP_PASS_W(13)
 #undef SHP_PASS_W
-    default: launch_k(k_band_pass<T, 0>, blocks, bt, 0, s, pb);
+    default:
+      if (i32) launch_k(k_band_pass<T, 0, int>, blocks, bt, 0, s, pb);
+      else launch_k(k_band_pass<T, 0, int64_t>, blocks, bt, 0, s, pb);
   }
   launch_end(cls, s, flops, bytes);
 }
@@ -1096,10 +1142,18 @@ __global__ void __launch_bounds__(256) k_quad_stress(double* __restrict__ G, dou
   const int64_t n3 = (int64_t)nq * nq * nq;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n3;
        o += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t q12 = o / nq;
-    const int i1 = (int)(o - q12 * nq);
-    const int i3 = (int)(q12 / nq);
-    const int i2 = (int)(q12 - (int64_t)i3 * nq);
+    int i1, i2, i3;
+    if (n3 < ((int64_t)1 << 31)) {   // 32-bit division (64-bit division runs on the FP64 pipe)
+      const int oi = (int)o, q12 = oi / nq;
+      i1 = oi - q12 * nq;
+      i3 = q12 / nq;
+      i2 = q12 - i3 * nq;
+    } else {
+      const int64_t q12 = o / nq;
+      i1 = (int)(o - q12 * nq);
+      i3 = (int)(q12 / nq);
+      i2 = (int)(q12 - (int64_t)i3 * nq);
+    }
     const double W = w[i1] * w[i2] * w[i3];
     double g[9];
 #pragma unroll

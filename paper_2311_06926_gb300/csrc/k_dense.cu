@@ -189,6 +189,10 @@ struct RowBatch {
 // (K x lb) are loaded once, coalesced, into shared memory; Op(i, j) is read through the
 // read-only cache. Outputs of products along contiguous lines (L = 1) are staged in shared memory
 // for coalesced stores.
+// IT: index type of the line and entry arithmetic (int when every job's tensors have fewer than
+// 2^31 entries: 64-bit integer division issues FP64-pipe instructions on this part, the pipe the
+// kernel is bound by).
+template <typename IT>
 __global__ void __launch_bounds__(512) k_mode_tile(const __grid_constant__ RowBatch rb) {
   pdl_begin();
   extern __shared__ double shd[];
@@ -197,50 +201,51 @@ __global__ void __launch_bounds__(512) k_mode_tile(const __grid_constant__ RowBa
   const RowJob& J = rb.job[jb];
   const int K = J.K, m = J.m;
   const int lb = J.groups;                       // lines per block for this job
-  const int64_t lines = J.L * J.R;
-  const int64_t line0 = ((int64_t)blockIdx.x - rb.first[jb]) * lb;
+  const IT JL = (IT)J.L;
+  const IT lines = JL * (IT)J.R;
+  const IT line0 = (IT)((int64_t)blockIdx.x - rb.first[jb]) * lb;
   const int nl = (int)(lines - line0 < lb ? lines - line0 : lb);
   const int P = lb + 1;
   double* xs = shd;                 // [K][P]
   double* ys = shd + K * P;         // [m][P] (L == 1 only)
   const int tid = threadIdx.x;
   const int nth = blockDim.x;
-  if (J.L == 1) {
+  if (JL == 1) {
     for (int idx = tid; idx < K * lb; idx += nth) {
       const int l = idx / K, j = idx - l * K;
-      xs[j * P + l] = l < nl ? J.X[(int64_t)K * (line0 + l) + j] : 0.0;
+      xs[j * P + l] = l < nl ? J.X[(IT)K * (line0 + l) + j] : 0.0;
     }
   } else {
     for (int idx = tid; idx < K * lb; idx += nth) {
       const int l = idx % lb, j = idx / lb;
       double v = 0.0;
       if (l < nl) {
-        const int64_t line = line0 + l;
-        const int64_t ll = line % J.L, r = line / J.L;
-        v = J.X[ll + J.L * (j + (int64_t)K * r)];
+        const IT line = line0 + l;
+        const IT r = line / JL, ll = line - r * JL;
+        v = J.X[ll + JL * (j + (IT)K * r)];
       }
       xs[j * P + l] = v;
     }
   }
   __syncthreads();
-  auto out_index = [&](int l, int i) -> int64_t {
-    if (J.L == 1) return (int64_t)m * (line0 + l) + i;
-    const int64_t line = line0 + l;
-    const int64_t ll = line % J.L, r = line / J.L;
-    return ll + J.L * ((int64_t)i + (int64_t)m * r);
+  auto out_index = [&](int l, int i) -> IT {
+    if (JL == 1) return (IT)m * (line0 + l) + i;
+    const IT line = line0 + l;
+    const IT r = line / JL, ll = line - r * JL;
+    return ll + JL * ((IT)i + (IT)m * r);
   };
   auto emit = [&](int l, int i, double v) {
-    const int64_t o = out_index(l, i);
+    const IT o = out_index(l, i);
     if (J.invd) {
       v *= J.invd[o];
     } else if (J.lam1) {
-      const int i1 = (int)(o % J.out.n1);
-      const int64_t t2 = o / J.out.n1;
-      v /= J.scale * (J.lam1[i1] + J.lam2[(int)(t2 % J.out.n2)] + J.lam3[(int)(t2 / J.out.n2)]);
+      const IT t2 = o / J.out.n1, t3 = t2 / J.out.n2;
+      const int i1 = (int)(o - t2 * J.out.n1), i2 = (int)(t2 - t3 * J.out.n2);
+      v /= J.scale * (J.lam1[i1] + J.lam2[i2] + J.lam3[(int)t3]);
     } else {
       v *= J.post;
     }
-    if (J.L == 1) ys[i * P + l] = v;
+    if (JL == 1) ys[i * P + l] = v;
     else J.Y[o] = v;
   };
   if (J.eo == 0) {
@@ -300,11 +305,11 @@ __global__ void __launch_bounds__(512) k_mode_tile(const __grid_constant__ RowBa
       }
     }
   }
-  if (J.L == 1) {
+  if (JL == 1) {
     __syncthreads();
     for (int idx = tid; idx < m * nl; idx += nth) {
       const int lo = idx / m, io = idx - lo * m;
-      J.Y[(int64_t)m * (line0 + lo) + io] = ys[io * P + lo];
+      J.Y[(IT)m * (line0 + lo) + io] = ys[io * P + lo];
     }
   }
 }
@@ -632,11 +637,20 @@ cudaError_t mode_product_multi<double>(const ModeArgs<double>* jobs, int njobs, 
   }
   first_block[njobs] = blocks;
   for (int j = 0; j <= njobs; ++j) rb.first[j] = first_block[j];
-  static std::atomic<int> attr{0};
-  const cudaError_t e = raise_smem_limit(k_mode_tile, attr, smem);
+  // 32-bit entry arithmetic when every tensor of the launch has fewer than 2^31 entries
+  bool i32 = true;
+  for (int j = 0; j < njobs; ++j) {
+    const ModeArgs<double>& m = jobs[j];
+    if (std::max(m.in.size(), m.in.with(m.axis, m.m).size()) + 1024 >= ((int64_t)1 << 31))
+      i32 = false;
+  }
+  static std::atomic<int> attr32{0}, attr64{0};
+  const cudaError_t e = i32 ? raise_smem_limit(k_mode_tile<int>, attr32, smem)
+                            : raise_smem_limit(k_mode_tile<int64_t>, attr64, smem);
   if (e != cudaSuccess) return e;
   launch_begin(kClassMode, s);
-  const cudaError_t l = launch_k(k_mode_tile, blocks, threads, smem, s, rb);
+  const cudaError_t l = i32 ? launch_k(k_mode_tile<int>, blocks, threads, smem, s, rb)
+                            : launch_k(k_mode_tile<int64_t>, blocks, threads, smem, s, rb);
   launch_end(kClassMode, s, flops, bytes);
   return l;
 }

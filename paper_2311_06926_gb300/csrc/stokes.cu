@@ -74,6 +74,13 @@ struct Arena {
 
 // The same banded matrix stored with a larger band width (zeros in the added slots); rows = 0 when
 // the matrix has fewer columns than the width.
+// s B (entrywise, FP64)
+Band scaled(const Band& B, double sc) {
+  Band S = B;
+  for (double& v : S.val) v *= sc;
+  return S;
+}
+
 Band widen(const Band& B, int width) {
   Band W;
   if (width <= B.width || B.cols < width) return W;
@@ -190,6 +197,10 @@ struct Ops {
   int64_t nvc = 0, nvel = 0, npres = 0;
   BandD<T> M{}, K{}, Mc{}, Tc{};
   BandD<T> Mc_w{};   // M-check padded with zeros to the band width of K and M (val null: none)
+  // FP64: nu M-check and 2 nu T-check, so that the two terms of a velocity pass form one FMA
+  // chain with unit coefficients (each product by nu, 2 nu is one FP64 instruction fewer per
+  // output on the FP64-bound passes)
+  BandD<T> Mc_nu{}, Tc_2nu{};
   const T *U_N = nullptr, *lam_N = nullptr, *U_T = nullptr, *lam_T = nullptr;
   const T* invd = nullptr;   // FP64: 1 / (2 nu (l1 + l2 + l3)) per velocity entry
   int eo_N = 0, eo_T = 0;    // FP64: even-mode counts of the parity-split eigenvectors
@@ -287,9 +298,11 @@ struct Ops {
       j[6 + k] = x1_done ? job(qx[k], Mc_w, 1, nullptr, nullptr, 0, dq, 2, f2 + k * npres)
                          : job(qx[k], Mc_w, 1, nullptr, nullptr, 0, dq, 1, f1 + k * npres);
     band_pass_multi<T>(j, 6 + nq, s);
+    const bool chain = Mc_nu.val != nullptr;   // FP64: one FMA chain over both terms
     for (int c = 0; c < 3; ++c) {
       const int64_t o = c * nvc;
-      j[2 * c] = job(tK + o, Mc, nu, tM + o, &Tc, nu2, comp(c), first_other(c), tS + o);
+      j[2 * c] = chain ? job(tK + o, Mc_nu, 1, tM + o, &Tc_2nu, 1, comp(c), first_other(c), tS + o)
+                       : job(tK + o, Mc, nu, tM + o, &Tc, nu2, comp(c), first_other(c), tS + o);
       j[2 * c + 1] = job(tM + o, Mc, 1, nullptr, nullptr, 0, comp(c), first_other(c), tR + o);
     }
     for (int k = 0; k < nq; ++k)
@@ -304,8 +317,10 @@ struct Ops {
     }
     for (int c = 0; c < 3; ++c) {
       const int64_t o = c * nvc;
-      j[c] = job(tS + o, Mc, 1, tR + o, &Tc, nu2, comp(c), second_other(c), y + o, nullptr, 0, g,
-                 own_axis(c));
+      j[c] = chain ? job(tS + o, Mc, 1, tR + o, &Tc_2nu, 1, comp(c), second_other(c), y + o,
+                         nullptr, 0, g, own_axis(c))
+                   : job(tS + o, Mc, 1, tR + o, &Tc, nu2, comp(c), second_other(c), y + o,
+                         nullptr, 0, g, own_axis(c));
       horner(j[c], h, o);
     }
     band_pass_multi<T>(j, 3, s);
@@ -1076,6 +1091,10 @@ void init_ops(stokes_ctx* c, Ops<T>& o, const Band& M, const Band& K, const Band
   o.K = upload_band<T>(ar, K, s);
   o.Mc = upload_band<T>(ar, Mc, s);
   o.Tc = upload_band<T>(ar, Tc, s);
+  if (std::is_same<T, double>::value) {
+    o.Mc_nu = upload_band<T>(ar, scaled(Mc, c->nu), s);
+    o.Tc_2nu = upload_band<T>(ar, scaled(Tc, 2.0 * c->nu), s);
+  }
   {
     const Band Mcw = widen(Mc, K.width);
     if (Mcw.rows > 0 && o.K.cval && o.M.cval && o.K.half == o.M.half && 2 * o.K.half + 1 == K.width)
