@@ -297,11 +297,12 @@ void multi_dot(const double* V, int64_t ldv, int nvec, const double* w, int64_t 
 // sweep over the vectors; deterministic; partials: (2 nvec + 1) * kMultiDotBlocks
 void multi_dot2(const double* V, int64_t ldv, int nvec, const double* w, const double* z,
                 int64_t n, double* partials, double* out, cudaStream_t s);
-// w += sign * sum_k h[k] V_k (h in device memory)
+// w += sign * sum_k h[k] V_k (h in device memory; one FMA chain per element from w, in the
+// order of k, with the coefficients sign h[k])
 void multi_axpy(const double* V, int64_t ldv, int nvec, const double* h, double sign, double* w,
                 int64_t n, cudaStream_t s);
-// out = (w + sign * sum_k h[k] V_k) * (1 / *div), in that order of operations (the same bits as
-// multi_axpy followed by scale_inv_dev); out may be w
+// out = (w + sign * sum_k h[k] V_k) * (1 / *div): the chain of multi_axpy, then the product
+// (the same bits as multi_axpy followed by scale_inv_dev); out may be w
 void multi_axpy_div(const double* V, int64_t ldv, int nvec, const double* h, double sign,
                     const double* w, const double* div, double* out, int64_t n, cudaStream_t s);
 // y = x * (1 / *alpha)

@@ -354,36 +354,46 @@ __global__ void __launch_bounds__(kThreads) k_multi_dot_final(const double* __re
   if (threadIdx.x == 0) out[blockIdx.x] = tot;
 }
 
-// w += sign * sum_k h[k] V_k: coefficients staged in shared memory, four independent partial
-// sums per element so the loads of several vectors are in flight together.
+// w += sign * sum_k h[k] V_k: coefficients (times sign) staged in shared memory, one FMA chain
+// per element starting from w, two elements per thread and step.
 constexpr int kAxpyMaxVec = 512;   // restart <= 400 (checked at setup)
 
-// out = (w + sign * sum_k h[k] V_k) / *div (div may be null: no division; out may be w).
+// out = (w + sum_k (sign h[k]) V_k) * (1 / *div), the sum one FMA chain from w in the order of k
+// (div may be null: no scaling; out may be w).
 __global__ void __launch_bounds__(kThreads) k_multi_axpy(const double* __restrict__ V, int64_t ldv,
                                                          int nvec, const double* __restrict__ h,
                                                          double sign, const double* w,
                                                          double* out, const double* div,
                                                          int64_t n) {
   pdl_begin();
+  // sign h_k (an exact sign change) and 1 / div once per block: every FP64 instruction counts on
+  // this part's FP64 pipe, so each element costs nvec FMAs (and one multiply when scaled)
   __shared__ double hs[kAxpyMaxVec];
-  for (int k = threadIdx.x; k < nvec; k += kThreads) hs[k] = h[k];
-  __syncthreads();
+  __shared__ double inv;
+  for (int k = threadIdx.x; k < nvec; k += kThreads) hs[k] = sign < 0 ? -h[k] : h[k];
   const bool scaled = div != nullptr;
-  const double a = scaled ? 1.0 / (*div) : 1.0;
-  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * kThreads) {
-    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  if (threadIdx.x == 0) inv = scaled ? 1.0 / (*div) : 1.0;
+  __syncthreads();
+  const double a = inv;
+  // two elements per thread and step: two independent FMA chains
+  const int64_t step = (int64_t)gridDim.x * kThreads;
+  int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+  for (; i + step < n; i += 2 * step) {
     const double* v = V + i;
-    int k = 0;
-    for (; k + 4 <= nvec; k += 4) {
-      s0 = fma(hs[k], v[k * ldv], s0);
-      s1 = fma(hs[k + 1], v[(k + 1) * ldv], s1);
-      s2 = fma(hs[k + 2], v[(k + 2) * ldv], s2);
-      s3 = fma(hs[k + 3], v[(k + 3) * ldv], s3);
+    double r0 = w[i], r1 = w[i + step];
+    for (int k = 0; k < nvec; ++k) {
+      const double hk = hs[k];
+      r0 = fma(hk, v[k * ldv], r0);
+      r1 = fma(hk, v[k * ldv + step], r1);
     }
-    for (; k < nvec; ++k) s0 = fma(hs[k], v[k * ldv], s0);
-    const double r = w[i] + sign * ((s0 + s1) + (s2 + s3));
-    out[i] = scaled ? a * r : r;
+    out[i] = scaled ? a * r0 : r0;
+    out[i + step] = scaled ? a * r1 : r1;
+  }
+  if (i < n) {
+    const double* v = V + i;
+    double r0 = w[i];
+    for (int k = 0; k < nvec; ++k) r0 = fma(hs[k], v[k * ldv], r0);
+    out[i] = scaled ? a * r0 : r0;
   }
 }
 
