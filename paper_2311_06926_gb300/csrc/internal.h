@@ -254,11 +254,14 @@ template <typename T>
 void div_band_x1(const T* u1, const T* u2, const T* u3, int a, int b, const T* q, T nu,
                  const BandD<T>& D, T* y0, T* y1, cudaStream_t s);
 
-// In-place banded Cholesky solves along one direction of a (b, b, b) tensor: x <- post (L L^T)^-1 x
-// with L lower triangular of bandwidth p stored as rows lb[i * (p + 1) + (k - i + p)] for
-// k in [i - p, i], and inv_diag[i] = 1 / L[i][i] (pressure mass inverse, FP64 path).
-void chol_solve_axis(double* x, int b, int p, int axis, const double* lb, const double* inv_diag,
-                     double post, cudaStream_t s);
+// Banded Cholesky solves along one direction of a (b, b, b) tensor: y <- post (L L^T)^-1 x (y may
+// be x) with L lower triangular of bandwidth p stored as rows lb[i * (p + 1) + (k - i + p)] for
+// k in [i - p, i], and inv_diag[i] = 1 / L[i][i] (pressure mass inverse). nb items, item k of x and
+// y at k * bs entries. Returns the launch status.
+template <typename T>
+cudaError_t chol_solve_axis(const T* x, T* y, int b, int p, int axis, const T* lb,
+                            const T* inv_diag, T post, cudaStream_t s, int nb = 1,
+                            int64_t bs = 0);
 
 // ---- vector kernels (k_vec.cu) -----------------------------------------------------------
 // Deterministic dot product: fixed grid, fixed-order tree reduction. Result written to *out

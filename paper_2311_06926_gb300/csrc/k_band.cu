@@ -744,84 +744,135 @@ __global__ void __launch_bounds__(256) k_div_transpose(const T* __restrict__ g, 
 
 // One thread per line: the block's lines are first copied into shared memory (coalesced), then
 // each thread runs forward substitution with L and backward substitution with L^T on its own
-// column of shared memory, and the block writes the lines back.
+// column of shared memory, and the block writes the lines to y (which may be x). nb items, item k
+// of x and y at k * bs entries; 32-bit line arithmetic (b^2 nb < 2^31, checked by the launcher).
 constexpr int kCholLines = 32;
 
-__global__ void __launch_bounds__(kCholLines) k_chol_line(double* __restrict__ x, int b, int p,
-                                                          int axis,
-                                                          const double* __restrict__ lb,
-                                                          const double* __restrict__ inv,
-                                                          double post) {
+template <typename T>
+__global__ void __launch_bounds__(kCholLines) k_chol_line(const T* x, T* y, int b, int p, int axis,
+                                                          const T* __restrict__ lb,
+                                                          const T* __restrict__ inv, T post,
+                                                          int nb, int64_t bs) {
   pdl_begin();
-  extern __shared__ double cs[];
+  extern __shared__ __align__(16) unsigned char chol_smem[];
   constexpr int P = kCholLines + 1;
-  const int lines = b * b;   // b <= 4096: fewer than 2^31 lines (32-bit division below)
+  const int w = p + 1;
+  // the factor in shared memory: one warp per block and few blocks per SM, so each step of the
+  // substitutions must not wait on a global load
+  T* lbs = reinterpret_cast<T*>(chol_smem);   // [b][p + 1]
+  T* invs = lbs + b * w;                      // [b]
+  T* cs = invs + b;                           // [b][P] the block's lines
+  for (int i = threadIdx.x; i < b * w; i += kCholLines) lbs[i] = lb[i];
+  for (int i = threadIdx.x; i < b; i += kCholLines) invs[i] = inv[i];
+  const int lines1 = b * b;
+  const int lines = lines1 * nb;
   const int line0 = blockIdx.x * kCholLines;
   const int nl = lines - line0 < kCholLines ? lines - line0 : kCholLines;
   const int l = threadIdx.x;
+  // offset of a line (over all items) and the stride along it
+  auto line_off = [&](int line, int64_t* stride) -> int64_t {
+    const int k = line / lines1, li = line - k * lines1;
+    int64_t base;
+    if (axis == 1) {
+      base = (int64_t)b * li;
+      *stride = 1;
+    } else if (axis == 2) {
+      const int q = li / b;
+      base = (li - q * b) + (int64_t)b * b * q;
+      *stride = b;
+    } else {
+      base = li;
+      *stride = (int64_t)b * b;
+    }
+    return (int64_t)k * bs + base;
+  };
   int64_t base = 0, stride = 0;
-  const int line = line0 + l;
+  if (l < nl) base = line_off(line0 + l, &stride);
+  // staging: batches of kCholBatch independent loads in flight before their shared stores (one
+  // warp per block: a load-store loop would wait a full memory latency per element)
+  constexpr int kCholBatch = 16;
   if (axis == 1) {
-    base = (int64_t)b * line;
-    stride = 1;
-  } else if (axis == 2) {
-    const int q = line / b;
-    base = (line - q * b) + (int64_t)b * b * q;
-    stride = b;
-  } else {
-    base = line;
-    stride = (int64_t)b * b;
-  }
-  if (axis == 1) {
-    // rows of x1: lanes along the row
-    for (int r = 0; r < nl; ++r) {
-      const double* row = x + (int64_t)b * (line0 + r);
-      for (int j = l; j < b; j += kCholLines) cs[j * P + r] = row[j];
+    // rows of x1 (contiguous): the warp walks the block's rows, lanes along each row
+    const int total = nl * b;
+    for (int q0 = 0; q0 < total; q0 += kCholBatch * kCholLines) {
+      T t[kCholBatch];
+#pragma unroll
+      for (int u = 0; u < kCholBatch; ++u) {
+        const int q = q0 + u * kCholLines + l;
+        if (q < total) {
+          const int r = q / b, j = q - r * b;
+          int64_t st;
+          t[u] = x[line_off(line0 + r, &st) + j];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kCholBatch; ++u) {
+        const int q = q0 + u * kCholLines + l;
+        if (q < total) {
+          const int r = q / b, j = q - r * b;
+          cs[j * P + r] = t[u];
+        }
+      }
     }
   } else if (l < nl) {
-    for (int j = 0; j < b; ++j) cs[j * P + l] = x[base + stride * j];
+    for (int j0 = 0; j0 < b; j0 += kCholBatch) {
+      T t[kCholBatch];
+#pragma unroll
+      for (int u = 0; u < kCholBatch; ++u)
+        if (j0 + u < b) t[u] = x[base + stride * (j0 + u)];
+#pragma unroll
+      for (int u = 0; u < kCholBatch; ++u)
+        if (j0 + u < b) cs[(j0 + u) * P + l] = t[u];
+    }
   }
   __syncthreads();
   if (l < nl) {
-    double* v = cs + l;
-    const int w = p + 1;
+    T* v = cs + l;
     for (int i = 0; i < b; ++i) {
-      double acc = v[i * P];
+      T acc = v[i * P];
       const int k0 = i - p < 0 ? 0 : i - p;
-      for (int k = k0; k < i; ++k) acc = fma(-lb[i * w + (k - i + p)], v[k * P], acc);
-      v[i * P] = acc * inv[i];
+      for (int k = k0; k < i; ++k) acc = fma(-lbs[i * w + (k - i + p)], v[k * P], acc);
+      v[i * P] = acc * invs[i];
     }
     for (int i = b - 1; i >= 0; --i) {
-      double acc = v[i * P];
+      T acc = v[i * P];
       const int k1 = i + p > b - 1 ? b - 1 : i + p;
-      for (int k = i + 1; k <= k1; ++k) acc = fma(-lb[k * w + (i - k + p)], v[k * P], acc);
-      v[i * P] = acc * inv[i];
+      for (int k = i + 1; k <= k1; ++k) acc = fma(-lbs[k * w + (i - k + p)], v[k * P], acc);
+      v[i * P] = acc * invs[i];
     }
   }
   __syncthreads();
   if (axis == 1) {
     for (int r = 0; r < nl; ++r) {
-      double* row = x + (int64_t)b * (line0 + r);
+      int64_t st;
+      T* row = y + line_off(line0 + r, &st);
       for (int j = l; j < b; j += kCholLines) row[j] = cs[j * P + r] * post;
     }
   } else if (l < nl) {
-    for (int j = 0; j < b; ++j) x[base + stride * j] = cs[j * P + l] * post;
+    for (int j = 0; j < b; ++j) y[base + stride * j] = cs[j * P + l] * post;
   }
 }
 
 }  // namespace
 
-void chol_solve_axis(double* x, int b, int p, int axis, const double* lb, const double* inv_diag,
-                     double post, cudaStream_t s) {
-  const int64_t lines = (int64_t)b * b;
-  const int smem = b * (kCholLines + 1) * (int)sizeof(double);
+template <typename T>
+cudaError_t chol_solve_axis(const T* x, T* y, int b, int p, int axis, const T* lb,
+                            const T* inv_diag, T post, cudaStream_t s, int nb, int64_t bs) {
+  if (nb < 1) nb = 1;
+  const int64_t lines = (int64_t)b * b * nb;
+  if (lines >= ((int64_t)1 << 31) - kCholLines) return cudaErrorInvalidValue;
+  const int smem = (b * (kCholLines + 1) + b * (p + 1) + b) * (int)sizeof(T);
   static std::atomic<int> attr{0};
-  raise_smem_limit(k_chol_line, attr, smem);
+  const cudaError_t e = raise_smem_limit(k_chol_line<T>, attr, smem);
+  if (e != cudaSuccess) return e;
   launch_begin(kClassLine, s);
-  launch_k(k_chol_line, (unsigned)((lines + kCholLines - 1) / kCholLines), kCholLines, smem, s, 
-      x, b, p, axis, lb, inv_diag, post);
-  launch_end(kClassLine, s, 4.0 * (p + 1) * lines * b, 2.0 * lines * b * sizeof(double));
+  const cudaError_t l = launch_k(k_chol_line<T>, (unsigned)((lines + kCholLines - 1) / kCholLines),
+                                 kCholLines, smem, s, x, y, b, p, axis, lb, inv_diag, post, nb, bs);
+  launch_end(kClassLine, s, 4.0 * (p + 1) * lines * b, 2.0 * lines * b * sizeof(T));
+  return l;
 }
+template cudaError_t chol_solve_axis<double>(const double*, double*, int, int, int, const double*,
+                                             const double*, double, cudaStream_t, int, int64_t);
 
 void band_tile_multi(const PassArgs<float>* jobs, int njobs, cudaStream_t s) {
   // FP32 passes write Y, then the vector kernel applies a Horner step (in FP32 the separate

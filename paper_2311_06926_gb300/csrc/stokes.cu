@@ -206,8 +206,8 @@ struct Ops {
   int eo_N = 0, eo_T = 0;    // FP64: even-mode counts of the parity-split eigenvectors
   int fd_fused = 0;          // FP64: fast diagonalisation by the fused plane / x3-line kernels,
                              // with this many blocks per plane (0: six single-direction passes)
-  const double* chol_lb = nullptr;     // FP64 pressure block: banded Cholesky factor of M-check
-  const double* chol_inv = nullptr;
+  const T* chol_lb = nullptr;          // pressure block: banded Cholesky factor of M-check
+  const T* chol_inv = nullptr;
   int chol_p = 0;
   T *tK = nullptr, *tM = nullptr, *tS = nullptr, *tR = nullptr;   // component-size temporaries
   T *f1 = nullptr, *f2 = nullptr;                                 // mode-product ping-pong
@@ -470,12 +470,16 @@ struct Ops {
   // y_c = (U3 U2 U1) diag(1 / (2 nu (l1 + l2 + l3))) (U3 U2 U1)^T x_c, with (U, l) = (U_N, lam_N)
   // in the own direction of c and (U_T, lam_T) in the other two.
   // tensor t (0..2 velocity components, 3 pressure): canonical x -> canonical y
+  // The pressure tensor (t = 3) takes three passes with the dense inverse of M-check instead:
+  // (M-check^-1)^(x)3 is a Kronecker product of one dense matrix, so one rotation of the three
+  // directions applies it (the eigenvector route U_T U_T^T needs six).
   void tc_fd(int t, const float* x, float* y) const {
     const Dims d = t < 3 ? comp(t) : Dims{b, b, b};
     pad_rows(x, d.n1, (int64_t)d.n2 * d.n3, tc_ld0[t], tc_p0[t], tc_bf16, s, nb, bs);
-    for (int st = 0; st < 6; ++st) {
+    const int passes = t < 3 ? 6 : 3;
+    for (int st = 0; st < passes; ++st) {
       RmpPlan p = tc_plan[t * 6 + st];
-      if (st == 5) {
+      if (st == passes - 1) {
         p.args.Y = y;
         p.args.ybs = bs;
       }
@@ -579,17 +583,18 @@ struct Ops {
 
   // pressure block: y = 2 nu (M-check^-1)^(x)3 x = 2 nu (U_T U_T^T)^(x)3 x
   void minv_Q(const T* x, T* y) const {
-    // FP64: banded Cholesky line solves for large b (few FP64 flops, enough lines in parallel);
-    // for small b their sequential recurrence is latency-bound and the dense route is faster
-    if (chol_lb && b >= 64) {
-      // 2 nu (M-check^-1)^(x)3 by banded Cholesky solves along each direction (exact; far fewer
-      // FP64 flops than the dense eigenvector route)
-      copy_async(y, x, npres * sizeof(T), s);
-      double* yd = reinterpret_cast<double*>(y);
-      chol_solve_axis(yd, b, chol_p, 1, chol_lb, chol_inv, 1.0, s);
-      chol_solve_axis(yd, b, chol_p, 2, chol_lb, chol_inv, 1.0, s);
-      chol_solve_axis(yd, b, chol_p, 3, chol_lb, chol_inv, 2.0 * (double)nu, s);
-      return;
+    // FP64: banded Cholesky line solves for large b (4(p + 1) FP64 flops per entry and direction
+    // instead of 2b, exact up to rounding); for small b their sequential recurrence is
+    // latency-bound and the dense route is faster. (In FP32 the tensor-core route below is
+    // faster at every size: the line solves have one thread per line, a few warps per SM.)
+    if constexpr (std::is_same<T, double>::value) {
+      if (chol_lb && b >= 64) {
+        ck(chol_solve_axis<T>(x, y, b, chol_p, 1, chol_lb, chol_inv, T(1), s, nb, bs), "chol");
+        ck(chol_solve_axis<T>(y, y, b, chol_p, 2, chol_lb, chol_inv, T(1), s, nb, bs), "chol");
+        ck(chol_solve_axis<T>(y, y, b, chol_p, 3, chol_lb, chol_inv, T(2) * nu, s, nb, bs),
+           "chol");
+        return;
+      }
     }
     if (tc) {
       tc_fd(3, reinterpret_cast<const float*>(x), reinterpret_cast<float*>(y));
@@ -1150,12 +1155,20 @@ void init_tc(stokes_ctx* c, const Dense& UN, const std::vector<double>& lN, cons
   const int align = 16 / elem;
   Arena& ar = c->arena;
   cudaStream_t s = c->stream;
-  // padded operators: op[0] = U_N^T, op[1] = U_N, op[2] = U_T^T, op[3] = U_T (Op[i][j] rows)
-  const Dense* srcs[4] = {&UN, &UN, &UT, &UT};
-  const bool transp[4] = {true, false, true, false};
-  void* op[4];
-  int npad_of[4], kpad_of[4];
-  for (int k = 0; k < 4; ++k) {
+  // padded operators: op[0] = U_N^T, op[1] = U_N, op[2] = U_T^T, op[3] = U_T (Op[i][j] rows),
+  // op[4] = M-check^-1 = U_T U_T^T (U_T^T M-check U_T = I), formed in FP64
+  Dense Minv(b, b);
+  for (int i = 0; i < b; ++i)
+    for (int j = 0; j < b; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < b; ++k) acc += UT(i, k) * UT(j, k);
+      Minv(i, j) = acc;
+    }
+  const Dense* srcs[5] = {&UN, &UN, &UT, &UT, &Minv};
+  const bool transp[5] = {true, false, true, false, false};
+  void* op[5];
+  int npad_of[5], kpad_of[5];
+  for (int k = 0; k < 5; ++k) {
     const int n = srcs[k]->rows;
     const int npad = rup(n, 16), kpad = rup(n, kchunk);
     npad_of[k] = npad;
@@ -1225,18 +1238,21 @@ void init_tc_plans(stokes_ctx* c, Ops<float>& o, std::vector<RmpPlan>& plans, vo
     for (int k = 0; k < 3; ++k) lam[k] = own[k] ? o.lam_N : o.lam_T;
     uint8_t* bufs_in[6] = {P0, F1, F2, F1, F2, F1};
     uint8_t* bufs_out[6] = {F1, F2, F1, F2, F1, nullptr};
+    if (t == 3) bufs_out[2] = nullptr;   // pressure: three passes, the third one canonical
     o.tc_p0[t] = P0 + (size_t)t * slot * elem;
     o.tc_ld0[t] = rup(ext[0], align);
-    for (int st = 0; st < 6; ++st) {
+    const int last = t < 3 ? 5 : 2;
+    for (int st = 0; st <= last; ++st) {
       const int ax = st % 3;   // contracted direction: x1, x2, x3, x1, x2, x3
       const int e1 = ext[ax], e2 = ext[(ax + 1) % 3], e3 = ext[(ax + 2) % 3];
       const bool fwd = st < 3;
-      // operator index: velocity own direction uses U_N, the rest U_T (pressure: always U_T)
+      // operator index: velocity own direction uses U_N, the other directions U_T; the
+      // pressure uses the dense inverse of M-check in each of its three passes
       const int base_op = (t < 3 && own[ax]) ? 0 : 2;
-      const int opk = base_op + (fwd ? 0 : 1);
+      const int opk = t == 3 ? 4 : base_op + (fwd ? 0 : 1);
       RmpPlan& p = plans[t * 6 + st];
       p.kind = kind;
-      p.out_bf16 = bf && st < 5;
+      p.out_bf16 = bf && st < last;
       RmpArgs& ra = p.args;
       ra.R = e2 * e3;
       ra.K = e1;
@@ -1244,8 +1260,8 @@ void init_tc_plans(stokes_ctx* c, Ops<float>& o, std::vector<RmpPlan>& plans, vo
       ra.npad = npad_of[opk];
       ra.e2 = e2;
       ra.e3 = e3;
-      ra.ldy = st < 5 ? rup(e2, align) : e2;
-      ra.round_tf32 = (!bf && st < 5) ? 1 : 0;
+      ra.ldy = st < last ? rup(e2, align) : e2;
+      ra.round_tf32 = (!bf && st < last) ? 1 : 0;
       ra.idesc = rmp_idesc(kind, ra.npad);
       ra.scale = (float)(2.0 * c->nu);
       ra.post = 1.f;
@@ -1254,7 +1270,7 @@ void init_tc_plans(stokes_ctx* c, Ops<float>& o, std::vector<RmpPlan>& plans, vo
         ra.lam_j3 = lam[1];
         ra.lam_i = lam[2];
       }
-      if (st == 5 && t == 3) ra.post = (float)(2.0 * c->nu);
+      if (st == last && t == 3) ra.post = (float)(2.0 * c->nu);
       ra.Y = bufs_out[st] ? (void*)(bufs_out[st] + (size_t)t * slot * elem) : nullptr;
       // items: the rotated output of item k follows item k - 1's (e3 * m rows of pitch ldy,
       // the next step's input rows); the final step's output is canonical (set at launch)
@@ -2188,6 +2204,7 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
       if (!(l > 0.0)) throw SetupError{"K is not positive definite"};
     const Band bM = to_band(u.M, 1e-15), bK = to_band(u.K, 1e-15);
     const Band bMc = to_band(u.Mc, 1e-15), bTc = to_band(u.Tc, 1e-15);
+    std::vector<double> chol_lb_h, chol_inv_h;   // banded Cholesky factor of M-check (host)
     init_ops<double>(c, c->od, bM, bK, bMc, bTc, UN.v, lN, UT.v, lT);
     c->od.eo_N = heN;
     c->od.eo_T = heT;
@@ -2220,13 +2237,15 @@ int stokes_setup(stokes_t* out, int n_elems, int degree_p, double nu, const stok
           L(i, j) = t / L(j, j);
         }
       }
-      std::vector<double> lb((size_t)b * w, 0.0), ld(b);
+      chol_lb_h.assign((size_t)b * w, 0.0);
+      chol_inv_h.assign(b, 0.0);
       for (int i = 0; i < b; ++i) {
-        ld[i] = 1.0 / L(i, i);
-        for (int k = std::max(0, i - p); k <= i; ++k) lb[(size_t)i * w + (k - i + p)] = L(i, k);
+        chol_inv_h[i] = 1.0 / L(i, i);
+        for (int k = std::max(0, i - p); k <= i; ++k)
+          chol_lb_h[(size_t)i * w + (k - i + p)] = L(i, k);
       }
-      c->od.chol_lb = upload<double>(c->arena, lb, c->stream);
-      c->od.chol_inv = upload<double>(c->arena, ld, c->stream);
+      c->od.chol_lb = upload<double>(c->arena, chol_lb_h, c->stream);
+      c->od.chol_inv = upload<double>(c->arena, chol_inv_h, c->stream);
       c->od.chol_p = p;
     }
     const Ops<double>* odq = nullptr;

@@ -113,6 +113,40 @@ def test_reduced_precision_batched_48(prec):
         assert e1 < reduced_tol(prec, 1), (k, e1)
 
 
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_reduced_precision_pressure_block_items(prec):
+    """The reduced-precision pressure block as three tensor-core passes with the dense inverse of
+    M-check ((M-check^-1)^(x)3, one rotation of the three directions) at 62^3, p = 3 (b = 65, an
+    odd tile count), in a 2-item context: each item of P_0^-1 equals the one-item context's bit
+    for bit and matches the oracle. Pressure-block bound: three chained contractions, each
+    reading two operands rounded to the format (relative error <= u each): twice
+    sqrt(3 x 2) u (the reduced_tol argument with three contractions instead of six)."""
+    from paper_2311_06926_gb300 import Stokes
+    from gpu_common import UNIT_ROUNDOFF
+    n, nrhs = 62, 2
+    S, base, Kop, F = oracle(n, P)
+    G2 = Stokes(n, P, precision=prec, nrhs=nrhs, max_order=2, max_steps=1)
+    G1 = Stokes(n, P, precision=prec, max_order=2, max_steps=1)
+    xs = [synthetic.random_vector(S.size, 4600 + k) for k in range(nrhs)]
+    G2.profile_begin()
+    Y = host(G2.apply_P(dev(np.concatenate(xs))))
+    prof = G2.profile_end()
+    # six velocity passes, three pressure passes
+    assert prof["mma_mode_product"]["launches"] == 9
+    u = UNIT_ROUNDOFF[prec]
+    for k, x in enumerate(xs):
+        y1 = host(G1.apply_P(dev(x)))
+        yk = Y[k * S.size:(k + 1) * S.size]
+        assert np.array_equal(yk, y1), k
+        e = relerr(yk, _ref_hp(base, S, x, 2, 0))
+        eq = relerr(yk[S.n_vel:], base.pq0_inv(x[S.n_vel:]))
+        print(f"[measured] {prec} 62^3 item {k}: P_0 {e:.3e}, pressure block {eq:.3e}")
+        assert e < reduced_tol(prec, 0), (k, e)
+        assert eq < 2 * 6 ** 0.5 * u, (k, eq)
+    G2.close()
+    G1.close()
+
+
 def _against_golden(x, g, prefix=""):
     """Relative errors of the GPU solution x (host, pressure zero-mean) against a stored oracle
     solution (prefix "": its MINRES solve to 1e-8; "exact_": its MINRES solve to 1e-11, the
