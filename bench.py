@@ -1309,7 +1309,7 @@ def run_sweep(args, wl):
             "config": workload_config(args, wl),
             "unknowns": G.size, "solves_per_step": len(sweep),
             "fp64_launch_shapes": dict(zip(("mode_block", "band_block", "fd_fused"),
-                                           G.tuning())),
+                                           G.tuning()[:3])),
             "per_preconditioner": per,
             "table1_form": table1,
             "sweep_concurrent": sweep_conc,

@@ -249,7 +249,7 @@ int stokes_profile_end(stokes_t ctx, stokes_kernel_stat* out, int capacity);
 int64_t stokes_kernel_launches(void);
 
 /* Launch shapes of the FP64 kernels, chosen at setup by timing when stokes_opts.autotune is set,
- * otherwise {512, 256, 0}:
+ * otherwise {512, 256, 0, 1}:
  *   mode_block: threads per block of the fast-diagonalisation mode products (128, 256 or 512);
  *   band_block: threads per block of the banded passes (128, 256 or 512);
  *   fd_fused:   how the fast diagonalisation (App. A.4) is launched: 0 = six single-direction
@@ -259,13 +259,19 @@ int64_t stokes_kernel_launches(void);
  *               backward x3 product of each line group in one block, then the x2 and x1
  *               products per plane); fused forms need every plane to fit in shared memory
  *               (2 x n1 x n2 doubles <= 200 KiB, meshes up to about 110 elements per direction).
- * Every output is computed by one thread in a fixed order whatever the choice, so results do not
- * depend on it. stokes_set_tuning rejects other values, and a fused form on a mesh whose planes
- * do not fit, with STOKES_ERR_ARG (the context keeps its shapes). */
+ *   tc_nsplit:  tile shape of the tensor-core mode products (TF32/BF16 contexts): the N columns
+ *               of each 128-row tile computed as one work unit (1) or as two units of at most
+ *               half the columns each (2; more units where a launch has few tiles); the tuner
+ *               times both on the context's fast diagonalisation; default 1.
+ * Every output is computed by one thread in a fixed order whatever the choice (and each output
+ * column by the same tensor-core operations), so results do not depend on it. stokes_set_tuning
+ * rejects other values, and a fused form on a mesh whose planes do not fit, with STOKES_ERR_ARG
+ * (the context keeps its shapes). */
 typedef struct stokes_tuning {
   int mode_block;
   int band_block;
   int fd_fused;
+  int tc_nsplit;
 } stokes_tuning;
 int stokes_get_tuning(stokes_t ctx, stokes_tuning* out);
 int stokes_set_tuning(stokes_t ctx, const stokes_tuning* tuning);

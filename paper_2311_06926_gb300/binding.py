@@ -30,7 +30,7 @@ class StokesError(RuntimeError):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("mode_block", ctypes.c_int), ("band_block", ctypes.c_int),
-                ("fd_fused", ctypes.c_int)]
+                ("fd_fused", ctypes.c_int), ("tc_nsplit", ctypes.c_int)]
 
 
 class _Opts(ctypes.Structure):
@@ -230,14 +230,17 @@ class Stokes:
 
     # -- C ABI ----------------------------------------------------------------------------------
     def tuning(self):
-        """(mode_block, band_block, fd_fused): FP64 launch shapes (stokes_tuning), picked by the
-        setup tuner unless autotune=False."""
+        """(mode_block, band_block, fd_fused, tc_nsplit): launch shapes (stokes_tuning), picked by
+        the setup tuner unless autotune=False."""
         t = _Tuning()
         self._check(self.lib.stokes_get_tuning(self.h, ctypes.byref(t)))
-        return t.mode_block, t.band_block, t.fd_fused
+        return t.mode_block, t.band_block, t.fd_fused, t.tc_nsplit
 
-    def set_tuning(self, mode_block, band_block, fd_fused=0):
-        t = _Tuning(int(mode_block), int(band_block), int(fd_fused))
+    def set_tuning(self, mode_block, band_block, fd_fused=0, tc_nsplit=None):
+        """tc_nsplit None keeps the context's tensor-core tile shape."""
+        if tc_nsplit is None:
+            tc_nsplit = self.tuning()[3]
+        t = _Tuning(int(mode_block), int(band_block), int(fd_fused), int(tc_nsplit))
         self._check(self.lib.stokes_set_tuning(self.h, ctypes.byref(t)))
 
     def set_wait_limit(self, polls):

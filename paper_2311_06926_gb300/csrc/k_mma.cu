@@ -172,12 +172,17 @@ struct RmpJob {
   int first_tile;   // index of this job's first tile in the launch
   int ntiles;
   int nchunks;
+  // N split: work unit h of a tile computes the output columns [n0[h], n0[h] + nc[h]) with the
+  // operator rows of that range (nc a multiple of 16) and its own instruction descriptor
+  int n0[2], nc[2];
+  uint32_t idesc[2];
 };
 
 struct RmpBatch {
   RmpJob job[kMaxRmpJobs];
   int njobs;
   int total_tiles;
+  int nsplit;            // work units per tile (1 or 2): the tile's N columns split in nsplit parts
   uint32_t spin_limit;   // polls of each pipeline wait before it gives up (drain waits: kSpinLimit)
 };
 
@@ -210,8 +215,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int t_begin = (int)(((int64_t)batch.total_tiles * blockIdx.x) / gridDim.x);
-  const int t_end = (int)(((int64_t)batch.total_tiles * (blockIdx.x + 1)) / gridDim.x);
+  // work units: nsplit per tile (consecutive units of one tile share its rows)
+  const int ns = batch.nsplit;
+  const int total_units = batch.total_tiles * ns;
+  const int u_begin = (int)(((int64_t)total_units * blockIdx.x) / gridDim.x);
+  const int u_end = (int)(((int64_t)total_units * (blockIdx.x + 1)) / gridDim.x);
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full_bar[s], 1);
@@ -243,7 +251,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int it = 0, cur = -1, nb = 0;
       bool ok = true;
-      for (int t = t_begin; ok && t < t_end && !*abort_p; ++t) {
+      for (int u = u_begin; ok && u < u_end && !*abort_p; ++u) {
+        const int t = u / ns;
         const int j = job_of(batch, t);
         const RmpJob& J = batch.job[j];
         if (j != cur) {
@@ -283,7 +292,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       bool ok = true;
       int it = 0, local = 0, cur = -1, nbw = 0;
-      for (int t = t_begin; ok && t < t_end; ++t, ++local) {
+      for (int u = u_begin; ok && u < u_end; ++u, ++local) {
+        const int t = u / ns, h = u - t * ns;
         const int j = job_of(batch, t);
         const RmpJob& J = batch.job[j];
         if (j != cur) {
@@ -303,16 +313,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t a_addr = smem_u32(a_ring + s * kStageBytes);
-          const uint32_t b_addr = smem_u32(b_tile + c * J.args.npad * kChunkBytes);
+          // the unit's operator rows start n0 rows into the chunk (n0 a multiple of 16: whole
+          // 8-row swizzle atoms of 1024 bytes)
+          const uint32_t b_addr =
+              smem_u32(b_tile + c * J.args.npad * kChunkBytes + J.n0[h] * kChunkBytes);
 #pragma unroll
           for (int k = 0; k < 4; ++k)   // 4 instructions of 32 bytes of K each
             umma<KIND>(d_tmem, sw128_desc(a_addr + 32 * k), sw128_desc(b_addr + 32 * k),
-                       J.args.idesc, (c > 0 || k > 0) ? 1u : 0u);
+                       J.idesc[h], (c > 0 || k > 0) ? 1u : 0u);
           umma_commit(&empty_bar[s]);   // stage free once these MMAs have read it
         }
         if (!ok) break;
         umma_commit(&tfull_bar[acc]);   // accumulator ready for the epilogue
-        if (t + 1 < t_end && job_of(batch, t + 1) != j) umma_commit(&b_free_bar);
+        if (u + 1 < u_end && job_of(batch, (u + 1) / ns) != j) umma_commit(&b_free_bar);
       }
       // bounded wait until every MMA this thread issued has completed
       umma_commit(&drain_bar);
@@ -325,9 +338,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int half = (warp - 2) / 4;
     const int row_in_tile = quarter * 32 + lane;
     int local = 0;
-    for (int t = t_begin; t < t_end; ++t, ++local) {
+    for (int u = u_begin; u < u_end; ++u, ++local) {
+      const int t = u / ns, h = u - t * ns;
       const RmpJob& J = batch.job[job_of(batch, t)];
       const RmpArgs& args = J.args;
+      const int n0 = J.n0[h], nc = J.nc[h];
       const int acc = local & 1;
       int ok = 1;
       if (lane == 0) ok = mbar_wait(&tfull_bar[acc], (local / 2) & 1, abort_p, err, batch.spin_limit) ? 1 : 0;
@@ -349,14 +364,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t stride_i = (int64_t)args.ldy * args.e3;
       const float post = args.post, scale = args.scale;
       const bool rt = args.round_tf32 != 0;
-      for (int c0 = half * 32; c0 < args.npad; c0 += 64) {
+      for (int c0 = half * 32; c0 < nc; c0 += 64) {
         float v[32];
         tmem_ld32(tmem + acc * 256 + ((uint32_t)(quarter * 32) << 16) + c0, v);
-        if (valid && c0 < args.m) {
-          const int kmax = args.m - c0 < 32 ? args.m - c0 : 32;
-          TO* yp = yrow + stride_i * c0;
+        const int gc = n0 + c0;   // output column of the chunk's first accumulator column
+        if (valid && gc < args.m) {
+          const int lim = args.m - gc < nc - c0 ? args.m - gc : nc - c0;
+          const int kmax = lim < 32 ? lim : 32;
+          TO* yp = yrow + stride_i * gc;
           if (args.lam_i) {
-            const float* li = args.lam_i + c0;
+            const float* li = args.lam_i + gc;
             if (kmax == 32) {
 #pragma unroll
               for (int k = 0; k < 32; ++k) {
@@ -495,9 +512,13 @@ uint32_t rmp_idesc(int kind, int npad) {
 
 template <int KIND, typename TO>
 void launch_rmp_t(const RmpPlan* const* plans, int njobs, int* err, int sms, cudaStream_t s,
-                  uint32_t spin_limit) {
+                  uint32_t spin_limit, int nsplit) {
   RmpBatch b{};
   b.njobs = njobs;
+  // two units per tile only when every job's N splits into two multiples of 16
+  for (int j = 0; j < njobs && nsplit > 1; ++j)
+    if (plans[j]->args.npad < 32) nsplit = 1;
+  b.nsplit = nsplit > 1 ? 2 : 1;
   int tiles = 0, smem = 0;
   double flops = 0, bytes = 0;
   const int elem = KIND == kMmaTF32 ? 4 : 2;
@@ -511,6 +532,17 @@ void launch_rmp_t(const RmpPlan* const* plans, int njobs, int* err, int sms, cud
     const int64_t rows = (int64_t)p.args.R * (p.args.nb > 1 ? p.args.nb : 1);
     J.ntiles = (int)((rows + kTileM - 1) / kTileM);
     J.nchunks = (p.args.K + kChunkBytes / elem - 1) / (kChunkBytes / elem);
+    if (b.nsplit == 2) {
+      J.nc[0] = round_up((p.args.npad + 1) / 2, 16);
+      J.nc[1] = p.args.npad - J.nc[0];
+    } else {
+      J.nc[0] = p.args.npad;
+      J.nc[1] = 0;
+    }
+    J.n0[0] = 0;
+    J.n0[1] = J.nc[0];
+    J.idesc[0] = rmp_idesc(KIND, J.nc[0]);
+    J.idesc[1] = b.nsplit == 2 ? rmp_idesc(KIND, J.nc[1]) : 0u;
     tiles += J.ntiles;
     const int sm = rmp_smem_bytes(KIND, p.args.K, p.args.npad);
     smem = sm > smem ? sm : smem;
@@ -519,7 +551,8 @@ void launch_rmp_t(const RmpPlan* const* plans, int njobs, int* err, int sms, cud
   }
   b.total_tiles = tiles;
   b.spin_limit = spin_limit > 0 ? spin_limit : kSpinLimit;
-  const int grid = tiles < sms ? tiles : sms;
+  const int units = tiles * b.nsplit;
+  const int grid = units < sms ? units : sms;
   if (smem < 116 * 1024) smem = 116 * 1024;   // one CTA, one 512-column TMEM allocation per SM
   static std::atomic<int> attr{0};
   raise_smem_limit(k_rmp<KIND, TO>, attr, 220 * 1024);
@@ -529,12 +562,18 @@ void launch_rmp_t(const RmpPlan* const* plans, int njobs, int* err, int sms, cud
 }
 
 void launch_rmp_multi(const RmpPlan* const* plans, int njobs, int* err, int sms, cudaStream_t s,
-                      uint32_t spin_limit) {
+                      uint32_t spin_limit, int nsplit) {
   const RmpPlan& p = *plans[0];
-  if (p.kind == kMmaTF32) launch_rmp_t<kMmaTF32, float>(plans, njobs, err, sms, s, spin_limit);
+  if (p.kind == kMmaTF32)
+    launch_rmp_t<kMmaTF32, float>(plans, njobs, err, sms, s, spin_limit, nsplit);
   else if (p.out_bf16)
-    launch_rmp_t<kMmaBF16, __nv_bfloat16>(plans, njobs, err, sms, s, spin_limit);
-  else launch_rmp_t<kMmaBF16, float>(plans, njobs, err, sms, s, spin_limit);
+    launch_rmp_t<kMmaBF16, __nv_bfloat16>(plans, njobs, err, sms, s, spin_limit, nsplit);
+  else launch_rmp_t<kMmaBF16, float>(plans, njobs, err, sms, s, spin_limit, nsplit);
+}
+void launch_rmp(const RmpPlan& p, int* err, int sms, cudaStream_t s, uint32_t spin_limit,
+                int nsplit) {
+  const RmpPlan* one = &p;
+  launch_rmp_multi(&one, 1, err, sms, s, spin_limit, nsplit);
 }
 
 void pad_rows(const float* x, int e1, int64_t R, int ld, void* y, bool to_bf16, cudaStream_t s,
@@ -551,11 +590,6 @@ void pad_rows(const float* x, int e1, int64_t R, int ld, void* y, bool to_bf16, 
     launch_k(k_pad_rows<float>, (int)blocks, 256, 0, s, x, e1, R, ld, static_cast<float*>(y), nb,
              xbs);
   launch_end(kClassVector, s, 0.0, (double)total * (to_bf16 ? 6.0 : 8.0));
-}
-
-void launch_rmp(const RmpPlan& p, int* err, int sms, cudaStream_t s, uint32_t spin_limit) {
-  const RmpPlan* one = &p;
-  launch_rmp_multi(&one, 1, err, sms, s, spin_limit);
 }
 
 }  // namespace shp

@@ -47,9 +47,13 @@ uint32_t rmp_idesc(int kind, int npad);
 // spin_limit: polls of each pipeline wait before it gives up and raises *err (0: the default,
 // 2^22 polls of at least 128 ns each after the first 64); the kernel's final waits for its own
 // copies and tensor-core operations in flight always use the default.
-void launch_rmp(const RmpPlan& p, int* err, int sms, cudaStream_t s, uint32_t spin_limit = 0);
+// nsplit: 1, or 2 to split every 128-row tile's N columns into two work units (two CTAs may then
+// share a tile; more units for launches with few tiles). Each output column takes the same
+// tensor-core operations either way, so the results are bit-identical.
+void launch_rmp(const RmpPlan& p, int* err, int sms, cudaStream_t s, uint32_t spin_limit = 0,
+                int nsplit = 1);
 void launch_rmp_multi(const RmpPlan* const* plans, int njobs, int* err, int sms, cudaStream_t s,
-                      uint32_t spin_limit = 0);
+                      uint32_t spin_limit = 0, int nsplit = 1);
 
 // Copy a canonical float tensor (rows of e1 entries, R rows) into rows of pitch ld, converting
 // to bfloat16 if to_bf16. nb items: item k's tensor starts xbs elements after item k - 1's in x,

@@ -225,6 +225,7 @@ struct Ops {
   int sms = 152;
   int* tc_err = nullptr;
   uint32_t tc_spin = 0;         // polls per pipeline wait of the tensor-core kernel (0: default)
+  int tc_nsplit = 1;            // tensor-core tile shape: N columns of a tile in 1 or 2 work units
   void* tc_p0[4] = {nullptr, nullptr, nullptr, nullptr};
   int tc_ld0[4] = {0, 0, 0, 0};
   RmpPlan* tc_plan = nullptr;   // [4][6], host memory
@@ -483,7 +484,7 @@ struct Ops {
         p.args.Y = y;
         p.args.ybs = bs;
       }
-      launch_rmp(p, tc_err, sms, s, tc_spin);
+      launch_rmp(p, tc_err, sms, s, tc_spin, tc_nsplit);
     }
   }
 
@@ -512,7 +513,7 @@ struct Ops {
           }
           pp[c] = &p[c];
         }
-        launch_rmp_multi(pp, 3, tc_err, sms, s, tc_spin);
+        launch_rmp_multi(pp, 3, tc_err, sms, s, tc_spin, tc_nsplit);
       }
       return;
     }
@@ -2001,6 +2002,7 @@ constexpr int kBandBlocks[] = {128, 256, 512};
 constexpr int kFdFused[] = {0, 1, 2, 4};
 
 void set_shapes(stokes_ctx* c, const stokes_tuning& t) {
+  c->of.tc_nsplit = c->ofq.tc_nsplit = t.tc_nsplit;
   c->od.mode_block = c->odq.mode_block = t.mode_block;
   c->od.band_block = c->odq.band_block = t.band_block;
   c->od.fd_fused = c->odq.fd_fused = t.fd_fused;
@@ -2079,6 +2081,24 @@ void autotune(stokes_ctx* c) {
     return ms;
   };
   int best_mode = c->od.mode_block, best_band = c->od.band_block, best_fused = c->od.fd_fused;
+  int best_split = c->of.tc_nsplit;
+  if (reduced(c) && c->of.tc) {
+    // tensor-core tile shape: the N columns of each 128-row tile in one work unit or two, timed
+    // on the velocity fast diagonalisation and the pressure inverse (identical bits)
+    float* xf = c->xf;
+    float* yf = c->yf;
+    fill_zero(xf, (size_t)c->nb * c->ntot * sizeof(float), s);
+    float best = 1e30f;
+    for (int ns : {1, 2}) {
+      c->of.tc_nsplit = ns;
+      const float t = time3([&] {
+        c->of.fd_V(xf, yf);
+        c->of.minv_Q(xf + c->nvel, yf + c->nvel);
+      });
+      if (t < best) { best = t; best_split = ns; }
+    }
+    c->of.tc_nsplit = best_split;
+  }
   if (!reduced(c)) {
     // FP64 fast diagonalisation: threads per block, six single-direction launches or three
     // fused ones (identical bits)
@@ -2107,7 +2127,7 @@ void autotune(stokes_ctx* c) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   check_launch("autotune");
-  set_shapes(c, stokes_tuning{best_mode, best_band, best_fused});
+  set_shapes(c, stokes_tuning{best_mode, best_band, best_fused, best_split});
 }
 
 
@@ -2761,6 +2781,7 @@ int stokes_get_tuning(stokes_t c, stokes_tuning* out) {
   out->mode_block = c->od.mode_block;
   out->band_block = c->od.band_block;
   out->fd_fused = c->od.fd_fused;
+  out->tc_nsplit = c->of.tc_nsplit;
   return STOKES_OK;
 }
 
@@ -2772,6 +2793,8 @@ int stokes_set_tuning(stokes_t c, const stokes_tuning* t) {
   for (int v : kFdFused) ok_f = ok_f || v == t->fd_fused;
   if (!ok_m || !ok_b) return fail(c, STOKES_ERR_ARG, "launch shape not among the candidates");
   if (!ok_f) return fail(c, STOKES_ERR_ARG, "fd_fused must be 0, 1, 2 or 4");
+  if (t->tc_nsplit != 1 && t->tc_nsplit != 2)
+    return fail(c, STOKES_ERR_ARG, "tc_nsplit must be 1 or 2");
   if (t->fd_fused) {
     const int keep = c->od.fd_fused;
     c->od.fd_fused = t->fd_fused;

@@ -253,7 +253,7 @@ def test_launch_shapes_do_not_change_results(n, p):
     generic-width kernel."""
     S, base, Kop, F = oracle(n, p)
     G = _ctx(n, p, 1.0, autotune=False)
-    assert G.tuning() == (512, 256, 0)
+    assert G.tuning() == (512, 256, 0, 1)
     x = dev(synthetic.random_vector(S.size, 700 + n))
     ref_K, ref_H = G.apply_K(x), G.apply_hyperpower(2, 1, x)
     ref_P = G.apply_P(x)
@@ -263,7 +263,7 @@ def test_launch_shapes_do_not_change_results(n, p):
         for mb in (128, 256, 512):
             for bb in (128, 256, 512):
                 G.set_tuning(mb, bb, ff)
-                assert G.tuning() == (mb, bb, ff)
+                assert G.tuning()[:3] == (mb, bb, ff)
                 assert torch.equal(G.apply_K(x), ref_K)
                 assert torch.equal(G.apply_P(x), ref_P)
                 assert torch.equal(G.apply_hyperpower(2, 1, x), ref_H)
@@ -278,6 +278,37 @@ def test_launch_shapes_do_not_change_results(n, p):
     assert Ga.tuning()[0] in (128, 256, 512) and Ga.tuning()[1] in (128, 256, 512)
     assert Ga.tuning()[2] in (0, 1, 2, 4)
     Ga.close()
+
+
+@pytest.mark.parametrize("n,p,prec,nrhs", [(20, 3, "tf32", 1), (29, 2, "bf16", 1),
+                                             (13, 3, "tf32", 3), (40, 4, "tf32", 1)])
+def test_tensor_core_tile_split_bit_identical(n, p, prec, nrhs):
+    """The tensor-core tile shape (each 128-row tile's N columns as one work unit or two, the
+    second starting at a multiple of 16 operator rows) changes which CTA computes which columns,
+    not the tensor-core operations of any output column: P_0^-1, the order-2, 1-step
+    preconditioner and a flexible GMRES solve give the same bits either way."""
+    from paper_2311_06926_gb300 import Stokes
+    G = Stokes(n, p, precision=prec, nrhs=nrhs, max_order=2, max_steps=1, autotune=False)
+    assert G.tuning()[3] == 1
+    x = torch.from_numpy(np.concatenate([synthetic.random_vector(G.size, 800 + k)
+                                         for k in range(nrhs)])).cuda()
+    G.set_preconditioner(2, 1)
+    f = torch.cat([G.rhs_cavity(1.0)] * nrhs) if nrhs > 1 else G.rhs_cavity(1.0)
+    out = {}
+    for ns in (1, 2):
+        mb, bb, ff, _ = G.tuning()
+        G.set_tuning(mb, bb, ff, ns)
+        assert G.tuning()[3] == ns
+        P0, P1 = G.apply_P(x).clone(), G.apply_hyperpower(2, 1, x).clone()
+        if nrhs == 1:
+            xs, it, _, _ = G.solve(f, 1e-8)
+            out[ns] = (P0, P1, xs.clone(), it)
+        else:
+            out[ns] = (P0, P1, None, None)
+    G.close()
+    assert torch.equal(out[1][0], out[2][0]) and torch.equal(out[1][1], out[2][1])
+    if nrhs == 1:
+        assert out[1][3] == out[2][3] and torch.equal(out[1][2], out[2][2])
 
 
 def test_fused_fast_diagonalisation_profile():
