@@ -87,6 +87,7 @@ struct BandD {
   int rows, cols, width;
   const int* start;
   const T* val;
+  const T* valT;   // the band transposed: valT[w * rows + i] = val[i * width + w]
   const T* cval;
   int half, cpitch;
   int tlo, thi;

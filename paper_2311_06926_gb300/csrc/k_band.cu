@@ -61,14 +61,16 @@ __device__ __forceinline__ T band_dot(const BandD<T>& D, int i, const T* __restr
 
 // Passes along x1 with flat1 set: threads enumerate (line, row) with the row fastest, so a warp
 // reads a contiguous stretch of the input and writes a contiguous stretch of the output; the band
-// coefficients of the job are staged in shared memory transposed ([term][w][row]) so that lanes
-// with consecutive rows read consecutive words.
+// coefficients come from the transposed copy of the band (valT, [w][row]) through the read-only
+// cache, so that lanes with consecutive rows read consecutive words. (An earlier form staged
+// them in shared memory per block: with one output per thread that staging, 2 W m values per
+// block, cost more instructions than the FMAs.)
 // IT: index type of the thread's (line, row) arithmetic: int when every job's outputs (all items)
 // and tensors fit below 2^31, so that no 64-bit division runs (on this part 64-bit integer
 // division issues FP64-pipe instructions, the pipe these FP64 passes are bound by); int64_t
 // otherwise. Item offsets k * bs are always 64-bit.
 template <typename T, int W, typename IT>
-__device__ __forceinline__ void band_pass_flat_x1(const PassArgs<T>& a, IT t, T* csh) {
+__device__ __forceinline__ void band_pass_flat_x1(const PassArgs<T>& a, IT t) {
   const int m = a.D0.rows;
   const Dims out = a.in.with(1, m);
   const int nb = a.nb > 1 ? a.nb : 1;
@@ -83,23 +85,25 @@ __device__ __forceinline__ void band_pass_flat_x1(const PassArgs<T>& a, IT t, T*
     kb = (int64_t)k * a.bs;
     line -= k * lines;
   }
-  const T* cs = csh + i;
+  const T* c0 = a.D0.valT + i;
   const int64_t base_in = kb + (int64_t)((IT)a.in.n1 * line);
   const T* x0 = a.X0 + base_in + __ldg(a.D0.start + i);
   T acc = 0;
 #pragma unroll
-  for (int w = 0; w < W; ++w) acc = fma(cs[w * m], __ldg(x0 + w), acc);
+  for (int w = 0; w < W; ++w) acc = fma(__ldg(c0 + w * m), __ldg(x0 + w), acc);
   if (a.chain) {
+    const T* c1 = a.D1.valT + i;
     const T* x1 = a.X1 + base_in + __ldg(a.D1.start + i);
 #pragma unroll
-    for (int w = 0; w < W; ++w) acc = fma(cs[(W + w) * m], __ldg(x1 + w), acc);
+    for (int w = 0; w < W; ++w) acc = fma(__ldg(c1 + w * m), __ldg(x1 + w), acc);
   } else {
     if (!a.c0_one) acc *= a.c0;   // (a product with 1 is exact: skipped)
     if (a.nterms > 1) {
+      const T* c1 = a.D1.valT + i;
       const T* x1 = a.X1 + base_in + __ldg(a.D1.start + i);
       T u = 0;
 #pragma unroll
-      for (int w = 0; w < W; ++w) u = fma(cs[(W + w) * m], __ldg(x1 + w), u);
+      for (int w = 0; w < W; ++w) u = fma(__ldg(c1 + w * m), __ldg(x1 + w), u);
       acc = fma(a.c1, u, acc);
     }
   }
@@ -125,18 +129,8 @@ __global__ void __launch_bounds__(512) k_band_pass(const __grid_constant__ PassB
   const int axis = a.axis;
   if constexpr (W > 0) {
     if (pb.flat1 && axis == 1) {
-      extern __shared__ __align__(16) unsigned char band_smem[];
-      T* csh = reinterpret_cast<T*>(band_smem);
-      const int m = a.D0.rows;
-      const int nt = a.nterms > 1 ? 2 : 1;
-      for (int idx = threadIdx.x; idx < nt * W * m; idx += blockDim.x) {
-        const int tt = idx / (W * m), r = idx - tt * (W * m);
-        const int w = r / m, i = r - w * m;
-        csh[idx] = (tt == 0 ? a.D0 : a.D1).val[(int64_t)i * W + w];
-      }
-      __syncthreads();
       band_pass_flat_x1<T, W, IT>(a, (IT)(blockIdx.x - pb.first_block[jb]) * (IT)blockDim.x +
-                                         (IT)threadIdx.x, csh);
+                                         (IT)threadIdx.x);
       return;
     }
   }
@@ -1058,18 +1052,14 @@ void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s) {
   // the instantiated widths; any other width (an even width where a band is clamped by a small
   // matrix) runs the generic kernel, which has no flat layout
   if (!(W >= 3 && W <= 13 && W % 2 == 1)) W = 0;
-  // x1 passes with the flat (line, row) layout when the band width is a compiled one and the
-  // transposed coefficients fit in shared memory (the block counts below depend on this choice)
-  int smem = 0;
+  // x1 passes with the flat (line, row) layout when the band width is a compiled one and every
+  // band of such a job has its transposed copy (the block counts below depend on this choice)
+  const int smem = 0;
   pb.flat1 = W > 0;
   for (int j = 0; j < njobs && pb.flat1; ++j)
-    if (jobs[j].axis == 1) {
-      const int nt = jobs[j].nterms > 1 ? 2 : 1;
-      const int sm = nt * W * jobs[j].D0.rows * (int)sizeof(T);
-      if (sm > 96 * 1024) pb.flat1 = 0;
-      smem = sm > smem ? sm : smem;
-    }
-  if (!pb.flat1) smem = 0;
+    if (jobs[j].axis == 1 &&
+        (!jobs[j].D0.valT || (jobs[j].nterms > 1 && !jobs[j].D1.valT)))
+      pb.flat1 = 0;
   int blocks = 0;
   double flops = 0, bytes = 0;
   for (int j = 0; j < njobs; ++j) {

@@ -116,6 +116,17 @@ BandD<T> upload_band(Arena& ar, const Band& b, cudaStream_t s, int min_half = 0)
      "upload band");
   d.start = st;
   d.val = v;
+  {
+    // transposed copy for the passes along x1 whose lanes take consecutive rows
+    std::vector<T> tt((size_t)b.rows * b.width);
+    for (int i = 0; i < b.rows; ++i)
+      for (int w = 0; w < b.width; ++w)
+        tt[(size_t)w * b.rows + i] = (T)b.val[(size_t)i * b.width + w];
+    T* vt = ar.alloc<T>(tt.size());
+    ck(cudaMemcpyAsync(vt, tt.data(), tt.size() * sizeof(T), cudaMemcpyHostToDevice, s),
+       "upload band");
+    d.valT = vt;
+  }
   d.cval = nullptr;
   d.half = 0;
   d.cpitch = 0;
