@@ -115,6 +115,9 @@ WORKLOADS = {
                          "step) inside FP64 flexible GMRES to 1e-8; the 64 grouped by mesh into 12 "
                          "contexts of 5-6 right-hand sides (one launch per kernel per group), "
                          "the groups solved concurrently by one stokes_solve_batch call"),
+    "cavity256": dict(n=256, p=3, sweep=[(2, 1)], precision="tf32",
+                      desc="3D lid-driven cavity, 256^3 elements, p=3 (69 M unknowns): operator "
+                           "probes where the tensors exceed the L2"),
     "cavity96": dict(n=96, p=3, sweep=[(2, 2)], precision="fp64",
                      desc="3D lid-driven cavity, 96^3 elements, p=3, nu=1, order 2, 2 steps"),
 }
