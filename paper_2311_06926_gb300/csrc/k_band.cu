@@ -138,7 +138,10 @@ __global__ void __launch_bounds__(512) k_band_pass(const __grid_constant__ PassB
   const int m = a.D0.rows;
   const int seg_n = pb.seg;
   const int nseg = (m + seg_n - 1) / seg_n;
-  const IT lines1 = (IT)(out.size() / m);              // lines of one item
+  // lines of one item: the product of the two other extents (no 64-bit division, which issues
+  // FP64-pipe instructions on this part)
+  const IT lines1 = axis == 1 ? (IT)out.n2 * out.n3
+                             : (axis == 2 ? (IT)out.n1 * out.n3 : (IT)out.n1 * out.n2);
   const int nb = a.nb > 1 ? a.nb : 1;
   const IT lines = lines1 * nb;
   const IT t = (IT)(blockIdx.x - pb.first_block[jb]) * (IT)blockDim.x + (IT)threadIdx.x;
@@ -261,7 +264,8 @@ __global__ void __launch_bounds__(256) k_band_tile(const __grid_constant__ PassB
   const int wt1 = W > 0 ? W : (nt > 1 ? a.D1.width : 0);
   const int wp = ((wt0 > wt1 ? wt0 : wt1) + 3) & ~3;   // coefficient row pitch (float4 loads)
   const Dims out = a.in.with(axis, m);
-  const int64_t lines = out.size() / m;
+  const int64_t lines = axis == 1 ? (int64_t)out.n2 * out.n3   // no 64-bit division
+                                 : (axis == 2 ? (int64_t)out.n1 * out.n3 : (int64_t)out.n1 * out.n2);
   const int64_t line0 = (int64_t)(blockIdx.x - pb.first_block[jb]) * kTileLines;
   const int nl = (int)(lines - line0 < kTileLines ? lines - line0 : kTileLines);
   constexpr int P = kTileLines + 1;   // shared pitch of the input slabs
@@ -455,7 +459,8 @@ __global__ void __launch_bounds__(256, 3) k_band_slide(const __grid_constant__ P
   const int rs = mr + 2 * H;   // slab rows
   const int nt = a.nterms;
   const Dims out = a.in;
-  const int lines1 = (int)(out.size() / m);        // lines of one item
+  const int lines1 = axis == 1 ? out.n2 * out.n3   // lines of one item (no 64-bit division)
+                              : (axis == 2 ? out.n1 * out.n3 : out.n1 * out.n2);
   const int nb = a.nb > 1 ? a.nb : 1;
   const int lines = lines1 * nb;
   const int line0 = ((int)blockIdx.x - pb.first_block[jb]) * kTileLines;
