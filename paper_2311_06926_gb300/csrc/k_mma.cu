@@ -373,18 +373,25 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int kmax = lim < 32 ? lim : 32;
           TO* yp = yrow + stride_i * gc;
           if (args.lam_i) {
+            // the chunk's eigenvalues into registers before the first store: loaded between
+            // the stores (which may alias them for the compiler), each waited a full load latency
             const float* li = args.lam_i + gc;
+            float lk[32];
             if (kmax == 32) {
 #pragma unroll
+              for (int k = 0; k < 32; ++k) lk[k] = __ldg(li + k);
+#pragma unroll
               for (int k = 0; k < 32; ++k) {
-                const float val = __fdividef(v[k], scale * (lam_r + li[k]));
+                const float val = __fdividef(v[k], scale * (lam_r + lk[k]));
                 store_val<TO>(yp + stride_i * k, rt ? round_tf32(val) : val);
               }
             } else {
 #pragma unroll
+              for (int k = 0; k < 32; ++k) lk[k] = k < kmax ? __ldg(li + k) : 1.f;
+#pragma unroll
               for (int k = 0; k < 32; ++k) {
                 if (k < kmax) {
-                  const float val = __fdividef(v[k], scale * (lam_r + li[k]));
+                  const float val = __fdividef(v[k], scale * (lam_r + lk[k]));
                   store_val<TO>(yp, rt ? round_tf32(val) : val);
                 }
                 yp += stride_i;
