@@ -14,11 +14,20 @@ namespace shp {
 // has formally completed, so part of its launch latency overlaps the end of the previous kernel.
 // Each kernel therefore begins with pdl_begin(): griddepcontrol.wait blocks until the preceding
 // grid has completed and its memory operations are visible, so no read or write of a kernel races
-// with its predecessor. (No kernel triggers its dependents early: blocks of a waiting grid would
-// hold warp slots and shared memory that a concurrent stream's kernel could use.) For a kernel
-// launched without the attribute the wait returns immediately.
+// with its predecessor. Only the tensor-core mode product and its staging copy trigger their
+// dependents early (pdl_trigger); elsewhere blocks of a waiting grid would hold warp slots and
+// shared memory that a concurrent stream's kernel could use. For a kernel launched without the
+// attribute the wait returns immediately.
 __device__ __forceinline__ void pdl_begin() {
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
+// Early trigger (tensor-core mode product and its staging copy only): the next kernel in the
+// stream may be scheduled once every block of this grid has executed it. Its blocks take SMs as
+// this grid's blocks exit and run the part before their own pdl_begin(), which reads nothing a
+// preceding kernel writes, while the rest of this grid finishes.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
 // Returns the launch's own status (configuration errors), not errors left pending by earlier work.

@@ -198,7 +198,9 @@ __device__ __forceinline__ int job_of(const RmpBatch& b, int t) {
 template <int KIND, typename TO>
 __global__ void __launch_bounds__(kThreads, 1)
     k_rmp(const __grid_constant__ RmpBatch batch, int* err) {
-  pdl_begin();
+  // The next launch (typically the next mode product, one CTA per SM) is scheduled as SMs free
+  // up; its set-up and operator copy then overlap the end of this grid.
+  pdl_trigger();
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const int elem = KIND == kMmaTF32 ? 4 : 2;
@@ -218,8 +220,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   // work units: nsplit per tile (consecutive units of one tile share its rows)
   const int ns = batch.nsplit;
   const int total_units = batch.total_tiles * ns;
-  const int u_begin = (int)(((int64_t)total_units * blockIdx.x) / gridDim.x);
-  const int u_end = (int)(((int64_t)total_units * (blockIdx.x + 1)) / gridDim.x);
+  // the first total_units % gridDim.x CTAs (launched first, onto the SMs that free up first)
+  // take one unit more than the others
+  const int uq = total_units / (int)gridDim.x, ur = total_units - uq * (int)gridDim.x;
+  const int bx = (int)blockIdx.x;
+  const int u_begin = bx * uq + (bx < ur ? bx : ur);
+  const int u_end = u_begin + uq + (bx < ur ? 1 : 0);
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full_bar[s], 1);
@@ -246,10 +252,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
   volatile int* abort_p = &abort_flag;
+  // The operators are written once at set-up, never by a preceding kernel: the first job's
+  // operator copy is issued before waiting for the preceding grid, together with the barrier and
+  // TMEM set-up above. Nothing else is read or written before the wait.
+  int first_job = -1;
+  if (warp == 0 && lane == 0 && u_begin < u_end) {
+    first_job = job_of(batch, u_begin / ns);
+    const RmpJob& J = batch.job[first_job];
+    mbar_expect_tx(&b_bar, (uint32_t)(J.nchunks * J.args.npad * kChunkBytes));
+    for (int c = 0; c < J.nchunks; ++c)
+      tma_load_2d(b_tile + c * J.args.npad * kChunkBytes, &J.map_op, c * chunk_elems, 0, &b_bar);
+  }
+  pdl_begin();
 
   if (warp == 0) {
     if (lane == 0) {
-      int it = 0, cur = -1, nb = 0;
+      int it = 0, cur = first_job, nb = first_job >= 0 ? 1 : 0;
       bool ok = true;
       for (int u = u_begin; ok && u < u_end && !*abort_p; ++u) {
         const int t = u / ns;
@@ -438,6 +456,7 @@ template <typename TO>
 // one division per row instead of one per element.
 __global__ void k_pad_rows(const float* __restrict__ x, int e1, int64_t R, int ld,
                            TO* __restrict__ y, int nb, int64_t xbs) {
+  pdl_trigger();   // the mode product that reads this copy sets up while the copy runs
   pdl_begin();
   const int64_t rows = R * nb;
   const int lane = threadIdx.x % 32;
