@@ -718,22 +718,30 @@ __global__ void __launch_bounds__(256) k_div_transpose(const T* __restrict__ g, 
     const int64_t k = nb > 1 ? t / per : 0;
     const int64_t o = t - k * per;
     const int64_t kb = k * bs;
-    const int c = (int)(o / nc);
-    const int64_t r = o - c * nc;
-    T* y = (c == 0 ? y1 : (c == 1 ? y2 : y3)) + kb;
-    // extents of component c: (e1, e2, e3) with a in the own direction, b elsewhere
-    const int e1 = c == 0 ? a : b, e2 = c == 1 ? a : b;
-    int i1, i2, i3;
-    if (per < ((int64_t)1 << 31)) {   // 32-bit index arithmetic within an item
-      const int r32 = (int)r, q = r32 / e1;
+    int c, i1, i2, i3;
+    int64_t r;
+    if (per < ((int64_t)1 << 31)) {
+      // 32-bit index arithmetic within an item (a 64-bit division per element, here the
+      // component index o / nc, issues FP64-pipe instructions on this part)
+      const int o32 = (int)o, nc32 = (int)nc;
+      c = o32 / nc32;
+      const int r32 = o32 - c * nc32;
+      r = r32;
+      const int e1 = c == 0 ? a : b, e2 = c == 1 ? a : b;
+      const int q = r32 / e1;
       i1 = r32 - q * e1;
       i3 = q / e2;
       i2 = q - i3 * e2;
     } else {
+      c = (int)(o / nc);
+      r = o - c * nc;
+      const int e1 = c == 0 ? a : b, e2 = c == 1 ? a : b;
       i1 = (int)(r % e1);
       i2 = (int)((r / e1) % e2);
       i3 = (int)(r / ((int64_t)e1 * e2));
     }
+    // extents of component c: (e1, e2, e3) with a in the own direction, b elsewhere
+    T* y = (c == 0 ? y1 : (c == 1 ? y2 : y3)) + kb;
     const int64_t gs = c == 0 ? 1 : (c == 1 ? (int64_t)b : (int64_t)b * b);
     const int64_t gi = kb + i1 + (int64_t)b * (i2 + (int64_t)b * i3);
     const T v = g[gi] - g[gi + gs];

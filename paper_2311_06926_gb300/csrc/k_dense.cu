@@ -117,10 +117,18 @@ __global__ void __launch_bounds__(Tile<T>::NTH) k_gemm(const __grid_constant__ G
         T v = acc[i][j];
         if (g.lam1) {
           const int64_t o = off + (int64_t)bz * g.c_b;
-          const int i1 = (int)(o % g.out.n1);
-          const int64_t t2 = o / g.out.n1;
-          const int i2 = (int)(t2 % g.out.n2);
-          const int i3 = (int)(t2 / g.out.n2);
+          int i1, i2, i3;
+          if (g.out.size() < ((int64_t)1 << 31)) {   // 32-bit division (64-bit: FP64 pipe)
+            const int o32 = (int)o, t2 = o32 / g.out.n1;
+            i1 = o32 - t2 * g.out.n1;
+            i3 = t2 / g.out.n2;
+            i2 = t2 - i3 * g.out.n2;
+          } else {
+            i1 = (int)(o % g.out.n1);
+            const int64_t t2 = o / g.out.n1;
+            i2 = (int)(t2 % g.out.n2);
+            i3 = (int)(t2 / g.out.n2);
+          }
           v = v / (g.scale * (g.lam1[i1] + g.lam2[i2] + g.lam3[i3]));
         } else {
           v = v * g.post;

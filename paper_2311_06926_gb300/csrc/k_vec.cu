@@ -85,8 +85,18 @@ __global__ void k_outer3_acc(const double* __restrict__ l1, const double* __rest
   const int64_t total = (int64_t)e1 * e2 * e3;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t q = t / e1;
-    const int i1 = (int)(t - q * e1), i2 = (int)(q % e2), i3 = (int)(q / e2);
+    int i1, i2, i3;
+    if (total < ((int64_t)1 << 31)) {   // 32-bit division (64-bit division uses the FP64 pipe)
+      const int t32 = (int)t, q = t32 / e1;
+      i1 = t32 - q * e1;
+      i3 = q / e2;
+      i2 = q - i3 * e2;
+    } else {
+      const int64_t q = t / e1;
+      i1 = (int)(t - q * e1);
+      i2 = (int)(q % e2);
+      i3 = (int)(q / e2);
+    }
     const double s23 = __dmul_rn(__dmul_rn(cf, l2[i2]), l3[i3]);
     dst[t] = __dadd_rn(dst[t], __dmul_rn(s23, l1[i1]));
   }
@@ -209,8 +219,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_sep_dot_partial(const double* _
   const int64_t n = (int64_t)e1 * e2 * e3;
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * kThreads) {
-    const int64_t q = i / e1;
-    const int i1 = (int)(i - q * e1), i2 = (int)(q % e2), i3 = (int)(q / e2);
+    int i1, i2, i3;
+    if (n < ((int64_t)1 << 31)) {   // 32-bit division (64-bit division uses the FP64 pipe)
+      const int i32 = (int)i, q = i32 / e1;
+      i1 = i32 - q * e1;
+      i3 = q / e2;
+      i2 = q - i3 * e2;
+    } else {
+      const int64_t q = i / e1;
+      i1 = (int)(i - q * e1);
+      i2 = (int)(q % e2);
+      i3 = (int)(q / e2);
+    }
     const double xv = x[i];
 #pragma unroll
     for (int g = 0; g < NG; ++g) {
