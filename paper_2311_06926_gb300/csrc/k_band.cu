@@ -598,52 +598,39 @@ __global__ void __launch_bounds__(256, 3) k_band_slide(const __grid_constant__ P
   }
 }
 
-// nb items: item k of every tensor argument at offset k * bs elements
+// nb items: item k of every tensor argument at offset k * bs elements. One warp per x1 row
+// (i2, i3) of the pressure grid, lanes along i1: the row's indices are formed once per row (the
+// per-element divisions of a flat index made these stencils issue-bound).
 template <typename T>
 __global__ void __launch_bounds__(256) k_divergence(const T* __restrict__ u1, const T* __restrict__ u2,
                                                     const T* __restrict__ u3, int a, int b,
                                                     T* __restrict__ delta, const T* __restrict__ q,
                                                     T nu, T* __restrict__ e, int nb, int64_t bs) {
   pdl_begin();
-  const int64_t per = (int64_t)b * b * b;
-  const int64_t total = per * nb;
-  const int64_t step = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += step) {
-    const int64_t k = nb > 1 ? t / per : 0;
-    const int64_t o = t - k * per;
+  const int lane = threadIdx.x % 32;
+  const int rows1 = b * b;   // (i2, i3) rows of one item
+  const int64_t rows = (int64_t)rows1 * nb;
+  const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
+  for (int64_t rw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; rw < rows; rw += nw) {
+    const int64_t k = nb > 1 ? rw / rows1 : 0;
+    const int r = (int)(rw - k * rows1);
+    const int i3 = r / b, i2 = r - i3 * b;
     const int64_t kb = k * bs;
-    int i1, i2, i3;
-    if (per < ((int64_t)1 << 31)) {   // 32-bit index arithmetic within an item
-      const int o32 = (int)o, q = o32 / b;
-      i1 = o32 - q * b;
-      i3 = q / b;
-      i2 = q - i3 * b;
-    } else {
-      i1 = (int)(o % b);
-      i2 = (int)((o / b) % b);
-      i3 = (int)(o / ((int64_t)b * b));
+    const T* p1 = u1 + kb + (int64_t)a * (i2 + (int64_t)b * i3);   // u1 extents (a, b, b)
+    const T* p2 = u2 + kb + (int64_t)b * a * i3;                   // u2 extents (b, a, b)
+    const T* p3 = u3 + kb + (int64_t)b * i2;                       // u3 extents (b, b, a)
+    const int64_t o = kb + (int64_t)b * r;
+    for (int i1 = lane; i1 < b; i1 += 32) {
+      T d = 0;
+      if (i1 < a) d += p1[i1];
+      if (i1 >= 1) d -= p1[i1 - 1];
+      if (i2 < a) d += p2[i1 + (int64_t)b * i2];
+      if (i2 >= 1) d -= p2[i1 + (int64_t)b * (i2 - 1)];
+      if (i3 < a) d += p3[i1 + (int64_t)b * b * i3];
+      if (i3 >= 1) d -= p3[i1 + (int64_t)b * b * (i3 - 1)];
+      delta[o + i1] = d;
+      if (e) e[o + i1] = fma(nu, d, q[o + i1]);
     }
-    T d = 0;
-    // u1 extents (a, b, b)
-    {
-      const int64_t row = kb + (int64_t)a * (i2 + (int64_t)b * i3);
-      if (i1 < a) d += u1[row + i1];
-      if (i1 >= 1) d -= u1[row + i1 - 1];
-    }
-    // u2 extents (b, a, b)
-    {
-      const int64_t off = kb + i1 + (int64_t)b * a * i3;
-      if (i2 < a) d += u2[off + (int64_t)b * i2];
-      if (i2 >= 1) d -= u2[off + (int64_t)b * (i2 - 1)];
-    }
-    // u3 extents (b, b, a)
-    {
-      const int64_t off = kb + i1 + (int64_t)b * i2;
-      if (i3 < a) d += u3[off + (int64_t)b * b * i3];
-      if (i3 >= 1) d -= u3[off + (int64_t)b * b * (i3 - 1)];
-    }
-    delta[kb + o] = d;
-    if (e) e[kb + o] = fma(nu, d, q[kb + o]);
   }
 }
 
@@ -705,47 +692,35 @@ __global__ void __launch_bounds__(512) k_div_band_x1(const T* __restrict__ u1,
   }
 }
 
+// y_c (+)= the difference transpose of g along direction c, for the three velocity components
+// (extents a in the own direction, b in the others). One warp per x1 row of a component, lanes
+// along i1 (row indices formed once per row).
 template <typename T>
 __global__ void __launch_bounds__(256) k_div_transpose(const T* __restrict__ g, int a, int b, T* y1,
                                                        T* y2, T* y3, int accumulate, int nb,
                                                        int64_t bs) {
   pdl_begin();
-  const int64_t nc = (int64_t)a * b * b;
-  const int64_t per = 3 * nc;
-  const int64_t total = per * nb;
-  const int64_t step = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += step) {
-    const int64_t k = nb > 1 ? t / per : 0;
-    const int64_t o = t - k * per;
+  const int lane = threadIdx.x % 32;
+  // rows of one item: b * b of component 1 (rows of a entries), a * b of components 2 and 3
+  const int r0 = b * b, r1 = a * b;
+  const int rows1 = r0 + 2 * r1;
+  const int64_t rows = (int64_t)rows1 * nb;
+  const int64_t nw = (int64_t)gridDim.x * blockDim.x / 32;
+  for (int64_t rw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; rw < rows; rw += nw) {
+    const int64_t k = nb > 1 ? rw / rows1 : 0;
+    int r = (int)(rw - k * rows1);
+    const int c = r < r0 ? 0 : (r < r0 + r1 ? 1 : 2);
+    r -= c == 0 ? 0 : (c == 1 ? r0 : r0 + r1);
+    const int e1 = c == 0 ? a : b, e2 = c == 1 ? a : b;
+    const int i3 = r / e2, i2 = r - i3 * e2;
     const int64_t kb = k * bs;
-    int c, i1, i2, i3;
-    int64_t r;
-    if (per < ((int64_t)1 << 31)) {
-      // 32-bit index arithmetic within an item (a 64-bit division per element, here the
-      // component index o / nc, issues FP64-pipe instructions on this part)
-      const int o32 = (int)o, nc32 = (int)nc;
-      c = o32 / nc32;
-      const int r32 = o32 - c * nc32;
-      r = r32;
-      const int e1 = c == 0 ? a : b, e2 = c == 1 ? a : b;
-      const int q = r32 / e1;
-      i1 = r32 - q * e1;
-      i3 = q / e2;
-      i2 = q - i3 * e2;
-    } else {
-      c = (int)(o / nc);
-      r = o - c * nc;
-      const int e1 = c == 0 ? a : b, e2 = c == 1 ? a : b;
-      i1 = (int)(r % e1);
-      i2 = (int)((r / e1) % e2);
-      i3 = (int)(r / ((int64_t)e1 * e2));
-    }
-    // extents of component c: (e1, e2, e3) with a in the own direction, b elsewhere
-    T* y = (c == 0 ? y1 : (c == 1 ? y2 : y3)) + kb;
+    T* y = (c == 0 ? y1 : (c == 1 ? y2 : y3)) + kb + (int64_t)e1 * r;
     const int64_t gs = c == 0 ? 1 : (c == 1 ? (int64_t)b : (int64_t)b * b);
-    const int64_t gi = kb + i1 + (int64_t)b * (i2 + (int64_t)b * i3);
-    const T v = g[gi] - g[gi + gs];
-    y[r] = accumulate ? y[r] + v : v;
+    const T* gr = g + kb + (int64_t)b * (i2 + (int64_t)b * i3);
+    for (int i1 = lane; i1 < e1; i1 += 32) {
+      const T v = gr[i1] - gr[i1 + gs];
+      y[i1] = accumulate ? y[i1] + v : v;
+    }
   }
 }
 
@@ -1144,8 +1119,8 @@ void divergence(const T* u1, const T* u2, const T* u3, int a, int b, T* delta, c
   if (nb < 1) nb = 1;
   const int64_t total = (int64_t)b * b * b * nb;
   launch_begin(kClassDiv, s);
-  launch_k(k_divergence<T>, grid_for(total, 256), 256, 0, s, u1, u2, u3, a, b, delta, nullptr, T(0),
-           nullptr, nb, bs);
+  launch_k(k_divergence<T>, grid_for((int64_t)b * b * nb * 32, 256), 256, 0, s, u1, u2, u3, a, b,
+           delta, nullptr, T(0), nullptr, nb, bs);
   launch_end(kClassDiv, s, 6.0 * total, (3.0 * a * b * b * nb + total) * sizeof(T));
 }
 
@@ -1172,8 +1147,8 @@ void divergence_plus(const T* u1, const T* u2, const T* u3, int a, int b, T* del
   if (nb < 1) nb = 1;
   const int64_t total = (int64_t)b * b * b * nb;
   launch_begin(kClassDiv, s);
-  launch_k(k_divergence<T>, grid_for(total, 256), 256, 0, s, u1, u2, u3, a, b, delta, q, nu, e, nb,
-           bs);
+  launch_k(k_divergence<T>, grid_for((int64_t)b * b * nb * 32, 256), 256, 0, s, u1, u2, u3, a, b,
+           delta, q, nu, e, nb, bs);
   launch_end(kClassDiv, s, 8.0 * total, (3.0 * a * b * b * nb + 3.0 * total) * sizeof(T));
 }
 
@@ -1183,8 +1158,8 @@ void div_transpose(const T* g, int a, int b, T* y1, T* y2, T* y3, int accumulate
   if (nb < 1) nb = 1;
   const int64_t total = 3 * (int64_t)a * b * b * nb;
   launch_begin(kClassDiv, s);
-  launch_k(k_div_transpose<T>, grid_for(total, 256), 256, 0, s, g, a, b, y1, y2, y3, accumulate,
-           nb, bs);
+  launch_k(k_div_transpose<T>, grid_for((int64_t)(b * b + 2 * a * b) * nb * 32, 256), 256, 0, s, g,
+           a, b, y1, y2, y3, accumulate, nb, bs);
   launch_end(kClassDiv, s, (accumulate ? 2.0 : 1.0) * total,
              ((double)b * b * b * nb + (accumulate ? 2.0 : 1.0) * total) * sizeof(T));
 }
