@@ -194,9 +194,11 @@ __device__ __forceinline__ int job_of(const RmpBatch& b, int t) {
 
 // KIND: kMmaTF32 (FP32 operands in memory) or kMmaBF16; TO: output element type. Each CTA owns a
 // contiguous range of tiles over all jobs; the operator is reloaded when the range crosses into
-// the next job, after the MMAs that read the previous operator have completed.
+// the next job, after the MMAs that read the previous operator have completed. Registers are
+// bounded so that two CTAs fit on an SM where shared memory allows (small meshes, concurrent
+// contexts): unbounded, the scaled epilogue's hoisted eigenvalues took 168 registers a thread.
 template <int KIND, typename TO>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     k_rmp(const __grid_constant__ RmpBatch batch, int* err) {
   // The next launch (typically the next mode product, one CTA per SM) is scheduled as SMs free
   // up; its set-up and operator copy then overlap the end of this grid.

@@ -2106,7 +2106,8 @@ void autotune(stokes_ctx* c) {
         c->of.fd_V(xf, yf);
         c->of.minv_Q(xf + c->nvel, yf + c->nvel);
       });
-      if (t < best) { best = t; best_split = ns; }
+      // two units per tile only when clearly faster (the timing of a small mesh is noisy)
+      if (ns == 1 ? t < best : t < 0.95f * best) { best = t; best_split = ns; }
     }
     c->of.tc_nsplit = best_split;
   }
