@@ -53,9 +53,9 @@ TRAFFIC = {
         "sha256": "d05c14c82b258149fb7e1b53760b0abff0cde9339623d5309a23fb8b03d0c98f",
         "profile": "profiles/k_mode_tile_fp64_cavity32.md"},
     ("band_pass_fp64", "tf32", "cavity128", "per-direction"): {
-        "bytes_per_launch": 202454047,
+        "bytes_per_launch": 202973463,
         "source": "k_band.cu",
-        "sha256": "5bdc285e2d05ffe3b349d623a4e4c9c8566b31cd10cc2e6a18934684e441f950",
+        "sha256": "8e34f1c3eefcc420a6a283fea03f5f2e0b1015f7f96d7a7612cde695e80b5b31",
         "profile": "profiles/k_band_pass_fp64_cavity128.md"},
     ("mode_product", "fp64", "cavity32", "fused, 4 block(s) per plane"): {
         "bytes_per_launch": 1029889,
