@@ -639,8 +639,9 @@ __global__ void __launch_bounds__(256) k_divergence(const T* __restrict__ u1, co
 // The divergence and the first pressure-mass pass in one launch (FP64 A and K applies): a block
 // owns lpb whole x1 lines of the pressure grid, forms delta (and e = nu delta + q when q is set)
 // on them in shared memory with the operations of k_divergence, and applies the band D along x1
-// with the single FMA chain of the flat x1 pass: y0 = D .x1 delta, y1 = D .x1 e.
-template <typename T>
+// with the single FMA chain of the flat x1 pass: y0 = D .x1 delta, y1 = D .x1 e. WC: the band
+// width when it is a compiled one (the chains unrolled), 0 for a runtime width.
+template <typename T, int WC>
 __global__ void __launch_bounds__(512) k_div_band_x1(const T* __restrict__ u1,
                                                      const T* __restrict__ u2,
                                                      const T* __restrict__ u3, int a, int b,
@@ -679,16 +680,18 @@ __global__ void __launch_bounds__(512) k_div_band_x1(const T* __restrict__ u1,
   }
   __syncthreads();
   if (!active) return;
-  const int W = D.width;
+  const int W = WC > 0 ? WC : D.width;
   const T* cv = D.val + (int64_t)i1 * W;
   const int s0i = __ldg(D.start + i1);
   const T* xd = sd + l * b + s0i;
   T s0 = 0;
+#pragma unroll
   for (int w = 0; w < W; ++w) s0 = fma(__ldg(cv + w), xd[w], s0);
   y0[(int64_t)line * b + i1] = s0;
   if (q) {
     const T* xe = se + l * b + s0i;
     T e0 = 0;
+#pragma unroll
     for (int w = 0; w < W; ++w) e0 = fma(__ldg(cv + w), xe[w], e0);
     y1[(int64_t)line * b + i1] = e0;
   }
@@ -1134,11 +1137,15 @@ void div_band_x1(const T* u1, const T* u2, const T* u3, int a, int b, const T* q
   const int threads = ((lpb * b + 31) / 32) * 32;
   const int blocks = (b * b + lpb - 1) / lpb;
   const int smem = (q ? 2 : 1) * lpb * b * (int)sizeof(T);
-  static std::atomic<int> attr{0};
-  raise_smem_limit(k_div_band_x1<T>, attr, smem);
   const double np = (double)b * b * b;
+  // shared memory stays below the 48 KiB default (b <= 512 lines of at most 2 x 512 values)
   launch_begin(kClassDiv, s);
-  launch_k(k_div_band_x1<T>, blocks, threads, smem, s, u1, u2, u3, a, b, q, nu, D, lpb, y0, y1);
+  if (D.width == 7)
+    launch_k(k_div_band_x1<T, 7>, blocks, threads, smem, s, u1, u2, u3, a, b, q, nu, D, lpb, y0, y1);
+  else if (D.width == 9)
+    launch_k(k_div_band_x1<T, 9>, blocks, threads, smem, s, u1, u2, u3, a, b, q, nu, D, lpb, y0, y1);
+  else
+    launch_k(k_div_band_x1<T, 0>, blocks, threads, smem, s, u1, u2, u3, a, b, q, nu, D, lpb, y0, y1);
   launch_end(kClassDiv, s, (q ? 8.0 : 6.0) * np + (q ? 4.0 : 2.0) * D.width * np,
              (3.0 * a * b * b + (q ? 3.0 : 1.0) * np) * sizeof(T));
 }

@@ -371,7 +371,9 @@ struct Ops {
     T* yq = y + nvel;
     if constexpr (std::is_same<T, double>::value) {
       if (fused_div()) {
-        div_band_x1<T>(x, x + nvc, x + 2 * nvc, a, b, q, nu, Mc_w, f1, f1 + npres, s);
+        // the x1 pass with M-check itself (width 7): the zero-padded copy Mc_w that the x2 pass
+        // rides with (the velocity launch of width 9) would add two FMAs by zero per output
+        div_band_x1<T>(x, x + nvc, x + 2 * nvc, a, b, q, nu, Mc, f1, f1 + npres, s);
         const T* in2[2] = {f1, f1 + npres};
         T* out2[2] = {yq, m2};
         const T coef2[2] = {1, 1};
@@ -396,7 +398,7 @@ struct Ops {
   void apply_A(const T* x, T* y, const Horner<T>* h = nullptr) const {
     if constexpr (std::is_same<T, double>::value) {
       if (fused_div()) {
-        div_band_x1<T>(x, x + nvc, x + 2 * nvc, a, b, nullptr, nu, Mc_w, f1, nullptr, s);
+        div_band_x1<T>(x, x + nvc, x + 2 * nvc, a, b, nullptr, nu, Mc, f1, nullptr, s);
         const T* in1[1] = {f1};
         T* out1[1] = {m2};
         const T coef1[1] = {nu};
