@@ -28,6 +28,8 @@ struct PassBatch {
   int njobs;
   int seg;     // outputs per thread along the band direction
   int flat1;   // FP64: passes along x1 enumerate (line, row) with the row fastest
+  int w7[kMaxPassJobs];   // FP64, launch width 9: the job's bands have width 7 (passes along x2
+                          // or x3), so its chains run over 7 entries instead of 9 zero-padded
 };
 
 // Each thread computes a segment of `seg` consecutive outputs along the band direction of one
@@ -206,13 +208,21 @@ __global__ void __launch_bounds__(512) k_band_pass(const __grid_constant__ PassB
   }
   const T* g = a.g ? a.g + kb : nullptr;
   const int i_end = min(m, (seg + 1) * seg_n);
+  constexpr int WN = W == 9 ? 7 : W;   // the narrower compiled width of a width-9 launch
+  const bool narrow = W == 9 && pb.w7[jb];
   for (int i = seg * seg_n; i < i_end; ++i) {
-    T acc = band_dot<W>(a.D0, i, X0, base_in, stride_in);
+    T acc = narrow ? band_dot<WN>(a.D0, i, X0, base_in, stride_in)
+                   : band_dot<W>(a.D0, i, X0, base_in, stride_in);
     if (a.chain) {
-      acc = band_dot<W>(a.D1, i, X1, base_in, stride_in, acc);
+      acc = narrow ? band_dot<WN>(a.D1, i, X1, base_in, stride_in, acc)
+                   : band_dot<W>(a.D1, i, X1, base_in, stride_in, acc);
     } else {
       if (!a.c0_one) acc *= a.c0;   // (a product with 1 is exact: skipped)
-      if (a.nterms > 1) acc = fma(a.c1, band_dot<W>(a.D1, i, X1, base_in, stride_in), acc);
+      if (a.nterms > 1)
+        acc = fma(a.c1,
+                  narrow ? band_dot<WN>(a.D1, i, X1, base_in, stride_in)
+                         : band_dot<W>(a.D1, i, X1, base_in, stride_in),
+                  acc);
     }
     const int64_t o = kb + (int64_t)(base_out + (IT)i * stride_out);
     if (a.Z) acc += a.cz * a.Z[o];
@@ -1040,8 +1050,18 @@ void band_pass_multi(const PassArgs<T>* jobs, int njobs, cudaStream_t s) {
   pb.njobs = njobs;
   const int bt = jobs[0].block > 0 ? std::min(jobs[0].block, 512) : 256;   // threads per block
   int W = jobs[0].D0.width;
-  for (int j = 0; j < njobs; ++j)
-    if (jobs[j].D0.width != W || (jobs[j].nterms > 1 && jobs[j].D1.width != W)) W = 0;
+  // a launch of width 9 may hold jobs of width 7 along x2 or x3 (the pressure-mass passes that
+  // ride with the first velocity pass): flagged, their chains run over their own 7 entries
+  const auto width_ok = [&](const PassArgs<T>& a, int w) {
+    return a.D0.width == w && (a.nterms < 2 || a.D1.width == w);
+  };
+  for (int j = 0; j < njobs; ++j) {
+    const PassArgs<T>& a = jobs[j];
+    pb.w7[j] = (sizeof(T) == 8 && W == 9 && a.axis != 1 && width_ok(a, 7)) ? 1 : 0;
+    if (!width_ok(a, W) && !pb.w7[j]) W = 0;
+  }
+  if (W != 9)
+    for (int j = 0; j < njobs; ++j) pb.w7[j] = 0;
   // the instantiated widths; any other width (an even width where a band is clamped by a small
   // matrix) runs the generic kernel, which has no flat layout
   if (!(W >= 3 && W <= 13 && W % 2 == 1)) W = 0;

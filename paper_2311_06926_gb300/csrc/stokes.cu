@@ -306,8 +306,12 @@ struct Ops {
       j[2 * c] = job(u + o, K, 1, nullptr, nullptr, 0, comp(c), own_axis(c), tK + o);
       j[2 * c + 1] = job(u + o, M, 1, nullptr, nullptr, 0, comp(c), own_axis(c), tM + o);
     }
+    // the x2 pass rides with M-check itself (FP64 launches take jobs of width 7 along x2 in a
+    // width-9 launch); the x1 pass, where the flat layout needs the launch's width, with the
+    // zero-padded copy
     for (int k = 0; k < nq; ++k)
-      j[6 + k] = x1_done ? job(qx[k], Mc_w, 1, nullptr, nullptr, 0, dq, 2, f2 + k * npres)
+      j[6 + k] = x1_done ? job(qx[k], std::is_same<T, double>::value ? Mc : Mc_w, 1, nullptr,
+                               nullptr, 0, dq, 2, f2 + k * npres)
                          : job(qx[k], Mc_w, 1, nullptr, nullptr, 0, dq, 1, f1 + k * npres);
     band_pass_multi<T>(j, 6 + nq, s);
     const bool chain = Mc_nu.val != nullptr;   // FP64: one FMA chain over both terms
