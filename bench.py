@@ -53,9 +53,9 @@ TRAFFIC = {
         "sha256": "d05c14c82b258149fb7e1b53760b0abff0cde9339623d5309a23fb8b03d0c98f",
         "profile": "profiles/k_mode_tile_fp64_cavity32.md"},
     ("band_pass_fp64", "tf32", "cavity128", "per-direction"): {
-        "bytes_per_launch": 202973463,
+        "bytes_per_launch": 202983358,
         "source": "k_band.cu",
-        "sha256": "8e34f1c3eefcc420a6a283fea03f5f2e0b1015f7f96d7a7612cde695e80b5b31",
+        "sha256": "e78575f2233db7e235a87cf1ac012c93873e1e8aa42a741bf11a5eac6349d39a",
         "profile": "profiles/k_band_pass_fp64_cavity128.md"},
     ("mode_product", "fp64", "cavity32", "fused, 4 block(s) per plane"): {
         "bytes_per_launch": 1029889,
